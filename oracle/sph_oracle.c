@@ -1,0 +1,586 @@
+/*
+ * sph_oracle.c -- plain FP64 CPU oracle for the SPH density and hydro-force
+ * passes. TEST INFRASTRUCTURE ONLY: it is loaded by tests/, by the
+ * __graft_entry__ smoke check and by the CPU-baseline leg of bench.py, and by
+ * nothing else. It shares no code, header or constant with the CUDA library.
+ *
+ * What it computes (the paper names the two SPH modules -- an iterated density
+ * pass and a force pass -- and that neighbours lie within a fixed distance,
+ * Sec. 1 and Sec. 2.4, but states no formula; the formulas below are the
+ * standard Gadget-2-style SPH the paper's code descends from):
+ *
+ *   positions   X = rint(frac(x/L) * 2^32) mod 2^32 per axis (uint32), minimum
+ *               image d = (int32)(X_j - X_i) (two's-complement wrap).
+ *   kernel      M4 cubic spline with support h:
+ *                 W(r,h) = 8/(pi h^3) w(q), q = r/h,
+ *                 w = 1 - 6q^2 + 6q^3 (q <= 1/2), 2(1-q)^3 (1/2 < q < 1), 0 else.
+ *   predicate   j is a neighbour of i at h  <=>  (double)D2 < H*H, with
+ *               D2 = dx^2+dy^2+dz^2 exact in uint64 (integer units) and
+ *               H = h * 2^32 / L in FP64.
+ *   h           root of N_eff(h) = (4 pi/3) h^3 sum_j W(r_ij,h) = N_t (self
+ *               included), found by bracketed Newton/bisection.
+ *   density     rho_i = sum_j m_j W(r_ij,h_i); drho/dh = sum_j m_j dW/dh;
+ *               Omega_i = 1 / (1 + h_i/(3 rho_i) drho/dh);
+ *               n_ngb = #{j != i : neighbour}.
+ *   force       P = (gamma-1) rho u, c = sqrt(gamma P / rho), A = Omega P / rho^2,
+ *               pair set j != i with r < max(h_i, h_j),
+ *               w_ij = v_ij . r_ij / |r_ij|, v_sig = c_i + c_j - 3 w_ij,
+ *               Pi_ij = -(alpha/2) v_sig w_ij / rho_bar if w_ij < 0 else 0,
+ *               a_i   = -sum_j m_j [A_i grad W(h_i) + A_j grad W(h_j) + Pi_ij gradbar W],
+ *               du_i  =  A_i sum_j m_j v_ij . grad W(h_i)
+ *                        + 1/2 sum_j m_j Pi_ij v_ij . gradbar W,
+ *               vsig_i = max(0, max_j v_sig).
+ *
+ * Everything is a direct sum in FP64 over an explicit candidate set: either
+ * every particle (brute force) or the particles of the cells around i in a
+ * Morton-ordered cell list (a plain lower_bound per cell). No blocking, no
+ * reordering of the arithmetic.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_TWO32 4294967296.0
+#define ORC_PI 3.14159265358979323846
+
+/* ------------------------------------------------------------------------- */
+/* Quantisation and Morton keys                                              */
+/* ------------------------------------------------------------------------- */
+
+/* X = rint(frac(x/L) * 2^32) mod 2^32; rint rounds half to even. */
+void orc_quantize(const double *pos, int64_t n3, double L, uint32_t *X)
+{
+    for (int64_t k = 0; k < n3; ++k) {
+        double t = pos[k] / L;
+        t = t - floor(t);
+        double v = rint(t * ORC_TWO32);
+        if (v >= ORC_TWO32) v -= ORC_TWO32;
+        X[k] = (uint32_t)(uint64_t)v;
+    }
+}
+
+/* Spread the low 21 bits of v so that bit b lands at bit 3b. Written as a
+ * loop over bits, the plainest possible form. */
+static uint64_t orc_spread3(uint32_t v)
+{
+    uint64_t r = 0;
+    for (int b = 0; b < 21; ++b)
+        r |= (uint64_t)((v >> b) & 1u) << (3 * b);
+    return r;
+}
+
+/* 63-bit Morton key of the top 21 bits of each axis; within each bit triple x
+ * is the most significant, then y, then z. */
+uint64_t orc_morton(uint32_t X, uint32_t Y, uint32_t Z)
+{
+    return (orc_spread3(X >> 11) << 2) | (orc_spread3(Y >> 11) << 1) | orc_spread3(Z >> 11);
+}
+
+/* Keys of a batch of boxes: box b in the top bb bits, the Morton key shifted
+ * down by bb bits below it (bb = ceil(log2(n_boxes)), 0 for one box). */
+void orc_keys(const uint32_t *X, int64_t n, int64_t box, int bb, uint64_t *key)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        uint64_t m = orc_morton(X[3 * i], X[3 * i + 1], X[3 * i + 2]);
+        key[i] = bb ? (((uint64_t)box << (63 - bb)) | (m >> bb)) : m;
+    }
+}
+
+typedef struct { uint64_t key; int64_t idx; } orc_ki;
+
+static int orc_ki_cmp(const void *a, const void *b)
+{
+    const orc_ki *x = (const orc_ki *)a, *y = (const orc_ki *)b;
+    if (x->key != y->key) return x->key < y->key ? -1 : 1;
+    return (x->idx > y->idx) - (x->idx < y->idx);
+}
+
+/* Sort (key, index) by key, ties by index; writes the permutation. */
+void orc_sort_keys(const uint64_t *key, int64_t n, int64_t *perm)
+{
+    orc_ki *a = (orc_ki *)malloc(sizeof(orc_ki) * (size_t)(n ? n : 1));
+    for (int64_t i = 0; i < n; ++i) { a[i].key = key[i]; a[i].idx = i; }
+    qsort(a, (size_t)n, sizeof(orc_ki), orc_ki_cmp);
+    for (int64_t i = 0; i < n; ++i) perm[i] = a[i].idx;
+    free(a);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Kernel                                                                    */
+/* ------------------------------------------------------------------------- */
+
+double orc_w(double q)
+{
+    if (q < 0.0) q = -q;
+    if (q <= 0.5) return 1.0 - 6.0 * q * q + 6.0 * q * q * q;
+    if (q < 1.0) { double a = 1.0 - q; return 2.0 * a * a * a; }
+    return 0.0;
+}
+
+double orc_dw(double q) /* dw/dq */
+{
+    if (q <= 0.5) return -12.0 * q + 18.0 * q * q;
+    if (q < 1.0) { double a = 1.0 - q; return -6.0 * a * a; }
+    return 0.0;
+}
+
+double orc_W(double r, double h) { return 8.0 / (ORC_PI * h * h * h) * orc_w(r / h); }
+double orc_dWdr(double r, double h) { return 8.0 / (ORC_PI * h * h * h * h) * orc_dw(r / h); }
+double orc_dWdh(double r, double h) { return -(3.0 * orc_W(r, h) + r * orc_dWdr(r, h)) / h; }
+
+/* ------------------------------------------------------------------------- */
+/* Particle positions: quantised (exact integer geometry) or continuous      */
+/* ------------------------------------------------------------------------- */
+
+typedef struct {
+    int mode;            /* 0: quantised X, 1: continuous FP64 positions */
+    const uint32_t *X;   /* n x 3, always present (continuous mode: for indexing) */
+    const double *xc;    /* n x 3, continuous mode only */
+    int64_t n;
+    double L;
+} orc_pos;
+
+/* Separation vector r_ij = x_i - x_j (physical units, minimum image) and the
+ * neighbour predicate "r < h" evaluated as the contract states. */
+static int orc_pair(const orc_pos *P, int64_t i, int64_t j, double h, double rij[3], double *r)
+{
+    if (P->mode == 0) {
+        const uint32_t *a = P->X + 3 * i, *b = P->X + 3 * j;
+        uint64_t D2 = 0;
+        for (int k = 0; k < 3; ++k) {
+            int32_t d = (int32_t)(a[k] - b[k]);
+            int64_t dd = d;
+            D2 += (uint64_t)(dd * dd);
+            rij[k] = (double)d * (P->L / ORC_TWO32);
+        }
+        double H = h * ORC_TWO32 / P->L;
+        *r = sqrt((double)D2) * (P->L / ORC_TWO32);
+        return (double)D2 < H * H;
+    } else {
+        const double *a = P->xc + 3 * i, *b = P->xc + 3 * j;
+        double r2 = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            double d = a[k] - b[k];
+            d -= P->L * rint(d / P->L);
+            rij[k] = d;
+            r2 += d * d;
+        }
+        *r = sqrt(r2);
+        return r2 < h * h;
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Morton cell list                                                          */
+/* ------------------------------------------------------------------------- */
+
+typedef struct {
+    int64_t n;
+    uint64_t *key;   /* sorted keys */
+    int64_t *idx;    /* particle index of each sorted key */
+} orc_index;
+
+void *orc_index_new(const uint32_t *X, int64_t n)
+{
+    orc_index *I = (orc_index *)calloc(1, sizeof(orc_index));
+    I->n = n;
+    uint64_t *k = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(n ? n : 1));
+    I->key = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(n ? n : 1));
+    I->idx = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n ? n : 1));
+    orc_keys(X, n, 0, 0, k);
+    orc_sort_keys(k, n, I->idx);
+    for (int64_t s = 0; s < n; ++s) I->key[s] = k[I->idx[s]];
+    free(k);
+    return I;
+}
+
+void orc_index_free(void *p)
+{
+    orc_index *I = (orc_index *)p;
+    if (!I) return;
+    free(I->key); free(I->idx); free(I);
+}
+
+static int64_t orc_lower_bound(const uint64_t *a, int64_t n, uint64_t v)
+{
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (a[mid] < v) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+typedef struct { int64_t *a; int64_t n, cap; } orc_buf;
+
+static void orc_push(orc_buf *b, int64_t v)
+{
+    if (b->n == b->cap) {
+        b->cap = b->cap ? 2 * b->cap : 1024;
+        b->a = (int64_t *)realloc(b->a, sizeof(int64_t) * (size_t)b->cap);
+    }
+    b->a[b->n++] = v;
+}
+
+/* Candidates for a sphere of radius H (integer units) around integer point
+ * C: every particle of the cells, at the finest level whose cell side is at
+ * least H, that touch the 3x3x3 block around C's cell (periodic). The caller
+ * applies the exact predicate. Requires H <= 2^31. */
+static void orc_candidates(const orc_index *I, const uint32_t C[3], double H, orc_buf *out)
+{
+    out->n = 0;
+    int lvl = 21;
+    while (lvl > 1 && ldexp(1.0, 32 - lvl) < H) --lvl;
+    uint32_t ncell = 1u << lvl;
+    int shift = 32 - lvl;
+    uint32_t c[3];
+    for (int k = 0; k < 3; ++k) c[k] = C[k] >> shift;
+    uint32_t seen[27][3];
+    int nseen = 0;
+    for (int dx = -1; dx <= 1; ++dx)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dz = -1; dz <= 1; ++dz) {
+                uint32_t cc[3] = {(c[0] + ncell + (uint32_t)dx) % ncell,
+                                  (c[1] + ncell + (uint32_t)dy) % ncell,
+                                  (c[2] + ncell + (uint32_t)dz) % ncell};
+                int dup = 0;
+                for (int s = 0; s < nseen; ++s)
+                    if (seen[s][0] == cc[0] && seen[s][1] == cc[1] && seen[s][2] == cc[2]) dup = 1;
+                if (dup) continue;
+                memcpy(seen[nseen++], cc, sizeof cc);
+                /* cell cc at level lvl covers keys [p << 3(21-lvl), (p+1) << 3(21-lvl)) */
+                uint64_t p = (orc_spread3(cc[0]) << 2) | (orc_spread3(cc[1]) << 1) | orc_spread3(cc[2]);
+                int sh = 3 * (21 - lvl);
+                uint64_t k0 = p << sh, k1 = (p + 1) << sh;
+                int64_t s0 = orc_lower_bound(I->key, I->n, k0);
+                int64_t s1 = orc_lower_bound(I->key, I->n, k1);
+                for (int64_t s = s0; s < s1; ++s) orc_push(out, I->idx[s]);
+            }
+}
+
+/* Candidate set for particle i: brute force (all particles) or cell list. */
+static void orc_cands_for(const orc_pos *P, const orc_index *I, int64_t i, double h, orc_buf *out)
+{
+    if (!I) {
+        out->n = 0;
+        for (int64_t j = 0; j < P->n; ++j) orc_push(out, j);
+        return;
+    }
+    /* Integer radius with a margin that covers the continuous-mode
+     * quantisation of the indexed positions (<= 1 unit per axis). */
+    double H = h * ORC_TWO32 / P->L * (1.0 + 1e-12) + 4.0;
+    orc_candidates(I, P->X + 3 * i, H, out);
+}
+
+/* splitmix64 finaliser (Steele, Lea, Flood 2014): order-independent
+ * neighbour-set checksum = sum over the set of splitmix64(index). */
+uint64_t orc_splitmix64(uint64_t x)
+{
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Density                                                                   */
+/* ------------------------------------------------------------------------- */
+
+typedef struct {
+    double neff, dneff, rho, drho;
+    int64_t nngb;
+    uint64_t hash;
+} orc_dens;
+
+static void orc_density_at(const orc_pos *P, const orc_index *I, const double *m, int64_t i,
+                           double h, orc_buf *cb, orc_dens *o)
+{
+    orc_cands_for(P, I, i, h, cb);
+    double sw = 0.0, sdw = 0.0, rho = 0.0, drho = 0.0;
+    int64_t nn = 0;
+    uint64_t hs = 0;
+    for (int64_t c = 0; c < cb->n; ++c) {
+        int64_t j = cb->a[c];
+        double rij[3], r;
+        int in = orc_pair(P, i, j, h, rij, &r);
+        if (j == i) { r = 0.0; in = 1; }
+        if (!in) continue;
+        double W = orc_W(r, h);
+        sw += W;
+        sdw += orc_dWdh(r, h);
+        rho += m[j] * W;
+        drho += m[j] * orc_dWdh(r, h);
+        if (j != i) { ++nn; hs += orc_splitmix64((uint64_t)j); }
+    }
+    double f = 4.0 * ORC_PI / 3.0 * h * h * h;
+    o->neff = f * sw;
+    /* d/dh [ (4pi/3) h^3 sum W ] */
+    o->dneff = 4.0 * ORC_PI * h * h * sw + f * sdw;
+    o->rho = rho;
+    o->drho = drho;
+    o->nngb = nn;
+    o->hash = hs;
+}
+
+/* Status bits per particle. */
+#define ORC_NOT_CONVERGED 1
+#define ORC_H_TOO_LARGE 2
+
+/*
+ * Density pass for the active particles (NULL = all). fixed_h != 0 evaluates
+ * at h_init without iterating. Otherwise h solves N_eff(h) = n_target to
+ * |N_eff - n_target| <= tol, starting from h_init[i] (<= 0: from a small
+ * global guess grown by factors of 2 until the root is bracketed), with a
+ * Newton step whenever it stays inside the bracket and bisection otherwise.
+ * Outputs are indexed by particle. Returns the OR of the status bits.
+ */
+int orc_density(int mode, const uint32_t *X, const double *xc, int64_t n, double L,
+                const double *m, const double *h_init, double n_target, double tol,
+                int max_iter, const int64_t *active, int64_t n_active, int brute, int fixed_h,
+                double *h_out, double *rho, double *drho_dh, double *omega, double *neff,
+                int64_t *n_ngb, uint64_t *hash, int32_t *status)
+{
+    orc_pos P = {mode, X, xc, n, L};
+    orc_index *I = brute ? NULL : (orc_index *)orc_index_new(X, n);
+    int64_t na = active ? n_active : n;
+    double h_glob = L * cbrt(3.0 * n_target / (4.0 * ORC_PI * (double)n));
+    double h_cap = 0.5 * L * (1.0 - 1e-9); /* h must stay below L/2 */
+    int any = 0;
+#pragma omp parallel reduction(| : any)
+    {
+        orc_buf cb = {0, 0, 0};
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t a = 0; a < na; ++a) {
+            int64_t i = active ? active[a] : a;
+            int st = 0;
+            orc_dens d;
+            double h = (h_init && h_init[i] > 0.0) ? h_init[i] : h_glob / 64.0;
+            if (h >= h_cap) h = 0.5 * h_cap;
+            orc_density_at(&P, I, m, i, h, &cb, &d);
+            if (!fixed_h) {
+                double lo = 0.0, hi = INFINITY;
+                int it = 0;
+                while (fabs(d.neff - n_target) > tol) {
+                    if (++it > max_iter) { st |= ORC_NOT_CONVERGED; break; }
+                    if (d.neff < n_target) lo = h; else hi = h;
+                    double hn;
+                    if (isinf(hi)) {
+                        /* not bracketed yet: grow (Newton if it grows by less) */
+                        if (h >= h_cap) { st |= ORC_H_TOO_LARGE; break; }
+                        hn = 2.0 * h;
+                        if (d.dneff > 0.0) {
+                            double hnewt = h - (d.neff - n_target) / d.dneff;
+                            if (hnewt > h && hnewt < hn) hn = hnewt;
+                        }
+                        if (hn >= h_cap) hn = h_cap;
+                    } else {
+                        hn = (d.dneff > 0.0) ? h - (d.neff - n_target) / d.dneff : NAN;
+                        if (!(hn > lo && hn < hi)) hn = 0.5 * (lo + hi);
+                    }
+                    h = hn;
+                    orc_density_at(&P, I, m, i, h, &cb, &d);
+                }
+            }
+            h_out[i] = h;
+            rho[i] = d.rho;
+            drho_dh[i] = d.drho;
+            omega[i] = 1.0 / (1.0 + h / (3.0 * d.rho) * d.drho);
+            if (neff) neff[i] = d.neff;
+            n_ngb[i] = d.nngb;
+            if (hash) hash[i] = d.hash;
+            if (status) status[i] = st;
+            any |= st;
+        }
+        free(cb.a);
+    }
+    orc_index_free(I);
+    return any;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Force                                                                     */
+/* ------------------------------------------------------------------------- */
+
+/* Morton cell lists of the particles grouped by smoothing-length level: level
+ * l holds the particles whose h fits one level-l cell (2^-l L >= h > 2^-l-1 L),
+ * so every j with r_ij < h_j lies in the 3x3x3 level-l cells around i. This
+ * finds the half of the symmetric pair set that i's own radius misses. */
+typedef struct {
+    orc_index *lv[22];
+    int64_t *map[22];   /* local index -> particle index */
+} orc_hindex;
+
+static int orc_hlevel(double h, double L)
+{
+    /* finest level whose cell side (integer units) exceeds H + 4 units */
+    double H = h * ORC_TWO32 / L + 4.0;
+    int l = 21;
+    while (l > 1 && ldexp(1.0, 32 - l) < H) --l;
+    return l;
+}
+
+static orc_hindex *orc_hindex_new(const orc_pos *P, const double *h)
+{
+    orc_hindex *Hx = (orc_hindex *)calloc(1, sizeof(orc_hindex));
+    int64_t cnt[22] = {0};
+    for (int64_t j = 0; j < P->n; ++j) cnt[orc_hlevel(h[j], P->L)]++;
+    for (int l = 0; l < 22; ++l) {
+        if (!cnt[l]) continue;
+        uint32_t *Xl = (uint32_t *)malloc(sizeof(uint32_t) * 3 * (size_t)cnt[l]);
+        Hx->map[l] = (int64_t *)malloc(sizeof(int64_t) * (size_t)cnt[l]);
+        int64_t k = 0;
+        for (int64_t j = 0; j < P->n; ++j)
+            if (orc_hlevel(h[j], P->L) == l) {
+                memcpy(Xl + 3 * k, P->X + 3 * j, 3 * sizeof(uint32_t));
+                Hx->map[l][k++] = j;
+            }
+        Hx->lv[l] = (orc_index *)orc_index_new(Xl, cnt[l]);
+        free(Xl);
+    }
+    return Hx;
+}
+
+static void orc_hindex_free(orc_hindex *Hx)
+{
+    if (!Hx) return;
+    for (int l = 0; l < 22; ++l) { orc_index_free(Hx->lv[l]); free(Hx->map[l]); }
+    free(Hx);
+}
+
+/*
+ * Hydro-force pass for the active particles (NULL = all). Inputs are indexed
+ * by particle (all n, neighbours included). Outputs, for active i only:
+ * acc (n x 3), dudt, vsig; scale_a / scale_u = sum over pairs of the
+ * magnitude of each pair's term (the per-particle absolute scale used for
+ * tolerances); n_pairs = |pair set|; hash = neighbour-set checksum.
+ */
+void orc_force(int mode, const uint32_t *X, const double *xc, int64_t n, double L,
+               const double *v, const double *m, const double *u, const double *h,
+               const double *rho, const double *omega, double alpha, double gamma,
+               const int64_t *active, int64_t n_active, int brute,
+               double *acc, double *dudt, double *vsig, double *scale_a, double *scale_u,
+               int64_t *n_pairs, uint64_t *hash)
+{
+    orc_pos P = {mode, X, xc, n, L};
+    orc_index *I = brute ? NULL : (orc_index *)orc_index_new(X, n);
+    orc_hindex *Hx = brute ? NULL : orc_hindex_new(&P, h);
+    int64_t na = active ? n_active : n;
+#pragma omp parallel
+    {
+        orc_buf cb = {0, 0, 0}, cl = {0, 0, 0};
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t a = 0; a < na; ++a) {
+            int64_t i = active ? active[a] : a;
+            /* Candidates: i's own sphere, plus (cell-list mode) every level's
+             * 3x3x3 block for the particles whose own sphere reaches i. Each j
+             * is taken once: from the first list if r < h_i, else from its
+             * level list if r < h_j. */
+            orc_cands_for(&P, I, i, h[i], &cb);
+            int64_t nfirst = cb.n;
+            if (Hx) {
+                for (int l = 0; l < 22; ++l) {
+                    if (!Hx->lv[l]) continue;
+                    orc_candidates(Hx->lv[l], X + 3 * i, ldexp(1.0, 32 - l), &cl);
+                    for (int64_t c = 0; c < cl.n; ++c) orc_push(&cb, Hx->map[l][cl.a[c]]);
+                }
+            }
+            double Pi = (gamma - 1.0) * rho[i] * u[i];
+            double ci = sqrt(gamma * Pi / rho[i]);
+            double Ai = omega[i] * Pi / (rho[i] * rho[i]);
+            double ax = 0, ay = 0, az = 0, du = 0, vs = 0.0, sa = 0.0, su = 0.0;
+            int64_t np = 0;
+            uint64_t hs = 0;
+            for (int64_t c = 0; c < cb.n; ++c) {
+                int64_t j = cb.a[c];
+                if (j == i) continue;
+                double rij[3], r;
+                int in_i = orc_pair(&P, i, j, h[i], rij, &r);
+                int in_j = orc_pair(&P, i, j, h[j], rij, &r);
+                int take;
+                if (!Hx) take = in_i || in_j;          /* brute force: every j once */
+                else if (c < nfirst) take = in_i;      /* i's own sphere */
+                else take = !in_i && in_j;             /* j's sphere only */
+                if (!take) continue;
+                ++np;
+                hs += orc_splitmix64((uint64_t)j);
+                double Pj = (gamma - 1.0) * rho[j] * u[j];
+                double cj = sqrt(gamma * Pj / rho[j]);
+                double Aj = omega[j] * Pj / (rho[j] * rho[j]);
+                double vij[3] = {v[3 * i] - v[3 * j], v[3 * i + 1] - v[3 * j + 1], v[3 * i + 2] - v[3 * j + 2]};
+                if (r == 0.0) {
+                    /* coincident: no direction, all pair terms vanish */
+                    double vsg = ci + cj;
+                    if (vsg > vs) vs = vsg;
+                    continue;
+                }
+                double vr = vij[0] * rij[0] + vij[1] * rij[1] + vij[2] * rij[2];
+                double wij = vr / r;
+                double vsg = ci + cj - 3.0 * wij;
+                if (vsg > vs) vs = vsg;
+                double Fi = orc_dWdr(r, h[i]) / r; /* grad_i W(h_i) = Fi * r_ij */
+                double Fj = orc_dWdr(r, h[j]) / r;
+                double Fbar = 0.5 * (Fi + Fj);
+                double PIij = 0.0;
+                if (wij < 0.0) PIij = -0.5 * alpha * vsg * wij / (0.5 * (rho[i] + rho[j]));
+                double coef = m[j] * (Ai * Fi + Aj * Fj + PIij * Fbar);
+                ax -= coef * rij[0];
+                ay -= coef * rij[1];
+                az -= coef * rij[2];
+                double dut = m[j] * (Ai * Fi * vr + 0.5 * PIij * Fbar * vr);
+                du += dut;
+                sa += fabs(coef) * r;
+                su += fabs(dut);
+            }
+            acc[3 * i] = ax; acc[3 * i + 1] = ay; acc[3 * i + 2] = az;
+            dudt[i] = du;
+            vsig[i] = vs;
+            if (scale_a) scale_a[i] = sa;
+            if (scale_u) scale_u[i] = su;
+            if (n_pairs) n_pairs[i] = np;
+            if (hash) hash[i] = hs;
+        }
+        free(cb.a);
+        free(cl.a);
+    }
+    orc_hindex_free(Hx);
+    orc_index_free(I);
+}
+
+/* Brute-force neighbour list of one particle at radius h (for pins). */
+int64_t orc_neighbours(int mode, const uint32_t *X, const double *xc, int64_t n, double L,
+                       int64_t i, double h, int brute, int64_t *out, int64_t cap)
+{
+    orc_pos P = {mode, X, xc, n, L};
+    orc_index *I = brute ? NULL : (orc_index *)orc_index_new(X, n);
+    orc_buf cb = {0, 0, 0};
+    orc_cands_for(&P, I, i, h, &cb);
+    int64_t k = 0;
+    for (int64_t c = 0; c < cb.n; ++c) {
+        int64_t j = cb.a[c];
+        double rij[3], r;
+        if (j == i) continue;
+        if (orc_pair(&P, i, j, h, rij, &r)) { if (k < cap) out[k] = j; ++k; }
+    }
+    free(cb.a);
+    orc_index_free(I);
+    return k;
+}
+
+int orc_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* Vectorised kernel evaluation for the pins (w, dw/dq at each q). */
+void orc_kernel_array(const double *q, int64_t n, double *w, double *dw)
+{
+    for (int64_t k = 0; k < n; ++k) { w[k] = orc_w(q[k]); dw[k] = orc_dw(q[k]); }
+}
