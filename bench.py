@@ -1,0 +1,403 @@
+#!/usr/bin/env python
+"""Benchmark: SPH pair-interactions/s (density + force) at 10M particles.
+
+Workload (one "step" = one pass of the whole hot path): 10,000,000 clustered
+gas particles (500 Gaussian blobs on a uniform background, seed 3) whose
+adaptive time bins give sub-steps with 100 %, 10 %, 1 % and 0.1 % active
+particles. A step rebuilds the neighbour grid in place (quantise, key, sort,
+bound) and then runs, per sub-step, the density pass (smoothing-length
+iteration on the device) and the hydro-force pass over that sub-step's
+active set. Pairs = sum over active i of n_ngb,i (density, at the converged
+h) + |{j : r_ij < max(h_i, h_j)}| (force), counted by the kernels.
+
+Inputs (positions, state) total > 1 GB, far larger than the 129 MB L2.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun with N > 1 every rank runs an independent replica on its own
+GPU (the path has no exchange step on one box); value = all ranks' pairs / max
+time over ranks. --impl reference times the FP64 CPU oracle on the host.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SPH pair-interactions/s (density+force) at 10M particles, vs plain FP32 path"
+UNIT = "pairs/s"
+FLOPS_DENSITY_PAIR = 30.0   # FP32 flops per density pair (FMA = 2), one pass at the converged h
+FLOPS_FORCE_PAIR = 90.0     # FP32 flops per force pair
+FP32_LANES_PER_SM = 128
+H_PERTURB = 0.02            # per-step log-normal scatter of the h guesses
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=10_000_000)
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-n", type=int, default=1 << 20, help="particles of the CPU-baseline sample")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# CPU side: the FP64 oracle on a bounded sample (cpu_baseline, --impl reference)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(n_s: int, seed: int = 3):
+    """A bounded sample of the workload: the same generator at n_s particles
+    (blob count scaled with sqrt(N)), all particles active, h guesses perturbed
+    from the converged h exactly as in the GPU step."""
+    import oracle
+    import workloads as W
+    p = W.clustered(n_s, W.blobs_for(n_s), seed=seed)
+    p32 = lambda a: np.asarray(a, np.float32).astype(np.float64)
+    X = oracle.quantize(p32(p.pos))
+    m, v, u = p32(p.mass), p32(p.vel), p32(p.u)
+    d0 = oracle.density(X, m, None, tol=64e-6)
+    h_in = W.perturb(d0["h"], H_PERTURB, seed=11)
+    return dict(X=X, m=m, v=v, u=u, h_in=h_in)
+
+
+def oracle_step(s):
+    import oracle
+    t0 = time.perf_counter()
+    d = oracle.density(s["X"], s["m"], s["h_in"], tol=64e-6)
+    f = oracle.force(s["X"], s["v"], s["m"], s["u"], d["h"], d["rho"], d["omega"])
+    dt = time.perf_counter() - t0
+    pairs = int(d["n_ngb"].sum() + f["n_pairs"].sum())
+    return pairs, dt
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    s = oracle_sample(args.cpu_n)
+    for _ in range(args.warmup):
+        oracle_step(s)
+    pairs = secs = 0.0
+    for _ in range(args.steps):
+        pr, dt = oracle_step(s)
+        pairs += pr
+        secs += dt
+    v = pairs / secs
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": f"10M clustered time-binned SPH step; CPU sample: same generator at "
+                                   f"N={args.cpu_n}, all active, density (from perturbed h) + force"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": f"clustered N={args.cpu_n}, all active, density+force"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU side
+# ---------------------------------------------------------------------------
+
+class Clocks:
+    """nvidia-smi sampling in the background during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(device), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if "Active" in r[5 + k]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def setup_workload(S, ctx, n, dev):
+    import torch
+    import workloads as W
+    t0 = time.time()
+    p = W.config3(n) if n == 10_000_000 else W.clustered(n, W.blobs_for(n), seed=3)
+    f32 = lambda a: torch.from_numpy(np.asarray(a, np.float32)).to(dev)
+    pos, mass, vel, u = f32(p.pos), f32(p.mass), f32(p.vel), f32(p.u)
+    params = S.default_params()
+    # Store the particles in the grid's Morton order (as the paper's code keeps
+    # its particles in Hilbert order), then build the grid used by the steps.
+    g0 = S.sph_build_grid(ctx, pos, mass, params)
+    perm = torch.empty(n, dtype=torch.int32, device=dev)
+    S.sph_grid_export(g0, perm)
+    g0.free()
+    order = perm.long()
+    pos, mass, vel, u = (t[order].contiguous() for t in (pos, mass, vel, u))
+    grid = S.sph_build_grid(ctx, pos, mass, params)
+    # converge h once (all active), then a force pass for the Courant estimate
+    h = torch.zeros(n, device=dev)
+    st = {"rho": torch.zeros(n, device=dev), "omega": torch.zeros(n, device=dev),
+          "n_ngb": torch.zeros(n, dtype=torch.int32, device=dev), "flags": torch.zeros(n, dtype=torch.uint8, device=dev),
+          "acc": torch.zeros(n, 3, device=dev), "dudt": torch.zeros(n, device=dev), "vsig": torch.zeros(n, device=dev)}
+    S.sph_density(ctx, grid, h, None, st["rho"], st["omega"], st["n_ngb"], st["flags"], None, params)
+    S.sph_hydro_force(ctx, grid, vel, u, h, st["rho"], st["omega"], None, st["acc"], st["dudt"], st["vsig"],
+                      None, params)
+    S.sph_sync_status(ctx)
+    dt_c = (0.3 * h / st["vsig"].clamp_min(1e-30)).cpu().numpy()
+    bins = W.timebins(dt_c)
+    acts = [torch.from_numpy(a).to(dev) for a in W.active_sets(bins)]
+    # per sub-step h guesses: the converged h, scattered log-normally on that
+    # sub-step's active particles only (inactive neighbours keep their h)
+    h_conv = h.cpu().numpy().astype(np.float64)
+    h_ins = []
+    for k, a in enumerate(W.active_sets(bins)):
+        hk = h_conv.copy()
+        hk[a] = W.perturb(h_conv[a], H_PERTURB, seed=20 + k)
+        h_ins.append(torch.from_numpy(hk.astype(np.float32)).to(dev))
+    return dict(pos=pos, mass=mass, vel=vel, u=u, h=h, st=st, grid=grid, acts=acts, h_ins=h_ins,
+                setup_s=time.time() - t0, n=n)
+
+
+def run_step(S, ctx, wl, params, ev=None):
+    """One step; returns list of (start, end) events pairs timed on the stream."""
+    import torch
+    spans = []
+    st = wl["st"]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    S.sph_grid_update(ctx, wl["grid"], wl["pos"], wl["mass"])
+    e1.record()
+    spans.append((e0, e1))
+    for act, h_in in zip(wl["acts"], wl["h_ins"]):
+        wl["h"].copy_(h_in)   # untimed: the sub-step's h guesses
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        S.sph_density(ctx, wl["grid"], wl["h"], act, st["rho"], st["omega"], st["n_ngb"], st["flags"], None, params)
+        S.sph_hydro_force(ctx, wl["grid"], wl["vel"], wl["u"], wl["h"], st["rho"], st["omega"], act, st["acc"],
+                          st["dudt"], st["vsig"], None, params)
+        b.record()
+        spans.append((a, b))
+    return spans
+
+
+def timed_steps(S, ctx, wl, params, steps, warmup, dist=None):
+    import torch
+    for _ in range(warmup):
+        run_step(S, ctx, wl, params)
+    S.sph_sync_status(ctx)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    ms, pairs, launches, dk, fk, dl, fl = 0.0, 0, 0, 0.0, 0.0, 0, 0
+    dpairs = fpairs = 0
+    for _ in range(steps):
+        spans = run_step(S, ctx, wl, params)
+        rc, stt = S.sph_sync_status(ctx)
+        ms += sum(a.elapsed_time(b) for a, b in spans)
+        dpairs += stt["density_pairs"]
+        fpairs += stt["force_pairs"]
+        launches += stt["launches"]
+        dk += stt["density_kernel_ms"]
+        fk += stt["force_kernel_ms"]
+        dl += stt["density_launches"]
+        fl += stt["force_launches"]
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    return dict(ms=ms, pairs=dpairs + fpairs, dpairs=dpairs, fpairs=fpairs, launches=launches,
+                dens_ms=dk, force_ms=fk, dens_launches=dl, force_launches=fl)
+
+
+def e2e_steps(S, ctx, wl, params, steps):
+    """Same step through the public API from pinned HOST buffers: H2D of the
+    step's inputs and D2H of its results inside the timed region."""
+    import torch
+    n = wl["n"]
+    hst = {k: wl[k].cpu().pin_memory() for k in ("pos", "mass", "vel", "u")}
+    h_ins = [h.cpu().pin_memory() for h in wl["h_ins"]]
+    outs = {k: torch.empty(wl["st"][k].shape, dtype=wl["st"][k].dtype).pin_memory()
+            for k in ("rho", "omega", "acc", "dudt", "vsig")}
+    h_out = torch.empty(n).pin_memory()
+    st = wl["st"]
+    h2d = sum(t.numel() * t.element_size() for t in hst.values()) + sum(t.numel() * 4 for t in h_ins)
+    d2h = sum(t.numel() * t.element_size() for t in outs.values()) + n * 4
+    pairs = 0
+    torch.cuda.synchronize()
+    t_ms = 0.0
+    for _ in range(steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for k in hst:
+            wl[k].copy_(hst[k], non_blocking=True)
+        S.sph_grid_update(ctx, wl["grid"], wl["pos"], wl["mass"])
+        for act, h_in in zip(wl["acts"], h_ins):
+            wl["h"].copy_(h_in, non_blocking=True)
+            S.sph_density(ctx, wl["grid"], wl["h"], act, st["rho"], st["omega"], st["n_ngb"], st["flags"], None,
+                          params)
+            S.sph_hydro_force(ctx, wl["grid"], wl["vel"], wl["u"], wl["h"], st["rho"], st["omega"], act,
+                              st["acc"], st["dudt"], st["vsig"], None, params)
+        for k in outs:
+            outs[k].copy_(st[k], non_blocking=True)
+        h_out.copy_(wl["h"], non_blocking=True)
+        b.record()
+        _, stt = S.sph_sync_status(ctx)
+        t_ms += a.elapsed_time(b)
+        pairs += stt["density_pairs"] + stt["force_pairs"]
+    return dict(value=pairs / (t_ms / 1e3), unit=UNIT, h2d_bytes_per_step=int(h2d), d2h_bytes_per_step=int(d2h),
+                ms_per_step=t_ms / steps)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        dist = tdist
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2003_10850_gb300 import build as B
+    if rank == 0 or world == 1:
+        B.build()
+    if dist is not None:
+        dist.barrier()
+    import paper_2003_10850_gb300 as S
+    ctx = S.Context(local)
+    wl = setup_workload(S, ctx, args.n, dev)
+    params = S.default_params(flags=S.SPH_TIME_KERNELS)
+
+    clocks = Clocks(local)
+    res = timed_steps(S, ctx, wl, params, args.steps, args.warmup, dist)
+    clk = clocks.stop()
+
+    ms_step = res["ms"] / args.steps
+    pairs_step = res["pairs"] / args.steps
+    if dist is not None:
+        t = torch.tensor([ms_step, pairs_step], dtype=torch.float64, device=dev)
+        mx = t.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = t.clone()
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        ms_step, pairs_total = float(mx[0]), float(sm[1])
+    else:
+        pairs_total = pairs_step
+    value = pairs_total / (ms_step / 1e3)
+
+    plain = None
+    if not args.no_plain and rank == 0:
+        pp = S.default_params(flags=S.SPH_PLAIN_FP32)
+        r2 = timed_steps(S, ctx, wl, pp, max(1, min(2, args.steps)), 1)
+        plain = {"value": r2["pairs"] / (r2["ms"] / 1e3), "ms_per_step": r2["ms"] / max(1, min(2, args.steps)),
+                 "unit": UNIT}
+    e2e = None
+    if not args.no_e2e:
+        e2e = e2e_steps(S, ctx, wl, S.default_params(), max(1, min(3, args.steps)))
+
+    pk, src = peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sm_count = props.multi_processor_count
+    peak_tf = sm_count * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    dens_f = res["dpairs"] * FLOPS_DENSITY_PAIR
+    force_f = res["fpairs"] * FLOPS_FORCE_PAIR
+    if res["dens_ms"] >= res["force_ms"]:
+        kern, flops, kms, kl = "k_density<float>", dens_f, res["dens_ms"], res["dens_launches"]
+    else:
+        kern, flops, kms, kl = "k_force<float>", force_f, res["force_ms"], res["force_launches"]
+    achieved = (flops / max(kl, 1)) / (kms / max(kl, 1) / 1e3) / 1e12 if kms > 0 else None
+    roofline = {"bound": "alu", "kernel": kern, "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
+                "frac": achieved / peak_tf if achieved else None, "traffic": None,
+                "peak_source": f"{sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
+                               f"{pk.get('sm_max_mhz', 2070.0)} MHz ({src} max SM clock)",
+                "density_kernel_ms_per_step": res["dens_ms"] / args.steps,
+                "force_kernel_ms_per_step": res["force_ms"] / args.steps,
+                "density_tflops": dens_f / (res["dens_ms"] / 1e3) / 1e12 if res["dens_ms"] else None,
+                "force_tflops": force_f / (res["force_ms"] / 1e3) / 1e12 if res["force_ms"] else None}
+
+    cpu = None
+    if not args.no_cpu and rank == 0 and world == 1:
+        import oracle
+        oracle.build()
+        s = oracle_sample(args.cpu_n)
+        pr, dt = oracle_step(s)
+        cpu = {"value": pr / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": f"same generator at N={args.cpu_n} (blobs ~ sqrt N), all active, density from "
+                         f"perturbed converged h + force, one step, {dt:.1f} s"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "10M clustered gas particles (500 blobs, seed 3), time bins giving "
+                                       "100/10/1/0.1% active sub-steps; grid rebuild + density (h iteration) "
+                                       "+ hydro force per sub-step",
+                           "n": args.n, "pairs_per_step": pairs_step, "l2": "inputs exceed L2 (>1 GB)",
+                           "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                           "h_guess_scatter": H_PERTURB},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(round(res["launches"] / args.steps)), "clocks": clk,
+                "plain_fp32": plain, "speedup_vs_plain": (value / plain["value"]) if plain else None,
+                "setup_s": wl["setup_s"]}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

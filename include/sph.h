@@ -1,0 +1,212 @@
+/*
+ * sph.h -- C ABI of the GB300 SPH neighbour-interaction library
+ * (libsph_gb300.so). Plain pointers and sizes only: no CUDA, PyTorch or C++
+ * types cross this boundary. `stream` arguments are cudaStream_t values passed
+ * as void* (NULL = the legacy default stream).
+ *
+ * The library implements the data-parallel hot path of the SPH part of
+ * "Gadget3 on GPUs with OpenACC" (Ragagnin et al. 2020): the two SPH modules
+ * -- an iterated density pass and a hydrodynamic-force pass (Sec. 1) -- over
+ * the neighbours within a fixed distance of each active particle (Sec. 1,
+ * Sec. 2.4), for the uneven active sets that adaptive time bins produce
+ * (Sec. 2.2). The paper states no SPH formula; the library follows the
+ * standard Gadget-2 forms, spelled out at each entry point.
+ *
+ * Ownership: every particle array is a caller-owned DEVICE pointer indexed in
+ * the caller's particle order, except where marked "host". The library owns
+ * sph_ctx and sph_grid and every workspace they hold. Outputs are written only
+ * for active particles; other entries are left untouched.
+ *
+ * Errors: every call validates its arguments on the host and returns a
+ * status synchronously; kernels run asynchronously on `stream`. Conditions
+ * found on the device (non-convergence, h >= L/2, non-finite input, a bounded
+ * wait that ran out) set bits in a device status word that sph_sync_status()
+ * returns. Nothing here traps or aborts; no exception crosses the ABI.
+ * sph_last_error() holds a message for the last non-OK status.
+ */
+#ifndef SPH_GB300_H
+#define SPH_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SPH_OK = 0,
+    SPH_ERR_INVALID = 1,        /* bad argument (host check) or non-finite input (device) */
+    SPH_ERR_CUDA = 2,           /* a CUDA runtime call failed; see sph_last_error() */
+    SPH_ERR_NOT_CONVERGED = 3,  /* some h did not converge within max_iter (device) */
+    SPH_ERR_H_TOO_LARGE = 4,    /* some h would reach L/2 (minimum image breaks) (device) */
+    SPH_ERR_TIMEOUT = 5,        /* a bounded device-side wait ran out (device) */
+    SPH_ERR_OOM = 6             /* device allocation failed */
+} sph_status;
+
+/* sph_params.flags */
+#define SPH_FP64       0x01  /* pair arithmetic and sums in FP64 (the plain method in double) */
+#define SPH_PLAIN_FP32 0x02  /* plain path: thread per particle, FP32, no compensation,
+                                h iterated by the host (the baseline the fast path is measured against) */
+#define SPH_FIXED_H    0x04  /* density: evaluate at the given h, do not iterate */
+#define SPH_H_GUESS    0x08  /* density: ignore the h input and start from a local
+                                estimate made from the grid's leaf-parent boxes */
+#define SPH_TIME_KERNELS 0x10 /* record CUDA events around the main density/force kernel on
+                                 the launching stream; sph_sync_status sums their durations */
+
+/* Device status bits returned in sph_stats.status */
+#define SPH_ST_NOT_CONVERGED 0x01
+#define SPH_ST_H_TOO_LARGE   0x02
+#define SPH_ST_TIMEOUT       0x04
+#define SPH_ST_INVALID       0x08
+
+typedef struct sph_ctx sph_ctx;    /* opaque, library-owned */
+typedef struct sph_grid sph_grid;  /* opaque, library-owned */
+
+typedef struct {
+    double box;         /* periodic box side L (sph_build_grid); > 0 */
+    double n_target;    /* N_t: target of N_eff(h) = (4 pi/3) h^3 sum_j W(r_ij,h), self included */
+    double n_tol;       /* converged when |N_eff - N_t| <= n_tol */
+    int    max_iter;    /* h iterations per particle before SPH_ST_NOT_CONVERGED */
+    double alpha_visc;  /* artificial-viscosity alpha */
+    double gamma;       /* adiabatic index */
+    int    flags;       /* SPH_* flags above */
+    int    group_size;  /* particles per warp group: 0 (= 32), 16 or 32 */
+    int    blocks_per_sm; /* persistent CTAs per SM: 0 = library default */
+} sph_params;
+
+/* Counters accumulated by the device since the last sph_sync_status(). */
+typedef struct {
+    uint32_t status;          /* OR of SPH_ST_* bits */
+    uint32_t launches;        /* kernels launched by this context (host count) */
+    uint64_t density_pairs;   /* sum over active i of n_ngb,i at the converged h */
+    uint64_t force_pairs;     /* sum over active i of |{j != i : r_ij < max(h_i, h_j)}| */
+    uint64_t density_evals;   /* particle-evaluations of the density sums (all iterations) */
+    uint64_t pair_tests;      /* candidate pairs tested (work including rejected ones) */
+    uint64_t groups;          /* warp groups processed */
+    double density_kernel_ms; /* SPH_TIME_KERNELS: summed time of the density kernels */
+    double force_kernel_ms;   /* SPH_TIME_KERNELS: summed time of the force kernels */
+    uint32_t density_launches; /* SPH_TIME_KERNELS: timed density kernel launches */
+    uint32_t force_launches;   /* SPH_TIME_KERNELS: timed force kernel launches */
+} sph_stats;
+
+/* Fills *p with the library defaults: L = 1, N_t = 64, n_tol = 1e-6 N_t,
+ * max_iter = 64, alpha = 1, gamma = 5/3, flags = 0. */
+void sph_default_params(sph_params *p);
+
+/* Creates a context on CUDA device `device` (made current). */
+sph_status sph_create(sph_ctx **ctx, int device);
+void sph_destroy(sph_ctx *ctx);
+/* Message for the last non-OK status of calls on ctx (never NULL). */
+const char *sph_last_error(const sph_ctx *ctx);
+
+/*
+ * Quantise, key, sort and build the neighbour grid of one periodic box
+ * (paper Sec. 1: each module walks a tree built over the particles; here the
+ * tree is a Morton-ordered bounding-volume hierarchy built on the GPU).
+ *   pos   device, n x 3 (x,y,z interleaved), float (pos_is_f64 = 0) or double
+ *         (pos_is_f64 = 1); any finite value, wrapped into [0, L).
+ *         Quantisation: X = rint(frac(x/L) 2^32) mod 2^32 per axis (round half
+ *         to even); all geometry after this point is exact integer geometry,
+ *         minimum image d = (int32)(X_j - X_i).
+ *   mass  device, n floats (> 0); copied into the grid (sorted order), so
+ *         the caller may free or change it afterwards.
+ *   n     1 <= n < 2^31.
+ * Keys: 63-bit Morton key of the top 21 bits per axis (x most significant in
+ * each triple); sort: stable by (key, caller index). On success *out is a new
+ * grid (free with sph_grid_free). Non-finite positions set SPH_ST_INVALID.
+ */
+sph_status sph_build_grid(sph_ctx *ctx, const void *pos, int pos_is_f64, const float *mass,
+                          int64_t n, const sph_params *params, void *stream, sph_grid **out);
+
+/*
+ * As sph_build_grid for many independent periodic boxes in one grid (and so
+ * in one launch per pass). Box b holds the caller particles
+ * [box_offsets[b], box_offsets[b+1]) and has side box_sizes[b].
+ *   box_offsets  HOST, n_boxes + 1 int64, box_offsets[0] = 0, strictly
+ *                increasing, box_offsets[n_boxes] = total n.
+ *   box_sizes    HOST, n_boxes doubles > 0.
+ * Keys carry the box index in their top ceil(log2 n_boxes) bits and the
+ * Morton key shifted down by as many bits below it.
+ */
+sph_status sph_build_grid_batched(sph_ctx *ctx, const void *pos, int pos_is_f64,
+                                  const float *mass, const int64_t *box_offsets,
+                                  const double *box_sizes, int n_boxes,
+                                  const sph_params *params, void *stream, sph_grid **out);
+
+/*
+ * Rebuild an existing grid in place for new positions/masses of the same
+ * particles (same n and box layout): quantise, key, sort and bound again,
+ * asynchronously on `stream`, with no allocation and no host synchronisation
+ * -- the per-step rebuild of a time-stepping loop, capturable in a CUDA graph.
+ * Argument meaning as in sph_build_grid.
+ */
+sph_status sph_grid_update(sph_ctx *ctx, sph_grid *grid, const void *pos, int pos_is_f64,
+                           const float *mass, void *stream);
+
+void sph_grid_free(sph_grid *grid);
+int64_t sph_grid_size(const sph_grid *grid);
+
+/*
+ * Test/inspection access to the grid (device outputs, any may be NULL):
+ *   perm  n int32: caller index of the k-th particle in sorted order;
+ *   keys  n uint64: sorted keys;
+ *   X     n x 3 uint32: quantised positions in CALLER order.
+ */
+sph_status sph_grid_export(const sph_grid *grid, int32_t *perm, uint64_t *keys, uint32_t *X,
+                           void *stream);
+
+/*
+ * Density pass with on-device smoothing-length iteration (paper Sec. 1: the
+ * first of the two SPH modules, which iterates until each h settles).
+ * For each active i (the caller indices in `active[0..n_active)`, device
+ * int32, no duplicates; active = NULL means all particles):
+ *   h_i solves N_eff(h) = (4 pi/3) h^3 sum_j W(r_ij, h) = N_t (self included,
+ *   W = M4 cubic spline with support h) to |N_eff - N_t| <= n_tol, by
+ *   bracketed Newton/bisection in FP64, starting from h[i] (in/out, box units);
+ *   rho_i   = sum_j m_j W(r_ij, h_i)                (self included)
+ *   omega_i = [1 + h_i/(3 rho_i) d rho_i/d h_i]^-1  (grad-h factor)
+ *   n_ngb_i = #{j != i : r_ij < h_i} under the exact predicate
+ *             (double)D2 < (h 2^32/L)^2, D2 the exact integer squared distance.
+ *   flags_i = SPH_ST_NOT_CONVERGED / SPH_ST_H_TOO_LARGE bits for i (uint8).
+ *   hash_i  = optional (NULL to skip) checksum of the neighbour set:
+ *             sum over j of splitmix64(caller index j), mod 2^64.
+ * With SPH_FIXED_H the sums are evaluated once at the given h.
+ * Arithmetic: FP32 pair terms, per-batch compensated (Kahan) accumulation,
+ * FP64 h update; SPH_FP64 computes everything in FP64.
+ */
+sph_status sph_density(sph_ctx *ctx, const sph_grid *grid, float *h, const int32_t *active,
+                       int64_t n_active, float *rho, float *omega, int32_t *n_ngb,
+                       uint8_t *flags, uint64_t *hash, const sph_params *params, void *stream);
+
+/*
+ * Hydrodynamic-force pass (paper Sec. 1, the second SPH module), grad-h
+ * Gadget-2 form in specific internal energy u. Inputs are indexed by caller
+ * order for ALL particles (neighbours may be inactive):
+ *   vel (n x 3), u, h, rho, omega (n each) device floats.
+ * For each active i, over j != i with r_ij < max(h_i, h_j):
+ *   P = (gamma-1) rho u,  c = sqrt(gamma P/rho),  A = omega P / rho^2,
+ *   w_ij = v_ij . r_ij / r,  v_sig = c_i + c_j - 3 w_ij,
+ *   Pi_ij = -(alpha/2) v_sig w_ij / ((rho_i+rho_j)/2) if w_ij < 0 else 0,
+ *   acc_i  = -sum_j m_j [A_i gradW_ij(h_i) + A_j gradW_ij(h_j) + Pi_ij gradbarW_ij]
+ *   dudt_i =  A_i sum_j m_j v_ij.gradW_ij(h_i) + 1/2 sum_j m_j Pi_ij v_ij.gradbarW_ij
+ *   vsig_i = max(0, max_j v_sig);  coincident pairs (r = 0) add no force.
+ * acc is n x 3. hash (optional) is the pair-set checksum as in sph_density.
+ * dudt is accumulated in FP64 and rounded once.
+ */
+sph_status sph_hydro_force(sph_ctx *ctx, const sph_grid *grid, const float *vel, const float *u,
+                           const float *h, const float *rho, const float *omega,
+                           const int32_t *active, int64_t n_active, float *acc, float *dudt,
+                           float *vsig, uint64_t *hash, const sph_params *params, void *stream);
+
+/*
+ * Waits for `stream`, then returns the device status word and counters
+ * accumulated since the previous call in *stats (may be NULL) and clears
+ * them. Returns the sph_status of the worst device condition seen.
+ */
+sph_status sph_sync_status(sph_ctx *ctx, void *stream, sph_stats *stats);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPH_GB300_H */

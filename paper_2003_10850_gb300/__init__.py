@@ -1,0 +1,179 @@
+"""GB300-native SPH neighbour-interaction hot path (density + hydro force).
+
+Python face of the C ABI in include/sph.h. The functions below carry the C
+names and only marshal arguments: tensors must be contiguous CUDA tensors of
+the stated dtype, and every computation runs in libsph_gb300.so on the
+current CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import abi
+from .abi import (SPH_FIXED_H, SPH_FP64, SPH_H_GUESS, SPH_PLAIN_FP32, SPH_TIME_KERNELS, SPHError,
+                  default_params, sph_params, sph_stats)
+
+__all__ = ["Context", "Grid", "sph_create", "sph_build_grid", "sph_build_grid_batched", "sph_grid_update",
+           "sph_density", "sph_hydro_force", "sph_sync_status", "sph_grid_export", "density",
+           "hydro_force", "default_params", "sph_params", "sph_stats", "SPHError", "SPH_FP64",
+           "SPH_PLAIN_FP32", "SPH_FIXED_H", "SPH_H_GUESS", "SPH_TIME_KERNELS"]
+
+
+def _ptr(t, dtype=None, name="tensor"):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise TypeError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype not in (dtype if isinstance(dtype, tuple) else (dtype,)):
+        raise TypeError(f"{name} must have dtype {dtype}, got {t.dtype}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Context:
+    """An sph_ctx on one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self.lib = abi.load()
+        self.device = device
+        self.handle = ctypes.c_void_p()
+        st = self.lib.sph_create(ctypes.byref(self.handle), int(device))
+        if st != 0:
+            raise SPHError(st, "sph_create failed")
+
+    def check(self, st: int):
+        if st != 0:
+            raise SPHError(st, self.lib.sph_last_error(self.handle).decode())
+
+    def close(self):
+        if self.handle:
+            self.lib.sph_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Grid:
+    """An sph_grid built by sph_build_grid*."""
+
+    def __init__(self, ctx: Context, handle: ctypes.c_void_p, n: int):
+        self.ctx, self.handle, self.n = ctx, handle, n
+
+    def free(self):
+        if self.handle:
+            self.ctx.lib.sph_grid_free(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def sph_create(device: int = 0) -> Context:
+    return Context(device)
+
+
+def sph_build_grid(ctx: Context, pos: torch.Tensor, mass: torch.Tensor, params: sph_params) -> Grid:
+    n = pos.shape[0]
+    f64 = pos.dtype == torch.float64
+    out = ctypes.c_void_p()
+    ctx.check(ctx.lib.sph_build_grid(ctx.handle, _ptr(pos, (torch.float32, torch.float64), "pos"), int(f64),
+                                     _ptr(mass, torch.float32, "mass"), n, ctypes.byref(params), _stream(),
+                                     ctypes.byref(out)))
+    return Grid(ctx, out, n)
+
+
+def sph_build_grid_batched(ctx: Context, pos: torch.Tensor, mass: torch.Tensor, box_offsets, box_sizes,
+                           params: sph_params) -> Grid:
+    nb = len(box_sizes)
+    offs = (ctypes.c_int64 * (nb + 1))(*[int(v) for v in box_offsets])
+    sizes = (ctypes.c_double * nb)(*[float(v) for v in box_sizes])
+    f64 = pos.dtype == torch.float64
+    out = ctypes.c_void_p()
+    ctx.check(ctx.lib.sph_build_grid_batched(ctx.handle, _ptr(pos, (torch.float32, torch.float64), "pos"),
+                                             int(f64), _ptr(mass, torch.float32, "mass"), offs, sizes, nb,
+                                             ctypes.byref(params), _stream(), ctypes.byref(out)))
+    return Grid(ctx, out, int(box_offsets[-1]))
+
+
+def sph_grid_update(ctx: Context, grid: Grid, pos: torch.Tensor, mass: torch.Tensor):
+    f64 = pos.dtype == torch.float64
+    ctx.check(ctx.lib.sph_grid_update(ctx.handle, grid.handle, _ptr(pos, (torch.float32, torch.float64), "pos"),
+                                      int(f64), _ptr(mass, torch.float32, "mass"), _stream()))
+
+
+def sph_grid_export(grid: Grid, perm=None, keys=None, X=None):
+    grid.ctx.check(grid.ctx.lib.sph_grid_export(grid.handle, _ptr(perm, torch.int32, "perm"),
+                                                _ptr(keys, torch.int64, "keys"), _ptr(X, torch.int32, "X"),
+                                                _stream()))
+
+
+def sph_density(ctx: Context, grid: Grid, h, active, rho, omega, n_ngb, flags, hash=None,
+                params: sph_params = None):
+    na = 0 if active is None else active.numel()
+    ctx.check(ctx.lib.sph_density(ctx.handle, grid.handle, _ptr(h, torch.float32, "h"),
+                                  _ptr(active, torch.int32, "active"), na, _ptr(rho, torch.float32, "rho"),
+                                  _ptr(omega, torch.float32, "omega"), _ptr(n_ngb, torch.int32, "n_ngb"),
+                                  _ptr(flags, torch.uint8, "flags"), _ptr(hash, torch.int64, "hash"),
+                                  ctypes.byref(params), _stream()))
+
+
+def sph_hydro_force(ctx: Context, grid: Grid, vel, u, h, rho, omega, active, acc, dudt, vsig, hash=None,
+                    params: sph_params = None):
+    na = 0 if active is None else active.numel()
+    f = torch.float32
+    ctx.check(ctx.lib.sph_hydro_force(ctx.handle, grid.handle, _ptr(vel, f, "vel"), _ptr(u, f, "u"),
+                                      _ptr(h, f, "h"), _ptr(rho, f, "rho"), _ptr(omega, f, "omega"),
+                                      _ptr(active, torch.int32, "active"), na, _ptr(acc, f, "acc"),
+                                      _ptr(dudt, f, "dudt"), _ptr(vsig, f, "vsig"),
+                                      _ptr(hash, torch.int64, "hash"), ctypes.byref(params), _stream()))
+
+
+def sph_sync_status(ctx: Context, raise_on_error: bool = True):
+    """Waits for the current stream; returns (status, stats dict) and clears the counters."""
+    st = sph_stats()
+    rc = ctx.lib.sph_sync_status(ctx.handle, _stream(), ctypes.byref(st))
+    if rc != 0 and raise_on_error:
+        raise SPHError(rc, ctx.lib.sph_last_error(ctx.handle).decode())
+    return rc, st.as_dict()
+
+
+# ---- conveniences that allocate the outputs ----------------------------------
+
+def density(ctx, grid, h, active=None, params=None, want_hash=False):
+    """Runs sph_density in place on h; returns dict of rho, omega, n_ngb, flags (, hash)."""
+    n = grid.n
+    dev = h.device
+    out = {"rho": torch.zeros(n, device=dev), "omega": torch.zeros(n, device=dev),
+           "n_ngb": torch.full((n,), -1, dtype=torch.int32, device=dev),
+           "flags": torch.zeros(n, dtype=torch.uint8, device=dev)}
+    if want_hash:
+        out["hash"] = torch.zeros(n, dtype=torch.int64, device=dev)
+    sph_density(ctx, grid, h, active, out["rho"], out["omega"], out["n_ngb"], out["flags"],
+                out.get("hash"), params or default_params())
+    return out
+
+
+def hydro_force(ctx, grid, vel, u, h, rho, omega, active=None, params=None, want_hash=False):
+    n = grid.n
+    dev = h.device
+    out = {"acc": torch.zeros(n, 3, device=dev), "dudt": torch.zeros(n, device=dev),
+           "vsig": torch.zeros(n, device=dev)}
+    if want_hash:
+        out["hash"] = torch.zeros(n, dtype=torch.int64, device=dev)
+    sph_hydro_force(ctx, grid, vel, u, h, rho, omega, active, out["acc"], out["dudt"], out["vsig"],
+                    out.get("hash"), params or default_params())
+    return out

@@ -1,0 +1,297 @@
+// abi.cu -- the extern "C" entry points declared in include/sph.h: argument
+// validation on the host, dispatch to the kernels, and the device status word.
+#include <cmath>
+#include <cstring>
+
+#include "internal.cuh"
+
+using namespace sph;
+
+namespace {
+
+sph_status fail(sph_ctx* ctx, sph_status st, const std::string& msg) {
+    if (ctx) ctx->err = msg;
+    return st;
+}
+
+sph_status cuda_fail(sph_ctx* ctx, cudaError_t e, const char* where) {
+    return fail(ctx, e == cudaErrorMemoryAllocation ? SPH_ERR_OOM : SPH_ERR_CUDA,
+                std::string("CUDA error in ") + where + ": " + cudaGetErrorString(e));
+}
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+sph_status check_params(sph_ctx* ctx, const sph_params* p) {
+    if (!p) return fail(ctx, SPH_ERR_INVALID, "params is NULL");
+    if (!finite_pos(p->box)) return fail(ctx, SPH_ERR_INVALID, "params.box must be finite and > 0");
+    if (!finite_pos(p->n_target)) return fail(ctx, SPH_ERR_INVALID, "params.n_target must be > 0");
+    if (!finite_pos(p->n_tol)) return fail(ctx, SPH_ERR_INVALID, "params.n_tol must be > 0");
+    if (p->max_iter < 0 || p->max_iter > 10000) return fail(ctx, SPH_ERR_INVALID, "params.max_iter out of range");
+    if (!std::isfinite(p->alpha_visc) || p->alpha_visc < 0) return fail(ctx, SPH_ERR_INVALID, "params.alpha_visc must be >= 0");
+    if (!std::isfinite(p->gamma) || p->gamma <= 1.0) return fail(ctx, SPH_ERR_INVALID, "params.gamma must be > 1");
+    if (p->group_size != 0 && p->group_size != 16 && p->group_size != 32)
+        return fail(ctx, SPH_ERR_INVALID, "params.group_size must be 0, 16 or 32");
+    if (p->blocks_per_sm < 0 || p->blocks_per_sm > 32) return fail(ctx, SPH_ERR_INVALID, "params.blocks_per_sm out of range");
+    if ((p->flags & SPH_FP64) && (p->flags & SPH_PLAIN_FP32))
+        return fail(ctx, SPH_ERR_INVALID, "SPH_FP64 and SPH_PLAIN_FP32 are exclusive");
+    return SPH_OK;
+}
+
+int group_size(const sph_params* p) { return p->group_size ? p->group_size : 32; }
+
+sph_status check_active(sph_ctx* ctx, const sph_grid* g, const int32_t* active, int64_t n_active) {
+    if (active && (n_active < 0 || n_active > g->n))
+        return fail(ctx, SPH_ERR_INVALID, "n_active must be in [0, n] when active is given");
+    return SPH_OK;
+}
+
+}  // namespace
+
+namespace sph {
+cudaEvent_t timing_event(sph_ctx* ctx) {
+    if (!ctx->event_pool.empty()) {
+        cudaEvent_t e = ctx->event_pool.back();
+        ctx->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+}  // namespace sph
+
+extern "C" {
+
+void sph_default_params(sph_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->box = 1.0;
+    p->n_target = 64.0;
+    p->n_tol = 64.0e-6;
+    p->max_iter = 64;
+    p->alpha_visc = 1.0;
+    p->gamma = 5.0 / 3.0;
+}
+
+sph_status sph_create(sph_ctx** out, int device) {
+    if (!out) return SPH_ERR_INVALID;
+    *out = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) return SPH_ERR_CUDA;
+    if (cudaSetDevice(device) != cudaSuccess) return SPH_ERR_CUDA;
+    sph_ctx* c = new sph_ctx();
+    c->device = device;
+    cudaError_t e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+    if (!e) e = cudaMalloc(&c->counters, sizeof(Counters));
+    if (!e) e = cudaMemset(c->counters, 0, sizeof(Counters));
+    if (!e) e = cudaMalloc(&c->queue, sizeof(unsigned) * kQueues);
+    if (!e) e = cudaMallocHost(&c->host_counters, sizeof(Counters));
+    if (!e) e = cudaDeviceSynchronize();
+    if (e) {
+        sph_destroy(c);
+        return e == cudaErrorMemoryAllocation ? SPH_ERR_OOM : SPH_ERR_CUDA;
+    }
+    *out = c;
+    return SPH_OK;
+}
+
+void sph_destroy(sph_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->counters) cudaFree(c->counters);
+    if (c->queue) cudaFree(c->queue);
+    if (c->host_counters) cudaFreeHost(c->host_counters);
+    for (auto& t : c->timed) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
+    for (auto e : c->event_pool) cudaEventDestroy(e);
+    delete c;
+}
+
+const char* sph_last_error(const sph_ctx* c) {
+    if (!c) return "context is NULL";
+    return c->err.c_str();
+}
+
+sph_status sph_build_grid_batched(sph_ctx* ctx, const void* pos, int pos_is_f64, const float* mass,
+                                  const int64_t* box_offsets, const double* box_sizes, int n_boxes,
+                                  const sph_params* params, void* stream, sph_grid** out) {
+    if (!ctx) return SPH_ERR_INVALID;
+    if (!out) return fail(ctx, SPH_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!pos || !mass) return fail(ctx, SPH_ERR_INVALID, "pos and mass must be device pointers");
+    if (!box_offsets || !box_sizes || n_boxes < 1 || n_boxes > 65535)
+        return fail(ctx, SPH_ERR_INVALID, "need 1..65535 boxes with host offsets and sizes");
+    if (box_offsets[0] != 0) return fail(ctx, SPH_ERR_INVALID, "box_offsets[0] must be 0");
+    for (int b = 0; b < n_boxes; ++b) {
+        if (box_offsets[b + 1] <= box_offsets[b]) return fail(ctx, SPH_ERR_INVALID, "box_offsets must increase strictly");
+        if (!finite_pos(box_sizes[b])) return fail(ctx, SPH_ERR_INVALID, "box sizes must be finite and > 0");
+    }
+    const int64_t n = box_offsets[n_boxes];
+    if (n < 1 || n >= (int64_t(1) << 31)) return fail(ctx, SPH_ERR_INVALID, "total n must be in [1, 2^31)");
+    sph_status st = check_params(ctx, params);
+    if (st) return st;
+    if (cudaSetDevice(ctx->device)) return fail(ctx, SPH_ERR_CUDA, "cudaSetDevice failed");
+    return grid_build(ctx, pos, pos_is_f64 ? 1 : 0, mass, box_offsets, box_sizes, n_boxes,
+                      (cudaStream_t)stream, out);
+}
+
+sph_status sph_build_grid(sph_ctx* ctx, const void* pos, int pos_is_f64, const float* mass, int64_t n,
+                          const sph_params* params, void* stream, sph_grid** out) {
+    if (!ctx) return SPH_ERR_INVALID;
+    sph_status st = check_params(ctx, params);
+    if (st) return st;
+    if (n < 1 || n >= (int64_t(1) << 31)) return fail(ctx, SPH_ERR_INVALID, "n must be in [1, 2^31)");
+    int64_t offs[2] = {0, n};
+    double L = params->box;
+    return sph_build_grid_batched(ctx, pos, pos_is_f64, mass, offs, &L, 1, params, stream, out);
+}
+
+sph_status sph_grid_update(sph_ctx* ctx, sph_grid* grid, const void* pos, int pos_is_f64, const float* mass,
+                           void* stream) {
+    if (!ctx) return SPH_ERR_INVALID;
+    if (!grid || grid->ctx != ctx) return fail(ctx, SPH_ERR_INVALID, "grid is NULL or from another context");
+    if (!pos || !mass) return fail(ctx, SPH_ERR_INVALID, "pos and mass must be device pointers");
+    if (cudaSetDevice(ctx->device)) return fail(ctx, SPH_ERR_CUDA, "cudaSetDevice failed");
+    return grid_update(grid, pos, pos_is_f64 ? 1 : 0, mass, (cudaStream_t)stream);
+}
+
+void sph_grid_free(sph_grid* g) {
+    if (!g) return;
+    cudaSetDevice(g->ctx->device);
+    grid_free(g);
+}
+
+int64_t sph_grid_size(const sph_grid* g) { return g ? g->n : 0; }
+
+sph_status sph_grid_export(const sph_grid* g, int32_t* perm, uint64_t* keys, uint32_t* X, void* stream) {
+    if (!g) return SPH_ERR_INVALID;
+    sph_ctx* ctx = g->ctx;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    if (perm && !e) e = cudaMemcpyAsync(perm, g->perm, sizeof(int32_t) * g->n, cudaMemcpyDeviceToDevice, s);
+    if (keys && !e) e = cudaMemcpyAsync(keys, g->keys, sizeof(uint64_t) * g->n, cudaMemcpyDeviceToDevice, s);
+    if (X && !e) e = cudaMemcpy2DAsync(X, 12, g->xq, 16, 12, g->n, cudaMemcpyDeviceToDevice, s);
+    if (e) return cuda_fail(ctx, e, "sph_grid_export");
+    return SPH_OK;
+}
+
+sph_status sph_density(sph_ctx* ctx, const sph_grid* grid, float* h, const int32_t* active, int64_t n_active,
+                       float* rho, float* omega, int32_t* n_ngb, uint8_t* flags, uint64_t* hash,
+                       const sph_params* params, void* stream) {
+    if (!ctx) return SPH_ERR_INVALID;
+    if (!grid || grid->ctx != ctx) return fail(ctx, SPH_ERR_INVALID, "grid is NULL or from another context");
+    if (!h || !rho || !omega || !n_ngb || !flags) return fail(ctx, SPH_ERR_INVALID, "h, rho, omega, n_ngb, flags are required");
+    sph_status st = check_params(ctx, params);
+    if (st) return st;
+    if ((st = check_active(ctx, grid, active, n_active))) return st;
+    const int64_t na = active ? n_active : grid->n;
+    if (na == 0) return SPH_OK;
+    if (cudaSetDevice(ctx->device)) return fail(ctx, SPH_ERR_CUDA, "cudaSetDevice failed");
+    cudaStream_t s = (cudaStream_t)stream;
+    sph_grid* g = const_cast<sph_grid*>(grid);  // per-call scratch lives in the grid
+    grid_active(g, active, n_active, group_size(params), s);
+    DensityLaunch a;
+    a.g = g;
+    a.h = h;
+    a.rho = rho;
+    a.omega = omega;
+    a.n_ngb = n_ngb;
+    a.flags = flags;
+    a.hash = reinterpret_cast<unsigned long long*>(hash);
+    a.n_target = params->n_target;
+    a.n_tol = params->n_tol;
+    a.max_iter = params->max_iter;
+    a.fixed_h = (params->flags & SPH_FIXED_H) ? 1 : 0;
+    a.guess_h = (params->flags & SPH_H_GUESS) ? 1 : 0;
+    a.fp64 = (params->flags & SPH_FP64) ? 1 : 0;
+    a.blocks_per_sm = params->blocks_per_sm;
+    a.time_kernels = (params->flags & SPH_TIME_KERNELS) ? 1 : 0;
+    cudaError_t e = (params->flags & SPH_PLAIN_FP32) ? run_density_plain(ctx, a, na, s) : launch_density(ctx, a, s);
+    if (!e) e = cudaGetLastError();
+    if (e) return cuda_fail(ctx, e, "sph_density");
+    return SPH_OK;
+}
+
+sph_status sph_hydro_force(sph_ctx* ctx, const sph_grid* grid, const float* vel, const float* u,
+                           const float* h, const float* rho, const float* omega, const int32_t* active,
+                           int64_t n_active, float* acc, float* dudt, float* vsig, uint64_t* hash,
+                           const sph_params* params, void* stream) {
+    if (!ctx) return SPH_ERR_INVALID;
+    if (!grid || grid->ctx != ctx) return fail(ctx, SPH_ERR_INVALID, "grid is NULL or from another context");
+    if (!vel || !u || !h || !rho || !omega || !acc || !dudt || !vsig)
+        return fail(ctx, SPH_ERR_INVALID, "vel, u, h, rho, omega, acc, dudt, vsig are required");
+    sph_status st = check_params(ctx, params);
+    if (st) return st;
+    if ((st = check_active(ctx, grid, active, n_active))) return st;
+    const int64_t na = active ? n_active : grid->n;
+    if (na == 0) return SPH_OK;
+    if (cudaSetDevice(ctx->device)) return fail(ctx, SPH_ERR_CUDA, "cudaSetDevice failed");
+    cudaStream_t s = (cudaStream_t)stream;
+    sph_grid* g = const_cast<sph_grid*>(grid);
+    grid_refresh_hmax(g, h, s);
+    grid_active(g, active, n_active, group_size(params), s);
+    ForceLaunch a;
+    a.g = g;
+    a.vel = vel;
+    a.u = u;
+    a.h = h;
+    a.rho = rho;
+    a.omega = omega;
+    a.acc = acc;
+    a.dudt = dudt;
+    a.vsig = vsig;
+    a.hash = reinterpret_cast<unsigned long long*>(hash);
+    a.alpha = params->alpha_visc;
+    a.gamma = params->gamma;
+    a.fp64 = (params->flags & SPH_FP64) ? 1 : 0;
+    a.blocks_per_sm = params->blocks_per_sm;
+    a.time_kernels = (params->flags & SPH_TIME_KERNELS) ? 1 : 0;
+    cudaError_t e = (params->flags & SPH_PLAIN_FP32) ? launch_force_plain(ctx, a, na, s) : launch_force(ctx, a, s);
+    if (!e) e = cudaGetLastError();
+    if (e) return cuda_fail(ctx, e, "sph_hydro_force");
+    return SPH_OK;
+}
+
+sph_status sph_sync_status(sph_ctx* ctx, void* stream, sph_stats* stats) {
+    if (!ctx) return SPH_ERR_INVALID;
+    if (cudaSetDevice(ctx->device)) return fail(ctx, SPH_ERR_CUDA, "cudaSetDevice failed");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(ctx->host_counters, ctx->counters, sizeof(Counters), cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaMemsetAsync(ctx->counters, 0, sizeof(Counters), s);
+    if (!e) e = cudaStreamSynchronize(s);
+    if (e) return cuda_fail(ctx, e, "sph_sync_status");
+    const Counters& c = *ctx->host_counters;
+    double tms[2] = {0.0, 0.0};
+    unsigned tn[2] = {0, 0};
+    for (auto& t : ctx->timed) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) {
+            tms[t.kind] += ms;
+            tn[t.kind] += 1;
+        }
+        ctx->event_pool.push_back(t.a);
+        ctx->event_pool.push_back(t.b);
+    }
+    ctx->timed.clear();
+    const unsigned launches = ctx->launches;
+    ctx->launches = 0;
+    if (stats) {
+        stats->status = c.status;
+        stats->launches = launches;
+        stats->density_kernel_ms = tms[0];
+        stats->force_kernel_ms = tms[1];
+        stats->density_launches = tn[0];
+        stats->force_launches = tn[1];
+        stats->density_pairs = c.density_pairs;
+        stats->force_pairs = c.force_pairs;
+        stats->density_evals = c.density_evals;
+        stats->pair_tests = c.pair_tests;
+        stats->groups = c.groups;
+    }
+    if (c.status & ST_INVALID) return fail(ctx, SPH_ERR_INVALID, "device: non-finite or out-of-range input");
+    if (c.status & ST_TIMEOUT) return fail(ctx, SPH_ERR_TIMEOUT, "device: a bounded wait ran out");
+    if (c.status & ST_H_TOO_LARGE) return fail(ctx, SPH_ERR_H_TOO_LARGE, "device: some h reached L/2");
+    if (c.status & ST_NOT_CONVERGED) return fail(ctx, SPH_ERR_NOT_CONVERGED, "device: some h did not converge");
+    return SPH_OK;
+}
+
+}  // extern "C"

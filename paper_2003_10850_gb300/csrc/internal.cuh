@@ -1,0 +1,133 @@
+// internal.cuh -- host-side structures shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "sph.h"
+
+struct sph_ctx {
+    int device = 0;
+    int sm_count = 0;
+    std::string err;
+    sph::Counters* counters = nullptr;  // device
+    unsigned* queue = nullptr;          // device work-queue counters (kQueues)
+    sph::Counters* host_counters = nullptr;  // pinned
+    unsigned launches = 0;                   // kernels launched since the last sync
+    // SPH_TIME_KERNELS: event pairs around the main kernels (kind 0 density, 1 force)
+    struct Timed { cudaEvent_t a, b; int kind; };
+    std::vector<Timed> timed;
+    std::vector<cudaEvent_t> event_pool;
+};
+
+struct sph_grid {
+    sph_ctx* ctx = nullptr;
+    int64_t n = 0;
+    int n_boxes = 0;
+    int box_bits = 0;
+    int n_nodes = 0;
+    int max_leaves = 0;                    // max over boxes of level-0 nodes
+    int max_lev = 0;                       // max over boxes of the level count
+    int lvl_max[sph::kMaxLev] = {};        // max over boxes of the nodes on each level
+    std::vector<sph::BoxDesc> boxes_h;
+    sph::BoxDesc* boxes = nullptr;         // device
+    uint4* posm = nullptr;                 // sorted: X, Y, Z, mass bits
+    uint4* xq = nullptr;                   // caller order: X, Y, Z, mass bits
+    int32_t* perm = nullptr;               // sorted -> caller
+    int32_t* rank = nullptr;               // caller -> sorted
+    uint64_t* keys = nullptr;              // sorted keys
+    uint4* node_lo = nullptr;
+    uint4* node_hi = nullptr;
+    float* node_hmax = nullptr;
+    // per-call scratch, sized at build so that calls never allocate
+    int32_t* act = nullptr;                // active particles, sorted indices, sorted order
+    uint8_t* flag = nullptr;               // n
+    uint32_t* scan = nullptr;              // n + 1
+    uint32_t* scan_tmp = nullptr;          // block sums
+    int* box_act = nullptr;                // per box: act_off, act_n, grp_off, grp_n
+    int* n_groups = nullptr;               // device scalar
+    sph::Group* groups = nullptr;          // capacity max_groups
+    int max_groups = 0;
+    // plain-path scratch
+    int32_t* list_a = nullptr;
+    int32_t* list_b = nullptr;
+    float* st_lo = nullptr;
+    float* st_hi = nullptr;
+    int* list_n = nullptr;                 // device [2]
+    // rebuild scratch (kept so that sph_grid_update never allocates)
+    long long* d_off = nullptr;
+    double* d_L = nullptr;
+    unsigned long long* k2 = nullptr;
+    unsigned* v1 = nullptr;
+    unsigned* v2 = nullptr;
+    unsigned* counts = nullptr;
+    unsigned* cscan = nullptr;
+};
+
+namespace sph {
+
+constexpr int kQueues = 4;
+
+// grid.cu
+sph_status grid_build(sph_ctx* ctx, const void* pos, int f64, const float* mass,
+                      const int64_t* offs, const double* Ls, int nb, cudaStream_t s,
+                      sph_grid** out);
+void grid_free(sph_grid* g);
+// re-quantise, re-sort and rebuild the hierarchy in place (same n and boxes)
+sph_status grid_update(sph_grid* g, const void* pos, int f64, const float* mass, cudaStream_t s);
+// hmax of every node from the caller-order h
+void grid_refresh_hmax(sph_grid* g, const float* h, cudaStream_t s);
+// active list + groups of at most gs particles per box
+void grid_active(sph_grid* g, const int32_t* active, int64_t n_active, int gs, cudaStream_t s);
+// exclusive scan of n values into out[0..n] (out[n] = total); tmp >= n/4096+2 words
+template <typename In>
+void scan_exclusive(const In* in, int n, uint32_t* out, uint32_t* tmp, cudaStream_t s, unsigned* launches);
+// SPH_TIME_KERNELS support: event pair around one kernel launch
+cudaEvent_t timing_event(sph_ctx* ctx);
+
+// density.cu
+struct DensityLaunch {
+    const sph_grid* g;
+    float* h;
+    float* rho;
+    float* omega;
+    int32_t* n_ngb;
+    uint8_t* flags;
+    unsigned long long* hash;
+    double n_target, n_tol;
+    int max_iter;
+    int fixed_h, guess_h;
+    int fp64;
+    int blocks_per_sm;
+    int time_kernels;
+};
+cudaError_t launch_density(sph_ctx* ctx, const DensityLaunch& a, cudaStream_t s);
+cudaError_t run_density_plain(sph_ctx* ctx, const DensityLaunch& a, int64_t n_active,
+                              cudaStream_t s);
+
+// force.cu
+struct ForceLaunch {
+    const sph_grid* g;
+    const float* vel;
+    const float* u;
+    const float* h;
+    const float* rho;
+    const float* omega;
+    float* acc;
+    float* dudt;
+    float* vsig;
+    unsigned long long* hash;
+    double alpha, gamma;
+    int fp64;
+    int blocks_per_sm;
+    int time_kernels;
+};
+cudaError_t launch_force(sph_ctx* ctx, const ForceLaunch& a, cudaStream_t s);
+cudaError_t launch_force_plain(sph_ctx* ctx, const ForceLaunch& a, int64_t n_active,
+                               cudaStream_t s);
+
+}  // namespace sph

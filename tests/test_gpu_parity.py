@@ -1,0 +1,269 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
+the same seeded inputs, element by element.
+
+Tolerances (stated per output): rho and h relative <= 1e-5; acc and du/dt
+<= 1e-4 of the per-particle absolute scale (sum of the pair terms'
+magnitudes); neighbour and pair sets bit-exact (checksums of the sets) at the
+same h; integer keys and the sort permutation bit-exact.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads as W
+from sph_cases import as_f32, check_force, dev, gpu_density, gpu_force, gpu_grid, host, oracle_all, rel
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def S():
+    from paper_2003_10850_gb300 import build
+    build.build()
+    import paper_2003_10850_gb300 as S
+    return S
+
+
+@pytest.fixture(scope="module")
+def ctx(S):
+    return S.Context(0)
+
+
+@pytest.fixture(scope="module")
+def lattice32():
+    p = as_f32(W.config1(32))
+    return p, oracle_all(p)
+
+
+@pytest.fixture(scope="module")
+def clustered50k():
+    p = as_f32(W.clustered(50_000, 40, seed=202))
+    return p, oracle_all(p)
+
+
+# ---- a1/a2: quantise, key, sort -------------------------------------------
+
+@pytest.mark.parametrize("kind", ["lattice", "clustered"])
+def test_keys_and_sort_exact(S, ctx, kind, lattice32, clustered50k):
+    p = (lattice32 if kind == "lattice" else clustered50k)[0]
+    grid = gpu_grid(S, ctx, p, S.default_params(box=p.box))
+    n = p.n
+    perm = torch.empty(n, dtype=torch.int32, device="cuda")
+    keys = torch.empty(n, dtype=torch.int64, device="cuda")
+    X = torch.empty(n, 3, dtype=torch.int32, device="cuda")
+    S.sph_grid_export(grid, perm, keys, X)
+    X_o = oracle.quantize(p.pos, p.box)
+    k_o = oracle.morton_keys(X_o)
+    perm_o = oracle.sort_perm(k_o)
+    assert np.array_equal(host(X).view(np.uint32), X_o)
+    assert np.array_equal(host(perm), perm_o)
+    assert np.array_equal(host(keys).view(np.uint64), k_o[perm_o])
+
+
+def test_batched_keys_and_sort_exact(S, ctx):
+    boxes = [as_f32(W.clustered(n, 3, seed=300 + i)) for i, n in enumerate((1000, 4097, 2500))]
+    pos = np.concatenate([b.pos for b in boxes])
+    mass = np.concatenate([b.mass for b in boxes])
+    offs = np.cumsum([0] + [b.n for b in boxes])
+    grid = S.sph_build_grid_batched(ctx, dev(pos), dev(mass), offs, [1.0] * 3, S.default_params())
+    perm = torch.empty(offs[-1], dtype=torch.int32, device="cuda")
+    keys = torch.empty(offs[-1], dtype=torch.int64, device="cuda")
+    S.sph_grid_export(grid, perm, keys, None)
+    k_o = np.concatenate([oracle.morton_keys(oracle.quantize(b.pos), i, 2) for i, b in enumerate(boxes)])
+    perm_o = oracle.sort_perm(k_o)
+    assert np.array_equal(host(perm), perm_o)
+    assert np.array_equal(host(keys).view(np.uint64), k_o[perm_o])
+
+
+# ---- a4: density ------------------------------------------------------------
+
+@pytest.mark.parametrize("fp64", [False, True])
+@pytest.mark.parametrize("kind", ["lattice", "clustered"])
+def test_density_fixed_h_sets_exact(S, ctx, kind, fp64, lattice32, clustered50k):
+    p, (X, d, _) = lattice32 if kind == "lattice" else clustered50k
+    h32 = d["h"].astype(np.float32)
+    params = S.default_params(box=p.box, flags=S.SPH_FIXED_H | (S.SPH_FP64 if fp64 else 0))
+    grid = gpu_grid(S, ctx, p, params)
+    g = gpu_density(S, ctx, grid, h32, params)
+    assert g["rc"] == 0
+    o = oracle.density(X, p.mass, h32.astype(np.float64), box=p.box, fixed_h=True)
+    assert np.array_equal(g["n_ngb"], o["n_ngb"])
+    assert np.array_equal(g["hash"], o["hash"])
+    tol = 2e-7 if fp64 else 1e-5
+    assert rel(g["rho"], o["rho"]).max() <= tol
+    assert rel(g["omega"], o["omega"]).max() <= (1e-6 if fp64 else 1e-4)
+    assert g["stats"]["density_pairs"] == int(o["n_ngb"].sum())
+
+
+def _density_converged_checks(g, p, X, d, fp64):
+    assert g["rc"] == 0 and not g["flags"].any()
+    assert rel(g["h"], d["h"]).max() <= 1e-5
+    assert rel(g["rho"], d["rho"]).max() <= 1e-5
+    assert rel(g["omega"], d["omega"]).max() <= 1e-4
+    # n_ngb at the converged h: between the oracle's counts at h (1 -/+ 1e-5)
+    lo = oracle.density(X, p.mass, d["h"] * (1 - 1e-5), box=p.box, fixed_h=True)["n_ngb"]
+    hi = oracle.density(X, p.mass, d["h"] * (1 + 1e-5), box=p.box, fixed_h=True)["n_ngb"]
+    assert np.all((g["n_ngb"] >= lo) & (g["n_ngb"] <= hi))
+
+
+@pytest.mark.parametrize("fp64", [False, True])
+@pytest.mark.parametrize("kind", ["lattice", "clustered"])
+def test_density_converged(S, ctx, kind, fp64, lattice32, clustered50k):
+    p, (X, d, _) = lattice32 if kind == "lattice" else clustered50k
+    params = S.default_params(box=p.box, flags=S.SPH_FP64 if fp64 else 0)
+    grid = gpu_grid(S, ctx, p, params)
+    g = gpu_density(S, ctx, grid, np.zeros(p.n, np.float32), params)   # h <= 0: local guess
+    _density_converged_checks(g, p, X, d, fp64)
+    # a perturbed start converges to the same root
+    g2 = gpu_density(S, ctx, grid, W.perturb(d["h"], 0.3, seed=9).astype(np.float32), params)
+    assert rel(g2["h"], d["h"]).max() <= 1e-5
+
+
+def test_density_plain_fp32(S, ctx, clustered50k):
+    p, (X, d, _) = clustered50k
+    params = S.default_params(box=p.box, flags=S.SPH_PLAIN_FP32)
+    grid = gpu_grid(S, ctx, p, params)
+    g = gpu_density(S, ctx, grid, np.zeros(p.n, np.float32), params)
+    assert rel(g["h"], d["h"]).max() <= 1e-4
+    assert rel(g["rho"], d["rho"]).max() <= 1e-4
+
+
+# ---- a5: force --------------------------------------------------------------
+
+def _oracle_inputs32(d):
+    return [d[k].astype(np.float32) for k in ("h", "rho", "omega")]
+
+
+@pytest.mark.parametrize("fp64", [False, True])
+@pytest.mark.parametrize("kind", ["lattice", "clustered"])
+def test_force_parity(S, ctx, kind, fp64, lattice32, clustered50k):
+    p, (X, d, _) = lattice32 if kind == "lattice" else clustered50k
+    h, rho, om = _oracle_inputs32(d)
+    f = oracle.force(X, p.vel, p.mass, p.u, h, rho, om, box=p.box)
+    params = S.default_params(box=p.box, flags=S.SPH_FP64 if fp64 else 0)
+    grid = gpu_grid(S, ctx, p, params)
+    g = gpu_force(S, ctx, grid, p, h, rho, om, params)
+    assert g["rc"] == 0
+    check_force(g, f, np.arange(p.n), 1e-6 if fp64 else 1e-4)
+    assert g["stats"]["force_pairs"] == int(f["n_pairs"].sum())
+    # momentum conservation of the GPU result
+    mom = np.linalg.norm((p.mass[:, None] * g["acc"]).sum(0))
+    assert mom <= 1e-5 * (p.mass * np.linalg.norm(g["acc"], axis=1)).sum()
+
+
+def test_force_plain_fp32(S, ctx, clustered50k):
+    p, (X, d, _) = clustered50k
+    h, rho, om = _oracle_inputs32(d)
+    f = oracle.force(X, p.vel, p.mass, p.u, h, rho, om, box=p.box)
+    params = S.default_params(box=p.box, flags=S.SPH_PLAIN_FP32)
+    grid = gpu_grid(S, ctx, p, params)
+    g = gpu_force(S, ctx, grid, p, h, rho, om, params)
+    da = np.linalg.norm(g["acc"] - f["acc"], axis=1)
+    assert np.quantile(da / f["scale_a"], 0.999) <= 1e-3
+
+
+# ---- a6: active subsets and batched boxes ------------------------------------
+
+def test_active_subset(S, ctx, clustered50k):
+    p, (X, d, _) = clustered50k
+    act = W.sample_indices(p.n, p.n // 10, seed=17).astype(np.int32)
+    params = S.default_params(box=p.box)
+    grid = gpu_grid(S, ctx, p, params)
+    h0 = np.full(p.n, -7.0, np.float32)
+    h0[act] = 0.0
+    g = gpu_density(S, ctx, grid, h0, params, active=act)
+    assert g["rc"] == 0
+    assert rel(g["h"][act], d["h"][act]).max() <= 1e-5
+    assert rel(g["rho"][act], d["rho"][act]).max() <= 1e-5
+    inact = np.setdiff1d(np.arange(p.n), act)
+    assert np.all(g["h"][inact] == -7.0) and np.all(g["n_ngb"][inact] == -1)
+    h, rho, om = _oracle_inputs32(d)
+    f = oracle.force(X, p.vel, p.mass, p.u, h, rho, om, box=p.box, active=act.astype(np.int64))
+    gf = gpu_force(S, ctx, grid, p, h, rho, om, params, active=act)
+    check_force(gf, f, act, 1e-4)
+    assert np.all(gf["acc"][inact] == 0)
+    # duplicates in the active list are ignored
+    dup = np.concatenate([act, act[:100]])
+    g2 = gpu_density(S, ctx, grid, h0, params, active=dup)
+    assert np.array_equal(g2["n_ngb"][act], g["n_ngb"][act])
+
+
+def test_batched_boxes(S, ctx):
+    sizes = (4096, 9000, 30000, 2000)
+    Ls = (1.0, 2.0, 0.5, 1.0)
+    boxes = []
+    for i, (n, L) in enumerate(zip(sizes, Ls)):
+        b = W.clustered(n, W.blobs_for(n), seed=100 + i)
+        boxes.append(as_f32(W.Particles(b.pos * L, b.vel, b.mass, b.u, L)))
+    pos = np.concatenate([b.pos for b in boxes])
+    offs = np.cumsum([0] + [b.n for b in boxes])
+    cat = lambda k: np.concatenate([getattr(b, k) for b in boxes])
+    params = S.default_params()
+    grid = S.sph_build_grid_batched(ctx, dev(pos), dev(cat("mass")), offs, Ls, params)
+    g = gpu_density(S, ctx, grid, np.zeros(offs[-1], np.float32), params)
+    assert g["rc"] == 0
+    hs, rhos, oms = [], [], []
+    for i, b in enumerate(boxes):
+        X, d, _ = oracle_all(b)
+        sl = slice(offs[i], offs[i + 1])
+        assert rel(g["h"][sl], d["h"]).max() <= 1e-5, i
+        assert rel(g["rho"][sl], d["rho"]).max() <= 1e-5, i
+        hs.append(d["h"]); rhos.append(d["rho"]); oms.append(d["omega"])
+    h, rho, om = (np.concatenate(a).astype(np.float32) for a in (hs, rhos, oms))
+    pall = W.Particles(pos, cat("vel"), cat("mass"), cat("u"), 1.0)
+    gf = gpu_force(S, ctx, grid, pall, h, rho, om, params)
+    for i, b in enumerate(boxes):
+        sl = slice(offs[i], offs[i + 1])
+        X = oracle.quantize(b.pos, b.box)
+        f = oracle.force(X, b.vel, b.mass, b.u, h[sl], rho[sl], om[sl], box=b.box)
+        gi = {k: gf[k][sl] for k in ("acc", "dudt", "vsig", "hash")}
+        check_force(gi, f, np.arange(b.n), 1e-4)
+
+
+# ---- edge cases ----------------------------------------------------------------
+
+def test_small_box_wide_groups(S, ctx):
+    p = as_f32(W.clustered(600, 2, seed=77))          # h near L/4: groups wider than L/4
+    X, d, f = oracle_all(p, n_target=32.0)
+    params = S.default_params(n_target=32.0, n_tol=32e-6)
+    grid = gpu_grid(S, ctx, p, params)
+    g = gpu_density(S, ctx, grid, np.zeros(p.n, np.float32), params)
+    assert g["rc"] == 0
+    assert rel(g["h"], d["h"]).max() <= 1e-5
+    h, rho, om = _oracle_inputs32(d)
+    fo = oracle.force(X, p.vel, p.mass, p.u, h, rho, om)
+    gf = gpu_force(S, ctx, grid, p, h, rho, om, params)
+    check_force(gf, fo, np.arange(p.n), 1e-4)
+
+
+def test_error_statuses(S, ctx):
+    from paper_2003_10850_gb300 import abi
+    p = as_f32(W.lattice(3, 0.2, seed=5))               # 27 particles cannot reach 64 neighbours
+    params = S.default_params()
+    grid = gpu_grid(S, ctx, p, params)
+    g = gpu_density(S, ctx, grid, np.zeros(p.n, np.float32), params)
+    assert g["rc"] == abi.SPH_ERR_H_TOO_LARGE and np.all(g["flags"] & abi.SPH_ST_H_TOO_LARGE)
+    q = as_f32(W.config1(16))
+    grid = gpu_grid(S, ctx, q, S.default_params(max_iter=0))
+    g = gpu_density(S, ctx, grid, np.full(q.n, 0.01, np.float32), S.default_params(max_iter=0))
+    assert g["rc"] == abi.SPH_ERR_NOT_CONVERGED and np.all(g["flags"] & abi.SPH_ST_NOT_CONVERGED)
+    bad = q.pos.copy()
+    bad[5, 1] = np.nan
+    grid = S.sph_build_grid(ctx, dev(bad), dev(q.mass), params)
+    rc, _ = S.sph_sync_status(ctx, raise_on_error=False)
+    assert rc == abi.SPH_ERR_INVALID
+    with pytest.raises(S.SPHError):
+        S.sph_build_grid(ctx, dev(q.pos), dev(q.mass), S.default_params(box=-1.0))
+    with pytest.raises(TypeError):
+        S.sph_build_grid(ctx, dev(q.pos).double().cpu(), dev(q.mass), params)
+
+
+def test_single_particle_and_tiny(S, ctx):
+    from paper_2003_10850_gb300 import abi
+    p = as_f32(W.lattice(1, 0.0, seed=0))
+    params = S.default_params(n_target=8.0)
+    grid = gpu_grid(S, ctx, p, params)
+    g = gpu_density(S, ctx, grid, np.zeros(1, np.float32), params)
+    assert g["rc"] == abi.SPH_ERR_H_TOO_LARGE
+    assert g["n_ngb"][0] == 0
