@@ -24,7 +24,10 @@ bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
 sph_status check_params(sph_ctx* ctx, const sph_params* p) {
     if (!p) return fail(ctx, SPH_ERR_INVALID, "params is NULL");
     if (!finite_pos(p->box)) return fail(ctx, SPH_ERR_INVALID, "params.box must be finite and > 0");
-    if (!finite_pos(p->n_target)) return fail(ctx, SPH_ERR_INVALID, "params.n_target must be > 0");
+    // N_eff(h) >= 32/3 (the particle's own w(0) term) for every h, so a
+    // target at or below it has no root
+    if (!finite_pos(p->n_target) || p->n_target <= 32.0 / 3.0)
+        return fail(ctx, SPH_ERR_INVALID, "params.n_target must exceed 32/3 (the self term of N_eff)");
     if (!finite_pos(p->n_tol)) return fail(ctx, SPH_ERR_INVALID, "params.n_tol must be > 0");
     if (p->max_iter < 0 || p->max_iter > 10000) return fail(ctx, SPH_ERR_INVALID, "params.max_iter out of range");
     if (!std::isfinite(p->alpha_visc) || p->alpha_visc < 0) return fail(ctx, SPH_ERR_INVALID, "params.alpha_visc must be >= 0");

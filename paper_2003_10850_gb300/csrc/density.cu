@@ -84,18 +84,24 @@ __device__ __forceinline__ float sqrt_t<float>(float x) { return x > 0.f ? x * r
 template <>
 __device__ __forceinline__ double sqrt_t<double>(double x) { return sqrt(x); }
 
-// Local starting guess for h: the number density of the particle's
-// leaf-parent node (64 consecutive sorted particles) inside its bounding box.
+// Local starting guess for h: the number density inside the bounding boxes
+// of the particle's leaf (8 sorted particles) and of the leaf's parent (64);
+// the smaller of the two estimates, since growing h from below is cheap while
+// a first evaluation far above the root touches many candidates.
 __device__ float guess_h(const BoxDesc& B, const uint4* node_lo, const uint4* node_hi, long long p,
                          double s, double n_target) {
-    int lev = B.nlev > 1 ? 1 : 0;
-    long long span = lev ? (long long)kLeaf * kFan : kLeaf;
-    long long t = (p - B.off) / span;
-    uint4 lo = node_lo[B.lvl_off[lev] + t], hi = node_hi[B.lvl_off[lev] + t];
-    double cnt = (double)min(span, B.n - t * span);
-    double V = ((double)(hi.x - lo.x) + 1.0) * ((double)(hi.y - lo.y) + 1.0) * ((double)(hi.z - lo.z) + 1.0) * s * s * s;
-    double hg = cbrt(3.0 * n_target * V / (4.0 * 3.141592653589793 * cnt));
-    return (float)fmin(hg, 0.25 * B.L);
+    double best = 0.25 * B.L;
+    const int top = B.nlev > 1 ? 1 : 0;
+    for (int lev = 0; lev <= top; ++lev) {
+        long long span = lev ? (long long)kLeaf * kFan : kLeaf;
+        long long t = (p - B.off) / span;
+        uint4 lo = node_lo[B.lvl_off[lev] + t], hi = node_hi[B.lvl_off[lev] + t];
+        double cnt = (double)min(span, B.n - t * span);
+        double V = ((double)(hi.x - lo.x) + 1.0) * ((double)(hi.y - lo.y) + 1.0) *
+                   ((double)(hi.z - lo.z) + 1.0) * s * s * s;
+        best = fmin(best, cbrt(3.0 * n_target * V / (4.0 * 3.141592653589793 * cnt)));
+    }
+    return (float)best;
 }
 
 template <typename T, bool HASH>
@@ -279,26 +285,31 @@ __global__ void __launch_bounds__(kDensWarps * 32) k_density(DensArgs a) {
                     st |= ST_NOT_CONVERGED;
                 } else {
                     if (f < 0) blo = h; else bhi = h;
-                    double hn = 0.0;
+                    // Newton on N^(1/3) - N_t^(1/3) (nearly linear in h, both for
+                    // uniform neighbourhoods, N ~ h^3, and at density fronts,
+                    // N ~ (h - r0)^3), kept inside the bracket; grow while
+                    // unbracketed; bisect when Newton leaves the bracket.
+                    double hn = dN > 0.0 ? (double)h - 3.0 * N * (1.0 - cbrt(a.n_target / N)) / dN : NAN;
                     if (isinf(bhi)) {
                         if ((double)h >= cap) {
                             st |= ST_H_TOO_LARGE;
                             conv = true;
                         } else {
-                            hn = 2.0 * (double)h;
-                            if (dN > 0.0) {
-                                double hnewt = (double)h - f / dN;
-                                if (hnewt > (double)h && hnewt < hn) hn = hnewt;
-                            }
-                            if (hn >= cap) hn = cap;
+                            if (!(hn > (double)h)) hn = 2.0 * (double)h;
+                            hn = fmin(hn, fmin(cap, 8.0 * (double)h));
                         }
-                    } else {
-                        hn = dN > 0.0 ? (double)h - f / dN : NAN;
-                        if (!(hn > blo && hn < bhi)) hn = 0.5 * (blo + bhi);
+                    } else if (!(hn > blo && hn < bhi)) {
+                        hn = 0.5 * (blo + bhi);
                     }
                     if (!conv) {
                         float hf = (float)hn;
-                        if (hf == h) conv = true;  // best representable h
+                        // rounding to float may land on a bracket end: if the
+                        // bracket is one float apart, h is the best float there is
+                        if (!(hf > (float)blo) || (!isinf(bhi) && !(hf < (float)bhi))) {
+                            const float mid = (float)(0.5 * (blo + bhi));
+                            hf = (mid > (float)blo && mid < (float)bhi) ? mid : h;
+                        }
+                        if (hf == h) conv = true;
                         else h = hf;
                     }
                 }
@@ -448,21 +459,15 @@ __global__ void k_density_plain(PlainDensArgs a) {
     float hn = h;
     if (!done) {
         if (f < 0.f) lo = h; else hi = h;
+        hn = dN > 0.f ? h - 3.f * N * (1.f - cbrtf(a.n_target / N)) / dN : NAN;
         if (isinf(hi)) {
-            hn = 2.f * h;
-            if (dN > 0.f) {
-                float t2 = h - f / dN;
-                if (t2 > h && t2 < hn) hn = t2;
-            }
-            if (hn >= 0.5f * L) {
-                if (h >= 0.499f * L) { st |= ST_H_TOO_LARGE; done = true; }
-                hn = 0.499f * L;
-            }
-        } else {
-            hn = dN > 0.f ? h - f / dN : NAN;
-            if (!(hn > lo && hn < hi)) hn = 0.5f * (lo + hi);
+            if (h >= 0.499f * L) { st |= ST_H_TOO_LARGE; done = true; }
+            if (!(hn > h)) hn = 2.f * h;
+            hn = fminf(hn, fminf(0.499f * L, 8.f * h));
+        } else if (!(hn > lo && hn < hi)) {
+            hn = 0.5f * (lo + hi);
         }
-        if (hn == h) done = true;
+        if (!(hn > lo) || (!isinf(hi) && !(hn < hi)) || hn == h) done = true;  // bracket is one float wide
     }
     if (done) {
         a.h[oi] = h;

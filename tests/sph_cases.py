@@ -74,7 +74,7 @@ def gpu_force(S, ctx, grid, p: W.Particles, h, rho, omega, params, active=None):
     return res
 
 
-def check_force(g, f, idx, tol):
+def check_force(g, f, idx, tol, check_hash=True):
     """|delta a| <= tol * S_a and |delta du| <= tol * S_u per particle (S = sum of
     the magnitudes of the pair terms), v_sig relative, pair sets exact."""
     da = np.linalg.norm(g["acc"][idx] - f["acc"][idx], axis=1)
@@ -83,4 +83,5 @@ def check_force(g, f, idx, tol):
     assert np.all(ddu <= tol * f["scale_u"][idx] + 1e-30), (ddu / f["scale_u"][idx]).max()
     dv = np.abs(g["vsig"][idx] - f["vsig"][idx])
     assert np.all(dv <= max(tol / 10, 2e-6) * (np.abs(f["vsig"][idx]) + np.median(f["vsig"][idx])))
-    assert np.array_equal(g["hash"][idx], f["hash"][idx])
+    if check_hash:
+        assert np.array_equal(g["hash"][idx], f["hash"][idx])
