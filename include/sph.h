@@ -199,6 +199,31 @@ sph_status sph_hydro_force(sph_ctx *ctx, const sph_grid *grid, const float *vel,
                            float *vsig, uint64_t *hash, const sph_params *params, void *stream);
 
 /*
+ * Stable sort of 64-bit keys that allocates nothing (the paper has no
+ * counterpart: this serves callers that cannot call cudaMalloc -- code that
+ * runs inside another framework's memory pool or budget, time-critical loops
+ * where cudaMalloc's implicit synchronisation is not acceptable, or callers
+ * without a sph_ctx, whose creation allocates).
+ *   keys         device, n uint64 (read only);
+ *   sorted_keys  device, n uint64: the keys in ascending order;
+ *   perm         device, n int32: perm[k] = index of the k-th smallest key,
+ *                equal keys in index order (stable) -- the same order
+ *                sph_build_grid sorts its Morton keys in;
+ *   1 <= n <= SPH_SORT_STATIC_MAX_KEYS, else SPH_ERR_INVALID (also for NULL
+ *   pointers); SPH_ERR_CUDA if a CUDA call fails.
+ * Runs asynchronously on `stream` on the current device. Its scratch is a
+ * fixed device array of about 12.6 MB inside the library, which every GPU
+ * that loads the library holds until the process exits. The first call on a
+ * device looks up that array's address (set-up); make that first call before
+ * any stream capture. All calls on a device share the array: calls whose
+ * kernels overlap on the GPU (different streams, or different host threads)
+ * race and corrupt each other's results -- serialise them.
+ */
+#define SPH_SORT_STATIC_MAX_KEYS (1 << 20)
+sph_status sph_sort_keys_static(const uint64_t *keys, int64_t n, uint64_t *sorted_keys,
+                                int32_t *perm, void *stream);
+
+/*
  * Waits for `stream`, then returns the device status word and counters
  * accumulated since the previous call in *stats (may be NULL) and clears
  * them. Returns the sph_status of the worst device condition seen.

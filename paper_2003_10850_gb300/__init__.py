@@ -16,7 +16,7 @@ from .abi import (SPH_FIXED_H, SPH_FP64, SPH_H_GUESS, SPH_PLAIN_FP32, SPH_TIME_K
                   default_params, sph_params, sph_stats)
 
 __all__ = ["Context", "Grid", "sph_create", "sph_build_grid", "sph_build_grid_batched", "sph_grid_update",
-           "sph_density", "sph_hydro_force", "sph_sync_status", "sph_grid_export", "density",
+           "sph_density", "sph_hydro_force", "sph_sync_status", "sph_grid_export", "sph_sort_keys_static", "density",
            "hydro_force", "default_params", "sph_params", "sph_stats", "SPHError", "SPH_FP64",
            "SPH_PLAIN_FP32", "SPH_FIXED_H", "SPH_H_GUESS", "SPH_TIME_KERNELS"]
 
@@ -149,6 +149,18 @@ def sph_sync_status(ctx: Context, raise_on_error: bool = True):
     if rc != 0 and raise_on_error:
         raise SPHError(rc, ctx.lib.sph_last_error(ctx.handle).decode())
     return rc, st.as_dict()
+
+
+def sph_sort_keys_static(keys, sorted_keys, perm):
+    """Stable sort of int64-viewed uint64 keys without any allocation (see
+    include/sph.h): fills sorted_keys and perm. Needs no Context."""
+    lib = abi.load()
+    rc = lib.sph_sort_keys_static(_ptr(keys, torch.int64, "keys"), keys.numel(),
+                                  _ptr(sorted_keys, torch.int64, "sorted_keys"), _ptr(perm, torch.int32, "perm"),
+                                  _stream())
+    if rc != 0:
+        raise SPHError(rc, "sph_sort_keys_static: n must be in [1, SPH_SORT_STATIC_MAX_KEYS] "
+                           "and pointers non-NULL" if rc == abi.SPH_ERR_INVALID else "CUDA call failed")
 
 
 # ---- conveniences that allocate the outputs ----------------------------------
