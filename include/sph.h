@@ -52,6 +52,9 @@ typedef enum {
                                 estimate made from the grid's leaf-parent boxes */
 #define SPH_TIME_KERNELS 0x10 /* record CUDA events around the main density/force kernel on
                                  the launching stream; sph_sync_status sums their durations */
+#define SPH_WARP_GROUP 0x20   /* alternative fast path: one warp per group of <= group_size
+                                 Morton-consecutive particles sharing one walk (default: one
+                                 thread per particle with its own walk) */
 
 /* Device status bits returned in sph_stats.status */
 #define SPH_ST_NOT_CONVERGED 0x01

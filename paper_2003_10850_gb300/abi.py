@@ -29,6 +29,7 @@ SPH_PLAIN_FP32 = 0x02
 SPH_FIXED_H = 0x04
 SPH_H_GUESS = 0x08
 SPH_TIME_KERNELS = 0x10
+SPH_WARP_GROUP = 0x20
 
 SPH_ST_NOT_CONVERGED = 0x01
 SPH_ST_H_TOO_LARGE = 0x02

@@ -37,6 +37,8 @@ sph_status check_params(sph_ctx* ctx, const sph_params* p) {
     if (p->blocks_per_sm < 0 || p->blocks_per_sm > 32) return fail(ctx, SPH_ERR_INVALID, "params.blocks_per_sm out of range");
     if ((p->flags & SPH_FP64) && (p->flags & SPH_PLAIN_FP32))
         return fail(ctx, SPH_ERR_INVALID, "SPH_FP64 and SPH_PLAIN_FP32 are exclusive");
+    if ((p->flags & SPH_WARP_GROUP) && (p->flags & SPH_PLAIN_FP32))
+        return fail(ctx, SPH_ERR_INVALID, "SPH_WARP_GROUP and SPH_PLAIN_FP32 are exclusive");
     return SPH_OK;
 }
 
@@ -191,7 +193,8 @@ sph_status sph_density(sph_ctx* ctx, const sph_grid* grid, float* h, const int32
     if (cudaSetDevice(ctx->device)) return fail(ctx, SPH_ERR_CUDA, "cudaSetDevice failed");
     cudaStream_t s = (cudaStream_t)stream;
     sph_grid* g = const_cast<sph_grid*>(grid);  // per-call scratch lives in the grid
-    grid_active(g, active, n_active, group_size(params), s);
+    const bool warp_group = (params->flags & SPH_WARP_GROUP) != 0;
+    grid_active(g, active, n_active, group_size(params), warp_group, s);
     DensityLaunch a;
     a.g = g;
     a.h = h;
@@ -208,7 +211,9 @@ sph_status sph_density(sph_ctx* ctx, const sph_grid* grid, float* h, const int32
     a.fp64 = (params->flags & SPH_FP64) ? 1 : 0;
     a.blocks_per_sm = params->blocks_per_sm;
     a.time_kernels = (params->flags & SPH_TIME_KERNELS) ? 1 : 0;
-    cudaError_t e = (params->flags & SPH_PLAIN_FP32) ? run_density_plain(ctx, a, na, s) : launch_density(ctx, a, s);
+    cudaError_t e = (params->flags & SPH_PLAIN_FP32) ? run_density_plain(ctx, a, na, s)
+                    : warp_group                       ? launch_density(ctx, a, s)
+                                                       : launch_density_tpp(ctx, a, na, s);
     if (!e) e = cudaGetLastError();
     if (e) return cuda_fail(ctx, e, "sph_density");
     return SPH_OK;
@@ -230,8 +235,9 @@ sph_status sph_hydro_force(sph_ctx* ctx, const sph_grid* grid, const float* vel,
     if (cudaSetDevice(ctx->device)) return fail(ctx, SPH_ERR_CUDA, "cudaSetDevice failed");
     cudaStream_t s = (cudaStream_t)stream;
     sph_grid* g = const_cast<sph_grid*>(grid);
+    const bool warp_group = (params->flags & SPH_WARP_GROUP) != 0;
     grid_refresh_hmax(g, h, s);
-    grid_active(g, active, n_active, group_size(params), s);
+    grid_active(g, active, n_active, group_size(params), warp_group, s);
     ForceLaunch a;
     a.g = g;
     a.vel = vel;
@@ -248,7 +254,9 @@ sph_status sph_hydro_force(sph_ctx* ctx, const sph_grid* grid, const float* vel,
     a.fp64 = (params->flags & SPH_FP64) ? 1 : 0;
     a.blocks_per_sm = params->blocks_per_sm;
     a.time_kernels = (params->flags & SPH_TIME_KERNELS) ? 1 : 0;
-    cudaError_t e = (params->flags & SPH_PLAIN_FP32) ? launch_force_plain(ctx, a, na, s) : launch_force(ctx, a, s);
+    cudaError_t e = (params->flags & SPH_PLAIN_FP32) ? launch_force_plain(ctx, a, na, s)
+                    : warp_group                       ? launch_force(ctx, a, s)
+                                                       : launch_force_tpp(ctx, a, na, s);
     if (!e) e = cudaGetLastError();
     if (e) return cuda_fail(ctx, e, "sph_hydro_force");
     return SPH_OK;

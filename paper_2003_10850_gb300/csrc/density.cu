@@ -568,7 +568,7 @@ cudaError_t run_density_plain(sph_ctx* ctx, const DensityLaunch& a, int64_t n_ac
     // the first pass reads the active count from the device (the compacted
     // active list drops duplicates); later passes read it back to decide
     int count = (int)n_active;
-    const int* count0 = n_active < g->n ? reinterpret_cast<const int*>(g->scan + g->n) : nullptr;
+    const int* count0 = reinterpret_cast<const int*>(g->scan + g->n);
     const int32_t* list = g->act;
     int32_t* bufs[2] = {g->list_a, g->list_b};
     int which = 0;

@@ -491,7 +491,7 @@ cudaError_t launch_force_plain(sph_ctx* ctx, const ForceLaunch& a, int64_t n_act
     pa.n_boxes = g->n_boxes;
     pa.act = g->act;
     pa.count = (int)n_active;
-    pa.count_ptr = n_active < g->n ? reinterpret_cast<const int*>(g->scan + g->n) : nullptr;
+    pa.count_ptr = reinterpret_cast<const int*>(g->scan + g->n);
     pa.posm = g->posm;
     pa.perm = g->perm;
     pa.node_lo = g->node_lo;

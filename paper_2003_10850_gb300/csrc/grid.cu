@@ -267,8 +267,17 @@ __global__ void k_gather(const uint4* __restrict__ xq, const unsigned* __restric
     rank[i] = k;
 }
 
+// Node centre (integer) and half extents (box units, padded by two integer
+// units) -- the form the thread-per-particle walk tests against.
+__device__ __forceinline__ void node_geom(uint4 a, uint4 b, double s, uint4& c, float4& e) {
+    c = make_uint4(a.x + ((b.x - a.x) >> 1), a.y + ((b.y - a.y) >> 1), a.z + ((b.z - a.z) >> 1), 0u);
+    e = make_float4((float)((double)(((b.x - a.x) >> 1) + 2u) * s), (float)((double)(((b.y - a.y) >> 1) + 2u) * s),
+                    (float)((double)(((b.z - a.z) >> 1) + 2u) * s), 0.f);
+}
+
 __global__ void k_leaf_bbox(const uint4* __restrict__ posm, const BoxDesc* __restrict__ boxes,
-                            uint4* __restrict__ lo, uint4* __restrict__ hi) {
+                            uint4* __restrict__ lo, uint4* __restrict__ hi, uint4* __restrict__ nc,
+                            float4* __restrict__ ne, float4* __restrict__ posf) {
     const BoxDesc& B = boxes[blockIdx.y];
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= B.lvl_n[0]) return;
@@ -279,12 +288,26 @@ __global__ void k_leaf_bbox(const uint4* __restrict__ posm, const BoxDesc* __res
         a.x = min(a.x, x.x); a.y = min(a.y, x.y); a.z = min(a.z, x.z);
         b.x = max(b.x, x.x); b.y = max(b.y, x.y); b.z = max(b.z, x.z);
     }
-    lo[B.lvl_off[0] + t] = a;
-    hi[B.lvl_off[0] + t] = b;
+    const int nd = B.lvl_off[0] + t;
+    lo[nd] = a;
+    hi[nd] = b;
+    const double s = ldexp(B.L, -32);
+    uint4 c;
+    float4 e;
+    node_geom(a, b, s, c, e);
+    nc[nd] = c;
+    ne[nd] = e;
+    // leaf-relative FP32 coordinates (box units) and mass of the leaf's particles
+    const float sf = (float)s;
+    for (long long p = p0; p < p1; ++p) {
+        uint4 x = posm[p];
+        posf[p] = make_float4((float)(int)(x.x - c.x) * sf, (float)(int)(x.y - c.y) * sf,
+                              (float)(int)(x.z - c.z) * sf, __uint_as_float(x.w));
+    }
 }
 
 __global__ void k_node_bbox(int lev, const BoxDesc* __restrict__ boxes, uint4* __restrict__ lo,
-                            uint4* __restrict__ hi) {
+                            uint4* __restrict__ hi, uint4* __restrict__ nc, float4* __restrict__ ne) {
     const BoxDesc& B = boxes[blockIdx.y];
     if (lev >= B.nlev) return;
     int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -296,12 +319,18 @@ __global__ void k_node_bbox(int lev, const BoxDesc* __restrict__ boxes, uint4* _
         a.x = min(a.x, x.x); a.y = min(a.y, x.y); a.z = min(a.z, x.z);
         b.x = max(b.x, y.x); b.y = max(b.y, y.y); b.z = max(b.z, y.z);
     }
-    lo[B.lvl_off[lev] + t] = a;
-    hi[B.lvl_off[lev] + t] = b;
+    const int nd = B.lvl_off[lev] + t;
+    lo[nd] = a;
+    hi[nd] = b;
+    uint4 c;
+    float4 e;
+    node_geom(a, b, ldexp(B.L, -32), c, e);
+    nc[nd] = c;
+    ne[nd] = e;
 }
 
 __global__ void k_leaf_hmax(const int32_t* __restrict__ perm, const float* __restrict__ h,
-                            const BoxDesc* __restrict__ boxes, float* __restrict__ hmax) {
+                            const BoxDesc* __restrict__ boxes, float* __restrict__ hmax, float4* __restrict__ ne) {
     const BoxDesc& B = boxes[blockIdx.y];
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= B.lvl_n[0]) return;
@@ -309,9 +338,11 @@ __global__ void k_leaf_hmax(const int32_t* __restrict__ perm, const float* __res
     float m = 0.f;
     for (long long p = p0; p < p1; ++p) m = fmaxf(m, h[perm[p]]);
     hmax[B.lvl_off[0] + t] = m;
+    ne[B.lvl_off[0] + t].w = m;
 }
 
-__global__ void k_node_hmax(int lev, const BoxDesc* __restrict__ boxes, float* __restrict__ hmax) {
+__global__ void k_node_hmax(int lev, const BoxDesc* __restrict__ boxes, float* __restrict__ hmax,
+                            float4* __restrict__ ne) {
     const BoxDesc& B = boxes[blockIdx.y];
     if (lev >= B.nlev) return;
     int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -320,6 +351,7 @@ __global__ void k_node_hmax(int lev, const BoxDesc* __restrict__ boxes, float* _
     float m = 0.f;
     for (int c = c0; c < c1; ++c) m = fmaxf(m, hmax[B.lvl_off[lev - 1] + c]);
     hmax[B.lvl_off[lev] + t] = m;
+    ne[B.lvl_off[lev] + t].w = m;
 }
 
 // ---------------------------------------------------------------------------
@@ -329,6 +361,14 @@ __global__ void k_node_hmax(int lev, const BoxDesc* __restrict__ boxes, float* _
 __global__ void k_iota(int32_t* a, int n) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k < n) a[k] = k;
+}
+
+// all particles active: the identity list, and its length where the subset
+// path leaves the compacted count (scan[n])
+__global__ void k_iota_count(int32_t* a, int n, uint32_t* count) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) a[k] = k;
+    if (k == 0) *count = (uint32_t)n;
 }
 
 __global__ void k_mark(const int32_t* __restrict__ active, int na, const int32_t* __restrict__ rank,
@@ -397,7 +437,8 @@ void grid_free(sph_grid* g) {
     void* ptrs[] = {g->boxes, g->posm, g->xq, g->perm, g->rank, g->keys, g->node_lo, g->node_hi,
                     g->node_hmax, g->act, g->flag, g->scan, g->scan_tmp, g->box_act, g->n_groups,
                     g->groups, g->list_a, g->list_b, g->st_lo, g->st_hi, g->list_n, g->d_off, g->d_L,
-                    g->k2, g->v1, g->v2, g->counts, g->cscan};
+                    g->k2, g->v1, g->v2, g->counts, g->cscan, g->node_c, g->node_e, g->posf,
+                    g->fvel, g->fthermo};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete g;
@@ -418,11 +459,11 @@ static void grid_fill(sph_grid* g, const void* pos, int f64, const float* mass, 
                &ctx->launches);
     k_gather<<<blocks, 256, 0, s>>>(g->xq, g->v1, n, g->posm, g->perm, g->rank);
     dim3 lg((g->max_leaves + 127) / 128, nb);
-    k_leaf_bbox<<<lg, 128, 0, s>>>(g->posm, g->boxes, g->node_lo, g->node_hi);
+    k_leaf_bbox<<<lg, 128, 0, s>>>(g->posm, g->boxes, g->node_lo, g->node_hi, g->node_c, g->node_e, g->posf);
     ctx->launches += 2;
     for (int lev = 1; lev < g->max_lev; ++lev) {
         dim3 ng((g->lvl_max[lev] + 127) / 128, nb);
-        k_node_bbox<<<ng, 128, 0, s>>>(lev, g->boxes, g->node_lo, g->node_hi);
+        k_node_bbox<<<ng, 128, 0, s>>>(lev, g->boxes, g->node_lo, g->node_hi, g->node_c, g->node_e);
         ++ctx->launches;
     }
 }
@@ -488,6 +529,12 @@ sph_status grid_build(sph_ctx* ctx, const void* pos, int f64, const float* mass,
     GRID_CHECK(cudaMalloc(&g->node_lo, sizeof(uint4) * node));
     GRID_CHECK(cudaMalloc(&g->node_hi, sizeof(uint4) * node));
     GRID_CHECK(cudaMalloc(&g->node_hmax, sizeof(float) * node));
+    GRID_CHECK(cudaMalloc(&g->node_c, sizeof(uint4) * node));
+    GRID_CHECK(cudaMalloc(&g->node_e, sizeof(float4) * node));
+    GRID_CHECK(cudaMemset(g->node_e, 0, sizeof(float4) * node));
+    GRID_CHECK(cudaMalloc(&g->posf, sizeof(float4) * n));
+    GRID_CHECK(cudaMalloc(&g->fvel, sizeof(float4) * n));
+    GRID_CHECK(cudaMalloc(&g->fthermo, sizeof(float4) * n));
     GRID_CHECK(cudaMalloc(&g->act, sizeof(int32_t) * n));
     GRID_CHECK(cudaMalloc(&g->flag, n));
     GRID_CHECK(cudaMalloc(&g->scan, sizeof(uint32_t) * (n + 1)));
@@ -525,21 +572,21 @@ sph_status grid_update(sph_grid* g, const void* pos, int f64, const float* mass,
 void grid_refresh_hmax(sph_grid* g, const float* h, cudaStream_t s) {
     int nb = g->n_boxes;
     dim3 lg((g->max_leaves + 127) / 128, nb);
-    k_leaf_hmax<<<lg, 128, 0, s>>>(g->perm, h, g->boxes, g->node_hmax);
+    k_leaf_hmax<<<lg, 128, 0, s>>>(g->perm, h, g->boxes, g->node_hmax, g->node_e);
     ++g->ctx->launches;
     for (int lev = 1; lev < g->max_lev; ++lev) {
         dim3 ng((g->lvl_max[lev] + 127) / 128, nb);
-        k_node_hmax<<<ng, 128, 0, s>>>(lev, g->boxes, g->node_hmax);
+        k_node_hmax<<<ng, 128, 0, s>>>(lev, g->boxes, g->node_hmax, g->node_e);
         ++g->ctx->launches;
     }
 }
 
-void grid_active(sph_grid* g, const int32_t* active, int64_t n_active, int gs, cudaStream_t s) {
+void grid_active(sph_grid* g, const int32_t* active, int64_t n_active, int gs, bool groups, cudaStream_t s) {
     int n = (int)g->n, nb = g->n_boxes;
     const uint32_t* sc = nullptr;
     unsigned& nl = g->ctx->launches;
     if (!active) {
-        k_iota<<<(n + 255) / 256, 256, 0, s>>>(g->act, n);
+        k_iota_count<<<(n + 255) / 256, 256, 0, s>>>(g->act, n, g->scan + n);
         ++nl;
     } else {
         cudaMemsetAsync(g->flag, 0, n, s);
@@ -553,6 +600,7 @@ void grid_active(sph_grid* g, const int32_t* active, int64_t n_active, int gs, c
         ++nl;
         sc = g->scan;
     }
+    if (!groups) return;
     k_box_groups<<<1, 32, 0, s>>>(g->boxes, nb, sc, gs, g->box_act, g->n_groups);
     nl += 2;
     long long mx = 0;

@@ -43,6 +43,11 @@ struct sph_grid {
     uint4* node_lo = nullptr;
     uint4* node_hi = nullptr;
     float* node_hmax = nullptr;
+    uint4* node_c = nullptr;               // node centre (integer)
+    float4* node_e = nullptr;              // node half extents (box units), w = h_max
+    float4* posf = nullptr;                // sorted: leaf-relative position (box units), mass
+    float4* fvel = nullptr;                // per force call, sorted: v, h
+    float4* fthermo = nullptr;             // per force call, sorted: rho, A, c, 1/h
     // per-call scratch, sized at build so that calls never allocate
     int32_t* act = nullptr;                // active particles, sorted indices, sorted order
     uint8_t* flag = nullptr;               // n
@@ -81,8 +86,9 @@ void grid_free(sph_grid* g);
 sph_status grid_update(sph_grid* g, const void* pos, int f64, const float* mass, cudaStream_t s);
 // hmax of every node from the caller-order h
 void grid_refresh_hmax(sph_grid* g, const float* h, cudaStream_t s);
-// active list + groups of at most gs particles per box
-void grid_active(sph_grid* g, const int32_t* active, int64_t n_active, int gs, cudaStream_t s);
+// active list (sorted indices in g->act, count in g->scan[n]) and, if asked,
+// groups of at most gs particles per box
+void grid_active(sph_grid* g, const int32_t* active, int64_t n_active, int gs, bool groups, cudaStream_t s);
 // exclusive scan of n values into out[0..n] (out[n] = total); tmp >= n/4096+2 words
 template <typename In>
 void scan_exclusive(const In* in, int n, uint32_t* out, uint32_t* tmp, cudaStream_t s, unsigned* launches);
@@ -129,5 +135,9 @@ struct ForceLaunch {
 cudaError_t launch_force(sph_ctx* ctx, const ForceLaunch& a, cudaStream_t s);
 cudaError_t launch_force_plain(sph_ctx* ctx, const ForceLaunch& a, int64_t n_active,
                                cudaStream_t s);
+
+// tpp.cu (default path)
+cudaError_t launch_density_tpp(sph_ctx* ctx, const DensityLaunch& a, int64_t n_active, cudaStream_t s);
+cudaError_t launch_force_tpp(sph_ctx* ctx, const ForceLaunch& a, int64_t n_active, cudaStream_t s);
 
 }  // namespace sph

@@ -78,12 +78,20 @@ def test_batched_keys_and_sort_exact(S, ctx):
 
 # ---- a4: density ------------------------------------------------------------
 
+PATHS = ["thread", "warp"]
+
+
+def _flags(S, path, fp64):
+    return (S.SPH_FP64 if fp64 else 0) | (S.SPH_WARP_GROUP if path == "warp" else 0)
+
+
+@pytest.mark.parametrize("path", PATHS)
 @pytest.mark.parametrize("fp64", [False, True])
 @pytest.mark.parametrize("kind", ["lattice", "clustered"])
-def test_density_fixed_h_sets_exact(S, ctx, kind, fp64, lattice32, clustered50k):
+def test_density_fixed_h_sets_exact(S, ctx, kind, fp64, path, lattice32, clustered50k):
     p, (X, d, _) = lattice32 if kind == "lattice" else clustered50k
     h32 = d["h"].astype(np.float32)
-    params = S.default_params(box=p.box, flags=S.SPH_FIXED_H | (S.SPH_FP64 if fp64 else 0))
+    params = S.default_params(box=p.box, flags=S.SPH_FIXED_H | _flags(S, path, fp64))
     grid = gpu_grid(S, ctx, p, params)
     g = gpu_density(S, ctx, grid, h32, params)
     assert g["rc"] == 0
@@ -107,11 +115,12 @@ def _density_converged_checks(g, p, X, d, fp64):
     assert np.all((g["n_ngb"] >= lo) & (g["n_ngb"] <= hi))
 
 
+@pytest.mark.parametrize("path", PATHS)
 @pytest.mark.parametrize("fp64", [False, True])
 @pytest.mark.parametrize("kind", ["lattice", "clustered"])
-def test_density_converged(S, ctx, kind, fp64, lattice32, clustered50k):
+def test_density_converged(S, ctx, kind, fp64, path, lattice32, clustered50k):
     p, (X, d, _) = lattice32 if kind == "lattice" else clustered50k
-    params = S.default_params(box=p.box, flags=S.SPH_FP64 if fp64 else 0)
+    params = S.default_params(box=p.box, flags=_flags(S, path, fp64))
     grid = gpu_grid(S, ctx, p, params)
     g = gpu_density(S, ctx, grid, np.zeros(p.n, np.float32), params)   # h <= 0: local guess
     _density_converged_checks(g, p, X, d, fp64)
@@ -135,13 +144,14 @@ def _oracle_inputs32(d):
     return [d[k].astype(np.float32) for k in ("h", "rho", "omega")]
 
 
+@pytest.mark.parametrize("path", PATHS)
 @pytest.mark.parametrize("fp64", [False, True])
 @pytest.mark.parametrize("kind", ["lattice", "clustered"])
-def test_force_parity(S, ctx, kind, fp64, lattice32, clustered50k):
+def test_force_parity(S, ctx, kind, fp64, path, lattice32, clustered50k):
     p, (X, d, _) = lattice32 if kind == "lattice" else clustered50k
     h, rho, om = _oracle_inputs32(d)
     f = oracle.force(X, p.vel, p.mass, p.u, h, rho, om, box=p.box)
-    params = S.default_params(box=p.box, flags=S.SPH_FP64 if fp64 else 0)
+    params = S.default_params(box=p.box, flags=_flags(S, path, fp64))
     grid = gpu_grid(S, ctx, p, params)
     g = gpu_force(S, ctx, grid, p, h, rho, om, params)
     assert g["rc"] == 0
@@ -165,10 +175,11 @@ def test_force_plain_fp32(S, ctx, clustered50k):
 
 # ---- a6: active subsets and batched boxes ------------------------------------
 
-def test_active_subset(S, ctx, clustered50k):
+@pytest.mark.parametrize("path", PATHS)
+def test_active_subset(S, ctx, path, clustered50k):
     p, (X, d, _) = clustered50k
     act = W.sample_indices(p.n, p.n // 10, seed=17).astype(np.int32)
-    params = S.default_params(box=p.box)
+    params = S.default_params(box=p.box, flags=_flags(S, path, False))
     grid = gpu_grid(S, ctx, p, params)
     h0 = np.full(p.n, -7.0, np.float32)
     h0[act] = 0.0
@@ -189,7 +200,8 @@ def test_active_subset(S, ctx, clustered50k):
     assert np.array_equal(g2["n_ngb"][act], g["n_ngb"][act])
 
 
-def test_batched_boxes(S, ctx):
+@pytest.mark.parametrize("path", PATHS)
+def test_batched_boxes(S, ctx, path):
     sizes = (4096, 9000, 30000, 2000)
     Ls = (1.0, 2.0, 0.5, 1.0)
     boxes = []
@@ -199,7 +211,7 @@ def test_batched_boxes(S, ctx):
     pos = np.concatenate([b.pos for b in boxes])
     offs = np.cumsum([0] + [b.n for b in boxes])
     cat = lambda k: np.concatenate([getattr(b, k) for b in boxes])
-    params = S.default_params()
+    params = S.default_params(flags=_flags(S, path, False))
     grid = S.sph_build_grid_batched(ctx, dev(pos), dev(cat("mass")), offs, Ls, params)
     g = gpu_density(S, ctx, grid, np.zeros(offs[-1], np.float32), params)
     assert g["rc"] == 0
@@ -229,10 +241,11 @@ def test_batched_boxes(S, ctx):
 
 # ---- edge cases ----------------------------------------------------------------
 
-def test_small_box_wide_groups(S, ctx):
+@pytest.mark.parametrize("path", PATHS)
+def test_small_box_wide_groups(S, ctx, path):
     p = as_f32(W.clustered(600, 2, seed=77))          # h near L/4: groups wider than L/4
     X, d, f = oracle_all(p, n_target=32.0)
-    params = S.default_params(n_target=32.0, n_tol=32e-6)
+    params = S.default_params(n_target=32.0, n_tol=32e-6, flags=_flags(S, path, False))
     grid = gpu_grid(S, ctx, p, params)
     g = gpu_density(S, ctx, grid, np.zeros(p.n, np.float32), params)
     assert g["rc"] == 0
