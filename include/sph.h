@@ -55,6 +55,9 @@ typedef enum {
 #define SPH_WARP_GROUP 0x20   /* alternative fast path: one warp per group of <= group_size
                                  Morton-consecutive particles sharing one walk (default: one
                                  thread per particle with its own walk) */
+#define SPH_DENSITY_BUFFERED 0x40 /* density, thread path: iterate h on a per-thread buffer of
+                                     the candidates found by one walk at 1.06 h, instead of
+                                     walking the tree at every iteration (the default) */
 
 /* Device status bits returned in sph_stats.status */
 #define SPH_ST_NOT_CONVERGED 0x01

@@ -211,6 +211,7 @@ sph_status sph_density(sph_ctx* ctx, const sph_grid* grid, float* h, const int32
     a.fp64 = (params->flags & SPH_FP64) ? 1 : 0;
     a.blocks_per_sm = params->blocks_per_sm;
     a.time_kernels = (params->flags & SPH_TIME_KERNELS) ? 1 : 0;
+    a.buffered = (params->flags & SPH_DENSITY_BUFFERED) ? 1 : 0;
     cudaError_t e = (params->flags & SPH_PLAIN_FP32) ? run_density_plain(ctx, a, na, s)
                     : warp_group                       ? launch_density(ctx, a, s)
                                                        : launch_density_tpp(ctx, a, na, s);

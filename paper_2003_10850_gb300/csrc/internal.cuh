@@ -110,6 +110,7 @@ struct DensityLaunch {
     int fp64;
     int blocks_per_sm;
     int time_kernels;
+    int buffered;
 };
 cudaError_t launch_density(sph_ctx* ctx, const DensityLaunch& a, cudaStream_t s);
 cudaError_t run_density_plain(sph_ctx* ctx, const DensityLaunch& a, int64_t n_active,

@@ -64,6 +64,38 @@ __device__ __forceinline__ T tpp_sqrt(T x) {
     else return sqrt(x);
 }
 
+
+// One bracketed step of the smoothing-length solve. f = N - N_t arrives in
+// FP64 (from the compensated FP32 sums); the bracket and the new h are kept in
+// FP64, while the Newton step on N^(1/3) - N_t^(1/3) is formed in FP32 (it is
+// a correction, and FP64 cbrt/division would cost ~60 FP32 slots each on this
+// part). Returns false when h cannot move (converged to the float grid or an
+// error bit was set).
+__device__ __forceinline__ bool h_update(float& h, double f, float N, float dN, float n_target, double cap,
+                                         double& blo, double& bhi, unsigned& st) {
+    if (f < 0) blo = h; else bhi = h;
+    float step = dN > 0.f ? 3.f * N * (1.f - cbrtf(n_target / N)) / dN : NAN;
+    double hn = (double)h - (double)step;
+    if (isinf(bhi)) {
+        if ((double)h >= cap) {
+            st |= ST_H_TOO_LARGE;
+            return false;
+        }
+        if (!(hn > (double)h)) hn = 2.0 * (double)h;
+        hn = fmin(hn, fmin(cap, 8.0 * (double)h));
+    } else if (!(hn > blo && hn < bhi)) {
+        hn = 0.5 * (blo + bhi);
+    }
+    float hf = (float)hn;
+    if (!(hf > (float)blo) || (!isinf(bhi) && !(hf < (float)bhi))) {
+        const float mid = (float)(0.5 * (blo + bhi));
+        hf = (mid > (float)blo && mid < (float)bhi) ? mid : h;
+    }
+    if (hf == h) return false;  // the bracket is one float wide: h is the best float
+    h = hf;
+    return true;
+}
+
 // ---------------------------------------------------------------------------
 // Density
 // ---------------------------------------------------------------------------
@@ -102,7 +134,8 @@ struct TppDSums {
 
 template <typename T, bool HASH>
 __device__ __forceinline__ void tpp_density_walk(const TppDensArgs& a, const BoxDesc& B, int p, uint4 Xi,
-                                                 float h, double HH, TppDSums<T>& S) {
+                                                 float h, TppDSums<T>& S) {
+    double HH = -1.0;  // (h 2^32/L)^2, formed on the first band pair only
     const double s = ldexp(B.L, -32);
     const float sf = (float)s;
     const T sT = (T)s;
@@ -150,7 +183,13 @@ __device__ __forceinline__ void tpp_density_walk(const TppDensArgs& a, const Box
             const T r2 = dx * dx + dy * dy + dz * dz;
             if (r2 < hi2) {
                 bool in = r2 < lo2;
-                if (!in) in = exact_pred(exact_d2(Xi, a.posm[q]), HH);
+                if (!in) {
+                    if (HH < 0.0) {
+                        const double Hd = (double)h * 4294967296.0 / B.L;
+                        HH = Hd * Hd;
+                    }
+                    in = exact_pred(exact_d2(Xi, a.posm[q]), HH);
+                }
                 if (in) {
                     const T qq = tpp_sqrt<T>(r2) * hinv;
                     T w, dw;
@@ -213,33 +252,15 @@ __global__ void __launch_bounds__(kTppThreads) k_density_tpp(TppDensArgs a) {
             S.nn = 0;
             S.hs = 0;
             S.tests = 0;
-            const double Hd = (double)h * 4294967296.0 / L;
-            tpp_density_walk<T, HASH>(a, B, p, Xi, h, Hd * Hd, S);
+            tpp_density_walk<T, HASH>(a, B, p, Xi, h, S);
             ++c_evals;
             c_tests += S.tests;
-            const double sw = (double)S.sw - (double)S.cw;
-            const double sdw = (double)S.sdw - (double)S.cdw;
-            const double N = (32.0 / 3.0) * sw;
-            const double dN = -(32.0 / 3.0) * sdw / (double)h;
-            const double f = N - a.n_target;
+            const double f = (32.0 / 3.0) * ((double)S.sw - (double)S.cw) - a.n_target;
             if (a.fixed_h || fabs(f) <= a.n_tol) break;
             if (it >= a.max_iter) { st |= ST_NOT_CONVERGED; break; }
-            if (f < 0) blo = h; else bhi = h;
-            double hn = dN > 0.0 ? (double)h - 3.0 * N * (1.0 - cbrt(a.n_target / N)) / dN : NAN;
-            if (isinf(bhi)) {
-                if ((double)h >= cap) { st |= ST_H_TOO_LARGE; break; }
-                if (!(hn > (double)h)) hn = 2.0 * (double)h;
-                hn = fmin(hn, fmin(cap, 8.0 * (double)h));
-            } else if (!(hn > blo && hn < bhi)) {
-                hn = 0.5 * (blo + bhi);
-            }
-            float hf = (float)hn;
-            if (!(hf > (float)blo) || (!isinf(bhi) && !(hf < (float)bhi))) {
-                const float mid = (float)(0.5 * (blo + bhi));
-                hf = (mid > (float)blo && mid < (float)bhi) ? mid : h;
-            }
-            if (hf == h) break;  // the bracket is one float wide: h is the best float
-            h = hf;
+            const float N = (float)((32.0 / 3.0) * ((double)S.sw - (double)S.cw));
+            const float dN = -(32.f / 3.f) * (float)((double)S.sdw - (double)S.cdw) / h;
+            if (!h_update(h, f, N, dN, (float)a.n_target, cap, blo, bhi, st)) break;
         }
         const double smw = (double)S.smw - (double)S.cmw, smdw = (double)S.smdw - (double)S.cmdw;
         const double hd = (double)h;
@@ -250,6 +271,227 @@ __global__ void __launch_bounds__(kTppThreads) k_density_tpp(TppDensArgs a) {
         a.flags[oi] = (uint8_t)st;
         if (HASH) a.hash[oi] = S.hs;
         c_pairs += (unsigned long long)S.nn;
+        c_status |= st;
+    }
+    c_pairs = warp_sum(c_pairs);
+    c_evals = warp_sum(c_evals);
+    c_tests = warp_sum(c_tests);
+    c_status = __reduce_or_sync(0xffffffffu, c_status);
+    if (lane_id() == 0) {
+        atomicAdd(&a.ctr->density_pairs, c_pairs);
+        atomicAdd(&a.ctr->density_evals, c_evals);
+        atomicAdd(&a.ctr->pair_tests, c_tests);
+        if (c_status) atomicOr(&a.ctr->status, c_status);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Buffered density (FP32 default): one walk per particle, iterations on a
+// per-thread buffer of (r^2, m) for every candidate within the walk radius
+// R = 1.06 h. N_eff is number-weighted, so each Newton step only re-sums
+// w(sqrt(r^2)/h) over the buffer; the walk is repeated only when the root
+// leaves [0, R). Particles whose buffer overflows, or whose final sums have a
+// pair inside the FP32 predicate band, are finished by the exact per-walk
+// loop (tpp_density_walk) at the h reached.
+// ---------------------------------------------------------------------------
+
+constexpr int kDensBuf = 96;
+constexpr float kWalkMargin = 1.06f;
+
+// Depth-first walk in "while-while" form: descend until this thread holds a
+// leaf (or has nothing left), then process it. The leaf work, the costly
+// part, runs with the warp reconverged instead of interleaved with node tests.
+template <class LeafFn>
+__device__ __forceinline__ void tpp_walk_leaves(const BoxDesc& B, const uint4* __restrict__ node_c,
+                                                const float4* __restrict__ node_e, uint4 Xi, float sf, float R,
+                                                bool use_hmax, LeafFn&& leaf) {
+    int stack[kTppStack];
+    int sp = 0;
+    stack[sp++] = B.nlev == 1 ? 0 : (B.nlev - 1) << 27;
+    for (;;) {
+        int lt = -1;
+        while (sp > 0) {
+            const int enc = stack[--sp];
+            const int lev = enc >> 27, t = enc & ((1 << 27) - 1);
+            if (lev == 0) {
+                lt = t;
+                break;
+            }
+            const int cl = lev - 1;
+            const int c0 = t * kFan, c1 = min(c0 + kFan, B.lvl_n[cl]);
+            const int base = B.lvl_off[cl];
+            for (int c = c0; c < c1; ++c) {
+                const float4 e = node_e[base + c];
+                if (tpp_node_near(node_c[base + c], e, Xi, sf, use_hmax ? fmaxf(R, e.w) : R))
+                    stack[sp++] = (cl << 27) | c;
+            }
+        }
+        if (lt < 0) break;
+        leaf(lt);
+    }
+}
+
+template <bool HASH>
+__global__ void __launch_bounds__(kTppThreads) k_density_buf(TppDensArgs a) {
+    const int cnt_all = a.count_ptr ? *a.count_ptr : a.count;
+    unsigned long long c_pairs = 0, c_evals = 0, c_tests = 0;
+    unsigned c_status = 0;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < cnt_all; t += gridDim.x * blockDim.x) {
+        const int p = a.act[t];
+        const BoxDesc& B = a.boxes[a.n_boxes == 1 ? 0 : tpp_box_of(a.boxes, a.n_boxes, p)];
+        const double L = B.L, s = ldexp(L, -32);
+        const float sf = (float)s;
+        const uint4 Xi = a.posm[p];
+        const int oi = a.perm[p];
+        float h = a.h[oi];
+        if (a.guess_h || !(h > 0.f) || !isfinite(h)) h = tpp_guess_h(B, a.node_lo, a.node_hi, p, s, a.n_target);
+        const double cap = 0.5 * L * (1.0 - 1e-9);
+        double blo = 0.0, bhi = INFINITY;
+        unsigned st = 0;
+        bool exact_finish = false, finished = false;
+        float2 buf[kDensBuf];
+        int it = 0;
+        double smw = 0.0, smdw = 0.0;
+        int nn = 0;
+        while (!finished) {
+            // walk once with radius R, buffering every candidate inside it
+            const float R = fminf(h * kWalkMargin, (float)cap);
+            int nb = 0;
+            float emax = 0.f;  // largest FP32 error bound of r over the leaves that fed the buffer
+            unsigned long long tests = 0;
+            tpp_walk_leaves(B, a.node_c, a.node_e, Xi, sf, R, false, [&](int lt) {
+                const int nd = B.lvl_off[0] + lt;
+                const uint4 C = a.node_c[nd];
+                const float4 E = a.node_e[nd];
+                const long long q0 = B.off + (long long)lt * kLeaf, q1 = min(q0 + kLeaf, B.off + B.n);
+                const bool wide = 2.f * (E.x + E.y + E.z) + R >= 0.45f * (float)B.L;
+                const float ox = (float)(int)(C.x - Xi.x) * sf, oy = (float)(int)(C.y - Xi.y) * sf,
+                            oz = (float)(int)(C.z - Xi.z) * sf;
+                // bound on the FP32 error of r for pairs in this leaf (as in tpp_density_walk)
+                const float eL = 9.5367431640625e-07f *
+                                 (4.f * (E.x + E.y + E.z) + 2.f * (fabsf(ox) + fabsf(oy) + fabsf(oz)));
+                const float Rb = R * (1.f + 3.814697265625e-06f) + eL;
+                const float Rb2 = Rb * Rb;
+                bool fed = false;
+                for (long long q = q0; q < q1; ++q) {
+                    float dx, dy, dz, m;
+                    if (!wide) {
+                        const float4 f = a.posf[q];
+                        dx = ox + f.x; dy = oy + f.y; dz = oz + f.z; m = f.w;
+                    } else {
+                        const uint4 Xj = a.posm[q];
+                        dx = (float)(int)(Xj.x - Xi.x) * sf; dy = (float)(int)(Xj.y - Xi.y) * sf;
+                        dz = (float)(int)(Xj.z - Xi.z) * sf; m = __uint_as_float(Xj.w);
+                    }
+                    const float r2 = dx * dx + dy * dy + dz * dz;
+                    if (r2 < Rb2) {
+                        if (nb < kDensBuf) buf[nb] = make_float2(r2, m);
+                        ++nb;
+                        fed = true;
+                    }
+                }
+                if (fed) emax = fmaxf(emax, eL);
+                tests += (unsigned long long)(q1 - q0);
+            });
+            c_tests += tests;
+            if (nb > kDensBuf) {  // too many candidates to buffer
+                exact_finish = true;
+                break;
+            }
+            // Newton/bisection on the buffer until converged or the root leaves [0, R)
+            for (;;) {
+                const float hinv = 1.f / h, h2 = h * h;
+                float Sw = 0.f, Cw = 0.f, Sdw = 0.f, Cdw = 0.f;
+                for (int k0 = 0; k0 < nb; k0 += 8) {
+                    float pw = 0.f, pdw = 0.f;
+                    const int k1 = min(k0 + 8, nb);
+                    for (int k = k0; k < k1; ++k) {
+                        const float r2 = buf[k].x;
+                        if (r2 < h2) {
+                            const float qq = (r2 > 0.f ? r2 * rsqrtf(r2) : 0.f) * hinv;
+                            float w, dw;
+                            spline<float>(qq, w, dw);
+                            pw += w;
+                            pdw += qq * dw;
+                        }
+                    }
+                    kahan_add(Sw, Cw, pw);
+                    kahan_add(Sdw, Cdw, pdw);
+                }
+                ++c_evals;
+                const double f = (32.0 / 3.0) * ((double)Sw - (double)Cw) - a.n_target;
+                if (fabs(f) <= a.n_tol) { finished = true; break; }
+                if (it >= a.max_iter) { st |= ST_NOT_CONVERGED; finished = true; break; }
+                ++it;
+                const float N = (32.f / 3.f) * (Sw - Cw);
+                const float dN = -(32.f / 3.f) * (Sdw - Cdw) / h;
+                if (!h_update(h, f, N, dN, (float)a.n_target, cap, blo, bhi, st)) { finished = true; break; }
+                if (h >= R * (1.f - 1.52587890625e-05f)) break;  // outside the buffer: walk again
+            }
+            if (!finished) continue;
+            // final mass-weighted sums and neighbour count at h; a pair inside
+            // the FP32 band of the exact predicate sends the particle to the
+            // exact walk
+            const float hinv = 1.f / h;
+            const float eb = emax + 1.9073486328125e-06f * h;  // + 2^-19 h, as the exact walk's band
+            const float lo2 = h > eb ? (h - eb) * (h - eb) * (1.f - 3.814697265625e-06f) : 0.f;
+            const float hi2 = (h + eb) * (h + eb) * (1.f + 3.814697265625e-06f);
+            float Smw = 0.f, Cmw = 0.f, Smdw = 0.f, Cmdw = 0.f;
+            int n_in = 0;
+            bool band = false;
+            for (int k0 = 0; k0 < nb; k0 += 8) {
+                float pmw = 0.f, pmdw = 0.f;
+                const int k1 = min(k0 + 8, nb);
+                for (int k = k0; k < k1; ++k) {
+                    const float2 e = buf[k];
+                    if (e.x < hi2) {
+                        if (e.x >= lo2) band = true;
+                        const float qq = (e.x > 0.f ? e.x * rsqrtf(e.x) : 0.f) * hinv;
+                        float w, dw;
+                        spline<float>(qq, w, dw);
+                        pmw += e.y * w;
+                        pmdw += e.y * qq * dw;
+                        ++n_in;
+                    }
+                }
+                kahan_add(Smw, Cmw, pmw);
+                kahan_add(Smdw, Cmdw, pmdw);
+            }
+            if (band) { exact_finish = true; break; }
+            smw = (double)Smw - (double)Cmw;
+            smdw = (double)Smdw - (double)Cmdw;
+            nn = n_in - 1;  // the particle itself is in its own buffer (r^2 = 0)
+        }
+        if (exact_finish) {
+            // exact walk at the h reached, iterating further if needed
+            for (;;) {
+                TppDSums<float> S;
+                S.sw = S.cw = S.sdw = S.cdw = S.smw = S.cmw = S.smdw = S.cmdw = 0.f;
+                S.nn = 0;
+                S.hs = 0;
+                S.tests = 0;
+                tpp_density_walk<float, HASH>(a, B, p, Xi, h, S);
+                ++c_evals;
+                c_tests += S.tests;
+                smw = (double)S.smw - (double)S.cmw;
+                smdw = (double)S.smdw - (double)S.cmdw;
+                nn = S.nn;
+                const double f = (32.0 / 3.0) * ((double)S.sw - (double)S.cw) - a.n_target;
+                if (st || fabs(f) <= a.n_tol) break;
+                if (it >= a.max_iter) { st |= ST_NOT_CONVERGED; break; }
+                ++it;
+                const float N = (32.f / 3.f) * (S.sw - S.cw);
+                const float dN = -(32.f / 3.f) * (S.sdw - S.cdw) / h;
+                if (!h_update(h, f, N, dN, (float)a.n_target, cap, blo, bhi, st)) break;
+            }
+        }
+        const double hd = (double)h;
+        a.h[oi] = h;
+        a.rho[oi] = (float)(8.0 / (3.141592653589793 * hd * hd * hd) * smw);
+        a.omega[oi] = (float)(smdw != 0.0 ? -3.0 * smw / smdw : 1.0);
+        a.n_ngb[oi] = nn;
+        a.flags[oi] = (uint8_t)st;
+        c_pairs += (unsigned long long)nn;
         c_status |= st;
     }
     c_pairs = warp_sum(c_pairs);
@@ -458,6 +700,138 @@ __global__ void __launch_bounds__(kTppThreads) k_force_tpp(TppForceArgs a) {
     }
 }
 
+// FP32 force (default): while-while walk; per leaf a cheap membership pass
+// builds a bit mask of the pairs in the symmetric set, then the expensive
+// pair terms run over the set bits only, so lanes whose leaf has few pairs
+// are not dragged through eight evaluations.
+template <bool HASH>
+__global__ void __launch_bounds__(kTppThreads) k_force_mask(TppForceArgs a) {
+    const int cnt = a.count_ptr ? *a.count_ptr : a.count;
+    const float alpha = (float)a.alpha;
+    const float kNorm = (float)(8.0 / 3.141592653589793);
+    const float rel = 9.5367431640625e-07f;  // 2^-20
+    const float elo = 1.f - 4.f * rel, ehi = 1.f + 4.f * rel;
+    unsigned long long c_pairs = 0, c_tests = 0;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < cnt; t += gridDim.x * blockDim.x) {
+        const int p = a.act[t];
+        const BoxDesc& B = a.boxes[a.n_boxes == 1 ? 0 : tpp_box_of(a.boxes, a.n_boxes, p)];
+        const double L = B.L, s = ldexp(L, -32);
+        const float sf = (float)s;
+        const uint4 Xi = a.posm[p];
+        const int oi = a.perm[p];
+        const float4 vi = a.fvel[p];
+        const float4 thi = a.fthermo[p];
+        const float hi = vi.w, hinvi = thi.w, rhoi = thi.x, Ai = thi.y, ci = thi.z;
+        const float normi = kNorm * hinvi * hinvi * hinvi * hinvi;
+        float Sx = 0.f, Cx = 0.f, Sy = 0.f, Cy = 0.f, Sz = 0.f, Cz = 0.f, Su = 0.f, Cu = 0.f, vsmax = 0.f;
+        double HHi = -1.0;  // (h_i 2^32/L)^2, formed on the first band pair only
+        int np = 0;
+        unsigned long long hs = 0, tests = 0;
+        tpp_walk_leaves(B, a.node_c, a.node_e, Xi, sf, hi, true, [&](int lt) {
+            const int nd = B.lvl_off[0] + lt;
+            const uint4 C = a.node_c[nd];
+            const float4 E = a.node_e[nd];
+            const long long q0 = B.off + (long long)lt * kLeaf, q1 = min(q0 + kLeaf, B.off + B.n);
+            const bool wide = 2.f * (E.x + E.y + E.z) + fmaxf(hi, E.w) >= 0.45f * (float)B.L;
+            const float ox = (float)(int)(C.x - Xi.x) * sf, oy = (float)(int)(C.y - Xi.y) * sf,
+                        oz = (float)(int)(C.z - Xi.z) * sf;
+            const float eL = rel * (4.f * (E.x + E.y + E.z) + 2.f * (fabsf(ox) + fabsf(oy) + fabsf(oz)));
+            const float ei = eL + 2.f * rel * hi;
+            const float lo2i = hi > ei ? (hi - ei) * (hi - ei) * elo : 0.f;
+            const float hi2i = (hi + ei) * (hi + ei) * ehi;
+            auto sep = [&](long long q, float& dx, float& dy, float& dz, float& m) {
+                if (!wide) {
+                    const float4 f = a.posf[q];
+                    dx = ox + f.x; dy = oy + f.y; dz = oz + f.z; m = f.w;
+                } else {
+                    const uint4 Xj = a.posm[q];
+                    dx = (float)(int)(Xj.x - Xi.x) * sf; dy = (float)(int)(Xj.y - Xi.y) * sf;
+                    dz = (float)(int)(Xj.z - Xi.z) * sf; m = __uint_as_float(Xj.w);
+                }
+            };
+            // pass 1: membership r < max(h_i, h_j), exact inside the band
+            unsigned mask = 0u;
+            for (long long q = q0; q < q1; ++q) {
+                if (q == p) continue;
+                float dx, dy, dz, m;
+                sep(q, dx, dy, dz, m);
+                const float r2 = dx * dx + dy * dy + dz * dz;
+                const float hj = a.fvel[q].w;
+                const float ej = eL + 2.f * rel * hj;
+                const bool mi = r2 < hi2i, mj = r2 < (hj + ej) * (hj + ej) * ehi;
+                if (!(mi || mj)) continue;
+                bool in = r2 < lo2i || r2 < (hj > ej ? (hj - ej) * (hj - ej) * elo : 0.f);
+                if (!in) {
+                    const unsigned long long D2 = exact_d2(Xi, a.posm[q]);
+                    if (HHi < 0.0) {
+                        const double Hd = (double)hi * 4294967296.0 / L;
+                        HHi = Hd * Hd;
+                    }
+                    const double Hj = (double)hj * 4294967296.0 / L;
+                    in = (mi && exact_pred(D2, HHi)) || (mj && exact_pred(D2, Hj * Hj));
+                }
+                if (in) mask |= 1u << (unsigned)(q - q0);
+            }
+            tests += (unsigned long long)(q1 - q0);
+            // pass 2: pair terms over the members
+            float pax = 0.f, pay = 0.f, paz = 0.f, pdu = 0.f;
+            while (mask) {
+                const int k = __ffs(mask) - 1;
+                mask &= mask - 1u;
+                const long long q = q0 + k;
+                float dx, dy, dz, mj;
+                sep(q, dx, dy, dz, mj);
+                const float r2 = dx * dx + dy * dy + dz * dz;
+                const float4 vj = a.fvel[q];
+                const float4 thj = a.fthermo[q];
+                ++np;
+                if (HASH) hs += splitmix64((unsigned long long)a.perm[q]);
+                if (r2 <= 0.f) {  // coincident: no direction, no force
+                    vsmax = fmaxf(vsmax, ci + thj.z);
+                    continue;
+                }
+                const float rinv = rsqrtf(r2);
+                const float r = r2 * rinv;
+                float w_, dwi, dwj;
+                spline<float>(r * hinvi, w_, dwi);
+                spline<float>(r * thj.w, w_, dwj);
+                const float hinvj = thj.w;
+                const float Fi = normi * dwi * rinv;
+                const float Fj = kNorm * hinvj * hinvj * hinvj * hinvj * dwj * rinv;
+                const float vr = -((vi.x - vj.x) * dx + (vi.y - vj.y) * dy + (vi.z - vj.z) * dz);
+                const float wij = vr * rinv;
+                const float vs = ci + thj.z - 3.f * wij;
+                vsmax = fmaxf(vsmax, vs);
+                const float PI = wij < 0.f ? -alpha * vs * wij / (rhoi + thj.x) : 0.f;
+                const float Fbar = 0.5f * (Fi + Fj);
+                const float coef = mj * (Ai * Fi + thj.y * Fj + PI * Fbar);
+                pax += coef * dx;
+                pay += coef * dy;
+                paz += coef * dz;
+                pdu += mj * vr * (Ai * Fi + 0.5f * PI * Fbar);
+            }
+            kahan_add(Sx, Cx, pax);
+            kahan_add(Sy, Cy, pay);
+            kahan_add(Sz, Cz, paz);
+            kahan_add(Su, Cu, pdu);
+        });
+        a.acc[3 * (size_t)oi] = (float)((double)Sx - (double)Cx);
+        a.acc[3 * (size_t)oi + 1] = (float)((double)Sy - (double)Cy);
+        a.acc[3 * (size_t)oi + 2] = (float)((double)Sz - (double)Cz);
+        a.dudt[oi] = (float)((double)Su - (double)Cu);  // final accumulation in FP64
+        a.vsig[oi] = vsmax;
+        if (HASH) a.hash[oi] = hs;
+        c_pairs += (unsigned long long)np;
+        c_tests += tests;
+    }
+    c_pairs = warp_sum(c_pairs);
+    c_tests = warp_sum(c_tests);
+    if (lane_id() == 0) {
+        atomicAdd(&a.ctr->force_pairs, c_pairs);
+        atomicAdd(&a.ctr->pair_tests, c_tests);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
@@ -518,8 +892,10 @@ cudaError_t launch_density_tpp(sph_ctx* ctx, const DensityLaunch& a, int64_t n_a
     if (a.fp64)
         return a.hash ? timed_launch(ctx, k_density_tpp<double, true>, da, blocks, 0, a.time_kernels, s)
                       : timed_launch(ctx, k_density_tpp<double, false>, da, blocks, 0, a.time_kernels, s);
-    return a.hash ? timed_launch(ctx, k_density_tpp<float, true>, da, blocks, 0, a.time_kernels, s)
-                  : timed_launch(ctx, k_density_tpp<float, false>, da, blocks, 0, a.time_kernels, s);
+    if (a.hash || a.fixed_h || !a.buffered)
+        return a.hash ? timed_launch(ctx, k_density_tpp<float, true>, da, blocks, 0, a.time_kernels, s)
+                      : timed_launch(ctx, k_density_tpp<float, false>, da, blocks, 0, a.time_kernels, s);
+    return timed_launch(ctx, k_density_buf<false>, da, blocks, 0, a.time_kernels, s);
 }
 
 cudaError_t launch_force_tpp(sph_ctx* ctx, const ForceLaunch& a, int64_t n_active, cudaStream_t s) {
@@ -554,8 +930,8 @@ cudaError_t launch_force_tpp(sph_ctx* ctx, const ForceLaunch& a, int64_t n_activ
     if (a.fp64)
         return a.hash ? timed_launch(ctx, k_force_tpp<double, true>, fa, blocks, 1, a.time_kernels, s)
                       : timed_launch(ctx, k_force_tpp<double, false>, fa, blocks, 1, a.time_kernels, s);
-    return a.hash ? timed_launch(ctx, k_force_tpp<float, true>, fa, blocks, 1, a.time_kernels, s)
-                  : timed_launch(ctx, k_force_tpp<float, false>, fa, blocks, 1, a.time_kernels, s);
+    return a.hash ? timed_launch(ctx, k_force_mask<true>, fa, blocks, 1, a.time_kernels, s)
+                  : timed_launch(ctx, k_force_mask<false>, fa, blocks, 1, a.time_kernels, s);
 }
 
 }  // namespace sph
