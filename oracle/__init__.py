@@ -60,6 +60,8 @@ def lib():
         L.orc_neighbours.argtypes = [i32, P, P, i64, f64, i64, f64, i32, P, i64]
         L.orc_neighbours.restype = i64
         L.orc_num_threads.restype = i32
+        L.orc_pair_list.argtypes = [i32, P, P, i64, f64, P, i32, P, P, i64]
+        L.orc_pair_list.restype = i64
         _lib = L
     return _lib
 
@@ -177,4 +179,20 @@ def neighbours(X=None, i=0, h=0.1, box=1.0, brute=True, xc=None) -> np.ndarray:
                                  int(bool(brute)), _p(out), cap)
         if k <= cap:
             return np.sort(out[:k])
+        cap = int(k)
+
+
+def pair_list(X=None, h=None, box=1.0, brute=False, xc=None):
+    """Ordered pairs (i, j), i != j, with r_ij < max(h_i, h_j): int64 arrays."""
+    mode, Xc, xcc = _geom(X, xc, box)
+    n = Xc.shape[0]
+    hh = _c(h, np.float64)
+    cap = max(1024, 80 * n)
+    while True:
+        oi = np.empty(cap, dtype=np.int64)
+        oj = np.empty(cap, dtype=np.int64)
+        k = lib().orc_pair_list(mode, _p(Xc), _p(xcc), n, float(box), _p(hh), int(bool(brute)),
+                                _p(oi), _p(oj), cap)
+        if k <= cap:
+            return oi[:k], oj[:k]
         cap = int(k)

@@ -584,3 +584,50 @@ void orc_kernel_array(const double *q, int64_t n, double *w, double *dw)
 {
     for (int64_t k = 0; k < n; ++k) { w[k] = orc_w(q[k]); dw[k] = orc_dw(q[k]); }
 }
+
+/*
+ * Symmetric pair set of the force pass: every ordered pair (i, j), i != j,
+ * with r_ij < max(h_i, h_j) under the contract's predicate, found by brute
+ * force (all j) or the two cell lists of orc_force. Writes up to cap pairs
+ * into out_i/out_j, returns the total count (call again with a larger cap if
+ * it exceeds cap). Serial, in order of i then candidate order.
+ */
+int64_t orc_pair_list(int mode, const uint32_t *X, const double *xc, int64_t n, double L,
+                      const double *h, int brute, int64_t *out_i, int64_t *out_j, int64_t cap)
+{
+    orc_pos P = {mode, X, xc, n, L};
+    orc_index *I = brute ? NULL : (orc_index *)orc_index_new(X, n);
+    orc_hindex *Hx = brute ? NULL : orc_hindex_new(&P, h);
+    orc_buf cb = {0, 0, 0}, cl = {0, 0, 0};
+    int64_t k = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        orc_cands_for(&P, I, i, h[i], &cb);
+        int64_t nfirst = cb.n;
+        if (Hx) {
+            for (int l = 0; l < 22; ++l) {
+                if (!Hx->lv[l]) continue;
+                orc_candidates(Hx->lv[l], X + 3 * i, ldexp(1.0, 32 - l), &cl);
+                for (int64_t c = 0; c < cl.n; ++c) orc_push(&cb, Hx->map[l][cl.a[c]]);
+            }
+        }
+        for (int64_t c = 0; c < cb.n; ++c) {
+            int64_t j = cb.a[c];
+            if (j == i) continue;
+            double rij[3], r;
+            int in_i = orc_pair(&P, i, j, h[i], rij, &r);
+            int in_j = orc_pair(&P, i, j, h[j], rij, &r);
+            int take;
+            if (!Hx) take = in_i || in_j;
+            else if (c < nfirst) take = in_i;
+            else take = !in_i && in_j;
+            if (!take) continue;
+            if (k < cap) { out_i[k] = i; out_j[k] = j; }
+            ++k;
+        }
+    }
+    free(cb.a);
+    free(cl.a);
+    orc_hindex_free(Hx);
+    orc_index_free(I);
+    return k;
+}
