@@ -205,6 +205,26 @@ sph_status sph_hydro_force(sph_ctx *ctx, const sph_grid *grid, const float *vel,
                            float *vsig, uint64_t *hash, const sph_params *params, void *stream);
 
 /*
+ * Adjoint of the density and force passes (an extension of the paper's hot
+ * path, which has no gradients). All particles are active. Given the forward
+ * state of the grid's particles -- vel, u (inputs of the force pass) and h,
+ * rho, omega as sph_density returned them with h converged (N_eff(h) = N_t) --
+ * and the seeds
+ *   g_acc  device, n x 3: dL/da_i;   g_rho  device, n, or NULL (zero): dL/drho_i,
+ * writes dL/dx (g_pos, n x 3), dL/du (g_u, n) and dL/dm (g_mass, n) through
+ * the whole chain: the implicit dependence of h on the positions
+ * (dh/dx = -(dN/dx)/(dN/dh)), rho and d rho/dh, the grad-h factor Omega, the
+ * pressure and viscosity terms. Velocities are constants. The pair sets are
+ * recomputed by walking the grid (no neighbour lists are stored). FP32 pair
+ * terms with compensated sums; deterministic (gathers, no atomics). The
+ * first call on a grid allocates its adjoint workspace (~56 bytes/particle).
+ */
+sph_status sph_backward(sph_ctx *ctx, const sph_grid *grid, const float *vel, const float *u,
+                        const float *h, const float *rho, const float *omega, const float *g_acc,
+                        const float *g_rho, float *g_pos, float *g_u, float *g_mass,
+                        const sph_params *params, void *stream);
+
+/*
  * Stable sort of 64-bit keys that allocates nothing (the paper has no
  * counterpart: this serves callers that cannot call cudaMalloc -- code that
  * runs inside another framework's memory pool or budget, time-critical loops

@@ -16,7 +16,7 @@ from .abi import (SPH_FIXED_H, SPH_FP64, SPH_H_GUESS, SPH_PLAIN_FP32, SPH_TIME_K
                   default_params, sph_params, sph_stats)
 
 __all__ = ["Context", "Grid", "sph_create", "sph_build_grid", "sph_build_grid_batched", "sph_grid_update",
-           "sph_density", "sph_hydro_force", "sph_sync_status", "sph_grid_export", "sph_sort_keys_static", "density",
+           "sph_density", "sph_hydro_force", "sph_backward", "sph_sync_status", "sph_grid_export", "sph_sort_keys_static", "density",
            "hydro_force", "default_params", "sph_params", "sph_stats", "SPHError", "SPH_FP64",
            "SPH_PLAIN_FP32", "SPH_FIXED_H", "SPH_H_GUESS", "SPH_TIME_KERNELS", "SPH_WARP_GROUP", "SPH_DENSITY_BUFFERED"]
 
@@ -140,6 +140,15 @@ def sph_hydro_force(ctx: Context, grid: Grid, vel, u, h, rho, omega, active, acc
                                       _ptr(active, torch.int32, "active"), na, _ptr(acc, f, "acc"),
                                       _ptr(dudt, f, "dudt"), _ptr(vsig, f, "vsig"),
                                       _ptr(hash, torch.int64, "hash"), ctypes.byref(params), _stream()))
+
+
+def sph_backward(ctx: Context, grid: Grid, vel, u, h, rho, omega, g_acc, g_rho, g_pos, g_u, g_mass,
+                 params: sph_params = None):
+    f = torch.float32
+    ctx.check(ctx.lib.sph_backward(ctx.handle, grid.handle, _ptr(vel, f, "vel"), _ptr(u, f, "u"), _ptr(h, f, "h"),
+                                   _ptr(rho, f, "rho"), _ptr(omega, f, "omega"), _ptr(g_acc, f, "g_acc"),
+                                   _ptr(g_rho, f, "g_rho"), _ptr(g_pos, f, "g_pos"), _ptr(g_u, f, "g_u"),
+                                   _ptr(g_mass, f, "g_mass"), ctypes.byref(params or default_params()), _stream()))
 
 
 def sph_sync_status(ctx: Context, raise_on_error: bool = True):

@@ -263,6 +263,36 @@ sph_status sph_hydro_force(sph_ctx* ctx, const sph_grid* grid, const float* vel,
     return SPH_OK;
 }
 
+sph_status sph_backward(sph_ctx* ctx, const sph_grid* grid, const float* vel, const float* u, const float* h,
+                        const float* rho, const float* omega, const float* g_acc, const float* g_rho,
+                        float* g_pos, float* g_u, float* g_mass, const sph_params* params, void* stream) {
+    if (!ctx) return SPH_ERR_INVALID;
+    if (!grid || grid->ctx != ctx) return fail(ctx, SPH_ERR_INVALID, "grid is NULL or from another context");
+    if (!vel || !u || !h || !rho || !omega || !g_acc || !g_pos || !g_u || !g_mass)
+        return fail(ctx, SPH_ERR_INVALID, "vel, u, h, rho, omega, g_acc, g_pos, g_u, g_mass are required");
+    sph_status st = check_params(ctx, params);
+    if (st) return st;
+    if (params->flags & (SPH_FP64 | SPH_PLAIN_FP32 | SPH_WARP_GROUP))
+        return fail(ctx, SPH_ERR_INVALID, "sph_backward runs the FP32 thread path only");
+    if (cudaSetDevice(ctx->device)) return fail(ctx, SPH_ERR_CUDA, "cudaSetDevice failed");
+    BackwardLaunch b;
+    b.vel = vel;
+    b.u = u;
+    b.h = h;
+    b.rho = rho;
+    b.omega = omega;
+    b.g_acc = g_acc;
+    b.g_rho = g_rho;
+    b.g_pos = g_pos;
+    b.g_u = g_u;
+    b.g_mass = g_mass;
+    b.alpha = params->alpha_visc;
+    b.gamma = params->gamma;
+    cudaError_t e = run_backward(ctx, const_cast<sph_grid*>(grid), b, (cudaStream_t)stream);
+    if (e) return cuda_fail(ctx, e, "sph_backward");
+    return SPH_OK;
+}
+
 sph_status sph_sync_status(sph_ctx* ctx, void* stream, sph_stats* stats) {
     if (!ctx) return SPH_ERR_INVALID;
     if (cudaSetDevice(ctx->device)) return fail(ctx, SPH_ERR_CUDA, "cudaSetDevice failed");

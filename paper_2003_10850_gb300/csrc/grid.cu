@@ -438,7 +438,7 @@ void grid_free(sph_grid* g) {
                     g->node_hmax, g->act, g->flag, g->scan, g->scan_tmp, g->box_act, g->n_groups,
                     g->groups, g->list_a, g->list_b, g->st_lo, g->st_hi, g->list_n, g->d_off, g->d_L,
                     g->k2, g->v1, g->v2, g->counts, g->cscan, g->node_c, g->node_e, g->posf,
-                    g->fvel, g->fthermo};
+                    g->fvel, g->fthermo, g->bw_ga, g->bw_xbar, g->bw_rd, g->bw_f};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete g;

@@ -71,6 +71,11 @@ struct sph_grid {
     unsigned* v2 = nullptr;
     unsigned* counts = nullptr;
     unsigned* cscan = nullptr;
+    // adjoint scratch (allocated by the first sph_backward on the grid)
+    float4* bw_ga = nullptr;
+    float4* bw_xbar = nullptr;
+    float2* bw_rd = nullptr;
+    float* bw_f = nullptr;
 };
 
 namespace sph {
@@ -137,7 +142,25 @@ cudaError_t launch_force(sph_ctx* ctx, const ForceLaunch& a, cudaStream_t s);
 cudaError_t launch_force_plain(sph_ctx* ctx, const ForceLaunch& a, int64_t n_active,
                                cudaStream_t s);
 
+// backward.cu
+struct BackwardLaunch {
+    const float* vel;
+    const float* u;
+    const float* h;
+    const float* rho;
+    const float* omega;
+    const float* g_acc;
+    const float* g_rho;
+    float* g_pos;
+    float* g_u;
+    float* g_mass;
+    double alpha, gamma;
+};
+cudaError_t run_backward(sph_ctx* ctx, sph_grid* g, const BackwardLaunch& b, cudaStream_t s);
+
 // tpp.cu (default path)
+void force_pack(const sph_grid* g, const float* vel, const float* u, const float* h, const float* rho,
+                const float* omega, float gamma, cudaStream_t s);
 cudaError_t launch_density_tpp(sph_ctx* ctx, const DensityLaunch& a, int64_t n_active, cudaStream_t s);
 cudaError_t launch_force_tpp(sph_ctx* ctx, const ForceLaunch& a, int64_t n_active, cudaStream_t s);
 

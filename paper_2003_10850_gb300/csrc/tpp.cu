@@ -898,11 +898,15 @@ cudaError_t launch_density_tpp(sph_ctx* ctx, const DensityLaunch& a, int64_t n_a
     return timed_launch(ctx, k_density_buf<false>, da, blocks, 0, a.time_kernels, s);
 }
 
+void force_pack(const sph_grid* g, const float* vel, const float* u, const float* h, const float* rho,
+                const float* omega, float gamma, cudaStream_t s) {
+    const int n = (int)g->n;
+    k_force_pack<<<(n + 255) / 256, 256, 0, s>>>(n, g->perm, vel, u, h, rho, omega, gamma, g->fvel, g->fthermo);
+}
+
 cudaError_t launch_force_tpp(sph_ctx* ctx, const ForceLaunch& a, int64_t n_active, cudaStream_t s) {
     const sph_grid* g = a.g;
-    const int n = (int)g->n;
-    k_force_pack<<<(n + 255) / 256, 256, 0, s>>>(n, g->perm, a.vel, a.u, a.h, a.rho, a.omega, (float)a.gamma,
-                                                g->fvel, g->fthermo);
+    force_pack(g, a.vel, a.u, a.h, a.rho, a.omega, (float)a.gamma, s);
     ++ctx->launches;
     TppForceArgs fa;
     fa.boxes = g->boxes;
