@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the batched-boxes and adjoint lines")
     ap.add_argument("--cpu-n", type=int, default=1 << 20, help="particles of the CPU-baseline sample")
     return ap.parse_args()
 
@@ -207,40 +208,46 @@ def setup_workload(S, ctx, n, dev):
                 setup_s=time.time() - t0, n=n)
 
 
-def run_step(S, ctx, wl, params, ev=None):
-    """One step; returns list of (start, end) events pairs timed on the stream."""
+def step_body(S, ctx, wl, dparams, fparams, spans=None):
+    """One step: grid rebuild, then density + force for each sub-step's active
+    set. With `spans`, CUDA events bracket the grid rebuild and each sub-step
+    (the h copy that loads a sub-step's guesses stays outside)."""
     import torch
-    spans = []
     st = wl["st"]
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
+
+    def ev():
+        e = torch.cuda.Event(enable_timing=True)
+        e.record()
+        return e
+
+    a = ev() if spans is not None else None
     S.sph_grid_update(ctx, wl["grid"], wl["pos"], wl["mass"])
-    e1.record()
-    spans.append((e0, e1))
+    if spans is not None:
+        spans.append((a, ev()))
     for act, h_in in zip(wl["acts"], wl["h_ins"]):
-        wl["h"].copy_(h_in)   # untimed: the sub-step's h guesses
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        S.sph_density(ctx, wl["grid"], wl["h"], act, st["rho"], st["omega"], st["n_ngb"], st["flags"], None, params)
+        wl["h"].copy_(h_in)
+        a = ev() if spans is not None else None
+        S.sph_density(ctx, wl["grid"], wl["h"], act, st["rho"], st["omega"], st["n_ngb"], st["flags"], None, dparams)
         S.sph_hydro_force(ctx, wl["grid"], wl["vel"], wl["u"], wl["h"], st["rho"], st["omega"], act, st["acc"],
-                          st["dudt"], st["vsig"], None, params)
-        b.record()
-        spans.append((a, b))
-    return spans
+                          st["dudt"], st["vsig"], None, fparams)
+        if spans is not None:
+            spans.append((a, ev()))
 
 
-def timed_steps(S, ctx, wl, params, steps, warmup, dist=None):
+def timed_steps(S, ctx, wl, dparams, fparams, steps, warmup, dist=None):
+    """Eager steps, each timed as the sum of its event-bracketed parts."""
     import torch
     for _ in range(warmup):
-        run_step(S, ctx, wl, params)
+        step_body(S, ctx, wl, dparams, fparams)
     S.sph_sync_status(ctx)
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
-    ms, pairs, launches, dk, fk, dl, fl = 0.0, 0, 0, 0.0, 0.0, 0, 0
+    ms, launches, dk, fk, dl, fl = 0.0, 0, 0.0, 0.0, 0, 0
     dpairs = fpairs = 0
     for _ in range(steps):
-        spans = run_step(S, ctx, wl, params)
+        spans = []
+        step_body(S, ctx, wl, dparams, fparams, spans)
         rc, stt = S.sph_sync_status(ctx)
         ms += sum(a.elapsed_time(b) for a, b in spans)
         dpairs += stt["density_pairs"]
@@ -257,7 +264,42 @@ def timed_steps(S, ctx, wl, params, steps, warmup, dist=None):
                 dens_ms=dk, force_ms=fk, dens_launches=dl, force_launches=fl)
 
 
-def e2e_steps(S, ctx, wl, params, steps):
+def graph_steps(S, ctx, wl, dparams, fparams, steps, warmup, dist=None):
+    """The whole step captured once as a CUDA graph and replayed: one event
+    pair around each replay (the sub-steps' h copies are inside the graph)."""
+    import torch
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        step_body(S, ctx, wl, dparams, fparams)
+    torch.cuda.current_stream().wait_stream(side)
+    S.sph_sync_status(ctx)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        step_body(S, ctx, wl, dparams, fparams)
+    _, cap = S.sph_sync_status(ctx)          # host count of the kernels put in the graph
+    for _ in range(warmup):
+        graph.replay()
+    S.sph_sync_status(ctx)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    ms, pairs = 0.0, 0
+    for _ in range(steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        graph.replay()
+        b.record()
+        _, stt = S.sph_sync_status(ctx)
+        ms += a.elapsed_time(b)
+        pairs += stt["density_pairs"] + stt["force_pairs"]
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    return dict(ms=ms, pairs=pairs, launches=cap["launches"])
+
+
+def e2e_steps(S, ctx, wl, dparams, fparams, steps):
     """Same step through the public API from pinned HOST buffers: H2D of the
     step's inputs and D2H of its results inside the timed region."""
     import torch
@@ -282,9 +324,9 @@ def e2e_steps(S, ctx, wl, params, steps):
         for act, h_in in zip(wl["acts"], h_ins):
             wl["h"].copy_(h_in, non_blocking=True)
             S.sph_density(ctx, wl["grid"], wl["h"], act, st["rho"], st["omega"], st["n_ngb"], st["flags"], None,
-                          params)
+                          dparams)
             S.sph_hydro_force(ctx, wl["grid"], wl["vel"], wl["u"], wl["h"], st["rho"], st["omega"], act,
-                              st["acc"], st["dudt"], st["vsig"], None, params)
+                              st["acc"], st["dudt"], st["vsig"], None, fparams)
         for k in outs:
             outs[k].copy_(st[k], non_blocking=True)
         h_out.copy_(wl["h"], non_blocking=True)
@@ -294,6 +336,80 @@ def e2e_steps(S, ctx, wl, params, steps):
         pairs += stt["density_pairs"] + stt["force_pairs"]
     return dict(value=pairs / (t_ms / 1e3), unit=UNIT, h2d_bytes_per_step=int(h2d), d2h_bytes_per_step=int(d2h),
                 ms_per_step=t_ms / steps)
+
+
+def batched_line(S, ctx, dev, reps=3):
+    """Secondary line: 64 independent boxes (N log-uniform in [4096, 524288])
+    in one grid, density (from 2%-scattered converged h) + force, one launch
+    per pass for all boxes."""
+    import torch
+    import workloads as W
+    boxes = W.config4()
+    offs = np.cumsum([0] + [b.n for b in boxes])
+    cat = lambda k: torch.from_numpy(np.concatenate([getattr(b, k) for b in boxes]).astype(np.float32)).to(dev)
+    pos, mass, vel, u = cat("pos"), cat("mass"), cat("vel"), cat("u")
+    params = S.default_params()
+    grid = S.sph_build_grid_batched(ctx, pos, mass, offs, [1.0] * len(boxes), params)
+    n = int(offs[-1])
+    h = torch.zeros(n, device=dev)
+    d = S.density(ctx, grid, h, None, params)
+    S.sph_sync_status(ctx)
+    h_in = torch.from_numpy(W.perturb(h.cpu().numpy().astype(np.float64), H_PERTURB, 31).astype(np.float32)).to(dev)
+    f = S.hydro_force(ctx, grid, vel, u, h, d["rho"], d["omega"], None, params)
+    S.sph_sync_status(ctx)
+    ms = 0.0
+    pairs = 0
+    for _ in range(reps):
+        h.copy_(h_in)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        S.sph_density(ctx, grid, h, None, d["rho"], d["omega"], d["n_ngb"], d["flags"], None, params)
+        S.sph_hydro_force(ctx, grid, vel, u, h, d["rho"], d["omega"], None, f["acc"], f["dudt"], f["vsig"], None, params)
+        b.record()
+        _, stt = S.sph_sync_status(ctx)
+        ms += a.elapsed_time(b)
+        pairs += stt["density_pairs"] + stt["force_pairs"]
+    grid.free()
+    return {"workload": "64 periodic boxes, N log-uniform in [4096, 524288] (seed 100+b), one grid, "
+                        "all active, density + force", "n_total": n, "boxes": len(boxes),
+            "value": pairs / (ms / 1e3), "unit": UNIT, "ms_per_pass": ms / reps}
+
+
+def adjoint_line(S, ctx, dev, reps=3):
+    """Secondary line: the differentiation workload (262,144 clustered
+    particles): forward density + force, then sph_backward for the loss
+    sum |a - a*|^2 + sum (rho - rho*)^2 with 1% scattered targets."""
+    import torch
+    import workloads as W
+    p = W.config5()
+    f32 = lambda a: torch.from_numpy(np.asarray(a, np.float32)).to(dev)
+    pos, mass, vel, u = f32(p.pos), f32(p.mass), f32(p.vel), f32(p.u)
+    params = S.default_params()
+    grid = S.sph_build_grid(ctx, pos, mass, params)
+    h = torch.zeros(p.n, device=dev)
+    d = S.density(ctx, grid, h, None, params)
+    f = S.hydro_force(ctx, grid, vel, u, h, d["rho"], d["omega"], None, params)
+    _, stt = S.sph_sync_status(ctx)
+    rng = np.random.default_rng(5)
+    g_acc = 2 * (f["acc"] - f["acc"] * (1 + 0.01 * torch.from_numpy(rng.normal(size=(p.n, 1))).float().to(dev)))
+    g_rho = 2 * (d["rho"] - d["rho"] * (1 + 0.01 * torch.from_numpy(rng.normal(size=p.n)).float().to(dev)))
+    g_pos = torch.empty(p.n, 3, device=dev)
+    g_u = torch.empty(p.n, device=dev)
+    g_m = torch.empty(p.n, device=dev)
+    S.sph_backward(ctx, grid, vel, u, h, d["rho"], d["omega"], g_acc, g_rho, g_pos, g_u, g_m, params)
+    S.sph_sync_status(ctx)
+    ms = 0.0
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        S.sph_backward(ctx, grid, vel, u, h, d["rho"], d["omega"], g_acc, g_rho, g_pos, g_u, g_m, params)
+        b.record()
+        S.sph_sync_status(ctx)
+        ms += a.elapsed_time(b)
+    grid.free()
+    return {"workload": "262,144 clustered (seed 5), loss |a-a*|^2 + (rho-rho*)^2, all active",
+            "backward_ms": ms / reps, "force_pairs": stt["force_pairs"],
+            "pair_visits_per_s": 3 * stt["force_pairs"] / (ms / reps / 1e3)}
 
 
 def main():
@@ -318,16 +434,25 @@ def main():
     if dist is not None:
         dist.barrier()
     import paper_2003_10850_gb300 as S
+    from paper_2003_10850_gb300 import autotune
     ctx = S.Context(local)
     wl = setup_workload(S, ctx, args.n, dev)
-    params = S.default_params(flags=S.SPH_TIME_KERNELS)
+    # launch shapes per pass, tuned on the 100 % sub-step
+    setup_s = wl["setup_s"]
+    dpar, fpar, tuned = autotune.tune(ctx, wl["grid"], wl["st"], wl["vel"], wl["u"], wl["h"], wl["h_ins"][0],
+                                      tag="clustered-100pct")
+    dtime = S.default_params(flags=dpar.flags | S.SPH_TIME_KERNELS, blocks_per_sm=dpar.blocks_per_sm,
+                             group_size=dpar.group_size)
+    ftime = S.default_params(flags=fpar.flags | S.SPH_TIME_KERNELS, blocks_per_sm=fpar.blocks_per_sm,
+                             group_size=fpar.group_size)
 
     clocks = Clocks(local)
-    res = timed_steps(S, ctx, wl, params, args.steps, args.warmup, dist)
+    res_g = graph_steps(S, ctx, wl, dpar, fpar, args.steps, args.warmup, dist)
     clk = clocks.stop()
+    res = timed_steps(S, ctx, wl, dtime, ftime, args.steps, max(1, args.warmup // 3), dist)
 
-    ms_step = res["ms"] / args.steps
-    pairs_step = res["pairs"] / args.steps
+    ms_step = res_g["ms"] / args.steps
+    pairs_step = res_g["pairs"] / args.steps
     if dist is not None:
         t = torch.tensor([ms_step, pairs_step], dtype=torch.float64, device=dev)
         mx = t.clone()
@@ -342,12 +467,19 @@ def main():
     plain = None
     if not args.no_plain and rank == 0:
         pp = S.default_params(flags=S.SPH_PLAIN_FP32)
-        r2 = timed_steps(S, ctx, wl, pp, max(1, min(2, args.steps)), 1)
-        plain = {"value": r2["pairs"] / (r2["ms"] / 1e3), "ms_per_step": r2["ms"] / max(1, min(2, args.steps)),
-                 "unit": UNIT}
+        k2 = max(1, min(2, args.steps))
+        r2 = timed_steps(S, ctx, wl, pp, pp, k2, 1)
+        plain = {"value": r2["pairs"] / (r2["ms"] / 1e3), "ms_per_step": r2["ms"] / k2, "unit": UNIT,
+                 "kind": "thread per particle, FP32 sums, h iterated by the host, eager launches"}
     e2e = None
     if not args.no_e2e:
-        e2e = e2e_steps(S, ctx, wl, S.default_params(), max(1, min(3, args.steps)))
+        e2e = e2e_steps(S, ctx, wl, dpar, fpar, max(1, min(3, args.steps)))
+    extra = {}
+    if not args.no_extra and rank == 0:
+        del wl
+        torch.cuda.empty_cache()
+        extra["batched_boxes"] = batched_line(S, ctx, dev)
+        extra["adjoint"] = adjoint_line(S, ctx, dev)
 
     pk, src = peaks()
     props = torch.cuda.get_device_properties(dev)
@@ -355,10 +487,11 @@ def main():
     peak_tf = sm_count * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     dens_f = res["dpairs"] * FLOPS_DENSITY_PAIR
     force_f = res["fpairs"] * FLOPS_FORCE_PAIR
+    dname = "k_density_buf" if dpar.flags & S.SPH_DENSITY_BUFFERED else "k_density_tpp<float>"
     if res["dens_ms"] >= res["force_ms"]:
-        kern, flops, kms, kl = "k_density<float>", dens_f, res["dens_ms"], res["dens_launches"]
+        kern, flops, kms, kl = dname, dens_f, res["dens_ms"], res["dens_launches"]
     else:
-        kern, flops, kms, kl = "k_force<float>", force_f, res["force_ms"], res["force_launches"]
+        kern, flops, kms, kl = "k_force_mask", force_f, res["force_ms"], res["force_launches"]
     achieved = (flops / max(kl, 1)) / (kms / max(kl, 1) / 1e3) / 1e12 if kms > 0 else None
     roofline = {"bound": "alu", "kernel": kern, "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
                 "frac": achieved / peak_tf if achieved else None, "traffic": None,
@@ -385,14 +518,18 @@ def main():
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": "10M clustered gas particles (500 blobs, seed 3), time bins giving "
                                        "100/10/1/0.1% active sub-steps; grid rebuild + density (h iteration) "
-                                       "+ hydro force per sub-step",
+                                       "+ hydro force per sub-step; whole step replayed as one CUDA graph",
                            "n": args.n, "pairs_per_step": pairs_step, "l2": "inputs exceed L2 (>1 GB)",
                            "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
-                           "h_guess_scatter": H_PERTURB},
+                           "h_guess_scatter": H_PERTURB,
+                           "tuned": {"density": tuned["density"], "force": tuned["force"]},
+                           "eager_ms_per_step": res["ms"] / args.steps,
+                           "eager_value": res["pairs"] / (res["ms"] / 1e3)},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": int(round(res["launches"] / args.steps)), "clocks": clk,
+                "gpu_launches": int(res_g["launches"]), "clocks": clk,
                 "plain_fp32": plain, "speedup_vs_plain": (value / plain["value"]) if plain else None,
-                "setup_s": wl["setup_s"]}
+                "setup_s": setup_s}
+        line.update(extra)
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.barrier()

@@ -1,0 +1,96 @@
+"""Launch-shape autotuner for the density and force passes.
+
+Times a small set of configurations of each pass on the caller's own grid and
+state (CUDA events on the current stream, best of `reps`), picks the fastest
+per pass, and caches the choice per (GPU name, particle count, workload tag)
+in paper_2003_10850_gb300/_build/autotune.json. The knobs are those of
+sph_params: persistent blocks per SM, the density iteration mode (walk per
+iteration, or one walk into a per-thread buffer) and the warp-group path.
+"""
+from __future__ import annotations
+
+import json
+import os
+
+import torch
+
+from . import (SPH_DENSITY_BUFFERED, SPH_WARP_GROUP, default_params, sph_density, sph_hydro_force,
+               sph_sync_status)
+
+CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
+
+DENSITY_CANDIDATES = [dict(flags=f, blocks_per_sm=b) for f in (0, SPH_DENSITY_BUFFERED) for b in (4, 8, 16)]
+FORCE_CANDIDATES = [dict(flags=0, blocks_per_sm=b) for b in (4, 8, 16)]
+WARP_CANDIDATE = dict(flags=SPH_WARP_GROUP, blocks_per_sm=4, group_size=32)
+
+
+def _load():
+    try:
+        with open(CACHE) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _save(c):
+    os.makedirs(os.path.dirname(CACHE), exist_ok=True)
+    tmp = CACHE + f".tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(c, f, indent=1, sort_keys=True)
+    os.replace(tmp, CACHE)
+
+
+def _time(fn, reps):
+    best = float("inf")
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        b.synchronize()
+        best = min(best, a.elapsed_time(b))
+    return best
+
+
+def tune(ctx, grid, st, vel, u, h, h_guess, active=None, tag="default", reps=2, use_cache=True,
+         include_warp=False):
+    """Returns (density_params, force_params, report). `st` holds the output
+    buffers rho, omega, n_ngb, flags, acc, dudt, vsig; h is overwritten with
+    h_guess before every density trial."""
+    key = f"{torch.cuda.get_device_name()}|n={grid.n}|{tag}"
+    cache = _load() if use_cache else {}
+    if key in cache:
+        e = cache[key]
+        return default_params(**e["density"]), default_params(**e["force"]), e
+    dens = list(DENSITY_CANDIDATES) + ([WARP_CANDIDATE] if include_warp else [])
+    rep = {"density": {}, "force": {}}
+
+    def run_d(kw):
+        h.copy_(h_guess)
+        sph_density(ctx, grid, h, active, st["rho"], st["omega"], st["n_ngb"], st["flags"], None,
+                    default_params(**kw))
+
+    best_d, best_dt = None, float("inf")
+    for kw in dens:
+        t = _time(lambda: run_d(kw), reps)
+        sph_sync_status(ctx, raise_on_error=False)
+        rep["density"][json.dumps(kw, sort_keys=True)] = t
+        if t < best_dt:
+            best_d, best_dt = kw, t
+    run_d(best_d)   # leave the converged state of the winner in place
+
+    def run_f(kw):
+        sph_hydro_force(ctx, grid, vel, u, h, st["rho"], st["omega"], active, st["acc"], st["dudt"], st["vsig"],
+                        None, default_params(**kw))
+
+    best_f, best_ft = None, float("inf")
+    for kw in FORCE_CANDIDATES + ([WARP_CANDIDATE] if include_warp else []):
+        t = _time(lambda: run_f(kw), reps)
+        rep["force"][json.dumps(kw, sort_keys=True)] = t
+        if t < best_ft:
+            best_f, best_ft = kw, t
+    sph_sync_status(ctx, raise_on_error=False)
+    entry = {"density": best_d, "force": best_f, "density_ms": best_dt, "force_ms": best_ft, "trials": rep}
+    cache[key] = entry
+    _save(cache)
+    return default_params(**best_d), default_params(**best_f), entry

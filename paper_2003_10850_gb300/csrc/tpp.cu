@@ -72,7 +72,7 @@ __device__ __forceinline__ T tpp_sqrt(T x) {
 // part). Returns false when h cannot move (converged to the float grid or an
 // error bit was set).
 __device__ __forceinline__ bool h_update(float& h, double f, float N, float dN, float n_target, double cap,
-                                         double& blo, double& bhi, unsigned& st) {
+                                         double& blo, double& bhi, float& dold, unsigned& st) {
     if (f < 0) blo = h; else bhi = h;
     float step = dN > 0.f ? 3.f * N * (1.f - cbrtf(n_target / N)) / dN : NAN;
     double hn = (double)h - (double)step;
@@ -83,9 +83,12 @@ __device__ __forceinline__ bool h_update(float& h, double f, float N, float dN, 
         }
         if (!(hn > (double)h)) hn = 2.0 * (double)h;
         hn = fmin(hn, fmin(cap, 8.0 * (double)h));
-    } else if (!(hn > blo && hn < bhi)) {
+    } else if (!(hn > blo && hn < bhi) || !(fabsf(step) <= 0.5f * dold)) {
+        // outside the bracket, or not converging fast (the step did not halve):
+        // bisect (the safeguard of Newton-Raphson with bracketing)
         hn = 0.5 * (blo + bhi);
     }
+    dold = fabsf((float)(hn - (double)h));
     float hf = (float)hn;
     if (!(hf > (float)blo) || (!isinf(bhi) && !(hf < (float)bhi))) {
         const float mid = (float)(0.5 * (blo + bhi));
@@ -245,6 +248,7 @@ __global__ void __launch_bounds__(kTppThreads) k_density_tpp(TppDensArgs a) {
         if (a.guess_h || !(h > 0.f) || !isfinite(h)) h = tpp_guess_h(B, a.node_lo, a.node_hi, p, s, a.n_target);
         const double cap = 0.5 * L * (1.0 - 1e-9);
         double blo = 0.0, bhi = INFINITY;
+        float dold = INFINITY;
         unsigned st = 0;
         TppDSums<T> S;
         for (int it = 0;; ++it) {
@@ -260,7 +264,7 @@ __global__ void __launch_bounds__(kTppThreads) k_density_tpp(TppDensArgs a) {
             if (it >= a.max_iter) { st |= ST_NOT_CONVERGED; break; }
             const float N = (float)((32.0 / 3.0) * ((double)S.sw - (double)S.cw));
             const float dN = -(32.f / 3.f) * (float)((double)S.sdw - (double)S.cdw) / h;
-            if (!h_update(h, f, N, dN, (float)a.n_target, cap, blo, bhi, st)) break;
+            if (!h_update(h, f, N, dN, (float)a.n_target, cap, blo, bhi, dold, st)) break;
         }
         const double smw = (double)S.smw - (double)S.cmw, smdw = (double)S.smdw - (double)S.cmdw;
         const double hd = (double)h;
@@ -347,6 +351,7 @@ __global__ void __launch_bounds__(kTppThreads) k_density_buf(TppDensArgs a) {
         if (a.guess_h || !(h > 0.f) || !isfinite(h)) h = tpp_guess_h(B, a.node_lo, a.node_hi, p, s, a.n_target);
         const double cap = 0.5 * L * (1.0 - 1e-9);
         double blo = 0.0, bhi = INFINITY;
+        float dold = INFINITY;
         unsigned st = 0;
         bool exact_finish = false, finished = false;
         float2 buf[kDensBuf];
@@ -425,7 +430,7 @@ __global__ void __launch_bounds__(kTppThreads) k_density_buf(TppDensArgs a) {
                 ++it;
                 const float N = (32.f / 3.f) * (Sw - Cw);
                 const float dN = -(32.f / 3.f) * (Sdw - Cdw) / h;
-                if (!h_update(h, f, N, dN, (float)a.n_target, cap, blo, bhi, st)) { finished = true; break; }
+                if (!h_update(h, f, N, dN, (float)a.n_target, cap, blo, bhi, dold, st)) { finished = true; break; }
                 if (h >= R * (1.f - 1.52587890625e-05f)) break;  // outside the buffer: walk again
             }
             if (!finished) continue;
@@ -482,7 +487,7 @@ __global__ void __launch_bounds__(kTppThreads) k_density_buf(TppDensArgs a) {
                 ++it;
                 const float N = (32.f / 3.f) * (S.sw - S.cw);
                 const float dN = -(32.f / 3.f) * (S.sdw - S.cdw) / h;
-                if (!h_update(h, f, N, dN, (float)a.n_target, cap, blo, bhi, st)) break;
+                if (!h_update(h, f, N, dN, (float)a.n_target, cap, blo, bhi, dold, st)) break;
             }
         }
         const double hd = (double)h;

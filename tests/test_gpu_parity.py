@@ -289,3 +289,52 @@ def test_single_particle_and_tiny(S, ctx):
     # a target at or below the self term 32/3 has no root: rejected on the host
     with pytest.raises(S.SPHError):
         gpu_density(S, ctx, grid, np.zeros(1, np.float32), S.default_params(n_target=10.0))
+
+
+# ---- a6: the step captured as a CUDA graph ------------------------------------
+
+def test_graph_capture_replays_eager_results(S, ctx, clustered50k):
+    """Grid rebuild + density + force over an active subset, captured once and
+    replayed: the outputs equal those of the eager calls bit for bit."""
+    p, (X, d, _) = clustered50k
+    params = S.default_params(box=p.box)
+    act = dev(W.sample_indices(p.n, p.n // 5, seed=23).astype(np.int32), torch.int32)
+    pos, mass, vel, u = dev(p.pos), dev(p.mass), dev(p.vel), dev(p.u)
+    grid = S.sph_build_grid(ctx, pos, mass, params)
+    h0 = dev(d["h"].astype(np.float32) * 1.01)
+    outs = {}
+    for mode in ("eager", "graph"):
+        h = h0.clone()
+        # inactive neighbours keep a valid state (the oracle's, rounded to FP32)
+        rho, om = dev(d["rho"].astype(np.float32)), dev(d["omega"].astype(np.float32))
+        nn, fl = torch.zeros(p.n, dtype=torch.int32, device="cuda"), torch.zeros(p.n, dtype=torch.uint8, device="cuda")
+        acc, du, vs = torch.zeros(p.n, 3, device="cuda"), torch.zeros(p.n, device="cuda"), torch.zeros(p.n, device="cuda")
+
+        def body():
+            h.copy_(h0)
+            S.sph_grid_update(ctx, grid, pos, mass)
+            S.sph_density(ctx, grid, h, act, rho, om, nn, fl, None, params)
+            S.sph_hydro_force(ctx, grid, vel, u, h, rho, om, act, acc, du, vs, None, params)
+
+        if mode == "eager":
+            body()
+        else:
+            side = torch.cuda.Stream()
+            side.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(side):
+                body()
+            torch.cuda.current_stream().wait_stream(side)
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                body()
+            for t in (acc, du, vs):
+                t.zero_()
+            rho.copy_(dev(d["rho"].astype(np.float32)))
+            om.copy_(dev(d["omega"].astype(np.float32)))
+            g.replay()
+            g.replay()
+        rc, _ = S.sph_sync_status(ctx, raise_on_error=False)
+        assert rc == 0
+        outs[mode] = [host(t) for t in (h, rho, om, nn, acc, du, vs)]
+    for a, b in zip(outs["eager"], outs["graph"]):
+        assert np.all(np.isfinite(a.astype(np.float64))) and np.array_equal(a, b)
