@@ -487,11 +487,15 @@ def main():
     peak_tf = sm_count * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     dens_f = res["dpairs"] * FLOPS_DENSITY_PAIR
     force_f = res["fpairs"] * FLOPS_FORCE_PAIR
-    dname = "k_density_buf" if dpar.flags & S.SPH_DENSITY_BUFFERED else "k_density_tpp<float>"
+    if dpar.flags & S.SPH_PER_THREAD_WALK:
+        dname = "k_density_buf" if dpar.flags & S.SPH_DENSITY_BUFFERED else "k_density_tpp<float>"
+    else:
+        dname = "k_density_coop"
+    fname = "k_force_mask" if fpar.flags & S.SPH_PER_THREAD_WALK else "k_force_coop"
     if res["dens_ms"] >= res["force_ms"]:
         kern, flops, kms, kl = dname, dens_f, res["dens_ms"], res["dens_launches"]
     else:
-        kern, flops, kms, kl = "k_force_mask", force_f, res["force_ms"], res["force_launches"]
+        kern, flops, kms, kl = fname, force_f, res["force_ms"], res["force_launches"]
     achieved = (flops / max(kl, 1)) / (kms / max(kl, 1) / 1e3) / 1e12 if kms > 0 else None
     roofline = {"bound": "alu", "kernel": kern, "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
                 "frac": achieved / peak_tf if achieved else None, "traffic": None,

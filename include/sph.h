@@ -52,12 +52,14 @@ typedef enum {
                                 estimate made from the grid's leaf-parent boxes */
 #define SPH_TIME_KERNELS 0x10 /* record CUDA events around the main density/force kernel on
                                  the launching stream; sph_sync_status sums their durations */
-#define SPH_WARP_GROUP 0x20   /* alternative fast path: one warp per group of <= group_size
-                                 Morton-consecutive particles sharing one walk (default: one
-                                 thread per particle with its own walk) */
-#define SPH_DENSITY_BUFFERED 0x40 /* density, thread path: iterate h on a per-thread buffer of
-                                     the candidates found by one walk at 1.06 h, instead of
-                                     walking the tree at every iteration (the default) */
+#define SPH_WARP_GROUP 0x20   /* alternative path: one warp per group of <= group_size
+                                 Morton-consecutive particles sharing one walk against the
+                                 group's bounding box (a common candidate set) */
+#define SPH_DENSITY_BUFFERED 0x40 /* density, per-thread walks: iterate h on a per-thread buffer
+                                     of the candidates found by one walk at 1.06 h */
+#define SPH_PER_THREAD_WALK 0x80  /* one thread per particle walking alone, instead of the default
+                                     warp-cooperative walk (per-lane spheres, shared node tests,
+                                     per-lane compacted leaf lists) */
 
 /* Device status bits returned in sph_stats.status */
 #define SPH_ST_NOT_CONVERGED 0x01

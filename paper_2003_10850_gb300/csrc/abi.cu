@@ -39,6 +39,8 @@ sph_status check_params(sph_ctx* ctx, const sph_params* p) {
         return fail(ctx, SPH_ERR_INVALID, "SPH_FP64 and SPH_PLAIN_FP32 are exclusive");
     if ((p->flags & SPH_WARP_GROUP) && (p->flags & SPH_PLAIN_FP32))
         return fail(ctx, SPH_ERR_INVALID, "SPH_WARP_GROUP and SPH_PLAIN_FP32 are exclusive");
+    if ((p->flags & SPH_WARP_GROUP) && (p->flags & SPH_PER_THREAD_WALK))
+        return fail(ctx, SPH_ERR_INVALID, "SPH_WARP_GROUP and SPH_PER_THREAD_WALK are exclusive");
     return SPH_OK;
 }
 
@@ -194,7 +196,9 @@ sph_status sph_density(sph_ctx* ctx, const sph_grid* grid, float* h, const int32
     cudaStream_t s = (cudaStream_t)stream;
     sph_grid* g = const_cast<sph_grid*>(grid);  // per-call scratch lives in the grid
     const bool warp_group = (params->flags & SPH_WARP_GROUP) != 0;
-    grid_active(g, active, n_active, group_size(params), warp_group, s);
+    const bool per_thread = (params->flags & (SPH_PER_THREAD_WALK | SPH_DENSITY_BUFFERED | SPH_FP64)) != 0;
+    const bool coop = !warp_group && !per_thread && !(params->flags & SPH_PLAIN_FP32);
+    grid_active(g, active, n_active, coop ? 32 : group_size(params), warp_group || coop, s);
     DensityLaunch a;
     a.g = g;
     a.h = h;
@@ -214,6 +218,7 @@ sph_status sph_density(sph_ctx* ctx, const sph_grid* grid, float* h, const int32
     a.buffered = (params->flags & SPH_DENSITY_BUFFERED) ? 1 : 0;
     cudaError_t e = (params->flags & SPH_PLAIN_FP32) ? run_density_plain(ctx, a, na, s)
                     : warp_group                       ? launch_density(ctx, a, s)
+                    : coop                             ? launch_density_coop(ctx, a, s)
                                                        : launch_density_tpp(ctx, a, na, s);
     if (!e) e = cudaGetLastError();
     if (e) return cuda_fail(ctx, e, "sph_density");
@@ -237,8 +242,10 @@ sph_status sph_hydro_force(sph_ctx* ctx, const sph_grid* grid, const float* vel,
     cudaStream_t s = (cudaStream_t)stream;
     sph_grid* g = const_cast<sph_grid*>(grid);
     const bool warp_group = (params->flags & SPH_WARP_GROUP) != 0;
+    const bool per_thread = (params->flags & (SPH_PER_THREAD_WALK | SPH_FP64)) != 0;
+    const bool coop = !warp_group && !per_thread && !(params->flags & SPH_PLAIN_FP32);
     grid_refresh_hmax(g, h, s);
-    grid_active(g, active, n_active, group_size(params), warp_group, s);
+    grid_active(g, active, n_active, coop ? 32 : group_size(params), warp_group || coop, s);
     ForceLaunch a;
     a.g = g;
     a.vel = vel;
@@ -257,6 +264,7 @@ sph_status sph_hydro_force(sph_ctx* ctx, const sph_grid* grid, const float* vel,
     a.time_kernels = (params->flags & SPH_TIME_KERNELS) ? 1 : 0;
     cudaError_t e = (params->flags & SPH_PLAIN_FP32) ? launch_force_plain(ctx, a, na, s)
                     : warp_group                       ? launch_force(ctx, a, s)
+                    : coop                             ? launch_force_coop(ctx, a, s)
                                                        : launch_force_tpp(ctx, a, na, s);
     if (!e) e = cudaGetLastError();
     if (e) return cuda_fail(ctx, e, "sph_hydro_force");

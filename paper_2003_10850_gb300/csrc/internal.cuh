@@ -158,7 +158,11 @@ struct BackwardLaunch {
 };
 cudaError_t run_backward(sph_ctx* ctx, sph_grid* g, const BackwardLaunch& b, cudaStream_t s);
 
-// tpp.cu (default path)
+// coop.cu (default path)
+cudaError_t launch_density_coop(sph_ctx* ctx, const DensityLaunch& a, cudaStream_t s);
+cudaError_t launch_force_coop(sph_ctx* ctx, const ForceLaunch& a, cudaStream_t s);
+
+// tpp.cu (per-thread walks)
 void force_pack(const sph_grid* g, const float* vel, const float* u, const float* h, const float* rho,
                 const float* omega, float gamma, cudaStream_t s);
 cudaError_t launch_density_tpp(sph_ctx* ctx, const DensityLaunch& a, int64_t n_active, cudaStream_t s);

@@ -78,11 +78,12 @@ def test_batched_keys_and_sort_exact(S, ctx):
 
 # ---- a4: density ------------------------------------------------------------
 
-PATHS = ["thread", "warp"]
+PATHS = ["coop", "thread", "warp"]
 
 
 def _flags(S, path, fp64):
-    return (S.SPH_FP64 if fp64 else 0) | (S.SPH_WARP_GROUP if path == "warp" else 0)
+    extra = {"coop": 0, "thread": S.SPH_PER_THREAD_WALK, "warp": S.SPH_WARP_GROUP}[path]
+    return (S.SPH_FP64 if fp64 else 0) | extra
 
 
 @pytest.mark.parametrize("path", PATHS)
