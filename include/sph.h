@@ -57,9 +57,12 @@ typedef enum {
                                  group's bounding box (a common candidate set) */
 #define SPH_DENSITY_BUFFERED 0x40 /* density, per-thread walks: iterate h on a per-thread buffer
                                      of the candidates found by one walk at 1.06 h */
-#define SPH_PER_THREAD_WALK 0x80  /* one thread per particle walking alone, instead of the default
-                                     warp-cooperative walk (per-lane spheres, shared node tests,
-                                     per-lane compacted leaf lists) */
+#define SPH_PER_THREAD_WALK 0x80  /* force one thread per particle walking alone */
+#define SPH_COOP_WALK 0x100       /* force the warp-cooperative walk: one warp per 32
+                                     Morton-consecutive active particles, per-lane spheres, shared
+                                     node tests, per-lane compacted leaf lists and hit buffers.
+                                     Default (neither flag): cooperative when >= 5 % of the
+                                     particles are active, per-thread walks below */
 
 /* Device status bits returned in sph_stats.status */
 #define SPH_ST_NOT_CONVERGED 0x01

@@ -14,7 +14,7 @@ import os
 
 import torch
 
-from . import (SPH_DENSITY_BUFFERED, SPH_PER_THREAD_WALK, SPH_WARP_GROUP, default_params, sph_density,
+from . import (SPH_COOP_WALK, SPH_DENSITY_BUFFERED, SPH_PER_THREAD_WALK, SPH_WARP_GROUP, default_params, sph_density,
                sph_hydro_force, sph_sync_status)
 
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")

@@ -16,6 +16,8 @@
 // Density iterates h per lane (FP64 bracket, as in tpp.cu), re-walking with
 // only the unconverged lanes in the root mask. FP32 pair terms with per-batch
 // Kahan compensation; exact neighbour predicate in a thin band, as elsewhere.
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace sph {
@@ -24,12 +26,17 @@ constexpr int kCoopWarps = 3;
 constexpr int kCoopMinBlocks = 8;  // register budget for 24 resident warps per SM
 constexpr int kCStack = 96;   // depth-first: <= 7 pending siblings per level + 1
 constexpr int kLL = 16;       // leaves per lane per chunk
+constexpr int kLCache = 64;   // leaves per lane remembered between density iterations
+constexpr int kCoopMaxBps = 16;
+constexpr float kWalkR = 1.06f;  // density walks cover 1.06 h so later iterations can reuse them
 constexpr int kHB = 16;       // buffered hits per lane (a leaf adds <= 8)
 
 // Per-warp shared memory: the walk stack, the per-lane leaf lists and the
 // per-lane hit buffers ((r^2, m) for density, the neighbour's index for force),
 // ~6.9 KB per warp.
 struct CoopSmem {
+    uint4 nc[kFan];     // children of the popped node, staged by one coalesced load
+    float4 ne[kFan];
     int stk[kCStack];
     unsigned stm[kCStack];
     int leaves[kLL][32];
@@ -61,6 +68,7 @@ struct CoopArgs {
     double n_target, n_tol;
     int max_iter;
     int guess_h, fixed_h;
+    int* lcache;        // per persistent warp: kLCache x 32 leaf indices of the last walk
     // force
     const float4* fvel;
     const float4* fthermo;
@@ -114,9 +122,15 @@ __device__ __forceinline__ void coop_walk(CoopSmem& sm, const BoxDesc& B, const 
             const int c0 = t * kFan, c1 = min(c0 + kFan, B.lvl_n[cl]);
             const int base = B.lvl_off[cl];
             const bool in = (M >> lane) & 1u;
+            // lanes 0-7 fetch the children's centres, lanes 8-15 their extents:
+            // one load per lane instead of a dependent load pair per child test
+            const int nch = c1 - c0;
+            if (lane < (unsigned)nch) sm.nc[lane] = node_c[base + c0 + lane];
+            else if (lane >= 8u && lane - 8u < (unsigned)nch) sm.ne[lane - 8] = node_e[base + c0 + lane - 8];
+            __syncwarp();
             for (int c = c0; c < c1; ++c) {
-                const uint4 nc = node_c[base + c];
-                const float4 ne = node_e[base + c];
+                const uint4 nc = sm.nc[c - c0];
+                const float4 ne = sm.ne[c - c0];
                 const bool pass = in && coop_near(nc, ne, X, sf, radius(ne));
                 const unsigned Mc = __ballot_sync(0xffffffffu, pass);
                 if (!Mc) continue;
@@ -222,9 +236,15 @@ __global__ void __launch_bounds__(kCoopWarps * 32, kCoopMinBlocks) k_density_coo
         float Sw = 0.f, Cw = 0.f, Sdw = 0.f, Cdw = 0.f, Smw = 0.f, Cmw = 0.f, Smdw = 0.f, Cmdw = 0.f;
         int nn = 0;
         unsigned long long hs = 0;
+        // Leaves of the last walk (radius Rw = 1.06 h), per lane: the h iteration
+        // re-tests their particles while h stays below Rw instead of walking again.
+        int* lc = a.lcache + (size_t)(blockIdx.x * kCoopWarps + (threadIdx.x >> 5)) * (kLCache * 32);
+        int ncache = 0;
+        float Rw = 0.f;
         for (int it = 0;; ++it) {
             const unsigned wm = __ballot_sync(0xffffffffu, !conv);
             if (!wm) break;
+            const bool rewalk = __any_sync(0xffffffffu, !conv && (ncache > kLCache || !(h <= Rw * 0.99999f)));
             const float hinv = 1.f / h;
             double HH = -1.0;
             if (!conv) {
@@ -262,6 +282,10 @@ __global__ void __launch_bounds__(kCoopWarps * 32, kCoopMinBlocks) k_density_coo
             auto leaf = [&](int lt) {
                 if (__any_sync(0xffffffffu, nh > kHB - 8)) drain();
                 if (lt < 0) return;
+                if (rewalk) {
+                    if (ncache < kLCache) lc[ncache * 32 + lane] = lt;
+                    ++ncache;
+                }
                 const int nd = B.lvl_off[0] + lt;
                 const uint4 C = a.node_c[nd];
                 const float4 E = a.node_e[nd];
@@ -303,7 +327,18 @@ __global__ void __launch_bounds__(kCoopWarps * 32, kCoopMinBlocks) k_density_coo
                 }
                 tests += (unsigned long long)(q1 - q0);
             };
-            coop_walk(sm, B, a.node_c, a.node_e, Xi, sf, wm, [&](float4) { return h; }, leaf, drain);
+            if (rewalk) {
+                if (!conv) {
+                    ncache = 0;
+                    Rw = h * kWalkR;
+                }
+                coop_walk(sm, B, a.node_c, a.node_e, Xi, sf, wm, [&](float4) { return Rw; }, leaf, drain);
+            } else {
+                // the lanes' leaves within their last walk radius, from the list
+                const int mx = warp_max(conv ? 0 : ncache);
+                for (int k = 0; k < mx; ++k) leaf(!conv && k < ncache ? lc[k * 32 + lane] : -1);
+                drain();
+            }
             c_tests += tests;
             if (!conv) {
                 ++c_evals;
@@ -503,7 +538,7 @@ __global__ void __launch_bounds__(kCoopWarps * 32, kCoopMinBlocks) k_force_coop(
 template <typename Kern>
 static cudaError_t coop_launch(sph_ctx* ctx, Kern k, const CoopArgs& args, int bps, int kind, int timed,
                                cudaStream_t s) {
-    const int blocks = ctx->sm_count * (bps > 0 ? bps : kCoopMinBlocks);
+    const int blocks = ctx->sm_count * std::min(bps > 0 ? bps : kCoopMinBlocks, kCoopMaxBps);
     cudaEvent_t ea = nullptr, eb = nullptr;
     if (timed) {
         ea = timing_event(ctx);
@@ -553,6 +588,7 @@ cudaError_t launch_density_coop(sph_ctx* ctx, const DensityLaunch& a, cudaStream
     c.max_iter = a.max_iter;
     c.guess_h = a.guess_h;
     c.fixed_h = a.fixed_h;
+    c.lcache = a.g->lcache;
     return a.hash ? coop_launch(ctx, k_density_coop<true>, c, a.blocks_per_sm, 0, a.time_kernels, s)
                   : coop_launch(ctx, k_density_coop<false>, c, a.blocks_per_sm, 0, a.time_kernels, s);
 }

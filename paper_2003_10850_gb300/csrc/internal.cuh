@@ -71,6 +71,7 @@ struct sph_grid {
     unsigned* v2 = nullptr;
     unsigned* counts = nullptr;
     unsigned* cscan = nullptr;
+    int* lcache = nullptr;                 // cooperative density: leaf lists reused across iterations
     // adjoint scratch (allocated by the first sph_backward on the grid)
     float4* bw_ga = nullptr;
     float4* bw_xbar = nullptr;

@@ -82,7 +82,7 @@ PATHS = ["coop", "thread", "warp"]
 
 
 def _flags(S, path, fp64):
-    extra = {"coop": 0, "thread": S.SPH_PER_THREAD_WALK, "warp": S.SPH_WARP_GROUP}[path]
+    extra = {"coop": S.SPH_COOP_WALK, "thread": S.SPH_PER_THREAD_WALK, "warp": S.SPH_WARP_GROUP}[path]
     return (S.SPH_FP64 if fp64 else 0) | extra
 
 
