@@ -234,6 +234,22 @@ def step_body(S, ctx, wl, dparams, fparams, spans=None):
             spans.append((a, ev()))
 
 
+def kernel_names(S, dflags, fflags):
+    """Names of the density and force kernels that the given path flags select."""
+    def pick(fl, names):
+        if fl & S.SPH_PLAIN_FP32:
+            return names[0]
+        if fl & S.SPH_WARP_GROUP:
+            return names[1]
+        if fl & S.SPH_COOP_WALK:
+            return names[2]
+        if fl & (S.SPH_PER_THREAD_WALK | S.SPH_DENSITY_BUFFERED | S.SPH_FP64):
+            return names[3] if not (fl & S.SPH_DENSITY_BUFFERED) else "k_density_buf"
+        return names[4]
+    return (pick(dflags, ("k_density_plain", "k_density", "k_density_coop", "k_density_tpp<float>", "k_density_wpp")),
+            pick(fflags, ("k_force_plain", "k_force", "k_force_coop", "k_force_mask", "k_force_wpp")))
+
+
 def timed_steps(S, ctx, wl, dparams, fparams, steps, warmup, dist=None):
     """Eager steps, each timed as the sum of its event-bracketed parts."""
     import torch
@@ -487,11 +503,7 @@ def main():
     peak_tf = sm_count * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     dens_f = res["dpairs"] * FLOPS_DENSITY_PAIR
     force_f = res["fpairs"] * FLOPS_FORCE_PAIR
-    if dpar.flags & S.SPH_PER_THREAD_WALK:
-        dname = "k_density_buf" if dpar.flags & S.SPH_DENSITY_BUFFERED else "k_density_tpp<float>"
-    else:
-        dname = "k_density_coop"
-    fname = "k_force_mask" if fpar.flags & S.SPH_PER_THREAD_WALK else "k_force_coop"
+    dname, fname = kernel_names(S, dpar.flags, fpar.flags)
     if res["dens_ms"] >= res["force_ms"]:
         kern, flops, kms, kl = dname, dens_f, res["dens_ms"], res["dens_launches"]
     else:

@@ -58,11 +58,14 @@ typedef enum {
 #define SPH_DENSITY_BUFFERED 0x40 /* density, per-thread walks: iterate h on a per-thread buffer
                                      of the candidates found by one walk at 1.06 h */
 #define SPH_PER_THREAD_WALK 0x80  /* force one thread per particle walking alone */
-#define SPH_COOP_WALK 0x100       /* force the warp-cooperative walk: one warp per 32
-                                     Morton-consecutive active particles, per-lane spheres, shared
-                                     node tests, per-lane compacted leaf lists and hit buffers.
-                                     Default (neither flag): cooperative when >= 5 % of the
-                                     particles are active, per-thread walks below */
+#define SPH_WARP_WALK 0x200       /* one warp per active particle (the default path when no other
+                                     path flag is given): the warp walks for its particle (four
+                                     nodes per step, one child per lane), keeps the leaf list in
+                                     shared memory across h iterations, tests 32 candidates per step
+                                     and evaluates the pair terms from a warp-wide hit buffer */
+#define SPH_COOP_WALK 0x100       /* alternative path: one warp per 32 Morton-consecutive active
+                                     particles, per-lane spheres, shared node tests, per-lane
+                                     compacted leaf lists and hit buffers */
 
 /* Device status bits returned in sph_stats.status */
 #define SPH_ST_NOT_CONVERGED 0x01

@@ -4,8 +4,8 @@ Times a small set of configurations of each pass on the caller's own grid and
 state (CUDA events on the current stream, best of `reps`), picks the fastest
 per pass, and caches the choice per (GPU name, particle count, workload tag)
 in paper_2003_10850_gb300/_build/autotune.json. The knobs are those of
-sph_params: persistent blocks per SM, cooperative versus per-thread walks,
-the density iteration mode of the per-thread walks, and the warp-group path.
+sph_params: persistent blocks per SM and the kernel family (warp per
+particle, warp-cooperative, per-thread walks, and the warp-group path).
 """
 from __future__ import annotations
 
@@ -14,18 +14,19 @@ import os
 
 import torch
 
-from . import (SPH_COOP_WALK, SPH_DENSITY_BUFFERED, SPH_PER_THREAD_WALK, SPH_WARP_GROUP, default_params, sph_density,
+from . import (SPH_COOP_WALK, SPH_PER_THREAD_WALK, SPH_WARP_GROUP, default_params, sph_density,
                sph_hydro_force, sph_sync_status)
 
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
 
-# warp-cooperative walks (default) at several persistent-grid sizes, and the
-# per-thread walks (re-walk or buffered density)
-DENSITY_CANDIDATES = ([dict(flags=0, blocks_per_sm=b) for b in (6, 8, 10)] +
-                      [dict(flags=SPH_PER_THREAD_WALK, blocks_per_sm=16),
-                       dict(flags=SPH_PER_THREAD_WALK | SPH_DENSITY_BUFFERED, blocks_per_sm=16)])
-FORCE_CANDIDATES = ([dict(flags=0, blocks_per_sm=b) for b in (6, 8, 10)] +
-                    [dict(flags=SPH_PER_THREAD_WALK, blocks_per_sm=16)])
+# warp-per-particle walks (the default path, flags 0) at two register budgets,
+# the warp-cooperative walks and the per-thread walks
+DENSITY_CANDIDATES = ([dict(flags=0, blocks_per_sm=b) for b in (6, 8)] +
+                      [dict(flags=SPH_COOP_WALK, blocks_per_sm=10),
+                       dict(flags=SPH_PER_THREAD_WALK, blocks_per_sm=16)])
+FORCE_CANDIDATES = ([dict(flags=0, blocks_per_sm=b) for b in (6, 8)] +
+                    [dict(flags=SPH_COOP_WALK, blocks_per_sm=8),
+                     dict(flags=SPH_PER_THREAD_WALK, blocks_per_sm=16)])
 WARP_CANDIDATE = dict(flags=SPH_WARP_GROUP, blocks_per_sm=4, group_size=32)
 
 

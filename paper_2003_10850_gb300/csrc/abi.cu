@@ -43,17 +43,26 @@ sph_status check_params(sph_ctx* ctx, const sph_params* p) {
         return fail(ctx, SPH_ERR_INVALID, "SPH_WARP_GROUP and SPH_PER_THREAD_WALK are exclusive");
     if ((p->flags & SPH_COOP_WALK) && (p->flags & (SPH_PER_THREAD_WALK | SPH_WARP_GROUP)))
         return fail(ctx, SPH_ERR_INVALID, "SPH_COOP_WALK excludes SPH_PER_THREAD_WALK and SPH_WARP_GROUP");
+    if ((p->flags & SPH_WARP_WALK) &&
+        (p->flags & (SPH_PER_THREAD_WALK | SPH_WARP_GROUP | SPH_COOP_WALK | SPH_PLAIN_FP32 | SPH_FP64 | SPH_DENSITY_BUFFERED)))
+        return fail(ctx, SPH_ERR_INVALID, "SPH_WARP_WALK excludes the other path flags and SPH_FP64");
     return SPH_OK;
 }
 
 int group_size(const sph_params* p) { return p->group_size ? p->group_size : 32; }
 
-// Below 5 % active the Morton-consecutive active particles of a warp lie far
-// apart, the union of their spheres grows towards 32 separate walks, and the
-// per-thread walks are faster (measured on the 10M clustered time bins: the
-// cooperative walk wins at 100 % and 10 %, loses at 1 % and 0.1 %).
-bool sparse_active(const sph_grid* g, const int32_t* active, int64_t na) {
-    return active != nullptr && na * 20 < g->n;
+// Which kernel family runs a density or force call. With no path flag the
+// warp-per-particle kernels run: on the 10M clustered time bins they are the
+// fastest at every active fraction measured (100, 10, 1 and 0.1 %). SPH_FP64
+// selects the per-thread walks in double (or the warp-group path in double
+// with SPH_WARP_GROUP).
+enum class Path { Plain, WarpGroup, Wpp, Coop, Thread };
+Path pick_path(int flags) {
+    if (flags & SPH_PLAIN_FP32) return Path::Plain;
+    if (flags & SPH_WARP_GROUP) return Path::WarpGroup;
+    if (flags & (SPH_PER_THREAD_WALK | SPH_DENSITY_BUFFERED | SPH_FP64)) return Path::Thread;
+    if (flags & SPH_COOP_WALK) return Path::Coop;
+    return Path::Wpp;
 }
 
 sph_status check_active(sph_ctx* ctx, const sph_grid* g, const int32_t* active, int64_t n_active) {
@@ -205,10 +214,8 @@ sph_status sph_density(sph_ctx* ctx, const sph_grid* grid, float* h, const int32
     if (cudaSetDevice(ctx->device)) return fail(ctx, SPH_ERR_CUDA, "cudaSetDevice failed");
     cudaStream_t s = (cudaStream_t)stream;
     sph_grid* g = const_cast<sph_grid*>(grid);  // per-call scratch lives in the grid
-    const bool warp_group = (params->flags & SPH_WARP_GROUP) != 0;
-    const bool per_thread = (params->flags & (SPH_PER_THREAD_WALK | SPH_DENSITY_BUFFERED | SPH_FP64)) != 0 ||
-                            (!(params->flags & SPH_COOP_WALK) && sparse_active(grid, active, na));
-    const bool coop = !warp_group && !per_thread && !(params->flags & SPH_PLAIN_FP32);
+    const Path path = pick_path(params->flags);
+    const bool coop = path == Path::Coop, warp_group = path == Path::WarpGroup;
     grid_active(g, active, n_active, coop ? 32 : group_size(params), warp_group || coop, s);
     DensityLaunch a;
     a.g = g;
@@ -227,10 +234,11 @@ sph_status sph_density(sph_ctx* ctx, const sph_grid* grid, float* h, const int32
     a.blocks_per_sm = params->blocks_per_sm;
     a.time_kernels = (params->flags & SPH_TIME_KERNELS) ? 1 : 0;
     a.buffered = (params->flags & SPH_DENSITY_BUFFERED) ? 1 : 0;
-    cudaError_t e = (params->flags & SPH_PLAIN_FP32) ? run_density_plain(ctx, a, na, s)
-                    : warp_group                       ? launch_density(ctx, a, s)
-                    : coop                             ? launch_density_coop(ctx, a, s)
-                                                       : launch_density_tpp(ctx, a, na, s);
+    cudaError_t e = path == Path::Plain       ? run_density_plain(ctx, a, na, s)
+                    : path == Path::WarpGroup ? launch_density(ctx, a, s)
+                    : path == Path::Wpp       ? launch_density_wpp(ctx, a, na, s)
+                    : path == Path::Coop      ? launch_density_coop(ctx, a, s)
+                                              : launch_density_tpp(ctx, a, na, s);
     if (!e) e = cudaGetLastError();
     if (e) return cuda_fail(ctx, e, "sph_density");
     return SPH_OK;
@@ -252,10 +260,8 @@ sph_status sph_hydro_force(sph_ctx* ctx, const sph_grid* grid, const float* vel,
     if (cudaSetDevice(ctx->device)) return fail(ctx, SPH_ERR_CUDA, "cudaSetDevice failed");
     cudaStream_t s = (cudaStream_t)stream;
     sph_grid* g = const_cast<sph_grid*>(grid);
-    const bool warp_group = (params->flags & SPH_WARP_GROUP) != 0;
-    const bool per_thread = (params->flags & (SPH_PER_THREAD_WALK | SPH_FP64)) != 0 ||
-                            (!(params->flags & SPH_COOP_WALK) && sparse_active(grid, active, na));
-    const bool coop = !warp_group && !per_thread && !(params->flags & SPH_PLAIN_FP32);
+    const Path path = pick_path(params->flags & ~SPH_DENSITY_BUFFERED);
+    const bool coop = path == Path::Coop, warp_group = path == Path::WarpGroup;
     grid_refresh_hmax(g, h, s);
     grid_active(g, active, n_active, coop ? 32 : group_size(params), warp_group || coop, s);
     ForceLaunch a;
@@ -274,10 +280,11 @@ sph_status sph_hydro_force(sph_ctx* ctx, const sph_grid* grid, const float* vel,
     a.fp64 = (params->flags & SPH_FP64) ? 1 : 0;
     a.blocks_per_sm = params->blocks_per_sm;
     a.time_kernels = (params->flags & SPH_TIME_KERNELS) ? 1 : 0;
-    cudaError_t e = (params->flags & SPH_PLAIN_FP32) ? launch_force_plain(ctx, a, na, s)
-                    : warp_group                       ? launch_force(ctx, a, s)
-                    : coop                             ? launch_force_coop(ctx, a, s)
-                                                       : launch_force_tpp(ctx, a, na, s);
+    cudaError_t e = path == Path::Plain       ? launch_force_plain(ctx, a, na, s)
+                    : path == Path::WarpGroup ? launch_force(ctx, a, s)
+                    : path == Path::Wpp       ? launch_force_wpp(ctx, a, na, s)
+                    : path == Path::Coop      ? launch_force_coop(ctx, a, s)
+                                              : launch_force_tpp(ctx, a, na, s);
     if (!e) e = cudaGetLastError();
     if (e) return cuda_fail(ctx, e, "sph_hydro_force");
     return SPH_OK;

@@ -36,6 +36,11 @@ struct BoxDesc {
     int pad;
     int lvl_off[kMaxLev];   // global node index of the box's first node on level k
     int lvl_n[kMaxLev];     // nodes of the box on level k
+    // FP32 forms for kernels that keep FP64 off their per-particle path
+    float sf;               // L / 2^32 (box units per integer step), rounded to FP32
+    float Lf;               // L rounded to FP32
+    float wideL;            // 0.45 L: a leaf whose extent plus radius reaches it takes exact separations
+    float capu;             // smallest float >= 0.5 L (1 - 1e-9), the bound h must stay below
 };
 
 // Active groups of one call: group g covers active-list entries

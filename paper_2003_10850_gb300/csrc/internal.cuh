@@ -48,6 +48,7 @@ struct sph_grid {
     float4* posf = nullptr;                // sorted: leaf-relative position (box units), mass
     float4* fvel = nullptr;                // per force call, sorted: v, h
     float4* fthermo = nullptr;             // per force call, sorted: rho, A, c, 1/h
+    float4* fposh = nullptr;               // per force call, sorted: leaf-relative position, h
     // per-call scratch, sized at build so that calls never allocate
     int32_t* act = nullptr;                // active particles, sorted indices, sorted order
     uint8_t* flag = nullptr;               // n
@@ -162,6 +163,10 @@ cudaError_t run_backward(sph_ctx* ctx, sph_grid* g, const BackwardLaunch& b, cud
 // coop.cu (default path)
 cudaError_t launch_density_coop(sph_ctx* ctx, const DensityLaunch& a, cudaStream_t s);
 cudaError_t launch_force_coop(sph_ctx* ctx, const ForceLaunch& a, cudaStream_t s);
+
+// wpp.cu (one warp per particle)
+cudaError_t launch_density_wpp(sph_ctx* ctx, const DensityLaunch& a, int64_t n_active, cudaStream_t s);
+cudaError_t launch_force_wpp(sph_ctx* ctx, const ForceLaunch& a, int64_t n_active, cudaStream_t s);
 
 // tpp.cu (per-thread walks)
 void force_pack(const sph_grid* g, const float* vel, const float* u, const float* h, const float* rho,

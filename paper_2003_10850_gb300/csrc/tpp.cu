@@ -518,15 +518,17 @@ __global__ void __launch_bounds__(kTppThreads) k_density_buf(TppDensArgs a) {
 // Per-call packed records in sorted order: (v, h) and (rho, A, c, 1/h).
 __global__ void k_force_pack(int n, const int32_t* __restrict__ perm, const float* __restrict__ vel,
                              const float* __restrict__ u, const float* __restrict__ h, const float* __restrict__ rho,
-                             const float* __restrict__ omega, float gam, float4* __restrict__ fvel,
-                             float4* __restrict__ fthermo) {
+                             const float* __restrict__ omega, float gam, const float4* __restrict__ posf,
+                             float4* __restrict__ fvel, float4* __restrict__ fthermo, float4* __restrict__ fposh) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
     const int o = perm[p];
     const float hh = h[o], r = rho[o];
     const float P = (gam - 1.f) * r * u[o];
+    const float4 f = posf[p];
     fvel[p] = make_float4(vel[3 * (size_t)o], vel[3 * (size_t)o + 1], vel[3 * (size_t)o + 2], hh);
     fthermo[p] = make_float4(r, omega[o] * P / (r * r), sqrtf(gam * P / r), 1.f / hh);
+    fposh[p] = make_float4(f.x, f.y, f.z, hh);
 }
 
 struct TppForceArgs {
@@ -906,7 +908,8 @@ cudaError_t launch_density_tpp(sph_ctx* ctx, const DensityLaunch& a, int64_t n_a
 void force_pack(const sph_grid* g, const float* vel, const float* u, const float* h, const float* rho,
                 const float* omega, float gamma, cudaStream_t s) {
     const int n = (int)g->n;
-    k_force_pack<<<(n + 255) / 256, 256, 0, s>>>(n, g->perm, vel, u, h, rho, omega, gamma, g->fvel, g->fthermo);
+    k_force_pack<<<(n + 255) / 256, 256, 0, s>>>(n, g->perm, vel, u, h, rho, omega, gamma, g->posf, g->fvel, g->fthermo,
+                                                 g->fposh);
 }
 
 cudaError_t launch_force_tpp(sph_ctx* ctx, const ForceLaunch& a, int64_t n_active, cudaStream_t s) {

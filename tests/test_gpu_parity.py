@@ -78,11 +78,14 @@ def test_batched_keys_and_sort_exact(S, ctx):
 
 # ---- a4: density ------------------------------------------------------------
 
-PATHS = ["coop", "thread", "warp"]
+PATHS = ["wpp", "coop", "thread", "warp"]
 
 
 def _flags(S, path, fp64):
-    extra = {"coop": S.SPH_COOP_WALK, "thread": S.SPH_PER_THREAD_WALK, "warp": S.SPH_WARP_GROUP}[path]
+    if path == "wpp" and fp64:
+        pytest.skip("the warp-per-particle path is FP32 only (FP64 runs the per-thread walks)")
+    extra = {"wpp": S.SPH_WARP_WALK, "coop": S.SPH_COOP_WALK, "thread": S.SPH_PER_THREAD_WALK,
+             "warp": S.SPH_WARP_GROUP}[path]
     return (S.SPH_FP64 if fp64 else 0) | extra
 
 
