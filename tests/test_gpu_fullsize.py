@@ -1,0 +1,124 @@
+"""GPU parity at the workloads' full sizes, in the launch configuration the
+benchmark times (default path and launch shape, all particles active).
+
+* 2,097,152 clustered particles (200 blobs, seed 2): the oracle solves the
+  density of every particle (a minute of CPU on a many-core host), so h and
+  rho are compared element by element for all 2M particles; the force pass is
+  then run on the oracle's h, rho, Omega (rounded to FP32) and compared with
+  the oracle's force on 4,096 sampled particles, pair sets bit-exact.
+* 10,000,000 clustered particles (500 blobs, seed 3): the oracle evaluates
+  2,048 sampled particles one by one (h, rho, the neighbour set at a fixed h);
+  the force pass over all 10M is checked through properties that hold at any
+  size: total momentum and total energy are conserved by the pairwise
+  antisymmetric force (Sec. 1: the force module; Gadget-2's grad-h form).
+
+Tolerances as in the small-case parity tests: h, rho relative <= 1e-5; acc and
+du/dt <= 1e-4 of the per-particle pair-term scale; neighbour and pair sets
+exact (checksums).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads as W
+from sph_cases import as_f32, check_force, dev, gpu_density, gpu_force, gpu_grid, host, rel
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def S():
+    from paper_2003_10850_gb300 import build
+    build.build()
+    import paper_2003_10850_gb300 as S
+    return S
+
+
+@pytest.fixture(scope="module")
+def ctx(S):
+    return S.Context(0)
+
+
+def _n_ngb_bracket(X, p, h, idx):
+    """Oracle neighbour counts at h (1 -/+ 1e-5) for the particles idx: a GPU
+    h within the 1e-5 tolerance must give a count between the two."""
+    lo = oracle.density(X, p.mass, h * (1 - 1e-5), box=p.box, fixed_h=True, active=idx)["n_ngb"][idx]
+    hi = oracle.density(X, p.mass, h * (1 + 1e-5), box=p.box, fixed_h=True, active=idx)["n_ngb"][idx]
+    return lo, hi
+
+
+def test_fullsize_2M_density_all_and_force_sampled(S, ctx):
+    p = as_f32(W.config2())
+    X = oracle.quantize(p.pos, p.box)
+    d = oracle.density(X, p.mass, None, box=p.box, n_target=64.0, tol=1e-10)
+    assert d["any_status"] == 0
+    params = S.default_params(box=p.box)
+    grid = gpu_grid(S, ctx, p, params)
+    g = gpu_density(S, ctx, grid, np.zeros(p.n, np.float32), params)
+    assert g["rc"] == 0 and not g["flags"].any()
+    assert rel(g["h"], d["h"]).max() <= 1e-5
+    assert rel(g["rho"], d["rho"]).max() <= 1e-5
+    assert rel(g["omega"], d["omega"]).max() <= 1e-4
+    idx = W.sample_indices(p.n, 4096, seed=41)
+    full = np.zeros(p.n, np.float64)
+    full[idx] = d["h"][idx]
+    lo, hi = _n_ngb_bracket(X, p, full, idx)
+    assert np.all((g["n_ngb"][idx] >= lo) & (g["n_ngb"][idx] <= hi))
+    # force on the oracle's density state, all particles active
+    h, rho, om = (d[k].astype(np.float32) for k in ("h", "rho", "omega"))
+    gf = gpu_force(S, ctx, grid, p, h, rho, om, params)
+    assert gf["rc"] == 0
+    f = oracle.force(X, p.vel, p.mass, p.u, h, rho, om, box=p.box, active=idx)
+    check_force(gf, f, idx, 1e-4)
+
+
+def test_fullsize_10M_density_sampled_force_conservation(S, ctx):
+    p = as_f32(W.config3())
+    n = p.n
+    X = oracle.quantize(p.pos, p.box)
+    idx = W.sample_indices(n, 2048, seed=43)
+    d = oracle.density(X, p.mass, None, box=p.box, n_target=64.0, tol=1e-10, active=idx)
+    assert d["any_status"] == 0
+    params = S.default_params(box=p.box)
+    grid = gpu_grid(S, ctx, p, params)
+    # all 10M active from no h guess (the benchmark's first pass)
+    h = torch.zeros(n, device="cuda")
+    out = S.density(ctx, grid, h, None, params)
+    rc, stats = S.sph_sync_status(ctx, raise_on_error=False)
+    assert rc == 0
+    hg, rhog = host(h), host(out["rho"])
+    assert rel(hg[idx], d["h"][idx]).max() <= 1e-5
+    assert rel(rhog[idx], d["rho"][idx]).max() <= 1e-5
+    assert rel(host(out["omega"])[idx], d["omega"][idx]).max() <= 1e-4
+    full = np.zeros(n, np.float64)
+    full[idx] = d["h"][idx]
+    lo, hi = _n_ngb_bracket(X, p, full, idx)
+    nn = host(out["n_ngb"])[idx]
+    assert np.all((nn >= lo) & (nn <= hi))
+    # neighbour sets bit-exact at a fixed h (the oracle's, rounded to FP32)
+    h32 = np.zeros(n, np.float32)
+    h32[idx] = d["h"][idx].astype(np.float32)
+    pf = S.default_params(box=p.box, flags=S.SPH_FIXED_H)
+    gfix = gpu_density(S, ctx, grid, h32, pf, active=idx.astype(np.int32))
+    ofix = oracle.density(X, p.mass, h32.astype(np.float64), box=p.box, fixed_h=True, active=idx)
+    assert np.array_equal(gfix["n_ngb"][idx], ofix["n_ngb"][idx])
+    assert np.array_equal(gfix["hash"][idx], ofix["hash"][idx])
+    # force over all 10M on the GPU's own density state: momentum and energy
+    # are conserved pair by pair, so their totals vanish up to FP32 rounding
+    vel, u = dev(p.vel), dev(p.u)
+    acc = torch.zeros(n, 3, device="cuda")
+    dudt, vsig = torch.zeros(n, device="cuda"), torch.zeros(n, device="cuda")
+    S.sph_hydro_force(ctx, grid, vel, u, h, out["rho"], out["omega"], None, acc, dudt, vsig, None, params)
+    rc, fst = S.sph_sync_status(ctx, raise_on_error=False)
+    assert rc == 0
+    a = host(acc).astype(np.float64)
+    du = host(dudt).astype(np.float64)
+    assert np.all(np.isfinite(a)) and np.all(np.isfinite(du))
+    m = p.mass
+    mom = np.linalg.norm((m[:, None] * a).sum(0))
+    assert mom <= 1e-5 * (m * np.linalg.norm(a, axis=1)).sum()
+    e_terms = m * ((p.vel * a).sum(1) + du)
+    assert abs(e_terms.sum()) <= 1e-5 * np.abs(m * (np.abs(p.vel * a).sum(1) + np.abs(du))).sum()
+    # pair counts: every density neighbour is a force partner (r < h_i)
+    assert fst["force_pairs"] >= stats["density_pairs"]
