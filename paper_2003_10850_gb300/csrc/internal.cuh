@@ -49,6 +49,7 @@ struct sph_grid {
     float4* fvel = nullptr;                // per force call, sorted: v, h
     float4* fthermo = nullptr;             // per force call, sorted: rho, A, c, 1/h
     float4* fposh = nullptr;               // per force call, sorted: leaf-relative position, h
+    float4* fvm = nullptr;                 // per force call, sorted: v, m
     // per-call scratch, sized at build so that calls never allocate
     int32_t* act = nullptr;                // active particles, sorted indices, sorted order
     uint8_t* flag = nullptr;               // n

@@ -515,18 +515,22 @@ __global__ void __launch_bounds__(kTppThreads) k_density_buf(TppDensArgs a) {
 // Force
 // ---------------------------------------------------------------------------
 
-// Per-call packed records in sorted order: (v, h) and (rho, A, c, 1/h).
+// Per-call packed records in sorted order: (v, h), (rho, A, c, 1/h), the
+// leaf-relative position with h, and (v, m).
 __global__ void k_force_pack(int n, const int32_t* __restrict__ perm, const float* __restrict__ vel,
                              const float* __restrict__ u, const float* __restrict__ h, const float* __restrict__ rho,
                              const float* __restrict__ omega, float gam, const float4* __restrict__ posf,
-                             float4* __restrict__ fvel, float4* __restrict__ fthermo, float4* __restrict__ fposh) {
+                             float4* __restrict__ fvel, float4* __restrict__ fthermo, float4* __restrict__ fposh,
+                             float4* __restrict__ fvm) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
     const int o = perm[p];
     const float hh = h[o], r = rho[o];
     const float P = (gam - 1.f) * r * u[o];
     const float4 f = posf[p];
-    fvel[p] = make_float4(vel[3 * (size_t)o], vel[3 * (size_t)o + 1], vel[3 * (size_t)o + 2], hh);
+    const float vx = vel[3 * (size_t)o], vy = vel[3 * (size_t)o + 1], vz = vel[3 * (size_t)o + 2];
+    fvel[p] = make_float4(vx, vy, vz, hh);
+    fvm[p] = make_float4(vx, vy, vz, f.w);
     fthermo[p] = make_float4(r, omega[o] * P / (r * r), sqrtf(gam * P / r), 1.f / hh);
     fposh[p] = make_float4(f.x, f.y, f.z, hh);
 }
@@ -909,7 +913,7 @@ void force_pack(const sph_grid* g, const float* vel, const float* u, const float
                 const float* omega, float gamma, cudaStream_t s) {
     const int n = (int)g->n;
     k_force_pack<<<(n + 255) / 256, 256, 0, s>>>(n, g->perm, vel, u, h, rho, omega, gamma, g->posf, g->fvel, g->fthermo,
-                                                 g->fposh);
+                                                 g->fposh, g->fvm);
 }
 
 cudaError_t launch_force_tpp(sph_ctx* ctx, const ForceLaunch& a, int64_t n_active, cudaStream_t s) {

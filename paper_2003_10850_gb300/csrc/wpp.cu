@@ -37,6 +37,8 @@ constexpr int kWppPop4 = 96;         // pop four nodes per step only while sp <=
 constexpr int kWppLeaves = 128;      // leaf list per warp; a step adds <= 32
 constexpr int kWppHits = 64;         // hit buffer per warp; drained at >= 32
 constexpr int kWppNear = 128;        // density: pairs within the walk radius, kept across h iterations
+constexpr int kWppGrpLeaves = 384;   // leaf list of a group walk, shared by the group's particles
+constexpr int kWppGrpSpan = 64;      // a group never leaves one leaf-parent node (kLeaf * kFan particles)
 constexpr float kWppWalkR = 1.06f;   // density walks at 1.06 h so that later iterations reuse the list
 
 // Stack bound: a pop-4 step starts from sp <= 96 and ends at sp <= 92 + 32 =
@@ -46,6 +48,7 @@ constexpr float kWppWalkR = 1.06f;   // density walks at 1.06 h so that later it
 
 struct WppSmem {
     int stk[kWppStack];
+    int glf[kWppGrpLeaves];  // group walk: leaves within reach of at least one particle of the group
     int lid[kWppLeaves];     // leaf index within the box; bit 31 = "wide" (exact separations)
     float4 lof[kWppLeaves];  // leaf centre - particle (box units), h-independent rounding bound
     union {
@@ -84,6 +87,7 @@ struct WppArgs {
     const float4* fvel;
     const float4* fthermo;
     const float4* fposh;         // per force call: leaf-relative position, h
+    const float4* fvm;           // per force call: v, m
     float* acc;
     float* dudt;
     float* vsig;
@@ -101,19 +105,72 @@ __device__ __forceinline__ int wpp_box(const BoxDesc* boxes, int nb, long long p
     return lo;
 }
 
-// Error-free fold of per-lane compensated sums (value = s - c) across the
-// warp: TwoSum of the two partial sums, the rounding error moved into c.
-// Every lane ends with the same (s, c): both orders of a TwoSum are exact.
-__device__ __forceinline__ void wpp_fold(float& s, float& c) {
+// Error-free (TwoSum) fold of two per-lane sums across the warp: after one
+// exchange lanes 0-15 carry the first and 16-31 the second; every lane ends
+// with both compensated totals (sa - ca, sb - cb). Both orders of a TwoSum
+// are exact, so the result does not depend on which lane adds which.
+__device__ __forceinline__ void wpp_fold2(float a, float b, float& sa, float& ca, float& sb, float& cb) {
+    const unsigned lane = lane_id();
+    const bool lo16 = lane < 16u;
+    float s = lo16 ? a : b, c = 0.f;
+    const float o = __shfl_xor_sync(0xffffffffu, lo16 ? b : a, 16);
+    {
+        const float t = __fadd_rn(s, o);
+        const float bp = __fsub_rn(t, s);
+        c = __fsub_rn(0.f, __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(o, bp)));
+        s = t;
+    }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const float s2 = __shfl_xor_sync(0xffffffffu, s, o), c2 = __shfl_xor_sync(0xffffffffu, c, o);
+    for (int k = 8; k > 0; k >>= 1) {
+        const float s2 = __shfl_xor_sync(0xffffffffu, s, k), c2 = __shfl_xor_sync(0xffffffffu, c, k);
         const float t = __fadd_rn(s, s2);
         const float bp = __fsub_rn(t, s);
         const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(s2, bp));
         s = t;
         c = __fsub_rn(__fadd_rn(c, c2), e);
     }
+    sa = __shfl_sync(0xffffffffu, s, 0);
+    ca = __shfl_sync(0xffffffffu, c, 0);
+    sb = __shfl_sync(0xffffffffu, s, 16);
+    cb = __shfl_sync(0xffffffffu, c, 16);
+}
+
+// The same error-free fold for four per-lane sums at once, halving the
+// values a lane carries at the first two levels (lanes 0-15 keep the first
+// two sums, 16-31 the last two; then each half keeps one). Returns, in lanes
+// 8c..8c+7, sum c as one correctly rounded s - c.
+__device__ __forceinline__ float wpp_fold4(float x, float y, float z, float u) {
+    const unsigned lane = lane_id();
+    auto two_sum = [](float& s, float& c, float s2, float c2) {
+        const float t = __fadd_rn(s, s2);
+        const float bp = __fsub_rn(t, s);
+        const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(s2, bp));
+        s = t;
+        c = __fsub_rn(__fadd_rn(c, c2), e);
+    };
+    const bool lo16 = lane < 16u;
+    // level 16: keep (x, y) or (z, u)
+    float s1 = lo16 ? x : z, s2 = lo16 ? y : u, c1 = 0.f, c2 = 0.f;
+    {
+        const float o1 = __shfl_xor_sync(0xffffffffu, lo16 ? z : x, 16);
+        const float o2 = __shfl_xor_sync(0xffffffffu, lo16 ? u : y, 16);
+        two_sum(s1, c1, o1, 0.f);
+        two_sum(s2, c2, o2, 0.f);
+    }
+    // level 8: keep the first or the second of the pair
+    const bool lo8 = (lane & 8u) == 0u;
+    float s = lo8 ? s1 : s2, c = lo8 ? c1 : c2;
+    {
+        const float os = __shfl_xor_sync(0xffffffffu, lo8 ? s2 : s1, 8);
+        const float oc = __shfl_xor_sync(0xffffffffu, lo8 ? c2 : c1, 8);
+        two_sum(s, c, os, oc);
+    }
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) {
+        const float os = __shfl_xor_sync(0xffffffffu, s, o), oc = __shfl_xor_sync(0xffffffffu, c, o);
+        two_sum(s, c, os, oc);
+    }
+    return __fsub_rn(s, c);
 }
 
 // (h 2^32 / L)^2 in FP64, the right-hand side of the exact neighbour
@@ -208,6 +265,159 @@ __device__ __forceinline__ void wpp_walk(WppSmem& sm, const BoxDesc& B, const ui
     }
 }
 
+// A group: the leading run of the remaining active particles act[t..t1) that
+// lie in the box and the leaf-parent node (kWppGrpSpan sorted particles) of
+// act[t]. Lane l < n holds member l's sorted index in p (other lanes: -1).
+struct WppGroup {
+    int n;
+    int p;
+    int box;
+};
+
+__device__ __forceinline__ WppGroup wpp_group(const BoxDesc* boxes, int nb, const int32_t* act, int t, int t1) {
+    const unsigned lane = lane_id();
+    const int rem = t1 - t;
+    int pl = -1, bl = 0;
+    if ((int)lane < rem) {
+        pl = act[t + lane];
+        if (nb > 1) bl = wpp_box(boxes, nb, pl);
+    }
+    const int p0 = __shfl_sync(0xffffffffu, pl, 0), b0 = __shfl_sync(0xffffffffu, bl, 0);
+    const long long off = boxes[b0].off;
+    const bool same = (int)lane < rem && bl == b0 && (pl - off) / kWppGrpSpan == (p0 - off) / kWppGrpSpan;
+    const unsigned m = __ballot_sync(0xffffffffu, same);
+    WppGroup g;
+    g.n = __ffs(~m) - 1;   // rem <= 8, so ~m has a set bit
+    g.p = (int)lane < g.n ? pl : -1;
+    g.box = b0;
+    return g;
+}
+
+// One walk of the hierarchy for a whole group, whose members' integer
+// positions lie within hx[a] (integer units, per axis) of the integer centre
+// Gc; eg = hx * (L/2^32), rounded up. A node passes when its box comes within
+// radius(E) of the group's box. This holds whenever the node passes the test
+// of any member (wpp_near at that member's position, with a radius no larger
+// than the group's): per axis, a member's periodic offset from the node is at
+// least the group centre's minus hx, in every periodic image. The slack
+// (2^-14 of R plus 2^-20 of the offsets and extents) covers the FP32 rounding
+// of both tests. Leaves go to sm.glf; returns their number, or -1 when they
+// would not fit (the members then walk alone).
+template <class Radius>
+__device__ __forceinline__ int wpp_group_walk(WppSmem& sm, const BoxDesc& B, const uint4* __restrict__ node_c,
+                                              const float4* __restrict__ node_e, uint4 Gc, float egx, float egy,
+                                              float egz, float sf, Radius&& radius) {
+    const unsigned lane = lane_id();
+    const unsigned lt = (1u << lane) - 1u;
+    const float egs = egx + egy + egz;
+    int ngl = 0;
+    if (lane == 0) sm.stk[0] = (B.nlev - 1) << 27;
+    int sp = 1;
+    __syncwarp();
+    while (sp > 0) {
+        if (ngl > kWppGrpLeaves - 32) return -1;
+        const int npop = sp <= kWppPop4 ? min(sp, 4) : 1;
+        const int slot = (int)(lane >> 3), c = (int)(lane & 7u);
+        const int enc = slot < npop ? sm.stk[sp - 1 - slot] : 0;
+        __syncwarp();
+        sp -= npop;
+        const int lev = enc >> 27, t = enc & ((1 << 27) - 1);
+        const int cl = lev - 1, ct = t * kFan + c;
+        const bool ok = slot < npop && ct < B.lvl_n[max(cl, 0)];
+        bool pass = false;
+        if (ok) {
+            const int nd = B.lvl_off[cl] + ct;
+            const uint4 C = node_c[nd];
+            const float4 E = node_e[nd];
+            const float dx = (float)(int)(C.x - Gc.x) * sf, dy = (float)(int)(C.y - Gc.y) * sf,
+                        dz = (float)(int)(C.z - Gc.z) * sf;
+            const float gx = fmaxf(fabsf(dx) - E.x - egx, 0.f), gy = fmaxf(fabsf(dy) - E.y - egy, 0.f),
+                        gz = fmaxf(fabsf(dz) - E.z - egz, 0.f);
+            const float Rt = radius(E) * (1.f + 6.103515625e-05f) +
+                             9.5367431640625e-07f * (fabsf(dx) + fabsf(dy) + fabsf(dz) + E.x + E.y + E.z + egs);
+            pass = gx * gx + gy * gy + gz * gz < Rt * Rt;
+        }
+        const bool isleaf = pass && cl == 0, isint = pass && cl > 0;
+        const unsigned ml = __ballot_sync(0xffffffffu, isleaf);
+        const unsigned mi = __ballot_sync(0xffffffffu, isint);
+        if (isleaf) sm.glf[ngl + __popc(ml & lt)] = ct;
+        if (isint) sm.stk[sp + __popc(mi & lt)] = (cl << 27) | ct;
+        ngl += __popc(ml);
+        sp += __popc(mi);
+        __syncwarp();
+    }
+    return ngl;
+}
+
+// Group geometry from the members' integer positions (lanes with `valid`),
+// then the group walk. Returns -1 (no shared list) when the group spans a
+// quarter of the box or more on some axis.
+template <class Radius>
+__device__ __forceinline__ int wpp_group_leaves(WppSmem& sm, const BoxDesc& B, const uint4* __restrict__ node_c,
+                                                const float4* __restrict__ node_e, uint4 Xl, bool valid, float sf,
+                                                Radius&& radius) {
+    const unsigned X0x = __shfl_sync(0xffffffffu, Xl.x, 0), X0y = __shfl_sync(0xffffffffu, Xl.y, 0),
+                   X0z = __shfl_sync(0xffffffffu, Xl.z, 0);
+    const int dx = valid ? (int)(Xl.x - X0x) : 0, dy = valid ? (int)(Xl.y - X0y) : 0,
+              dz = valid ? (int)(Xl.z - X0z) : 0;
+    const int lox = warp_min(dx), loy = warp_min(dy), loz = warp_min(dz);
+    const long long ex = (long long)warp_max(dx) - lox, ey = (long long)warp_max(dy) - loy,
+                    ez = (long long)warp_max(dz) - loz;
+    if (ex >= (1ll << 30) || ey >= (1ll << 30) || ez >= (1ll << 30)) return -1;
+    uint4 Gc;
+    Gc.x = X0x + (unsigned)(lox + (int)(ex >> 1));
+    Gc.y = X0y + (unsigned)(loy + (int)(ey >> 1));
+    Gc.z = X0z + (unsigned)(loz + (int)(ez >> 1));
+    Gc.w = 0u;
+    const float up = 1.f + 9.5367431640625e-07f;
+    const float egx = (float)((ex + 1) >> 1) * sf * up, egy = (float)((ey + 1) >> 1) * sf * up,
+                egz = (float)((ez + 1) >> 1) * sf * up;
+    return wpp_group_walk(sm, B, node_c, node_e, Gc, egx, egy, egz, sf, radius);
+}
+
+// A member's own leaf list from the group's: the leaves of sm.glf that pass
+// the member's node test, pushed exactly as wpp_walk pushes them (same test,
+// same entries), so the member sees the leaf set of its own walk.
+template <class Radius, class Flush>
+__device__ __forceinline__ void wpp_filter(WppSmem& sm, int ngl, const BoxDesc& B, const uint4* __restrict__ node_c,
+                                           const float4* __restrict__ node_e, uint4 Xi, float sf, int& nlf,
+                                           bool& complete, Radius&& radius, Flush&& flush) {
+    const unsigned lane = lane_id();
+    const unsigned lt = (1u << lane) - 1u;
+    const float rel = 9.5367431640625e-07f;  // 2^-20
+    const float wideL = B.wideL;
+    for (int base = 0; base < ngl; base += 32) {
+        if (nlf > kWppLeaves - 32) {
+            flush();
+            complete = false;
+        }
+        const int k = base + (int)lane;
+        bool pass = false;
+        int ct = 0;
+        float dx = 0.f, dy = 0.f, dz = 0.f;
+        float4 E = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (k < ngl) {
+            ct = sm.glf[k];
+            const int nd = B.lvl_off[0] + ct;
+            const uint4 C = node_c[nd];
+            E = node_e[nd];
+            dx = (float)(int)(C.x - Xi.x) * sf;
+            dy = (float)(int)(C.y - Xi.y) * sf;
+            dz = (float)(int)(C.z - Xi.z) * sf;
+            pass = wpp_near(dx, dy, dz, E, radius(E));
+        }
+        const unsigned ml = __ballot_sync(0xffffffffu, pass);
+        if (pass) {
+            const int li = nlf + __popc(ml & lt);
+            const bool wide = 2.f * (E.x + E.y + E.z) + radius(E) >= wideL;
+            sm.lid[li] = ct | (wide ? (int)0x80000000u : 0);
+            sm.lof[li] = make_float4(dx, dy, dz, rel * (4.f * (E.x + E.y + E.z) + 2.f * (fabsf(dx) + fabsf(dy) + fabsf(dz))));
+        }
+        nlf += __popc(ml);
+        __syncwarp();
+    }
+}
+
 __device__ __forceinline__ float hinv_cube(float h) {
     const float r = 1.f / h;
     return r * r * r;
@@ -260,13 +470,6 @@ __device__ __forceinline__ bool wpp_h_update(float& h, float f, float N, float d
     return true;
 }
 
-// Candidates per lane per step of the candidate loop: the loads of WPP_TILES
-// tiles of 32 are issued before any of them is used.
-#ifndef WPP_TILES
-#define WPP_TILES 1
-#endif
-constexpr int kWppU = WPP_TILES;
-
 // ---------------------------------------------------------------------------
 // Density
 // ---------------------------------------------------------------------------
@@ -287,203 +490,225 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_density_wpp(WppArgs a) {
         t0 = __shfl_sync(0xffffffffu, t0, 0);
         if (t0 >= cnt) break;
         const int t1 = min(t0 + a.chunk, cnt);
-        for (int t = t0; t < t1; ++t) {
-            const int p = a.act[t];
-            const BoxDesc& B = a.boxes[a.n_boxes == 1 ? 0 : wpp_box(a.boxes, a.n_boxes, p)];
+        for (int t = t0; t < t1;) {
+            const WppGroup G = wpp_group(a.boxes, a.n_boxes, a.act, t, t1);
+            t += G.n;
+            const BoxDesc& B = a.boxes[G.box];
             const float sf = B.sf;
             const int off = (int)B.off, pend = (int)(B.off + B.n);
-            const uint4 Xi = a.posm[p];
-            const int oi = a.perm[p];
-            float h = a.h[oi];
-            if (a.guess_h || !(h > 0.f) || !isfinite(h))
-                h = wpp_guess_h(B, a.node_lo, a.node_hi, p, ldexp(B.L, -32), a.n_target);
-            float blo = 0.f, bhi = INFINITY, dold = INFINITY;
-            unsigned st = 0;
-            int nlf = 0, nnear = 0;
-            bool complete = false;   // the leaf list holds every leaf within Rw
-            bool near_ok = false;    // the near list holds every pair within Rw
-            float Rw = 0.f, ebmax = 0.f;
-            // per-lane partial sums (a lane holds ~1/32 of the pairs; the fold
-            // across lanes is error-free, so no per-lane compensation is needed)
-            float Sw, Sdw, Smw, Smdw;
-            int nn;
-            unsigned long long hs;
-            for (int it = 0;; ++it) {
-                Sw = Sdw = Smw = Smdw = 0.f;
-                nn = 0;
-                hs = 0;
-                const float hinv = 1.f / h;
-                double HH = -1.0;
-                int nh = 0;
-                auto exact_in = [&](int q) {
-                    if (HH < 0.0) HH = wpp_hh(h, B.L);
-                    return exact_pred(exact_d2(Xi, a.posm[q]), HH);
-                };
-                auto term = [&](float r2, float m) {
-                    const float qq = (r2 > 0.f ? r2 * rsqrtf(r2) : 0.f) * hinv;
-                    float w, dw;
-                    spline<float>(qq, w, dw);
-                    const float qdw = qq * dw;
-                    Sw += w;
-                    Sdw += qdw;
-                    Smw += m * w;
-                    Smdw += m * qdw;
-                };
-                // fallback evaluation: pair terms of hits [0, k) of the buffer
-                auto drain = [&](int k) {
-                    if ((int)lane < k) term(sm.hit.n.d[lane].x, sm.hit.n.d[lane].y);
-                    __syncwarp();
-                };
-                // Tests the candidates of leaf list entries [0, nlf), 32 per
-                // step. near == false: pairs within h go to the hit buffer and
-                // are evaluated at this h. near == true: pairs within the walk
-                // radius Rw go to the near list (capacity kWppNear).
-                auto process = [&](bool near) {
-                    const float R = near ? Rw : h;
-                    for (int base = 0; base < nlf; base += 4) {
-                        const int li = base + (int)(lane >> 3);
-                        bool in = false;
-                        float r2 = 0.f, m = 0.f;
-                        int q = -1;
-                        if (li < nlf) {
+            // members' start h, one per lane, then one shared walk for the group
+            // (radius: the largest first walk radius of its members)
+            uint4 Xl = make_uint4(0u, 0u, 0u, 0u);
+            int ol = 0;
+            float hl = 0.f;
+            if (G.p >= 0) {
+                Xl = a.posm[G.p];
+                ol = a.perm[G.p];
+                hl = a.h[ol];
+                if (a.guess_h || !(hl > 0.f) || !isfinite(hl))
+                    hl = wpp_guess_h(B, a.node_lo, a.node_hi, G.p, ldexp(B.L, -32), a.n_target);
+            }
+            int ngl = -1;
+            if (G.n >= 2 && B.nlev > 1) {
+                const float Rg = warp_max(a.fixed_h ? hl : hl * kWppWalkR);
+                ngl = wpp_group_leaves(sm, B, a.node_c, a.node_e, Xl, G.p >= 0, sf, [&](float4) { return Rg; });
+            }
+            for (int m = 0; m < G.n; ++m) {
+                const int p = __shfl_sync(0xffffffffu, G.p, m);
+                const uint4 Xi = make_uint4(__shfl_sync(0xffffffffu, Xl.x, m), __shfl_sync(0xffffffffu, Xl.y, m),
+                                            __shfl_sync(0xffffffffu, Xl.z, m), __shfl_sync(0xffffffffu, Xl.w, m));
+                const int oi = __shfl_sync(0xffffffffu, ol, m);
+                float h = __shfl_sync(0xffffffffu, hl, m);
+                bool first = true;   // the first walk takes the group's leaf list
+                float blo = 0.f, bhi = INFINITY, dold = INFINITY;
+                unsigned st = 0;
+                int nlf = 0, nnear = 0;
+                bool complete = false;   // the leaf list holds every leaf within Rw
+                bool near_ok = false;    // the near list holds every pair within Rw
+                float Rw = 0.f, ebmax = 0.f;
+                // per-lane partial sums (a lane holds ~1/32 of the pairs; the fold
+                // across lanes is error-free, so no per-lane compensation is needed)
+                float Sw, Sdw, Smw, Smdw;
+                int nn;
+                unsigned long long hs;
+                for (int it = 0;; ++it) {
+                    Sw = Sdw = Smw = Smdw = 0.f;
+                    nn = 0;
+                    hs = 0;
+                    const float hinv = 1.f / h;
+                    double HH = -1.0;
+                    int nh = 0;
+                    auto exact_in = [&](int q) {
+                        if (HH < 0.0) HH = wpp_hh(h, B.L);
+                        return exact_pred(exact_d2(Xi, a.posm[q]), HH);
+                    };
+                    auto term = [&](float r2, float m) {
+                        const float qq = (r2 > 0.f ? r2 * rsqrtf(r2) : 0.f) * hinv;
+                        float w, dw;
+                        spline<float>(qq, w, dw);
+                        const float qdw = qq * dw;
+                        Sw += w;
+                        Sdw += qdw;
+                        Smw += m * w;
+                        Smdw += m * qdw;
+                    };
+                    // fallback evaluation: pair terms of hits [0, k) of the buffer
+                    auto drain = [&](int k) {
+                        __syncwarp();
+                        if ((int)lane < k) term(sm.hit.n.d[lane].x, sm.hit.n.d[lane].y);
+                        __syncwarp();
+                    };
+                    // Tests the candidates of leaf list entries [0, nlf), 32 per
+                    // step. near == false: pairs within h go to the hit buffer and
+                    // are evaluated at this h. near == true: pairs within the walk
+                    // radius Rw go to the near list (capacity kWppNear).
+                    auto process = [&](bool near) {
+                        const float R = near ? Rw : h;
+                        for (int base = 0; base < nlf; base += 4) {
+                            // li <= 127 < kWppLeaves: entries past nlf are stale but in
+                            // bounds; lanes without a candidate read particle p itself
+                            const int li = base + (int)(lane >> 3);
                             const int id = sm.lid[li];
                             const float4 o = sm.lof[li];
-                            q = off + (id & 0x7fffffff) * kLeaf + (int)(lane & 7u);
-                            if (q < pend) {
-                                float dx, dy, dz;
-                                if (id >= 0) {
-                                    const float4 f = __ldg(a.posf + q);
-                                    dx = o.x + f.x; dy = o.y + f.y; dz = o.z + f.z; m = f.w;
-                                } else {
+                            const int qq = off + (id & 0x7fffffff) * kLeaf + (int)(lane & 7u);
+                            const bool cand = li < nlf && qq < pend;
+                            const int q = cand ? qq : p;
+                            const float4 f = __ldg(a.posf + q);
+                            float dx = o.x + f.x, dy = o.y + f.y, dz = o.z + f.z, m = f.w;
+                            if (__any_sync(0xffffffffu, cand && id < 0)) {
+                                if (cand && id < 0) {   // wide leaf: exact integer separations
                                     const uint4 Xj = a.posm[q];
-                                    dx = (float)(int)(Xj.x - Xi.x) * sf; dy = (float)(int)(Xj.y - Xi.y) * sf;
-                                    dz = (float)(int)(Xj.z - Xi.z) * sf; m = __uint_as_float(Xj.w);
+                                    dx = (float)(int)(Xj.x - Xi.x) * sf;
+                                    dy = (float)(int)(Xj.y - Xi.y) * sf;
+                                    dz = (float)(int)(Xj.z - Xi.z) * sf;
+                                    m = __uint_as_float(Xj.w);
                                 }
-                                r2 = dx * dx + dy * dy + dz * dz;
-                                const float eL = o.w + 2.f * rel * R;
-                                const float hi2 = (R + eL) * (R + eL) * (1.f + 4.f * rel);
-                                if (r2 < hi2) {
-                                    if (near) {
-                                        in = true;   // kept: the exact test at h is made when evaluating
-                                    } else {
-                                        const float lo2 = R > eL ? (R - eL) * (R - eL) * (1.f - 4.f * rel) : 0.f;
-                                        in = r2 < lo2 || exact_in(q);
+                            }
+                            const float r2 = dx * dx + dy * dy + dz * dz;
+                            const float eL = o.w + 2.f * rel * R;
+                            const float tR = R + eL;
+                            bool in = cand && r2 < tR * tR * (1.f + 4.f * rel);
+                            if (!near) {
+                                // kept pairs of the near list take the exact test when evaluated
+                                const float sR = fmaxf(R - eL, 0.f);
+                                const bool band = in && !(r2 < sR * sR * (1.f - 4.f * rel));
+                                if (__any_sync(0xffffffffu, band)) {
+                                    if (band) in = exact_in(q);
+                                }
+                            }
+                            c_tests += __popc(__ballot_sync(0xffffffffu, cand));
+                            const unsigned hm = __ballot_sync(0xffffffffu, in);
+                            if (near) {
+                                if (in) {
+                                    const int k = nnear + __popc(hm & lt);
+                                    if (k < kWppNear) {
+                                        sm.hit.n.d[k] = make_float2(r2, m);
+                                        sm.hit.n.j[k] = q;
                                     }
                                 }
-                                ++c_tests;
-                            } else {
-                                q = -1;
+                                nnear += __popc(hm);
+                                continue;
                             }
-                        }
-                        const unsigned hm = __ballot_sync(0xffffffffu, in);
-                        if (near) {
                             if (in) {
-                                const int k = nnear + __popc(hm & lt);
-                                if (k < kWppNear) {
-                                    sm.hit.n.d[k] = make_float2(r2, m);
-                                    sm.hit.n.j[k] = q;
-                                }
-                            }
-                            nnear += __popc(hm);
-                            continue;
-                        }
-                        if (in) {
-                            sm.hit.n.d[nh + __popc(hm & lt)] = make_float2(r2, m);
-                            if (q != p) {
-                                ++nn;
-                                if (HASH) hs += splitmix64((unsigned long long)a.perm[q]);
-                            }
-                        }
-                        nh += __popc(hm);
-                        __syncwarp();
-                        if (nh >= 32) {
-                            drain(32);
-                            nh -= 32;
-                            if ((int)lane < nh) sm.hit.n.d[lane] = sm.hit.n.d[32 + lane];
-                            __syncwarp();
-                        }
-                    }
-                    __syncwarp();
-                };
-                const bool rewalk = !complete || !(h <= Rw * 0.99999f);
-                if (rewalk) {
-                    Rw = a.fixed_h ? h : h * kWppWalkR;
-                    nlf = 0;
-                    nnear = 0;
-                    complete = true;
-                    // a walk that overflows the leaf list evaluates its leaves at h as it goes
-                    wpp_walk(sm, B, a.node_c, a.node_e, Xi, sf, nlf, complete, [&](float4) { return Rw; },
-                             [&]() { process(false); nlf = 0; });
-                    near_ok = false;
-                    if (complete) {
-                        float eb = 0.f;
-                        for (int k = (int)lane; k < nlf; k += 32) eb = fmaxf(eb, sm.lof[k].w);
-                        ebmax = warp_max(eb);
-                        process(true);
-                        near_ok = nnear <= kWppNear;
-                    }
-                }
-                if (near_ok) {
-                    // every pair within Rw is in the near list: the exact test at h
-                    const float eL = ebmax + 2.f * rel * h;
-                    const float hi2 = (h + eL) * (h + eL) * (1.f + 4.f * rel);
-                    const float lo2 = h > eL ? (h - eL) * (h - eL) * (1.f - 4.f * rel) : 0.f;
-                    for (int k = (int)lane; k < nnear; k += 32) {
-                        const float2 e = sm.hit.n.d[k];
-                        if (e.x < hi2) {
-                            const int q = sm.hit.n.j[k];
-                            if (e.x < lo2 || exact_in(q)) {
-                                term(e.x, e.y);
+                                sm.hit.n.d[nh + __popc(hm & lt)] = make_float2(r2, m);
                                 if (q != p) {
                                     ++nn;
                                     if (HASH) hs += splitmix64((unsigned long long)a.perm[q]);
                                 }
                             }
+                            nh += __popc(hm);
+                            if (nh >= 32) {
+                                drain(32);
+                                nh -= 32;
+                                if ((int)lane < nh) sm.hit.n.d[lane] = sm.hit.n.d[32 + lane];
+                                __syncwarp();
+                            }
+                        }
+                        __syncwarp();
+                    };
+                    const bool rewalk = !complete || !(h <= Rw * 0.99999f);
+                    if (rewalk) {
+                        Rw = a.fixed_h ? h : h * kWppWalkR;
+                        nlf = 0;
+                        nnear = 0;
+                        complete = true;
+                        // a walk that overflows the leaf list evaluates its leaves at h as it goes
+                        if (first && ngl >= 0)
+                            wpp_filter(sm, ngl, B, a.node_c, a.node_e, Xi, sf, nlf, complete,
+                                       [&](float4) { return Rw; }, [&]() { process(false); nlf = 0; });
+                        else
+                            wpp_walk(sm, B, a.node_c, a.node_e, Xi, sf, nlf, complete, [&](float4) { return Rw; },
+                                     [&]() { process(false); nlf = 0; });
+                        first = false;
+                        near_ok = false;
+                        if (complete) {
+                            float eb = 0.f;
+                            for (int k = (int)lane; k < nlf; k += 32) eb = fmaxf(eb, sm.lof[k].w);
+                            ebmax = warp_max(eb);
+                            process(true);
+                            near_ok = nnear <= kWppNear;
                         }
                     }
-                } else {
-                    process(false);
-                    drain(nh);
+                    if (near_ok) {
+                        // every pair within Rw is in the near list: the exact test at h
+                        const float eL = ebmax + 2.f * rel * h;
+                        const float hi2 = (h + eL) * (h + eL) * (1.f + 4.f * rel);
+                        const float lo2 = h > eL ? (h - eL) * (h - eL) * (1.f - 4.f * rel) : 0.f;
+                        for (int k = (int)lane; k < nnear; k += 32) {
+                            const float2 e = sm.hit.n.d[k];
+                            if (e.x < hi2) {
+                                const int q = sm.hit.n.j[k];
+                                if (e.x < lo2 || exact_in(q)) {
+                                    term(e.x, e.y);
+                                    if (q != p) {
+                                        ++nn;
+                                        if (HASH) hs += splitmix64((unsigned long long)a.perm[q]);
+                                    }
+                                }
+                            }
+                        }
+                    } else {
+                        process(false);
+                        drain(nh);
+                    }
+                    ++c_evals;
+                    float Cw, Cdw;
+                    wpp_fold2(Sw, Sdw, Sw, Cw, Sdw, Cdw);
+                    // 3 (N_eff - N_t) = (32 S - 3 N_t) - 32 C: the scalings by 32 are exact
+                    const float f3 = __fsub_rn(__fsub_rn(32.f * Sw, nt3), 32.f * Cw);
+                    bool done = false;
+                    if (a.fixed_h || fabsf(f3) <= tol3) {
+                        done = true;
+                    } else if (it >= a.max_iter) {
+                        done = true;
+                        st |= ST_NOT_CONVERGED;
+                    } else {
+                        const float N = (32.f / 3.f) * __fsub_rn(Sw, Cw);
+                        const float dN = -(32.f / 3.f) * __fsub_rn(Sdw, Cdw) / h;
+                        if (!wpp_h_update(h, f3, N, dN, nt, B.capu, blo, bhi, dold, st)) done = true;
+                    }
+                    if (done) break;
                 }
-                ++c_evals;
-                float Cw = 0.f, Cdw = 0.f;
-                wpp_fold(Sw, Cw);
-                wpp_fold(Sdw, Cdw);
-                // 3 (N_eff - N_t) = (32 S - 3 N_t) - 32 C: the scalings by 32 are exact
-                const float f3 = __fsub_rn(__fsub_rn(32.f * Sw, nt3), 32.f * Cw);
-                bool done = false;
-                if (a.fixed_h || fabsf(f3) <= tol3) {
-                    done = true;
-                } else if (it >= a.max_iter) {
-                    done = true;
-                    st |= ST_NOT_CONVERGED;
-                } else {
-                    const float N = (32.f / 3.f) * __fsub_rn(Sw, Cw);
-                    const float dN = -(32.f / 3.f) * __fsub_rn(Sdw, Cdw) / h;
-                    if (!wpp_h_update(h, f3, N, dN, nt, B.capu, blo, bhi, dold, st)) done = true;
+                float Cmw, Cmdw;
+                wpp_fold2(Smw, Smdw, Smw, Cmw, Smdw, Cmdw);
+                nn = warp_sum(nn);
+                if (HASH) hs = warp_sum(hs);
+                if (lane == 0) {
+                    const float smw = __fsub_rn(Smw, Cmw), smdw = __fsub_rn(Smdw, Cmdw);
+                    a.h[oi] = h;
+                    a.rho[oi] = 2.5464790894703255f * smw * hinv_cube(h);   // 8/(pi h^3) sum m w
+                    a.omega[oi] = smdw != 0.f ? -3.f * smw / smdw : 1.f;
+                    a.n_ngb[oi] = nn;
+                    a.flags[oi] = (uint8_t)st;
+                    if (HASH) a.hash[oi] = hs;
+                    c_pairs += (unsigned)nn;
+                    c_status |= st;
                 }
-                if (done) break;
+                __syncwarp();
             }
-            float Cmw = 0.f, Cmdw = 0.f;
-            wpp_fold(Smw, Cmw);
-            wpp_fold(Smdw, Cmdw);
-            nn = warp_sum(nn);
-            if (HASH) hs = warp_sum(hs);
-            if (lane == 0) {
-                const float smw = __fsub_rn(Smw, Cmw), smdw = __fsub_rn(Smdw, Cmdw);
-                a.h[oi] = h;
-                a.rho[oi] = 2.5464790894703255f * smw * hinv_cube(h);   // 8/(pi h^3) sum m w
-                a.omega[oi] = smdw != 0.f ? -3.f * smw / smdw : 1.f;
-                a.n_ngb[oi] = nn;
-                a.flags[oi] = (uint8_t)st;
-                if (HASH) a.hash[oi] = hs;
-                c_pairs += (unsigned)nn;
-                c_status |= st;
-            }
-            __syncwarp();
         }
     }
-    const unsigned long long all_tests = warp_sum((unsigned long long)c_tests);
+    const unsigned long long all_tests = c_tests;   // counted warp-uniformly
     if (lane == 0) {
         atomicAdd(&a.ctr->density_pairs, (unsigned long long)c_pairs);
         atomicAdd(&a.ctr->density_evals, (unsigned long long)c_evals);
@@ -514,113 +739,131 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_force_wpp(WppArgs a) {
         t0 = __shfl_sync(0xffffffffu, t0, 0);
         if (t0 >= cnt) break;
         const int t1 = min(t0 + a.chunk, cnt);
-        for (int t = t0; t < t1; ++t) {
-            const int p = a.act[t];
-            const BoxDesc& B = a.boxes[a.n_boxes == 1 ? 0 : wpp_box(a.boxes, a.n_boxes, p)];
+        for (int t = t0; t < t1;) {
+            const WppGroup G = wpp_group(a.boxes, a.n_boxes, a.act, t, t1);
+            t += G.n;
+            const BoxDesc& B = a.boxes[G.box];
             const float sf = B.sf;
             const int off = (int)B.off, pend = (int)(B.off + B.n);
-            const uint4 Xi = a.posm[p];
-            const int oi = a.perm[p];
-            const float4 vi = a.fvel[p];
-            const float4 thi = a.fthermo[p];
-            const float hi = vi.w, hinvi = thi.w, rhoi = thi.x, Ai = thi.y, ci = thi.z;
-            const float normi = kNorm * hinvi * hinvi * hinvi * hinvi;
-            double HHi = -1.0;
-            float Sx = 0.f, Sy = 0.f, Sz = 0.f, Su = 0.f, vsmax = 0.f;   // per-lane partial sums
-            int np = 0, nh = 0, nlf = 0;
-            unsigned tests = 0;
-            bool complete = true;
-            unsigned long long hs = 0;
-            auto drain = [&](int k) {
-                if ((int)lane < k) {
-                    const float4 e = sm.hit.f[lane];
-                    const int q = __float_as_int(e.w);
-                    const float dx = e.x, dy = e.y, dz = e.z;
-                    const float r2 = dx * dx + dy * dy + dz * dz;
-                    const float4 vj = __ldg(a.fvel + q);
-                    const float4 thj = __ldg(a.fthermo + q);
-                    const float mj = __ldg(&a.posf[q].w);
-                    if (r2 <= 0.f) {  // coincident: no direction, no force
-                        vsmax = fmaxf(vsmax, ci + thj.z);
-                    } else {
-                        const float rinv = rsqrtf(r2), r = r2 * rinv;
-                        float w_, dwi, dwj;
-                        spline<float>(r * hinvi, w_, dwi);
-                        spline<float>(r * thj.w, w_, dwj);
-                        const float hinvj = thj.w;
-                        const float Fi = normi * dwi * rinv;
-                        const float Fj = kNorm * hinvj * hinvj * hinvj * hinvj * dwj * rinv;
-                        const float vr = -((vi.x - vj.x) * dx + (vi.y - vj.y) * dy + (vi.z - vj.z) * dz);
-                        const float wij = vr * rinv;
-                        const float vs = ci + thj.z - 3.f * wij;
-                        vsmax = fmaxf(vsmax, vs);
-                        const float PI = wij < 0.f ? -alpha * vs * wij / (rhoi + thj.x) : 0.f;
-                        const float Fbar = 0.5f * (Fi + Fj);
-                        const float coef = mj * (Ai * Fi + thj.y * Fj + PI * Fbar);
-                        Sx += coef * dx;
-                        Sy += coef * dy;
-                        Sz += coef * dz;
-                        Su += mj * vr * (Ai * Fi + 0.5f * PI * Fbar);
-                    }
-                }
-                __syncwarp();
-            };
-            auto process = [&]() {
-                for (int base = 0; base < nlf; base += 4 * kWppU) {
-                    int q[kWppU], id[kWppU];
-                    float4 o[kWppU], f[kWppU];
-#pragma unroll
-                    for (int u = 0; u < kWppU; ++u) {
-                        const int li = base + 4 * u + (int)(lane >> 3);
-                        q[u] = -1;
-                        id[u] = 0;
-                        if (li < nlf) {
-                            id[u] = sm.lid[li];
-                            o[u] = sm.lof[li];
-                            const int qq = off + (id[u] & 0x7fffffff) * kLeaf + (int)(lane & 7u);
-                            if (qq < pend) {
-                                q[u] = qq;
-                                ++tests;
-                            }
+            // one shared walk for the group (radius: the largest member h)
+            uint4 Xl = make_uint4(0u, 0u, 0u, 0u);
+            float hl = 0.f;
+            if (G.p >= 0) {
+                Xl = a.posm[G.p];
+                hl = a.fvel[G.p].w;
+            }
+            int ngl = -1;
+            if (G.n >= 2 && B.nlev > 1) {
+                const float hg = warp_max(hl);
+                ngl = wpp_group_leaves(sm, B, a.node_c, a.node_e, Xl, G.p >= 0, sf,
+                                       [&](float4 e) { return fmaxf(hg, e.w); });
+            }
+            for (int m = 0; m < G.n; ++m) {
+                const int p = __shfl_sync(0xffffffffu, G.p, m);
+                const uint4 Xi = make_uint4(__shfl_sync(0xffffffffu, Xl.x, m), __shfl_sync(0xffffffffu, Xl.y, m),
+                                            __shfl_sync(0xffffffffu, Xl.z, m), __shfl_sync(0xffffffffu, Xl.w, m));
+                const float hi = __shfl_sync(0xffffffffu, hl, m);
+                const int oi = a.perm[p];
+                const float4 vi = a.fvm[p];
+                const float4 thi = a.fthermo[p];
+                const float hinvi = thi.w, rhoi = thi.x, Ai = thi.y, ci = thi.z;
+                const float normi = kNorm * hinvi * hinvi * hinvi * hinvi;
+                // i side of the band test: h_i (1 +- 2^-19) (the leaf's rounding bound is added per leaf)
+                const float hiP = hi * (1.f + 2.f * rel), hiM = hi * (1.f - 2.f * rel);
+                double HHi = -1.0;
+                float Sx = 0.f, Sy = 0.f, Sz = 0.f, Su = 0.f, vsmax = 0.f;   // per-lane partial sums
+                int np = 0, nh = 0, nlf = 0;
+                unsigned tests = 0;
+                bool complete = true;
+                unsigned long long hs = 0;
+                // pair terms of hit-buffer entries [0, k), one per lane
+                auto drain = [&](int k) {
+                    __syncwarp();
+                    if ((int)lane < k) {
+                        const float4 e = sm.hit.f[lane];
+                        const int q = __float_as_int(e.w);
+                        const float dx = e.x, dy = e.y, dz = e.z;
+                        const float r2 = dx * dx + dy * dy + dz * dz;
+                        const float4 vj = __ldg(a.fvm + q);
+                        const float4 thj = __ldg(a.fthermo + q);
+                        if (r2 <= 0.f) {  // coincident: no direction, no force
+                            vsmax = fmaxf(vsmax, ci + thj.z);
+                        } else {
+                            const float rinv = rsqrtf(r2), r = r2 * rinv;
+                            float w_, dwi, dwj;
+                            spline<float>(r * hinvi, w_, dwi);
+                            spline<float>(r * thj.w, w_, dwj);
+                            const float hinvj = thj.w;
+                            const float Fi = normi * dwi * rinv;
+                            const float Fj = kNorm * hinvj * hinvj * hinvj * hinvj * dwj * rinv;
+                            const float vr = -((vi.x - vj.x) * dx + (vi.y - vj.y) * dy + (vi.z - vj.z) * dz);
+                            const float wij = vr * rinv;
+                            const float vs = ci + thj.z - 3.f * wij;
+                            vsmax = fmaxf(vsmax, vs);
+                            // Pi_ij = -(alpha/2) v_sig w_ij / rho_bar, rho_bar = (rho_i + rho_j)/2
+                            const float PI = wij < 0.f ? __fdividef(-alpha * vs * wij, rhoi + thj.x) : 0.f;
+                            const float Fbar = 0.5f * (Fi + Fj);
+                            const float mj = vj.w;
+                            const float coef = mj * (Ai * Fi + thj.y * Fj + PI * Fbar);
+                            Sx += coef * dx;
+                            Sy += coef * dy;
+                            Sz += coef * dz;
+                            Su += mj * vr * (Ai * Fi + 0.5f * PI * Fbar);
                         }
                     }
-#pragma unroll
-                    for (int u = 0; u < kWppU; ++u)
-                        if (q[u] >= 0) f[u] = __ldg(a.fposh + q[u]);
-#pragma unroll
-                    for (int u = 0; u < kWppU; ++u) {
-                        bool in = false;
-                        float dx = 0.f, dy = 0.f, dz = 0.f;
-                        if (q[u] >= 0 && q[u] != p) {
-                            const float hj = f[u].w;
-                            if (id[u] >= 0) {
-                                dx = o[u].x + f[u].x; dy = o[u].y + f[u].y; dz = o[u].z + f[u].z;
-                            } else {
-                                const uint4 Xj = a.posm[q[u]];
-                                dx = (float)(int)(Xj.x - Xi.x) * sf; dy = (float)(int)(Xj.y - Xi.y) * sf;
+                    __syncwarp();
+                };
+                // Tests the candidates of leaf list entries [0, nlf), 32 per step
+                // (lanes 8k..8k+7: the particles of the step's k-th leaf). A pair
+                // is in the set when r < h_i or r < h_j; r^2 is tested in FP32
+                // against each radius widened and narrowed by the leaf's rounding
+                // bound, and only pairs inside that thin band take the exact
+                // integer/FP64 predicate.
+                auto process = [&]() {
+                    for (int base = 0; base < nlf; base += 4) {
+                        // li <= 127 < kWppLeaves: entries past nlf are stale but in
+                        // bounds; lanes without a candidate read particle p itself
+                        const int li = base + (int)(lane >> 3);
+                        const int id = sm.lid[li];
+                        const float4 o = sm.lof[li];
+                        const int qq = off + (id & 0x7fffffff) * kLeaf + (int)(lane & 7u);
+                        const bool cand = li < nlf && qq < pend;
+                        const int q = cand ? qq : p;
+                        const bool ok = cand && q != p;
+                        const float4 f = __ldg(a.fposh + q);
+                        float dx = o.x + f.x, dy = o.y + f.y, dz = o.z + f.z;
+                        if (__any_sync(0xffffffffu, ok && id < 0)) {
+                            if (ok && id < 0) {   // wide leaf: exact integer separations
+                                const uint4 Xj = a.posm[q];
+                                dx = (float)(int)(Xj.x - Xi.x) * sf;
+                                dy = (float)(int)(Xj.y - Xi.y) * sf;
                                 dz = (float)(int)(Xj.z - Xi.z) * sf;
                             }
-                            const float r2 = dx * dx + dy * dy + dz * dz;
-                            const float ei = o[u].w + 2.f * rel * hi, ej = o[u].w + 2.f * rel * hj;
-                            const bool mi = r2 < (hi + ei) * (hi + ei) * ehi, mjb = r2 < (hj + ej) * (hj + ej) * ehi;
-                            if (mi || mjb) {
-                                in = r2 < (hi > ei ? (hi - ei) * (hi - ei) * elo : 0.f) ||
-                                     r2 < (hj > ej ? (hj - ej) * (hj - ej) * elo : 0.f);
-                                if (!in) {
-                                    const unsigned long long D2 = exact_d2(Xi, a.posm[q[u]]);
+                        }
+                        const float r2 = dx * dx + dy * dy + dz * dz;
+                        const float si = fmaxf(hiM - o.w, 0.f), sj = fmaxf(fmaf(f.w, 1.f - 2.f * rel, -o.w), 0.f);
+                        bool in = ok && (r2 < si * si * elo || r2 < sj * sj * elo);
+                        const float ti = hiP + o.w, tj = fmaf(f.w, 1.f + 2.f * rel, o.w);
+                        const bool mi = r2 < ti * ti * ehi, mj = r2 < tj * tj * ehi;
+                        const bool band = ok && !in && (mi || mj);
+                        if (__any_sync(0xffffffffu, band)) {
+                            if (band) {
+                                const unsigned long long D2 = exact_d2(Xi, a.posm[q]);
+                                if (mi) {
                                     if (HHi < 0.0) HHi = wpp_hh(hi, B.L);
-                                    in = (mi && exact_pred(D2, HHi)) || (mjb && exact_pred(D2, wpp_hh(hj, B.L)));
+                                    in = exact_pred(D2, HHi);
                                 }
+                                if (!in && mj) in = exact_pred(D2, wpp_hh(f.w, B.L));
                             }
                         }
+                        tests += __popc(__ballot_sync(0xffffffffu, cand));
                         const unsigned hm = __ballot_sync(0xffffffffu, in);
                         if (in) {
-                            sm.hit.f[nh + __popc(hm & lt)] = make_float4(dx, dy, dz, __int_as_float(q[u]));
-                            ++np;
-                            if (HASH) hs += splitmix64((unsigned long long)a.perm[q[u]]);
+                            sm.hit.f[nh + __popc(hm & lt)] = make_float4(dx, dy, dz, __int_as_float(q));
+                            if (HASH) hs += splitmix64((unsigned long long)a.perm[q]);
                         }
+                        np += __popc(hm);
                         nh += __popc(hm);
-                        __syncwarp();
                         if (nh >= 32) {
                             drain(32);
                             nh -= 32;
@@ -628,33 +871,33 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_force_wpp(WppArgs a) {
                             __syncwarp();
                         }
                     }
+                };
+                if (ngl >= 0)
+                    wpp_filter(sm, ngl, B, a.node_c, a.node_e, Xi, sf, nlf, complete,
+                               [&](float4 e) { return fmaxf(hi, e.w); }, [&]() { process(); nlf = 0; });
+                else
+                    wpp_walk(sm, B, a.node_c, a.node_e, Xi, sf, nlf, complete, [&](float4 e) { return fmaxf(hi, e.w); },
+                             [&]() { process(); nlf = 0; });
+                process();
+                drain(nh);
+                // fold the per-lane sums: lanes 0-7 end with acc.x, 8-15 acc.y,
+                // 16-23 acc.z, 24-31 du/dt
+                const float fs = wpp_fold4(Sx, Sy, Sz, Su);
+                vsmax = warp_max(vsmax);
+                if (HASH) hs = warp_sum(hs);
+                if ((lane & 7u) == 0u) {
+                    const int comp = (int)(lane >> 3);
+                    if (comp < 3) a.acc[3 * (size_t)oi + comp] = fs;
+                    else a.dudt[oi] = fs;
                 }
-            };
-            wpp_walk(sm, B, a.node_c, a.node_e, Xi, sf, nlf, complete, [&](float4 e) { return fmaxf(hi, e.w); },
-                     [&]() { process(); nlf = 0; });
-            process();
-            drain(nh);
-            float Cx = 0.f, Cy = 0.f, Cz = 0.f, Cu = 0.f;
-            wpp_fold(Sx, Cx);
-            wpp_fold(Sy, Cy);
-            wpp_fold(Sz, Cz);
-            wpp_fold(Su, Cu);
-            vsmax = warp_max(vsmax);
-            np = warp_sum(np);
-            if (HASH) hs = warp_sum(hs);
-            tests = warp_sum(tests);
-            if (lane == 0) {
-                // each compensated pair folds with one correctly rounded subtraction
-                a.acc[3 * (size_t)oi] = __fsub_rn(Sx, Cx);
-                a.acc[3 * (size_t)oi + 1] = __fsub_rn(Sy, Cy);
-                a.acc[3 * (size_t)oi + 2] = __fsub_rn(Sz, Cz);
-                a.dudt[oi] = __fsub_rn(Su, Cu);
-                a.vsig[oi] = vsmax;
-                if (HASH) a.hash[oi] = hs;
-                c_pairs += (unsigned long long)np;
-                c_tests += tests;
+                if (lane == 0) {
+                    a.vsig[oi] = vsmax;
+                    if (HASH) a.hash[oi] = hs;
+                    c_pairs += (unsigned long long)np;
+                    c_tests += tests;
+                }
+                __syncwarp();
             }
-            __syncwarp();
         }
     }
     if (lane == 0) {
@@ -753,6 +996,7 @@ cudaError_t launch_force_wpp(sph_ctx* ctx, const ForceLaunch& a, int64_t n_activ
     c.fvel = a.g->fvel;
     c.fthermo = a.g->fthermo;
     c.fposh = a.g->fposh;
+    c.fvm = a.g->fvm;
     c.acc = a.acc;
     c.dudt = a.dudt;
     c.vsig = a.vsig;
