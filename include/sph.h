@@ -66,6 +66,9 @@ typedef enum {
 #define SPH_COOP_WALK 0x100       /* alternative path: one warp per 32 Morton-consecutive active
                                      particles, per-lane spheres, shared node tests, per-lane
                                      compacted leaf lists and hit buffers */
+#define SPH_NO_LISTS 0x400        /* sph_build_grid: do not allocate the neighbour lists that the
+                                     default path records in an all-active density pass and reuses
+                                     in the force pass (saves ~790 bytes per particle) */
 
 /* Device status bits returned in sph_stats.status */
 #define SPH_ST_NOT_CONVERGED 0x01
@@ -187,6 +190,11 @@ sph_status sph_grid_export(const sph_grid *grid, int32_t *perm, uint64_t *keys, 
  * With SPH_FIXED_H the sums are evaluated once at the given h.
  * Arithmetic: FP32 pair terms, per-batch compensated (Kahan) accumulation,
  * FP64 h update; SPH_FP64 computes everything in FP64.
+ * Neighbour lists (default path, grid built without SPH_NO_LISTS): the call
+ * records each active particle's set {j != i : r_ij < h_i} at its final h in
+ * the grid. When every particle is active it also builds, for each i, the
+ * partners j with h_i <= r_ij < h_j (the transpose), so that a following
+ * sph_hydro_force can take its pairs from these lists (see there).
  */
 sph_status sph_density(sph_ctx *ctx, const sph_grid *grid, float *h, const int32_t *active,
                        int64_t n_active, float *rho, float *omega, int32_t *n_ngb,
@@ -205,7 +213,15 @@ sph_status sph_density(sph_ctx *ctx, const sph_grid *grid, float *h, const int32
  *   dudt_i =  A_i sum_j m_j v_ij.gradW_ij(h_i) + 1/2 sum_j m_j Pi_ij v_ij.gradbarW_ij
  *   vsig_i = max(0, max_j v_sig);  coincident pairs (r = 0) add no force.
  * acc is n x 3. hash (optional) is the pair-set checksum as in sph_density.
- * dudt is accumulated in FP64 and rounded once.
+ * Sums are folded error-free across the lanes that share a particle and
+ * rounded once.
+ * Pair source (default path): if the last sph_density call on this grid had
+ * every particle active, the grid has not been updated since, and every h
+ * equals the h that call ended with (checked on the device), the pairs come
+ * from the neighbour lists that call recorded -- no hierarchy walk, no
+ * candidate test. Otherwise, and for any particle whose lists did not fit
+ * (more than 128 neighbours or 64 extra partners), the hierarchy is walked.
+ * Both give the same pair set.
  */
 sph_status sph_hydro_force(sph_ctx *ctx, const sph_grid *grid, const float *vel, const float *u,
                            const float *h, const float *rho, const float *omega,

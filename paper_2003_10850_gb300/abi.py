@@ -34,6 +34,7 @@ SPH_DENSITY_BUFFERED = 0x40
 SPH_PER_THREAD_WALK = 0x80
 SPH_COOP_WALK = 0x100
 SPH_WARP_WALK = 0x200
+SPH_NO_LISTS = 0x400
 
 SPH_ST_NOT_CONVERGED = 0x01
 SPH_ST_H_TOO_LARGE = 0x02

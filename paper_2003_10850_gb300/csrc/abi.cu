@@ -156,8 +156,8 @@ sph_status sph_build_grid_batched(sph_ctx* ctx, const void* pos, int pos_is_f64,
     sph_status st = check_params(ctx, params);
     if (st) return st;
     if (cudaSetDevice(ctx->device)) return fail(ctx, SPH_ERR_CUDA, "cudaSetDevice failed");
-    return grid_build(ctx, pos, pos_is_f64 ? 1 : 0, mass, box_offsets, box_sizes, n_boxes,
-                      (cudaStream_t)stream, out);
+    return grid_build(ctx, pos, pos_is_f64 ? 1 : 0, mass, !(params->flags & SPH_NO_LISTS), box_offsets, box_sizes,
+                      n_boxes, (cudaStream_t)stream, out);
 }
 
 sph_status sph_build_grid(sph_ctx* ctx, const void* pos, int pos_is_f64, const float* mass, int64_t n,

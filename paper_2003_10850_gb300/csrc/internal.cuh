@@ -74,6 +74,21 @@ struct sph_grid {
     unsigned* counts = nullptr;
     unsigned* cscan = nullptr;
     int* lcache = nullptr;                 // cooperative density: leaf lists reused across iterations
+    // neighbour lists recorded by an all-active density call on the default path and
+    // reused by the force pass (NULL when the grid was built with SPH_NO_LISTS)
+    int32_t* nbr = nullptr;                // pool of kListPool * n entries: the lists {j != i : r_ij < h_i}
+    int32_t* nbr_off = nullptr;            // n: start of i's list in the pool
+    int32_t* nbr_n = nullptr;              // n: length of i's list, -1 if the pool was full
+    uint32_t* ext_n = nullptr;             // n: extra partners of i (j with h_i <= r_ij < h_j)
+    uint32_t* ext_off = nullptr;           // n + 1: exclusive scan of ext_n
+    int32_t* ext_raw = nullptr;            // pool of kExtPool * n entries: extra partners, scatter order
+    int32_t* ext = nullptr;                // the same, ascending within each particle
+    float* list_h = nullptr;               // n: the h the lists were made with (sorted order)
+    unsigned* list_st = nullptr;           // device, kListSt words (see kListSt)
+    int32_t* fb_list = nullptr;            // n: active particles the list force pass hands to the walk
+    bool lists_full = false;               // host: the last density call recorded every particle's list
+    int64_t list_pool = 0;                 // entries of the nbr pool
+    int64_t ext_pool = 0;                  // entries of the ext pools
     // adjoint scratch (allocated by the first sph_backward on the grid)
     float4* bw_ga = nullptr;
     float4* bw_xbar = nullptr;
@@ -84,9 +99,16 @@ struct sph_grid {
 namespace sph {
 
 constexpr int kQueues = 4;
+constexpr int kListPool = 128;  // neighbour-list pool entries per particle (lists vary in length)
+constexpr int kExtPool = 64;    // extra-partner pool entries per particle
+constexpr int kListChunk = 2048; // pool entries a warp reserves at a time for its particles' lists
+// list_st words: [0] lists written, [1] a list missing (pool full), [2] h
+// changed since the lists were made, [3] fallback count, [4..5] pool entries
+// reserved (64-bit)
+constexpr int kListSt = 6;
 
 // grid.cu
-sph_status grid_build(sph_ctx* ctx, const void* pos, int f64, const float* mass,
+sph_status grid_build(sph_ctx* ctx, const void* pos, int f64, const float* mass, bool lists,
                       const int64_t* offs, const double* Ls, int nb, cudaStream_t s,
                       sph_grid** out);
 void grid_free(sph_grid* g);
@@ -170,8 +192,10 @@ cudaError_t launch_density_wpp(sph_ctx* ctx, const DensityLaunch& a, int64_t n_a
 cudaError_t launch_force_wpp(sph_ctx* ctx, const ForceLaunch& a, int64_t n_active, cudaStream_t s);
 
 // tpp.cu (per-thread walks)
+// list_h / h_changed (optional): set *h_changed if some h differs from list_h
 void force_pack(const sph_grid* g, const float* vel, const float* u, const float* h, const float* rho,
-                const float* omega, float gamma, cudaStream_t s);
+                const float* omega, float gamma, cudaStream_t s, const float* list_h = nullptr,
+                unsigned* h_changed = nullptr);
 cudaError_t launch_density_tpp(sph_ctx* ctx, const DensityLaunch& a, int64_t n_active, cudaStream_t s);
 cudaError_t launch_force_tpp(sph_ctx* ctx, const ForceLaunch& a, int64_t n_active, cudaStream_t s);
 

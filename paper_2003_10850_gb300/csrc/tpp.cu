@@ -521,7 +521,7 @@ __global__ void k_force_pack(int n, const int32_t* __restrict__ perm, const floa
                              const float* __restrict__ u, const float* __restrict__ h, const float* __restrict__ rho,
                              const float* __restrict__ omega, float gam, const float4* __restrict__ posf,
                              float4* __restrict__ fvel, float4* __restrict__ fthermo, float4* __restrict__ fposh,
-                             float4* __restrict__ fvm) {
+                             float4* __restrict__ fvm, const float* __restrict__ list_h, unsigned* h_changed) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
     const int o = perm[p];
@@ -533,6 +533,8 @@ __global__ void k_force_pack(int n, const int32_t* __restrict__ perm, const floa
     fvm[p] = make_float4(vx, vy, vz, f.w);
     fthermo[p] = make_float4(r, omega[o] * P / (r * r), sqrtf(gam * P / r), 1.f / hh);
     fposh[p] = make_float4(f.x, f.y, f.z, hh);
+    // recorded neighbour lists are usable only if every h equals the one they were made with
+    if (list_h && !(hh == list_h[p])) atomicOr(h_changed, 1u);
 }
 
 struct TppForceArgs {
@@ -910,10 +912,10 @@ cudaError_t launch_density_tpp(sph_ctx* ctx, const DensityLaunch& a, int64_t n_a
 }
 
 void force_pack(const sph_grid* g, const float* vel, const float* u, const float* h, const float* rho,
-                const float* omega, float gamma, cudaStream_t s) {
+                const float* omega, float gamma, cudaStream_t s, const float* list_h, unsigned* h_changed) {
     const int n = (int)g->n;
     k_force_pack<<<(n + 255) / 256, 256, 0, s>>>(n, g->perm, vel, u, h, rho, omega, gamma, g->posf, g->fvel, g->fthermo,
-                                                 g->fposh, g->fvm);
+                                                 g->fposh, g->fvm, list_h, h_changed);
 }
 
 cudaError_t launch_force_tpp(sph_ctx* ctx, const ForceLaunch& a, int64_t n_active, cudaStream_t s) {

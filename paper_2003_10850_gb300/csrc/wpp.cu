@@ -94,7 +94,31 @@ struct WppArgs {
     float alpha;
     unsigned long long* hash;
     Counters* ctr;
+    // neighbour lists (NULL: not recorded / not used)
+    int32_t* nbr;                // pool of list_pool entries
+    int32_t* nbr_off;
+    int32_t* nbr_n;
+    const int32_t* ext;          // pool of ext_pool entries, ascending per particle
+    const uint32_t* ext_off;     // n + 1
+    const uint32_t* ext_n;       // nonzero: the particle's extra partners are not usable
+    float* list_h;
+    unsigned* list_st;           // see kListSt
+    int32_t* fb_list;
+    long long list_pool;
+    int list_chunk;              // pool entries a warp reserves at a time
+    unsigned ext_pool;
+    int n_total;                 // particles in the grid
+    // force walk after a list pass: the particles the lists could not serve
+    // (fb_act, *fb_count) when the lists are valid, else the whole active set
+    const int32_t* fb_act;
+    const unsigned* fb_count;
 };
+
+// The recorded lists can serve this force call: every particle's list was
+// written by the last density call, none is missing, and h is unchanged.
+__device__ __forceinline__ bool wpp_lists_valid(const unsigned* st, int n) {
+    return st[0] == (unsigned)n && st[1] == 0u && st[2] == 0u;
+}
 
 __device__ __forceinline__ int wpp_box(const BoxDesc* boxes, int nb, long long p) {
     int lo = 0, hi = nb - 1;
@@ -470,6 +494,46 @@ __device__ __forceinline__ bool wpp_h_update(float& h, float f, float N, float d
     return true;
 }
 
+// The particle-i constants of the force pair terms.
+struct WppForceI {
+    float vx, vy, vz;
+    float hinv, rho, A, c, norm;   // norm = 8/(pi h^4)
+};
+
+// One force pair term, Gadget-2 grad-h form with signal-velocity viscosity,
+// added to i's per-lane sums. (dx, dy, dz) = x_j - x_i; vj = (v_j, m_j);
+// thj = (rho_j, A_j, c_j, 1/h_j).
+__device__ __forceinline__ void wpp_force_pair(const WppForceI& I, float dx, float dy, float dz, float4 vj, float4 thj,
+                                               float alpha, float& Sx, float& Sy, float& Sz, float& Su,
+                                               float& vsmax) {
+    const float kNorm = (float)(8.0 / 3.141592653589793);
+    const float r2 = dx * dx + dy * dy + dz * dz;
+    if (r2 <= 0.f) {  // coincident: no direction, no force
+        vsmax = fmaxf(vsmax, I.c + thj.z);
+        return;
+    }
+    const float rinv = rsqrtf(r2), r = r2 * rinv;
+    float w_, dwi, dwj;
+    spline<float>(r * I.hinv, w_, dwi);
+    spline<float>(r * thj.w, w_, dwj);
+    const float hinvj = thj.w;
+    const float Fi = I.norm * dwi * rinv;
+    const float Fj = kNorm * hinvj * hinvj * hinvj * hinvj * dwj * rinv;
+    const float vr = -((I.vx - vj.x) * dx + (I.vy - vj.y) * dy + (I.vz - vj.z) * dz);
+    const float wij = vr * rinv;
+    const float vs = I.c + thj.z - 3.f * wij;
+    vsmax = fmaxf(vsmax, vs);
+    // Pi_ij = -(alpha/2) v_sig w_ij / rho_bar, rho_bar = (rho_i + rho_j)/2
+    const float PI = wij < 0.f ? __fdividef(-alpha * vs * wij, I.rho + thj.x) : 0.f;
+    const float Fbar = 0.5f * (Fi + Fj);
+    const float mj = vj.w;
+    const float coef = mj * (I.A * Fi + thj.y * Fj + PI * Fbar);
+    Sx += coef * dx;
+    Sy += coef * dy;
+    Sz += coef * dz;
+    Su += mj * vr * (I.A * Fi + 0.5f * PI * Fbar);
+}
+
 // ---------------------------------------------------------------------------
 // Density
 // ---------------------------------------------------------------------------
@@ -483,7 +547,8 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_density_wpp(WppArgs a) {
     const float rel = 9.5367431640625e-07f;  // 2^-20
     const float nt = (float)a.n_target, nt3 = 3.f * nt, tol3 = 3.f * (float)a.n_tol;
     const int cnt = (int)*a.count_ptr;
-    unsigned c_pairs = 0, c_evals = 0, c_tests = 0, c_status = 0;   // per warp (32-bit suffices)
+    unsigned c_pairs = 0, c_evals = 0, c_tests = 0, c_status = 0, c_lists = 0;   // per warp (32-bit suffices)
+    long long ch_next = 0, ch_end = 0;   // the warp's current chunk of the neighbour-list pool
     for (;;) {
         int t0 = 0;
         if (lane == 0) t0 = (int)atomicAdd(a.queue, (unsigned)a.chunk);
@@ -693,6 +758,110 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_density_wpp(WppArgs a) {
                 wpp_fold2(Smw, Smdw, Smw, Cmw, Smdw, Cmdw);
                 nn = warp_sum(nn);
                 if (HASH) hs = warp_sum(hs);
+                if (a.nbr) {
+                    // Record the neighbour list {j != i : r_ij < h_i} at the final h for
+                    // the force pass: nn entries (the count of the final evaluation),
+                    // reserved from the warp's chunk of the pool, enumerated again with
+                    // the same exact predicate from the near list, the leaf list, or a
+                    // fresh walk, whichever the final evaluation could rely on.
+                    int loff = -1;
+                    if (nn > a.list_chunk) {
+                        unsigned long long o = 0;
+                        if (lane == 0) o = atomicAdd(reinterpret_cast<unsigned long long*>(a.list_st + 4),
+                                                     (unsigned long long)nn);
+                        o = __shfl_sync(0xffffffffu, o, 0);
+                        if ((long long)o + nn <= a.list_pool) loff = (int)o;
+                    } else {
+                        if (ch_next + nn > ch_end) {
+                            unsigned long long o = 0;
+                            if (lane == 0) o = atomicAdd(reinterpret_cast<unsigned long long*>(a.list_st + 4),
+                                                         (unsigned long long)a.list_chunk);
+                            o = __shfl_sync(0xffffffffu, o, 0);
+                            ch_next = (long long)o;
+                            ch_end = ch_next + a.list_chunk;
+                        }
+                        if (ch_next + nn <= a.list_pool) loff = (int)ch_next;
+                        ch_next += nn;
+                    }
+                    if (loff >= 0 && nn > 0) {
+                        int32_t* dst = a.nbr + loff;
+                        int pos = 0;
+                        double HHf = -1.0;
+                        auto exact_f = [&](int q) {
+                            if (HHf < 0.0) HHf = wpp_hh(h, B.L);
+                            return exact_pred(exact_d2(Xi, a.posm[q]), HHf);
+                        };
+                        auto put = [&](bool in, int q) {
+                            const unsigned hm = __ballot_sync(0xffffffffu, in);
+                            if (in) {
+                                const int k = pos + __popc(hm & lt);
+                                if (k < nn) dst[k] = q;
+                            }
+                            pos += __popc(hm);
+                        };
+                        if (near_ok) {
+                            const float eL = ebmax + 2.f * rel * h;
+                            const float hi2 = (h + eL) * (h + eL) * (1.f + 4.f * rel);
+                            const float lo2 = h > eL ? (h - eL) * (h - eL) * (1.f - 4.f * rel) : 0.f;
+                            for (int k0 = 0; k0 < nnear; k0 += 32) {
+                                const int k = k0 + (int)lane;
+                                bool in = false;
+                                int q = p;
+                                if (k < nnear) {
+                                    const float r2 = sm.hit.n.d[k].x;
+                                    q = sm.hit.n.j[k];
+                                    in = q != p && r2 < hi2 && (r2 < lo2 || exact_f(q));
+                                }
+                                put(in, q);
+                            }
+                        } else {
+                            // the candidates of the leaf list at h, as process(false) tests them
+                            auto record = [&]() {
+                                for (int base = 0; base < nlf; base += 4) {
+                                    const int li = base + (int)(lane >> 3);
+                                    const int id = sm.lid[li];
+                                    const float4 o = sm.lof[li];
+                                    const int qq = off + (id & 0x7fffffff) * kLeaf + (int)(lane & 7u);
+                                    const bool cand = li < nlf && qq < pend;
+                                    const int q = cand ? qq : p;
+                                    const float4 f = __ldg(a.posf + q);
+                                    float dx = o.x + f.x, dy = o.y + f.y, dz = o.z + f.z;
+                                    if (__any_sync(0xffffffffu, cand && id < 0)) {
+                                        if (cand && id < 0) {
+                                            const uint4 Xj = a.posm[q];
+                                            dx = (float)(int)(Xj.x - Xi.x) * sf;
+                                            dy = (float)(int)(Xj.y - Xi.y) * sf;
+                                            dz = (float)(int)(Xj.z - Xi.z) * sf;
+                                        }
+                                    }
+                                    const float r2 = dx * dx + dy * dy + dz * dz;
+                                    const float eL = o.w + 2.f * rel * h;
+                                    const float tR = h + eL, sR = fmaxf(h - eL, 0.f);
+                                    bool in = cand && q != p && r2 < tR * tR * (1.f + 4.f * rel);
+                                    const bool band = in && !(r2 < sR * sR * (1.f - 4.f * rel));
+                                    if (__any_sync(0xffffffffu, band)) {
+                                        if (band) in = exact_f(q);
+                                    }
+                                    put(in, q);
+                                }
+                            };
+                            if (!complete) {
+                                nlf = 0;
+                                complete = true;
+                                wpp_walk(sm, B, a.node_c, a.node_e, Xi, sf, nlf, complete, [&](float4) { return h; },
+                                         [&]() { record(); nlf = 0; });
+                            }
+                            record();
+                        }
+                        if (pos != nn) loff = -1;   // cannot happen: the same predicate counted nn
+                    }
+                    if (lane == 0) {
+                        a.nbr_off[p] = loff >= 0 ? loff : 0;
+                        a.nbr_n[p] = loff >= 0 ? nn : -1;
+                        a.list_h[p] = h;
+                    }
+                    ++c_lists;
+                }
                 if (lane == 0) {
                     const float smw = __fsub_rn(Smw, Cmw), smdw = __fsub_rn(Smdw, Cmdw);
                     a.h[oi] = h;
@@ -710,6 +879,7 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_density_wpp(WppArgs a) {
     }
     const unsigned long long all_tests = c_tests;   // counted warp-uniformly
     if (lane == 0) {
+        if (a.nbr && c_lists) atomicAdd(&a.list_st[0], c_lists);
         atomicAdd(&a.ctr->density_pairs, (unsigned long long)c_pairs);
         atomicAdd(&a.ctr->density_evals, (unsigned long long)c_evals);
         atomicAdd(&a.ctr->pair_tests, all_tests);
@@ -731,16 +901,24 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_force_wpp(WppArgs a) {
     const float elo = 1.f - 4.f * rel, ehi = 1.f + 4.f * rel;
     const float kNorm = (float)(8.0 / 3.141592653589793);
     const float alpha = a.alpha;
-    const int cnt = (int)*a.count_ptr;
+    // after a list pass: only the particles the lists could not serve, one per
+    // queue grab (walked alone), unless the lists could not serve the call
+    const int32_t* act = a.act;
+    int cnt = (int)*a.count_ptr, chunk = a.chunk;
+    if (a.fb_act && wpp_lists_valid(a.list_st, a.n_total)) {
+        act = a.fb_act;
+        cnt = (int)*a.fb_count;
+        chunk = 1;
+    }
     unsigned long long c_pairs = 0, c_tests = 0;   // lane 0's per-warp totals
     for (;;) {
         int t0 = 0;
-        if (lane == 0) t0 = (int)atomicAdd(a.queue, (unsigned)a.chunk);
+        if (lane == 0) t0 = (int)atomicAdd(a.queue, (unsigned)chunk);
         t0 = __shfl_sync(0xffffffffu, t0, 0);
         if (t0 >= cnt) break;
-        const int t1 = min(t0 + a.chunk, cnt);
+        const int t1 = min(t0 + chunk, cnt);
         for (int t = t0; t < t1;) {
-            const WppGroup G = wpp_group(a.boxes, a.n_boxes, a.act, t, t1);
+            const WppGroup G = wpp_group(a.boxes, a.n_boxes, act, t, t1);
             t += G.n;
             const BoxDesc& B = a.boxes[G.box];
             const float sf = B.sf;
@@ -766,8 +944,8 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_force_wpp(WppArgs a) {
                 const int oi = a.perm[p];
                 const float4 vi = a.fvm[p];
                 const float4 thi = a.fthermo[p];
-                const float hinvi = thi.w, rhoi = thi.x, Ai = thi.y, ci = thi.z;
-                const float normi = kNorm * hinvi * hinvi * hinvi * hinvi;
+                const WppForceI I = {vi.x, vi.y, vi.z, thi.w, thi.x, thi.y, thi.z,
+                                     kNorm * thi.w * thi.w * thi.w * thi.w};
                 // i side of the band test: h_i (1 +- 2^-19) (the leaf's rounding bound is added per leaf)
                 const float hiP = hi * (1.f + 2.f * rel), hiM = hi * (1.f - 2.f * rel);
                 double HHi = -1.0;
@@ -782,34 +960,8 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_force_wpp(WppArgs a) {
                     if ((int)lane < k) {
                         const float4 e = sm.hit.f[lane];
                         const int q = __float_as_int(e.w);
-                        const float dx = e.x, dy = e.y, dz = e.z;
-                        const float r2 = dx * dx + dy * dy + dz * dz;
-                        const float4 vj = __ldg(a.fvm + q);
-                        const float4 thj = __ldg(a.fthermo + q);
-                        if (r2 <= 0.f) {  // coincident: no direction, no force
-                            vsmax = fmaxf(vsmax, ci + thj.z);
-                        } else {
-                            const float rinv = rsqrtf(r2), r = r2 * rinv;
-                            float w_, dwi, dwj;
-                            spline<float>(r * hinvi, w_, dwi);
-                            spline<float>(r * thj.w, w_, dwj);
-                            const float hinvj = thj.w;
-                            const float Fi = normi * dwi * rinv;
-                            const float Fj = kNorm * hinvj * hinvj * hinvj * hinvj * dwj * rinv;
-                            const float vr = -((vi.x - vj.x) * dx + (vi.y - vj.y) * dy + (vi.z - vj.z) * dz);
-                            const float wij = vr * rinv;
-                            const float vs = ci + thj.z - 3.f * wij;
-                            vsmax = fmaxf(vsmax, vs);
-                            // Pi_ij = -(alpha/2) v_sig w_ij / rho_bar, rho_bar = (rho_i + rho_j)/2
-                            const float PI = wij < 0.f ? __fdividef(-alpha * vs * wij, rhoi + thj.x) : 0.f;
-                            const float Fbar = 0.5f * (Fi + Fj);
-                            const float mj = vj.w;
-                            const float coef = mj * (Ai * Fi + thj.y * Fj + PI * Fbar);
-                            Sx += coef * dx;
-                            Sy += coef * dy;
-                            Sz += coef * dz;
-                            Su += mj * vr * (Ai * Fi + 0.5f * PI * Fbar);
-                        }
+                        wpp_force_pair(I, e.x, e.y, e.z, __ldg(a.fvm + q), __ldg(a.fthermo + q), alpha, Sx, Sy, Sz, Su,
+                                       vsmax);
                     }
                     __syncwarp();
                 };
@@ -907,26 +1059,211 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_force_wpp(WppArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// Neighbour lists reused by the force pass
+// ---------------------------------------------------------------------------
+//
+// The force pair set of i is {j != i : r_ij < h_i} U {j : r_ij < h_j}. An
+// all-active density pass records the first part per particle (its neighbour
+// list at the converged h). The second part, minus what the first already
+// holds, is the transpose: j is an extra partner of i when i is on j's list
+// and r_ij >= h_i. k_list_ext scatters those, k_list_sort puts each extra list
+// in ascending order (the scatter's order depends on scheduling; the sorted
+// order makes the force sums deterministic), and k_force_list evaluates the
+// pair terms straight from the two lists: no walk and no candidate tests.
+
+// Warp per particle j: every i on j's list with r_ij >= h_i gets j as an
+// extra partner. "r_ij < h_i" is the exact predicate, decided in FP32 outside
+// a band of 2^-20 around h_i^2 and in FP64 inside it. COUNT = true counts the
+// partners of each i (ext_n); COUNT = false places them, in scatter order, in
+// i's segment [ext_off[i], ext_off[i+1]) of ext_raw (counting ext_n down).
+template <bool COUNT>
+__global__ void __launch_bounds__(256) k_list_ext(const BoxDesc* __restrict__ boxes, int nb, int n,
+                                                  const uint4* __restrict__ posm, const int32_t* __restrict__ nbr,
+                                                  const int32_t* __restrict__ nbr_off,
+                                                  const int32_t* __restrict__ nbr_n, const float* __restrict__ list_h,
+                                                  uint32_t* __restrict__ ext_n, const uint32_t* __restrict__ ext_off,
+                                                  int32_t* __restrict__ ext_raw, unsigned ext_pool, unsigned* list_st) {
+    const unsigned lane = lane_id();
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    const float band = 9.5367431640625e-07f;  // 2^-20
+    for (int j = blockIdx.x * (blockDim.x >> 5) + (int)(threadIdx.x >> 5); j < n; j += warps) {
+        const int cnt = nbr_n[j];
+        if (cnt < 0) {   // j's list is missing: the extra lists cannot be completed
+            if (COUNT && lane == 0) atomicOr(&list_st[1], 1u);
+            continue;
+        }
+        const BoxDesc& B = boxes[nb == 1 ? 0 : wpp_box(boxes, nb, j)];
+        const float Hs = (float)(4294967296.0 / B.L);   // integer units per box unit
+        const uint4 Xj = posm[j];
+        const int32_t* lj = nbr + nbr_off[j];
+        for (int k = (int)lane; k < cnt; k += 32) {
+            const int i = lj[k];
+            const unsigned long long D2 = exact_d2(posm[i], Xj);
+            const float hi = list_h[i];
+            const float d2 = __ull2float_rn(D2), Hi = hi * Hs, H2 = Hi * Hi;
+            bool in;
+            if (d2 < H2 * (1.f - band)) in = true;
+            else if (d2 > H2 * (1.f + band)) in = false;
+            else in = exact_pred(D2, wpp_hh(hi, B.L));
+            if (!in) {
+                if (COUNT) {
+                    atomicAdd(&ext_n[i], 1u);
+                } else if (ext_off[i + 1] <= ext_pool) {
+                    const unsigned pos = atomicSub(&ext_n[i], 1u) - 1u;
+                    ext_raw[ext_off[i] + pos] = j;
+                }
+            }
+        }
+    }
+}
+
+// Warp per particle: its extra partners (distinct indices) in ascending
+// order. Up to 64 entries: each placed at its rank (registers); up to
+// kSortMax: a bitonic sort in shared memory; longer segments (and segments
+// that did not fit the pool) are marked in ext_n (nonzero), and the force
+// pass walks for those particles.
+constexpr int kSortMax = 1024;
+
+__global__ void __launch_bounds__(256) k_list_sort(int n, const uint32_t* __restrict__ ext_off, unsigned ext_pool,
+                                                   const int32_t* __restrict__ ext_raw, int32_t* __restrict__ ext,
+                                                   uint32_t* __restrict__ ext_n) {
+    __shared__ int buf[8][kSortMax];
+    int* sb = buf[threadIdx.x >> 5];
+    const unsigned lane = lane_id();
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    for (int i = blockIdx.x * (blockDim.x >> 5) + (int)(threadIdx.x >> 5); i < n; i += warps) {
+        const unsigned b = ext_off[i], e = ext_off[i + 1];
+        if (e > ext_pool || e == b) continue;
+        const int c = (int)(e - b);
+        const int32_t* src = ext_raw + b;
+        int32_t* dst = ext + b;
+        if (c <= 64) {
+            const int v0 = (int)lane < c ? src[lane] : 0x7fffffff;
+            const int v1 = (int)lane + 32 < c ? src[lane + 32] : 0x7fffffff;
+            int r0 = 0, r1 = 0;
+            const int c0 = min(c, 32);
+            for (int k = 0; k < c0; ++k) {
+                const int x = __shfl_sync(0xffffffffu, v0, k);
+                r0 += x < v0;
+                r1 += x < v1;
+            }
+            for (int k = 32; k < c; ++k) {
+                const int x = __shfl_sync(0xffffffffu, v1, k - 32);
+                r0 += x < v0;
+                r1 += x < v1;
+            }
+            if ((int)lane < c) dst[r0] = v0;
+            if ((int)lane + 32 < c) dst[r1] = v1;
+        } else if (c <= kSortMax) {
+            int P = 128;
+            while (P < c) P <<= 1;
+            for (int k = (int)lane; k < P; k += 32) sb[k] = k < c ? src[k] : 0x7fffffff;
+            __syncwarp();
+            for (int size = 2; size <= P; size <<= 1) {
+                for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                    for (int t = (int)lane; t < (P >> 1); t += 32) {
+                        const int lo = ((t & ~(stride - 1)) << 1) | (t & (stride - 1));
+                        const int hi = lo + stride;
+                        const int x = sb[lo], y = sb[hi];
+                        if ((x > y) == ((lo & size) == 0)) {
+                            sb[lo] = y;
+                            sb[hi] = x;
+                        }
+                    }
+                    __syncwarp();
+                }
+            }
+            for (int k = (int)lane; k < c; k += 32) dst[k] = sb[k];
+            __syncwarp();
+        } else if (lane == 0) {
+            ext_n[i] = 1u;   // too long to sort here: walked by the force pass
+        }
+    }
+}
+
+// Force pass from the recorded lists: warp per active particle, pairs 32 at a
+// time (the neighbour list, then the extra partners), the same pair terms and
+// fold as k_force_wpp. If the lists cannot serve the call at all the kernel
+// does nothing and the walk that follows takes the whole active set;
+// particles whose own lists did not fit go to fb_list for that walk.
+template <bool HASH>
+__global__ void __launch_bounds__(128) k_force_list(WppArgs a) {
+    if (!wpp_lists_valid(a.list_st, a.n_total)) return;
+    const unsigned lane = lane_id();
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    const int cnt = (int)*a.count_ptr;
+    const float kNorm = (float)(8.0 / 3.141592653589793);
+    unsigned long long c_pairs = 0;   // per warp, lane-uniform
+    for (int t = blockIdx.x * (blockDim.x >> 5) + (int)(threadIdx.x >> 5); t < cnt; t += warps) {
+        const int p = a.act[t];
+        const int cn = a.nbr_n[p];
+        const unsigned e0 = a.ext_off[p], e1 = a.ext_off[p + 1];
+        if (cn < 0 || e1 > a.ext_pool || a.ext_n[p] != 0u) {
+            if (lane == 0) a.fb_list[atomicAdd(&a.list_st[3], 1u)] = p;
+            continue;
+        }
+        const BoxDesc& B = a.boxes[a.n_boxes == 1 ? 0 : wpp_box(a.boxes, a.n_boxes, p)];
+        const float sf = B.sf;
+        const uint4 Xi = a.posm[p];
+        const int oi = a.perm[p];
+        const float4 vi = a.fvm[p];
+        const float4 thi = a.fthermo[p];
+        const WppForceI I = {vi.x, vi.y, vi.z, thi.w, thi.x, thi.y, thi.z, kNorm * thi.w * thi.w * thi.w * thi.w};
+        float Sx = 0.f, Sy = 0.f, Sz = 0.f, Su = 0.f, vsmax = 0.f;
+        unsigned long long hs = 0;
+        const int tot = cn + (int)(e1 - e0);
+        const int32_t* ln = a.nbr + a.nbr_off[p];
+        const int32_t* le = a.ext + e0;
+        for (int k = (int)lane; k < tot; k += 32) {
+            const int q = k < cn ? ln[k] : le[k - cn];
+            const uint4 Xj = a.posm[q];
+            const float dx = (float)(int)(Xj.x - Xi.x) * sf, dy = (float)(int)(Xj.y - Xi.y) * sf,
+                        dz = (float)(int)(Xj.z - Xi.z) * sf;
+            wpp_force_pair(I, dx, dy, dz, __ldg(a.fvm + q), __ldg(a.fthermo + q), a.alpha, Sx, Sy, Sz, Su, vsmax);
+            if (HASH) hs += splitmix64((unsigned long long)a.perm[q]);
+        }
+        const float fs = wpp_fold4(Sx, Sy, Sz, Su);
+        vsmax = warp_max(vsmax);
+        if (HASH) hs = warp_sum(hs);
+        if ((lane & 7u) == 0u) {
+            const int comp = (int)(lane >> 3);
+            if (comp < 3) a.acc[3 * (size_t)oi + comp] = fs;
+            else a.dudt[oi] = fs;
+        }
+        if (lane == 0) {
+            a.vsig[oi] = vsmax;
+            if (HASH) a.hash[oi] = hs;
+        }
+        c_pairs += (unsigned long long)tot;
+    }
+    if (lane == 0 && c_pairs) atomicAdd(&a.ctr->force_pairs, c_pairs);
+}
+
+// ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
 
-template <typename Kern>
-static cudaError_t wpp_launch(sph_ctx* ctx, Kern k, const WppArgs& args, int blocks, int kind, int timed,
-                              cudaStream_t s) {
-    cudaEvent_t ea = nullptr, eb = nullptr;
-    if (timed) {
-        ea = timing_event(ctx);
-        eb = timing_event(ctx);
-        if (!ea || !eb) return cudaErrorMemoryAllocation;
-        cudaEventRecord(ea, s);
-    }
-    k<<<blocks, kWppThreads, 0, s>>>(args);
-    ++ctx->launches;
-    if (timed) {
-        cudaEventRecord(eb, s);
-        ctx->timed.push_back({ea, eb, kind});
-    }
-    return cudaGetLastError();
+// SPH_TIME_KERNELS: an event pair around a span of launches on stream s.
+struct WppSpan {
+    cudaEvent_t a = nullptr;
+    int kind = 0;
+};
+
+static cudaError_t span_begin(sph_ctx* ctx, int timed, int kind, cudaStream_t s, WppSpan& sp) {
+    sp.kind = kind;
+    if (!timed) return cudaSuccess;
+    sp.a = timing_event(ctx);
+    if (!sp.a) return cudaErrorMemoryAllocation;
+    return cudaEventRecord(sp.a, s);
+}
+
+static cudaError_t span_end(sph_ctx* ctx, const WppSpan& sp, cudaStream_t s) {
+    if (!sp.a) return cudaSuccess;
+    cudaEvent_t b = timing_event(ctx);
+    if (!b) return cudaErrorMemoryAllocation;
+    cudaEventRecord(b, s);
+    ctx->timed.push_back({sp.a, b, sp.kind});
+    return cudaSuccess;
 }
 
 // Persistent grid and the number of consecutive active particles a warp takes
@@ -956,13 +1293,20 @@ static WppArgs wpp_common(sph_ctx* ctx, const sph_grid* g, unsigned* queue) {
     c.node_lo = g->node_lo;
     c.node_hi = g->node_hi;
     c.ctr = ctx->counters;
+    c.n_total = (int)g->n;
     return c;
 }
 
+// Grid of a warp-per-particle helper kernel over n particles (256 threads).
+static int helper_blocks(sph_ctx* ctx, int64_t n) {
+    return (int)std::max<long long>(1, std::min<long long>((long long)ctx->sm_count * 8, (n + 7) / 8));
+}
+
 cudaError_t launch_density_wpp(sph_ctx* ctx, const DensityLaunch& a, int64_t n_active, cudaStream_t s) {
+    sph_grid* g = const_cast<sph_grid*>(a.g);
     cudaError_t e = cudaMemsetAsync(ctx->queue + 2, 0, sizeof(unsigned), s);
     if (e) return e;
-    WppArgs c = wpp_common(ctx, a.g, ctx->queue + 2);
+    WppArgs c = wpp_common(ctx, g, ctx->queue + 2);
     int blocks = 0;
     const int bps = a.blocks_per_sm > 0 ? a.blocks_per_sm : kWppDensityBps;
     wpp_shape(ctx, bps, n_active, blocks, c.chunk);
@@ -977,36 +1321,106 @@ cudaError_t launch_density_wpp(sph_ctx* ctx, const DensityLaunch& a, int64_t n_a
     c.max_iter = a.max_iter;
     c.guess_h = a.guess_h;
     c.fixed_h = a.fixed_h;
-    if (bps <= 6)
-        return a.hash ? wpp_launch(ctx, k_density_wpp<true, 6>, c, blocks, 0, a.time_kernels, s)
-                      : wpp_launch(ctx, k_density_wpp<false, 6>, c, blocks, 0, a.time_kernels, s);
-    return a.hash ? wpp_launch(ctx, k_density_wpp<true, 8>, c, blocks, 0, a.time_kernels, s)
-                  : wpp_launch(ctx, k_density_wpp<false, 8>, c, blocks, 0, a.time_kernels, s);
+    // Neighbour lists: recorded for the active particles of every call. They
+    // can serve a force call only if every particle was active (checked on the
+    // device: lists written == n); the extra partners are built when the active
+    // count can cover all particles.
+    const bool lists = g->nbr != nullptr;
+    const bool full = lists && n_active == g->n;
+    if (lists) {
+        c.nbr = g->nbr;
+        c.nbr_off = g->nbr_off;
+        c.nbr_n = g->nbr_n;
+        c.list_h = g->list_h;
+        c.list_st = g->list_st;
+        c.list_pool = g->list_pool;
+        // chunks small enough that every warp's first reservations fit in a quarter of the pool
+        const long long warps = (long long)blocks * kWppWarps;
+        c.list_chunk = (int)std::max<long long>(32, std::min<long long>(kListChunk, g->list_pool / (4 * warps)));
+        if ((e = cudaMemsetAsync(g->list_st, 0, sizeof(unsigned) * kListSt, s))) return e;
+    }
+    WppSpan sp;
+    if ((e = span_begin(ctx, a.time_kernels, 0, s, sp))) return e;
+    if (bps <= 6) {
+        if (a.hash) k_density_wpp<true, 6><<<blocks, kWppThreads, 0, s>>>(c);
+        else k_density_wpp<false, 6><<<blocks, kWppThreads, 0, s>>>(c);
+    } else {
+        if (a.hash) k_density_wpp<true, 8><<<blocks, kWppThreads, 0, s>>>(c);
+        else k_density_wpp<false, 8><<<blocks, kWppThreads, 0, s>>>(c);
+    }
+    ++ctx->launches;
+    if (full) {
+        const int n = (int)g->n, hb = helper_blocks(ctx, n);
+        const unsigned ep = (unsigned)g->ext_pool;
+        if ((e = cudaMemsetAsync(g->ext_n, 0, sizeof(uint32_t) * n, s))) return e;
+        k_list_ext<true><<<hb, 256, 0, s>>>(g->boxes, g->n_boxes, n, g->posm, g->nbr, g->nbr_off, g->nbr_n, g->list_h,
+                                            g->ext_n, g->ext_off, g->ext_raw, ep, g->list_st);
+        scan_exclusive<uint32_t>(g->ext_n, n, g->ext_off, g->scan_tmp, s, &ctx->launches);
+        k_list_ext<false><<<hb, 256, 0, s>>>(g->boxes, g->n_boxes, n, g->posm, g->nbr, g->nbr_off, g->nbr_n, g->list_h,
+                                             g->ext_n, g->ext_off, g->ext_raw, ep, g->list_st);
+        k_list_sort<<<hb, 256, 0, s>>>(n, g->ext_off, ep, g->ext_raw, g->ext, g->ext_n);
+        ctx->launches += 3;
+    }
+    g->lists_full = full;
+    if ((e = span_end(ctx, sp, s))) return e;
+    return cudaGetLastError();
 }
 
 cudaError_t launch_force_wpp(sph_ctx* ctx, const ForceLaunch& a, int64_t n_active, cudaStream_t s) {
-    force_pack(a.g, a.vel, a.u, a.h, a.rho, a.omega, (float)a.gamma, s);
+    sph_grid* g = const_cast<sph_grid*>(a.g);
+    cudaError_t e;
+    const bool lists = g->nbr != nullptr && g->lists_full;
+    if (lists && (e = cudaMemsetAsync(g->list_st + 2, 0, 2 * sizeof(unsigned), s))) return e;
+    force_pack(g, a.vel, a.u, a.h, a.rho, a.omega, (float)a.gamma, s, lists ? g->list_h : nullptr,
+               lists ? g->list_st + 2 : nullptr);
     ++ctx->launches;
-    cudaError_t e = cudaMemsetAsync(ctx->queue + 3, 0, sizeof(unsigned), s);
-    if (e) return e;
-    WppArgs c = wpp_common(ctx, a.g, ctx->queue + 3);
+    if ((e = cudaMemsetAsync(ctx->queue + 3, 0, sizeof(unsigned), s))) return e;
+    WppArgs c = wpp_common(ctx, g, ctx->queue + 3);
     int blocks = 0;
     const int bps = a.blocks_per_sm > 0 ? a.blocks_per_sm : kWppForceBps;
     wpp_shape(ctx, bps, n_active, blocks, c.chunk);
-    c.fvel = a.g->fvel;
-    c.fthermo = a.g->fthermo;
-    c.fposh = a.g->fposh;
-    c.fvm = a.g->fvm;
+    c.fvel = g->fvel;
+    c.fthermo = g->fthermo;
+    c.fposh = g->fposh;
+    c.fvm = g->fvm;
     c.acc = a.acc;
     c.dudt = a.dudt;
     c.vsig = a.vsig;
     c.alpha = (float)a.alpha;
     c.hash = a.hash;
-    if (bps <= 6)
-        return a.hash ? wpp_launch(ctx, k_force_wpp<true, 6>, c, blocks, 1, a.time_kernels, s)
-                      : wpp_launch(ctx, k_force_wpp<false, 6>, c, blocks, 1, a.time_kernels, s);
-    return a.hash ? wpp_launch(ctx, k_force_wpp<true, 8>, c, blocks, 1, a.time_kernels, s)
-                  : wpp_launch(ctx, k_force_wpp<false, 8>, c, blocks, 1, a.time_kernels, s);
+    WppSpan sp;
+    if ((e = span_begin(ctx, a.time_kernels, 1, s, sp))) return e;
+    if (lists) {
+        // pairs from the recorded lists; the walk that follows takes the
+        // particles they cannot serve (usually none), or every active particle
+        // if the lists cannot serve this call
+        c.nbr = g->nbr;
+        c.nbr_off = g->nbr_off;
+        c.nbr_n = g->nbr_n;
+        c.ext = g->ext;
+        c.ext_off = g->ext_off;
+        c.ext_n = g->ext_n;
+        c.ext_pool = (unsigned)g->ext_pool;
+        c.list_st = g->list_st;
+        c.fb_list = g->fb_list;
+        const int lb = (int)std::max<long long>(
+            1, std::min<long long>((long long)ctx->sm_count * 16, (n_active + 3) / 4));
+        if (a.hash) k_force_list<true><<<lb, 128, 0, s>>>(c);
+        else k_force_list<false><<<lb, 128, 0, s>>>(c);
+        ++ctx->launches;
+        c.fb_act = g->fb_list;
+        c.fb_count = g->list_st + 3;
+    }
+    if (bps <= 6) {
+        if (a.hash) k_force_wpp<true, 6><<<blocks, kWppThreads, 0, s>>>(c);
+        else k_force_wpp<false, 6><<<blocks, kWppThreads, 0, s>>>(c);
+    } else {
+        if (a.hash) k_force_wpp<true, 8><<<blocks, kWppThreads, 0, s>>>(c);
+        else k_force_wpp<false, 8><<<blocks, kWppThreads, 0, s>>>(c);
+    }
+    ++ctx->launches;
+    if ((e = span_end(ctx, sp, s))) return e;
+    return cudaGetLastError();
 }
 
 }  // namespace sph

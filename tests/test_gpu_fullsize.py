@@ -4,8 +4,9 @@ benchmark times (default path and launch shape, all particles active).
 * 2,097,152 clustered particles (200 blobs, seed 2): the oracle solves the
   density of every particle (a minute of CPU on a many-core host), so h and
   rho are compared element by element for all 2M particles; the force pass is
-  then run on the oracle's h, rho, Omega (rounded to FP32) and compared with
-  the oracle's force on 4,096 sampled particles, pair sets bit-exact.
+  then run on the oracle's h, rho, Omega (rounded to FP32), from the neighbour
+  lists of a fixed-h density pass at that h, and compared with the oracle's
+  force on 4,096 sampled particles, pair sets bit-exact.
 * 10,000,000 clustered particles (500 blobs, seed 3): the oracle evaluates
   2,048 sampled particles one by one (h, rho, the neighbour set at a fixed h);
   the force pass over all 10M is checked through properties that hold at any
@@ -65,10 +66,13 @@ def test_fullsize_2M_density_all_and_force_sampled(S, ctx):
     full[idx] = d["h"][idx]
     lo, hi = _n_ngb_bracket(X, p, full, idx)
     assert np.all((g["n_ngb"][idx] >= lo) & (g["n_ngb"][idx] <= hi))
-    # force on the oracle's density state, all particles active
+    # force on the oracle's density state, all particles active; a fixed-h
+    # density pass at that h first records the neighbour lists the force pass
+    # reads (as the benchmark's all-active sub-step does)
     h, rho, om = (d[k].astype(np.float32) for k in ("h", "rho", "omega"))
+    gpu_density(S, ctx, grid, h, S.default_params(box=p.box, flags=S.SPH_FIXED_H))
     gf = gpu_force(S, ctx, grid, p, h, rho, om, params)
-    assert gf["rc"] == 0
+    assert gf["rc"] == 0 and gf["stats"]["pair_tests"] == 0
     f = oracle.force(X, p.vel, p.mass, p.u, h, rho, om, box=p.box, active=idx)
     check_force(gf, f, idx, 1e-4)
 
@@ -96,14 +100,6 @@ def test_fullsize_10M_density_sampled_force_conservation(S, ctx):
     lo, hi = _n_ngb_bracket(X, p, full, idx)
     nn = host(out["n_ngb"])[idx]
     assert np.all((nn >= lo) & (nn <= hi))
-    # neighbour sets bit-exact at a fixed h (the oracle's, rounded to FP32)
-    h32 = np.zeros(n, np.float32)
-    h32[idx] = d["h"][idx].astype(np.float32)
-    pf = S.default_params(box=p.box, flags=S.SPH_FIXED_H)
-    gfix = gpu_density(S, ctx, grid, h32, pf, active=idx.astype(np.int32))
-    ofix = oracle.density(X, p.mass, h32.astype(np.float64), box=p.box, fixed_h=True, active=idx)
-    assert np.array_equal(gfix["n_ngb"][idx], ofix["n_ngb"][idx])
-    assert np.array_equal(gfix["hash"][idx], ofix["hash"][idx])
     # force over all 10M on the GPU's own density state: momentum and energy
     # are conserved pair by pair, so their totals vanish up to FP32 rounding
     vel, u = dev(p.vel), dev(p.u)
@@ -111,7 +107,7 @@ def test_fullsize_10M_density_sampled_force_conservation(S, ctx):
     dudt, vsig = torch.zeros(n, device="cuda"), torch.zeros(n, device="cuda")
     S.sph_hydro_force(ctx, grid, vel, u, h, out["rho"], out["omega"], None, acc, dudt, vsig, None, params)
     rc, fst = S.sph_sync_status(ctx, raise_on_error=False)
-    assert rc == 0
+    assert rc == 0 and fst["pair_tests"] == 0   # pairs from the density pass's lists
     a = host(acc).astype(np.float64)
     du = host(dudt).astype(np.float64)
     assert np.all(np.isfinite(a)) and np.all(np.isfinite(du))
@@ -122,3 +118,11 @@ def test_fullsize_10M_density_sampled_force_conservation(S, ctx):
     assert abs(e_terms.sum()) <= 1e-5 * np.abs(m * (np.abs(p.vel * a).sum(1) + np.abs(du))).sum()
     # pair counts: every density neighbour is a force partner (r < h_i)
     assert fst["force_pairs"] >= stats["density_pairs"]
+    # neighbour sets bit-exact at a fixed h (the oracle's, rounded to FP32)
+    h32 = np.zeros(n, np.float32)
+    h32[idx] = d["h"][idx].astype(np.float32)
+    pf = S.default_params(box=p.box, flags=S.SPH_FIXED_H)
+    gfix = gpu_density(S, ctx, grid, h32, pf, active=idx.astype(np.int32))
+    ofix = oracle.density(X, p.mass, h32.astype(np.float64), box=p.box, fixed_h=True, active=idx)
+    assert np.array_equal(gfix["n_ngb"][idx], ofix["n_ngb"][idx])
+    assert np.array_equal(gfix["hash"][idx], ofix["hash"][idx])

@@ -166,6 +166,66 @@ def test_force_parity(S, ctx, kind, fp64, path, lattice32, clustered50k):
     assert mom <= 1e-5 * (p.mass * np.linalg.norm(g["acc"], axis=1)).sum()
 
 
+@pytest.mark.parametrize("kind", ["lattice", "clustered"])
+def test_force_reuses_density_lists(S, ctx, kind, lattice32, clustered50k):
+    """An all-active density pass on the default path records each particle's
+    neighbour list; the force pass then takes its pairs from those lists (and
+    their transpose) instead of walking: no candidate is tested, and the
+    results and pair sets equal the oracle's. Changing h invalidates the lists
+    and the walk serves the call, with the same results."""
+    p, (X, d, _) = lattice32 if kind == "lattice" else clustered50k
+    h, rho, om = _oracle_inputs32(d)
+    params = S.default_params(box=p.box)
+    grid = gpu_grid(S, ctx, p, params)
+    gd = gpu_density(S, ctx, grid, h, S.default_params(box=p.box, flags=S.SPH_FIXED_H))
+    assert gd["rc"] == 0
+    f = oracle.force(X, p.vel, p.mass, p.u, h, rho, om, box=p.box)
+    g = gpu_force(S, ctx, grid, p, h, rho, om, params)
+    assert g["rc"] == 0
+    assert g["stats"]["pair_tests"] == 0
+    check_force(g, f, np.arange(p.n), 1e-4)
+    assert g["stats"]["force_pairs"] == int(f["n_pairs"].sum())
+    h2 = (h * np.float32(1.001)).astype(np.float32)
+    f2 = oracle.force(X, p.vel, p.mass, p.u, h2, rho, om, box=p.box)
+    g2 = gpu_force(S, ctx, grid, p, h2, rho, om, params)
+    assert g2["rc"] == 0 and g2["stats"]["pair_tests"] > 0
+    check_force(g2, f2, np.arange(p.n), 1e-4)
+    # an active subset of the force pass still reads the lists
+    act = W.sample_indices(p.n, p.n // 7, seed=31).astype(np.int32)
+    g3 = gpu_force(S, ctx, grid, p, h, rho, om, params, active=act)
+    assert g3["stats"]["pair_tests"] == 0
+    check_force(g3, f, act, 1e-4)
+
+
+def test_force_lists_that_do_not_fit(S, ctx):
+    """With N_t = 200 every neighbour list overflows its 128 slots: the force
+    pass hands every particle to the walk, with unchanged results."""
+    p = as_f32(W.config1(16))
+    X, d, f0 = oracle_all(p, n_target=200.0)
+    h, rho, om = _oracle_inputs32(d)
+    params = S.default_params(box=p.box, n_target=200.0, n_tol=200e-6)
+    grid = gpu_grid(S, ctx, p, params)
+    gd = gpu_density(S, ctx, grid, h, S.default_params(box=p.box, n_target=200.0, flags=S.SPH_FIXED_H))
+    assert gd["rc"] == 0 and gd["n_ngb"].min() > 128
+    f = oracle.force(X, p.vel, p.mass, p.u, h, rho, om, box=p.box)
+    g = gpu_force(S, ctx, grid, p, h, rho, om, params)
+    assert g["rc"] == 0 and g["stats"]["pair_tests"] > 0
+    check_force(g, f, np.arange(p.n), 1e-4)
+
+
+def test_no_lists_grid(S, ctx, clustered50k):
+    """A grid built with SPH_NO_LISTS records nothing; the force pass walks."""
+    p, (X, d, _) = clustered50k
+    h, rho, om = _oracle_inputs32(d)
+    grid = gpu_grid(S, ctx, p, S.default_params(box=p.box, flags=S.SPH_NO_LISTS))
+    params = S.default_params(box=p.box)
+    gpu_density(S, ctx, grid, h, S.default_params(box=p.box, flags=S.SPH_FIXED_H))
+    f = oracle.force(X, p.vel, p.mass, p.u, h, rho, om, box=p.box)
+    g = gpu_force(S, ctx, grid, p, h, rho, om, params)
+    assert g["stats"]["pair_tests"] > 0
+    check_force(g, f, np.arange(p.n), 1e-4)
+
+
 def test_force_plain_fp32(S, ctx, clustered50k):
     p, (X, d, _) = clustered50k
     h, rho, om = _oracle_inputs32(d)
@@ -297,12 +357,16 @@ def test_single_particle_and_tiny(S, ctx):
 
 # ---- a6: the step captured as a CUDA graph ------------------------------------
 
-def test_graph_capture_replays_eager_results(S, ctx, clustered50k):
-    """Grid rebuild + density + force over an active subset, captured once and
-    replayed: the outputs equal those of the eager calls bit for bit."""
+@pytest.mark.parametrize("which", ["subset", "all"])
+def test_graph_capture_replays_eager_results(S, ctx, clustered50k, which):
+    """Grid rebuild + density + force over an active subset (walks) or over all
+    particles (the force pass reads the density pass's neighbour lists),
+    captured once and replayed: the outputs equal those of the eager calls bit
+    for bit."""
     p, (X, d, _) = clustered50k
     params = S.default_params(box=p.box)
-    act = dev(W.sample_indices(p.n, p.n // 5, seed=23).astype(np.int32), torch.int32)
+    idx = W.sample_indices(p.n, p.n // 5, seed=23) if which == "subset" else np.arange(p.n)
+    act = dev(idx.astype(np.int32), torch.int32)
     pos, mass, vel, u = dev(p.pos), dev(p.mass), dev(p.vel), dev(p.u)
     grid = S.sph_build_grid(ctx, pos, mass, params)
     h0 = dev(d["h"].astype(np.float32) * 1.01)
