@@ -78,6 +78,7 @@ struct sph_grid {
     // reused by the force pass (NULL when the grid was built with SPH_NO_LISTS)
     int32_t* nbr = nullptr;                // pool of kListPool * n entries: the lists {j != i : r_ij < h_i}
     int32_t* nbr_off = nullptr;            // n: start of i's list in the pool
+    uint8_t* nbr_x = nullptr;              // pool-sized: 1 where the entry (j on i's list) makes i an extra partner of j
     int32_t* nbr_n = nullptr;              // n: length of i's list, -1 if the pool was full
     uint32_t* ext_n = nullptr;             // n: extra partners of i (j with h_i <= r_ij < h_j)
     uint32_t* ext_off = nullptr;           // n + 1: exclusive scan of ext_n

@@ -1,23 +1,30 @@
-// wpp.cu -- warp-per-particle density and force kernels.
+// wpp.cu -- warp-per-particle density and force kernels (the default path).
 //
-// One warp per active particle. The warp walks the hierarchy for its particle
-// alone, popping up to four nodes per step and testing their children one per
-// lane, and keeps the particle's leaf list (with each leaf's centre offset and
-// rounding bound) in shared memory. The candidates of that list are then
-// tested 32 at a time, one per lane (lanes 8k..8k+7 on the eight particles of
-// the k-th leaf of the step, a coalesced 128-byte load), and the pairs in the
-// neighbour set are compacted by ballot into a warp-wide hit buffer whose
-// pair terms are evaluated 32 at a time, one per lane. Every step therefore
-// runs with (nearly) all lanes busy, whatever the lengths of the neighbour
-// lists of nearby particles. Per-lane partial sums are compensated (Kahan) and
-// folded across the warp with an error-free (TwoSum) butterfly, so the result
-// is deterministic and carries the compensation of a sequential sum.
+// Work is handed out in chunks of up to 8 Morton-consecutive active particles.
+// Those of one leaf-parent node form a group: the warp walks the hierarchy
+// once for the whole group (popping up to four nodes per step, one child per
+// lane) and keeps the group's leaf list in shared memory. Each particle then
+// takes its own leaf list from the group's by the same node test its own walk
+// would make, and is processed by the whole warp: its candidates are tested 32
+// at a time, one per lane (lanes 8k..8k+7 on the eight particles of a leaf, a
+// coalesced 128-byte load), and the pairs in its neighbour set are compacted
+// by ballot into a warp-wide hit buffer whose pair terms are evaluated 32 at a
+// time. Every step therefore runs with (nearly) all lanes busy, whatever the
+// lengths of the neighbour lists of nearby particles. Per-lane FP32 partial
+// sums are folded across the warp with error-free (TwoSum) transformations,
+// so the result is deterministic and carries the compensation of the fold.
 //
-// Density keeps the leaf list of a walk at 1.06 h across the h iterations
-// (Newton on N^(1/3) with an FP64 bracket, as in the other paths) and walks
-// again only when h leaves the walk radius. The neighbour predicate is the
-// exact one ((double)D2 < (h 2^32/L)^2) inside a thin band around the FP32
-// radius test, as elsewhere.
+// Density keeps the pairs within 1.06 h of one walk (the "near list") across
+// the h iterations (safeguarded Newton on N^(1/3), FP32) and walks again only
+// when h leaves the walk radius. The neighbour predicate is the exact one,
+// (double)D2 < (h 2^32/L)^2, decided in FP64 only inside a thin band around
+// the FP32 radius test.
+//
+// Neighbour lists: a density call records each active particle's neighbour
+// set at its final h. When every particle was active, the transpose adds each
+// particle's partners with h_i <= r_ij < h_j, and the force pass then reads
+// its pairs from the two lists (k_force_list) instead of walking; the walk
+// (k_force_wpp) serves the particles, or calls, the lists cannot.
 #include <algorithm>
 
 #include "internal.cuh"
@@ -27,8 +34,8 @@ namespace sph {
 constexpr int kWppWarps = 4;
 constexpr int kWppThreads = kWppWarps * 32;
 // Register budgets: 8 resident blocks (32 warps, 64 registers) or 6 (24 warps,
-// 80 registers); the launch takes the one matching blocks_per_sm. Defaults
-// (measured, 10M clustered): 8 for both passes.
+// 80 registers); the launch takes the one matching blocks_per_sm. The
+// autotuner picks between them per pass.
 constexpr int kWppDensityBps = 8;
 constexpr int kWppForceBps = 8;
 constexpr int kWppMaxBps = 16;
@@ -1072,17 +1079,20 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_force_wpp(WppArgs a) {
 // pair terms straight from the two lists: no walk and no candidate tests.
 
 // Warp per particle j: every i on j's list with r_ij >= h_i gets j as an
-// extra partner. "r_ij < h_i" is the exact predicate, decided in FP32 outside
-// a band of 2^-20 around h_i^2 and in FP64 inside it. COUNT = true counts the
-// partners of each i (ext_n); COUNT = false places them, in scatter order, in
-// i's segment [ext_off[i], ext_off[i+1]) of ext_raw (counting ext_n down).
+// extra partner (possible only if h_i < h_j, which is tested first). "r_ij <
+// h_i" is the exact predicate, decided in FP32 outside a band of 2^-20 around
+// h_i^2 and in FP64 inside it. COUNT = true counts each i's extra partners in
+// ext_n and marks the list entries that make one in nbr_x; COUNT = false
+// places the marked pairs in i's segment [ext_off[i], ext_off[i+1]) of
+// ext_raw (scatter order; ext_n counts down to 0).
 template <bool COUNT>
 __global__ void __launch_bounds__(256) k_list_ext(const BoxDesc* __restrict__ boxes, int nb, int n,
                                                   const uint4* __restrict__ posm, const int32_t* __restrict__ nbr,
                                                   const int32_t* __restrict__ nbr_off,
-                                                  const int32_t* __restrict__ nbr_n, const float* __restrict__ list_h,
-                                                  uint32_t* __restrict__ ext_n, const uint32_t* __restrict__ ext_off,
-                                                  int32_t* __restrict__ ext_raw, unsigned ext_pool, unsigned* list_st) {
+                                                  const int32_t* __restrict__ nbr_n, uint8_t* __restrict__ nbr_x,
+                                                  const float* __restrict__ list_h, uint32_t* __restrict__ ext_n,
+                                                  const uint32_t* __restrict__ ext_off, int32_t* __restrict__ ext_raw,
+                                                  unsigned ext_pool, unsigned* list_st) {
     const unsigned lane = lane_id();
     const int warps = gridDim.x * (blockDim.x >> 5);
     const float band = 9.5367431640625e-07f;  // 2^-20
@@ -1092,23 +1102,31 @@ __global__ void __launch_bounds__(256) k_list_ext(const BoxDesc* __restrict__ bo
             if (COUNT && lane == 0) atomicOr(&list_st[1], 1u);
             continue;
         }
-        const BoxDesc& B = boxes[nb == 1 ? 0 : wpp_box(boxes, nb, j)];
-        const float Hs = (float)(4294967296.0 / B.L);   // integer units per box unit
-        const uint4 Xj = posm[j];
-        const int32_t* lj = nbr + nbr_off[j];
-        for (int k = (int)lane; k < cnt; k += 32) {
-            const int i = lj[k];
-            const unsigned long long D2 = exact_d2(posm[i], Xj);
-            const float hi = list_h[i];
-            const float d2 = __ull2float_rn(D2), Hi = hi * Hs, H2 = Hi * Hi;
-            bool in;
-            if (d2 < H2 * (1.f - band)) in = true;
-            else if (d2 > H2 * (1.f + band)) in = false;
-            else in = exact_pred(D2, wpp_hh(hi, B.L));
-            if (!in) {
-                if (COUNT) {
-                    atomicAdd(&ext_n[i], 1u);
-                } else if (ext_off[i + 1] <= ext_pool) {
+        const int off = nbr_off[j];
+        const int32_t* lj = nbr + off;
+        if (COUNT) {
+            const BoxDesc& B = boxes[nb == 1 ? 0 : wpp_box(boxes, nb, j)];
+            const float Hs = (float)(4294967296.0 / B.L);   // integer units per box unit
+            const uint4 Xj = posm[j];
+            const float hj = list_h[j];
+            for (int k = (int)lane; k < cnt; k += 32) {
+                const int i = lj[k];
+                const float hi = list_h[i];
+                bool x = false;
+                if (hi < hj) {
+                    const unsigned long long D2 = exact_d2(posm[i], Xj);
+                    const float d2 = __ull2float_rn(D2), Hi = hi * Hs, H2 = Hi * Hi;
+                    if (d2 > H2 * (1.f + band)) x = true;
+                    else if (!(d2 < H2 * (1.f - band))) x = !exact_pred(D2, wpp_hh(hi, B.L));
+                }
+                nbr_x[off + k] = x ? 1 : 0;
+                if (x) atomicAdd(&ext_n[i], 1u);
+            }
+        } else {
+            for (int k = (int)lane; k < cnt; k += 32) {
+                if (!nbr_x[off + k]) continue;
+                const int i = lj[k];
+                if (ext_off[i + 1] <= ext_pool) {
                     const unsigned pos = atomicSub(&ext_n[i], 1u) - 1u;
                     ext_raw[ext_off[i] + pos] = j;
                 }
@@ -1353,11 +1371,11 @@ cudaError_t launch_density_wpp(sph_ctx* ctx, const DensityLaunch& a, int64_t n_a
         const int n = (int)g->n, hb = helper_blocks(ctx, n);
         const unsigned ep = (unsigned)g->ext_pool;
         if ((e = cudaMemsetAsync(g->ext_n, 0, sizeof(uint32_t) * n, s))) return e;
-        k_list_ext<true><<<hb, 256, 0, s>>>(g->boxes, g->n_boxes, n, g->posm, g->nbr, g->nbr_off, g->nbr_n, g->list_h,
-                                            g->ext_n, g->ext_off, g->ext_raw, ep, g->list_st);
+        k_list_ext<true><<<hb, 256, 0, s>>>(g->boxes, g->n_boxes, n, g->posm, g->nbr, g->nbr_off, g->nbr_n, g->nbr_x,
+                                            g->list_h, g->ext_n, g->ext_off, g->ext_raw, ep, g->list_st);
         scan_exclusive<uint32_t>(g->ext_n, n, g->ext_off, g->scan_tmp, s, &ctx->launches);
-        k_list_ext<false><<<hb, 256, 0, s>>>(g->boxes, g->n_boxes, n, g->posm, g->nbr, g->nbr_off, g->nbr_n, g->list_h,
-                                             g->ext_n, g->ext_off, g->ext_raw, ep, g->list_st);
+        k_list_ext<false><<<hb, 256, 0, s>>>(g->boxes, g->n_boxes, n, g->posm, g->nbr, g->nbr_off, g->nbr_n, g->nbr_x,
+                                             g->list_h, g->ext_n, g->ext_off, g->ext_raw, ep, g->list_st);
         k_list_sort<<<hb, 256, 0, s>>>(n, g->ext_off, ep, g->ext_raw, g->ext, g->ext_n);
         ctx->launches += 3;
     }
