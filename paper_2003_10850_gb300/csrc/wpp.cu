@@ -1367,6 +1367,8 @@ cudaError_t launch_density_wpp(sph_ctx* ctx, const DensityLaunch& a, int64_t n_a
         else k_density_wpp<false, 8><<<blocks, kWppThreads, 0, s>>>(c);
     }
     ++ctx->launches;
+    // SPH_TIME_KERNELS times the density kernel alone; the list build follows
+    if ((e = span_end(ctx, sp, s))) return e;
     if (full) {
         const int n = (int)g->n, hb = helper_blocks(ctx, n);
         const unsigned ep = (unsigned)g->ext_pool;
@@ -1380,7 +1382,6 @@ cudaError_t launch_density_wpp(sph_ctx* ctx, const DensityLaunch& a, int64_t n_a
         ctx->launches += 3;
     }
     g->lists_full = full;
-    if ((e = span_end(ctx, sp, s))) return e;
     return cudaGetLastError();
 }
 
