@@ -55,8 +55,9 @@ def lib():
         L.orc_density.argtypes = [i32, P, P, i64, f64, P, P, f64, f64, i32, P, i64, i32, i32,
                                   P, P, P, P, P, P, P, P]
         L.orc_density.restype = i32
-        L.orc_force.argtypes = [i32, P, P, i64, f64, P, P, P, P, P, P, f64, f64, P, i64, i32,
+        L.orc_force.argtypes = [i32, P, P, i64, f64, P, P, P, P, P, P, f64, f64, P, P, P, i64, i32,
                                 P, P, P, P, P, P, P]
+        L.orc_divcurl.argtypes = [i32, P, P, i64, f64, P, P, P, P, P, i64, i32, P, P]
         L.orc_neighbours.argtypes = [i32, P, P, i64, f64, i64, f64, i32, P, i64]
         L.orc_neighbours.restype = i64
         L.orc_num_threads.restype = i32
@@ -148,13 +149,29 @@ def density(X=None, mass=None, h_init=None, box=1.0, n_target=64.0, tol=1e-10, m
     return out
 
 
+def divcurl(X=None, vel=None, mass=None, h=None, rho=None, box=1.0, active=None, brute=False, xc=None):
+    """Velocity divergence and |curl| at the given h and rho (entries of
+    inactive particles NaN)."""
+    mode, Xc, xcc = _geom(X, xc, box)
+    n = Xc.shape[0]
+    args = [_c(a, np.float64) for a in (vel, mass, h, rho)]
+    act = None if active is None else _c(active, np.int64)
+    divv = np.full(n, np.nan)
+    curlv = np.full(n, np.nan)
+    lib().orc_divcurl(mode, _p(Xc), _p(xcc), n, float(box), *[_p(a) for a in args], _p(act),
+                      0 if act is None else act.size, int(bool(brute)), _p(divv), _p(curlv))
+    return divv, curlv
+
+
 def force(X=None, vel=None, mass=None, u=None, h=None, rho=None, omega=None, box=1.0,
-          alpha=1.0, gamma=5.0 / 3.0, active=None, brute=False, xc=None):
+          alpha=1.0, gamma=5.0 / 3.0, active=None, brute=False, xc=None, divv=None, curlv=None):
     """Hydro-force pass. Returns acc (N,3), dudt, vsig, scale_a, scale_u,
-    n_pairs, hash (entries of inactive particles NaN / -1)."""
+    n_pairs, hash (entries of inactive particles NaN / -1). With divv and
+    curlv, Balsara's switch limits the viscosity."""
     mode, Xc, xcc = _geom(X, xc, box)
     n = Xc.shape[0]
     args = [_c(a, np.float64) for a in (vel, mass, u, h, rho, omega)]
+    sw = [None, None] if divv is None else [_c(divv, np.float64), _c(curlv, np.float64)]
     act = None if active is None else _c(active, np.int64)
     out = {"acc": np.full((n, 3), np.nan)}
     for k in ("dudt", "vsig", "scale_a", "scale_u"):
@@ -162,7 +179,7 @@ def force(X=None, vel=None, mass=None, u=None, h=None, rho=None, omega=None, box
     out["n_pairs"] = np.full(n, -1, dtype=np.int64)
     out["hash"] = np.zeros(n, dtype=np.uint64)
     lib().orc_force(mode, _p(Xc), _p(xcc), n, float(box), *[_p(a) for a in args], float(alpha),
-                    float(gamma), _p(act), 0 if act is None else act.size, int(bool(brute)),
+                    float(gamma), _p(sw[0]), _p(sw[1]), _p(act), 0 if act is None else act.size, int(bool(brute)),
                     _p(out["acc"]), _p(out["dudt"]), _p(out["vsig"]), _p(out["scale_a"]),
                     _p(out["scale_u"]), _p(out["n_pairs"]), _p(out["hash"]))
     return out

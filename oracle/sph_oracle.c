@@ -30,6 +30,11 @@
  *               du_i  =  A_i sum_j m_j v_ij . grad W(h_i)
  *                        + 1/2 sum_j m_j Pi_ij v_ij . gradbar W,
  *               vsig_i = max(0, max_j v_sig).
+ *   switch      (optional) velocity divergence and curl from the density
+ *               pass's neighbours, div_i = -(1/rho_i) sum_j m_j v_ij . grad_i W(h_i),
+ *               curl_i = |(1/rho_i) sum_j m_j v_ij x grad_i W(h_i)|, and
+ *               Balsara's factor f_i = |div_i| / (|div_i| + curl_i + 1e-4 c_i/h_i)
+ *               multiplying Pi_ij by (f_i + f_j)/2.
  *
  * Everything is a direct sum in FP64 over an explicit candidate set: either
  * every particle (brute force) or the particles of the cells around i in a
@@ -452,15 +457,70 @@ static void orc_hindex_free(orc_hindex *Hx)
 }
 
 /*
+ * Velocity divergence and curl of the active particles (NULL = all) at the
+ * given h and rho (the density pass's): over j != i with r_ij < h_i,
+ *   div_i  = -(1/rho_i) sum_j m_j v_ij . grad_i W_ij(h_i)
+ *   curl_i = |(1/rho_i) sum_j m_j v_ij x grad_i W_ij(h_i)|
+ * with v_ij = v_i - v_j, r_ij = x_i - x_j, grad_i W_ij = dW/dr(r_ij, h_i)
+ * r_ij / |r_ij| (coincident pairs add nothing). These are the SPH estimates
+ * of the velocity gradient that Gadget-2 forms in its density loop for the
+ * Balsara switch; the paper's code runs an "improved SPH" of this lineage
+ * (Sec. 1).
+ */
+void orc_divcurl(int mode, const uint32_t *X, const double *xc, int64_t n, double L,
+                 const double *v, const double *m, const double *h, const double *rho,
+                 const int64_t *active, int64_t n_active, int brute, double *divv, double *curlv)
+{
+    orc_pos P = {mode, X, xc, n, L};
+    orc_index *I = brute ? NULL : (orc_index *)orc_index_new(X, n);
+    int64_t na = active ? n_active : n;
+#pragma omp parallel
+    {
+        orc_buf cb = {0, 0, 0};
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t a = 0; a < na; ++a) {
+            int64_t i = active ? active[a] : a;
+            orc_cands_for(&P, I, i, h[i], &cb);
+            double sd = 0.0, sc[3] = {0.0, 0.0, 0.0};
+            for (int64_t c = 0; c < cb.n; ++c) {
+                int64_t j = cb.a[c];
+                if (j == i) continue;
+                double rij[3], r;
+                if (!orc_pair(&P, i, j, h[i], rij, &r) || r == 0.0) continue;
+                double g = m[j] * orc_dWdr(r, h[i]) / r;   /* m_j grad_i W = g * r_ij */
+                double vij[3] = {v[3 * i] - v[3 * j], v[3 * i + 1] - v[3 * j + 1], v[3 * i + 2] - v[3 * j + 2]};
+                sd += g * (vij[0] * rij[0] + vij[1] * rij[1] + vij[2] * rij[2]);
+                sc[0] += g * (vij[1] * rij[2] - vij[2] * rij[1]);
+                sc[1] += g * (vij[2] * rij[0] - vij[0] * rij[2]);
+                sc[2] += g * (vij[0] * rij[1] - vij[1] * rij[0]);
+            }
+            divv[i] = -sd / rho[i];
+            curlv[i] = sqrt(sc[0] * sc[0] + sc[1] * sc[1] + sc[2] * sc[2]) / rho[i];
+        }
+        free(cb.a);
+    }
+    orc_index_free(I);
+}
+
+/* Balsara's viscosity limiter from div v, |curl v|, sound speed and h. */
+static double orc_balsara(double div, double curl, double cs, double h)
+{
+    double ad = fabs(div);
+    return ad / (ad + curl + 1e-4 * cs / h);
+}
+
+/*
  * Hydro-force pass for the active particles (NULL = all). Inputs are indexed
  * by particle (all n, neighbours included). Outputs, for active i only:
  * acc (n x 3), dudt, vsig; scale_a / scale_u = sum over pairs of the
  * magnitude of each pair's term (the per-particle absolute scale used for
  * tolerances); n_pairs = |pair set|; hash = neighbour-set checksum.
+ * divv / curlv (both NULL or both given): Balsara's switch on Pi_ij.
  */
 void orc_force(int mode, const uint32_t *X, const double *xc, int64_t n, double L,
                const double *v, const double *m, const double *u, const double *h,
                const double *rho, const double *omega, double alpha, double gamma,
+               const double *divv, const double *curlv,
                const int64_t *active, int64_t n_active, int brute,
                double *acc, double *dudt, double *vsig, double *scale_a, double *scale_u,
                int64_t *n_pairs, uint64_t *hash)
@@ -491,6 +551,7 @@ void orc_force(int mode, const uint32_t *X, const double *xc, int64_t n, double 
             double Pi = (gamma - 1.0) * rho[i] * u[i];
             double ci = sqrt(gamma * Pi / rho[i]);
             double Ai = omega[i] * Pi / (rho[i] * rho[i]);
+            double fi = divv ? orc_balsara(divv[i], curlv[i], ci, h[i]) : 1.0;
             double ax = 0, ay = 0, az = 0, du = 0, vs = 0.0, sa = 0.0, su = 0.0;
             int64_t np = 0;
             uint64_t hs = 0;
@@ -526,6 +587,7 @@ void orc_force(int mode, const uint32_t *X, const double *xc, int64_t n, double 
                 double Fbar = 0.5 * (Fi + Fj);
                 double PIij = 0.0;
                 if (wij < 0.0) PIij = -0.5 * alpha * vsg * wij / (0.5 * (rho[i] + rho[j]));
+                if (divv) PIij *= 0.5 * (fi + orc_balsara(divv[j], curlv[j], cj, h[j]));
                 double coef = m[j] * (Ai * Fi + Aj * Fj + PIij * Fbar);
                 ax -= coef * rij[0];
                 ay -= coef * rij[1];
