@@ -40,7 +40,7 @@ UNIT = "pairs/s"
 FLOPS_DENSITY_PAIR = 30.0   # FP32 flops per density pair (FMA = 2), one pass at the converged h
 FLOPS_FORCE_PAIR = 90.0     # FP32 flops per force pair
 FP32_LANES_PER_SM = 128
-H_PERTURB = 0.02            # per-step log-normal scatter of the h guesses
+H_PERTURB = 0.02            # per-step log-normal scatter of the h guesses: the density change between steps
 
 
 def parse():
@@ -354,6 +354,48 @@ def e2e_steps(S, ctx, wl, dparams, fparams, steps):
                 ms_per_step=t_ms / steps)
 
 
+def balsara_line(S, ctx, wl, dparams, fparams, reps=3):
+    """Secondary line: the 100 % sub-step of the 10M clustered step with
+    Balsara's switch (density + velocity divergence and curl, then the
+    switched force), next to the same sub-step without it."""
+    import torch
+    st, n, dev = wl["st"], wl["n"], wl["h"].device
+    act, h_in = wl["acts"][0], wl["h_ins"][0]
+    dv, cv = torch.zeros(n, device=dev), torch.zeros(n, device=dev)
+
+    def switched():
+        S.sph_density_divcurl(ctx, wl["grid"], wl["h"], act, st["rho"], st["omega"], st["n_ngb"], st["flags"], None,
+                              wl["vel"], dv, cv, dparams)
+        S.sph_hydro_force_balsara(ctx, wl["grid"], wl["vel"], wl["u"], wl["h"], st["rho"], st["omega"], dv, cv, act,
+                                  st["acc"], st["dudt"], st["vsig"], None, fparams)
+
+    def plain():
+        S.sph_density(ctx, wl["grid"], wl["h"], act, st["rho"], st["omega"], st["n_ngb"], st["flags"], None, dparams)
+        S.sph_hydro_force(ctx, wl["grid"], wl["vel"], wl["u"], wl["h"], st["rho"], st["omega"], act, st["acc"],
+                          st["dudt"], st["vsig"], None, fparams)
+
+    out = {}
+    for name, fn in (("switched", switched), ("plain", plain)):
+        wl["h"].copy_(h_in)
+        fn()
+        S.sph_sync_status(ctx)
+        ms, pairs = 0.0, 0
+        for _ in range(reps):
+            wl["h"].copy_(h_in)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            _, stt = S.sph_sync_status(ctx)
+            ms += a.elapsed_time(b)
+            pairs += stt["density_pairs"] + stt["force_pairs"]
+        out[name] = (pairs / (ms / 1e3), ms / reps)
+    return {"workload": "10M clustered, 100 % active sub-step: density + velocity divergence and curl, "
+                        "then the force with Balsara's switch",
+            "value": out["switched"][0], "unit": UNIT, "ms_per_pass": out["switched"][1],
+            "without_switch_ms_per_pass": out["plain"][1]}
+
+
 def batched_line(S, ctx, dev, reps=3):
     """Secondary line: 64 independent boxes (N log-uniform in [4096, 524288])
     in one grid, density (from 2%-scattered converged h) + force, one launch
@@ -492,6 +534,7 @@ def main():
         e2e = e2e_steps(S, ctx, wl, dpar, fpar, max(1, min(3, args.steps)))
     extra = {}
     if not args.no_extra and rank == 0:
+        extra["balsara"] = balsara_line(S, ctx, wl, dpar, fpar)
         del wl
         torch.cuda.empty_cache()
         extra["batched_boxes"] = batched_line(S, ctx, dev)

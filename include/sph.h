@@ -229,6 +229,41 @@ sph_status sph_hydro_force(sph_ctx *ctx, const sph_grid *grid, const float *vel,
                            float *vsig, uint64_t *hash, const sph_params *params, void *stream);
 
 /*
+ * Velocity divergence and curl for Balsara's viscosity switch (the paper's
+ * code runs an "improved SPH", Sec. 1; the forms are Gadget-2's, which
+ * estimates them in its density loop). The density pass of sph_density
+ * (default path only: no path flag), plus, for each active i, over its
+ * neighbour set {j != i : r_ij < h_i} at the final h:
+ *   divv_i  = -(1/rho_i) sum_j m_j v_ij . grad_i W_ij(h_i)
+ *   curlv_i = |(1/rho_i) sum_j m_j v_ij x grad_i W_ij(h_i)|
+ * with v_ij = v_i - v_j, r_ij = x_i - x_j, grad_i W_ij = dW/dr r_ij/r_ij.
+ *   vel    device, n x 3 floats (caller order, all particles);
+ *   divv, curlv  device, n floats: written for active particles.
+ * Other arguments, outputs and the neighbour-list recording as sph_density.
+ * SPH_ERR_INVALID for a missing pointer or a path flag.
+ */
+sph_status sph_density_divcurl(sph_ctx *ctx, const sph_grid *grid, float *h, const int32_t *active,
+                               int64_t n_active, float *rho, float *omega, int32_t *n_ngb, uint8_t *flags,
+                               uint64_t *hash, const float *vel, float *divv, float *curlv,
+                               const sph_params *params, void *stream);
+
+/*
+ * sph_hydro_force with Balsara's switch on the artificial viscosity
+ * (default path only):
+ *   f_i = |divv_i| / (|divv_i| + curlv_i + 1e-4 c_i/h_i),
+ *   Pi_ij -> Pi_ij (f_i + f_j)/2,
+ * so the viscosity fades where the flow is shear-dominated. divv and curlv
+ * are device arrays of n floats for all particles (caller order), e.g. from
+ * sph_density_divcurl. Everything else as sph_hydro_force (same pair source:
+ * the recorded neighbour lists when they match).
+ */
+sph_status sph_hydro_force_balsara(sph_ctx *ctx, const sph_grid *grid, const float *vel, const float *u,
+                                   const float *h, const float *rho, const float *omega, const float *divv,
+                                   const float *curlv, const int32_t *active, int64_t n_active, float *acc,
+                                   float *dudt, float *vsig, uint64_t *hash, const sph_params *params,
+                                   void *stream);
+
+/*
  * Adjoint of the density and force passes (an extension of the paper's hot
  * path, which has no gradients). All particles are active. Given the forward
  * state of the grid's particles -- vel, u (inputs of the force pass) and h,

@@ -57,7 +57,7 @@ def lib():
         L.orc_density.restype = i32
         L.orc_force.argtypes = [i32, P, P, i64, f64, P, P, P, P, P, P, f64, f64, P, P, P, i64, i32,
                                 P, P, P, P, P, P, P]
-        L.orc_divcurl.argtypes = [i32, P, P, i64, f64, P, P, P, P, P, i64, i32, P, P]
+        L.orc_divcurl.argtypes = [i32, P, P, i64, f64, P, P, P, P, P, i64, i32, P, P, P, P]
         L.orc_neighbours.argtypes = [i32, P, P, i64, f64, i64, f64, i32, P, i64]
         L.orc_neighbours.restype = i64
         L.orc_num_threads.restype = i32
@@ -149,18 +149,22 @@ def density(X=None, mass=None, h_init=None, box=1.0, n_target=64.0, tol=1e-10, m
     return out
 
 
-def divcurl(X=None, vel=None, mass=None, h=None, rho=None, box=1.0, active=None, brute=False, xc=None):
+def divcurl(X=None, vel=None, mass=None, h=None, rho=None, box=1.0, active=None, brute=False, xc=None,
+            scales=False):
     """Velocity divergence and |curl| at the given h and rho (entries of
-    inactive particles NaN)."""
+    inactive particles NaN); with scales=True also the per-particle sums of
+    the pair terms' magnitudes (divergence, curl)."""
     mode, Xc, xcc = _geom(X, xc, box)
     n = Xc.shape[0]
     args = [_c(a, np.float64) for a in (vel, mass, h, rho)]
     act = None if active is None else _c(active, np.int64)
     divv = np.full(n, np.nan)
     curlv = np.full(n, np.nan)
+    sd = np.full(n, np.nan)
+    sc = np.full(n, np.nan)
     lib().orc_divcurl(mode, _p(Xc), _p(xcc), n, float(box), *[_p(a) for a in args], _p(act),
-                      0 if act is None else act.size, int(bool(brute)), _p(divv), _p(curlv))
-    return divv, curlv
+                      0 if act is None else act.size, int(bool(brute)), _p(divv), _p(curlv), _p(sd), _p(sc))
+    return (divv, curlv, sd, sc) if scales else (divv, curlv)
 
 
 def force(X=None, vel=None, mass=None, u=None, h=None, rho=None, omega=None, box=1.0,

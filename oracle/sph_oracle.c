@@ -465,11 +465,14 @@ static void orc_hindex_free(orc_hindex *Hx)
  * r_ij / |r_ij| (coincident pairs add nothing). These are the SPH estimates
  * of the velocity gradient that Gadget-2 forms in its density loop for the
  * Balsara switch; the paper's code runs an "improved SPH" of this lineage
- * (Sec. 1).
+ * (Sec. 1). scale_d / scale_c (optional): (1/rho_i) sum_j of the magnitudes
+ * of the pair terms of the divergence and of the curl vector (per-particle
+ * absolute scales for tolerances).
  */
 void orc_divcurl(int mode, const uint32_t *X, const double *xc, int64_t n, double L,
                  const double *v, const double *m, const double *h, const double *rho,
-                 const int64_t *active, int64_t n_active, int brute, double *divv, double *curlv)
+                 const int64_t *active, int64_t n_active, int brute, double *divv, double *curlv,
+                 double *scale_d, double *scale_c)
 {
     orc_pos P = {mode, X, xc, n, L};
     orc_index *I = brute ? NULL : (orc_index *)orc_index_new(X, n);
@@ -481,7 +484,7 @@ void orc_divcurl(int mode, const uint32_t *X, const double *xc, int64_t n, doubl
         for (int64_t a = 0; a < na; ++a) {
             int64_t i = active ? active[a] : a;
             orc_cands_for(&P, I, i, h[i], &cb);
-            double sd = 0.0, sc[3] = {0.0, 0.0, 0.0};
+            double sd = 0.0, sc[3] = {0.0, 0.0, 0.0}, ad = 0.0, ac = 0.0;
             for (int64_t c = 0; c < cb.n; ++c) {
                 int64_t j = cb.a[c];
                 if (j == i) continue;
@@ -489,13 +492,20 @@ void orc_divcurl(int mode, const uint32_t *X, const double *xc, int64_t n, doubl
                 if (!orc_pair(&P, i, j, h[i], rij, &r) || r == 0.0) continue;
                 double g = m[j] * orc_dWdr(r, h[i]) / r;   /* m_j grad_i W = g * r_ij */
                 double vij[3] = {v[3 * i] - v[3 * j], v[3 * i + 1] - v[3 * j + 1], v[3 * i + 2] - v[3 * j + 2]};
-                sd += g * (vij[0] * rij[0] + vij[1] * rij[1] + vij[2] * rij[2]);
-                sc[0] += g * (vij[1] * rij[2] - vij[2] * rij[1]);
-                sc[1] += g * (vij[2] * rij[0] - vij[0] * rij[2]);
-                sc[2] += g * (vij[0] * rij[1] - vij[1] * rij[0]);
+                double td = g * (vij[0] * rij[0] + vij[1] * rij[1] + vij[2] * rij[2]);
+                double tc[3] = {g * (vij[1] * rij[2] - vij[2] * rij[1]), g * (vij[2] * rij[0] - vij[0] * rij[2]),
+                                g * (vij[0] * rij[1] - vij[1] * rij[0])};
+                sd += td;
+                sc[0] += tc[0];
+                sc[1] += tc[1];
+                sc[2] += tc[2];
+                ad += fabs(td);
+                ac += sqrt(tc[0] * tc[0] + tc[1] * tc[1] + tc[2] * tc[2]);
             }
             divv[i] = -sd / rho[i];
             curlv[i] = sqrt(sc[0] * sc[0] + sc[1] * sc[1] + sc[2] * sc[2]) / rho[i];
+            if (scale_d) scale_d[i] = ad / rho[i];
+            if (scale_c) scale_c[i] = ac / rho[i];
         }
         free(cb.a);
     }

@@ -16,7 +16,7 @@ from .abi import (SPH_FIXED_H, SPH_FP64, SPH_H_GUESS, SPH_PLAIN_FP32, SPH_TIME_K
                   default_params, sph_params, sph_stats)
 
 __all__ = ["Context", "Grid", "sph_create", "sph_build_grid", "sph_build_grid_batched", "sph_grid_update",
-           "sph_density", "sph_hydro_force", "sph_backward", "sph_sync_status", "sph_grid_export", "sph_sort_keys_static", "density",
+           "sph_density", "sph_hydro_force", "sph_density_divcurl", "sph_hydro_force_balsara", "sph_backward", "sph_sync_status", "sph_grid_export", "sph_sort_keys_static", "density",
            "hydro_force", "default_params", "sph_params", "sph_stats", "SPHError", "SPH_FP64",
            "SPH_PLAIN_FP32", "SPH_FIXED_H", "SPH_H_GUESS", "SPH_TIME_KERNELS", "SPH_WARP_GROUP", "SPH_DENSITY_BUFFERED", "SPH_PER_THREAD_WALK", "SPH_COOP_WALK", "SPH_WARP_WALK", "SPH_NO_LISTS"]
 
@@ -140,6 +140,31 @@ def sph_hydro_force(ctx: Context, grid: Grid, vel, u, h, rho, omega, active, acc
                                       _ptr(active, torch.int32, "active"), na, _ptr(acc, f, "acc"),
                                       _ptr(dudt, f, "dudt"), _ptr(vsig, f, "vsig"),
                                       _ptr(hash, torch.int64, "hash"), ctypes.byref(params), _stream()))
+
+
+def sph_density_divcurl(ctx: Context, grid: Grid, h, active, rho, omega, n_ngb, flags, hash, vel, divv, curlv,
+                        params: sph_params = None):
+    na = 0 if active is None else active.numel()
+    f = torch.float32
+    ctx.check(ctx.lib.sph_density_divcurl(ctx.handle, grid.handle, _ptr(h, f, "h"),
+                                          _ptr(active, torch.int32, "active"), na, _ptr(rho, f, "rho"),
+                                          _ptr(omega, f, "omega"), _ptr(n_ngb, torch.int32, "n_ngb"),
+                                          _ptr(flags, torch.uint8, "flags"), _ptr(hash, torch.int64, "hash"),
+                                          _ptr(vel, f, "vel"), _ptr(divv, f, "divv"), _ptr(curlv, f, "curlv"),
+                                          ctypes.byref(params or default_params()), _stream()))
+
+
+def sph_hydro_force_balsara(ctx: Context, grid: Grid, vel, u, h, rho, omega, divv, curlv, active, acc, dudt, vsig,
+                            hash=None, params: sph_params = None):
+    na = 0 if active is None else active.numel()
+    f = torch.float32
+    ctx.check(ctx.lib.sph_hydro_force_balsara(ctx.handle, grid.handle, _ptr(vel, f, "vel"), _ptr(u, f, "u"),
+                                              _ptr(h, f, "h"), _ptr(rho, f, "rho"), _ptr(omega, f, "omega"),
+                                              _ptr(divv, f, "divv"), _ptr(curlv, f, "curlv"),
+                                              _ptr(active, torch.int32, "active"), na, _ptr(acc, f, "acc"),
+                                              _ptr(dudt, f, "dudt"), _ptr(vsig, f, "vsig"),
+                                              _ptr(hash, torch.int64, "hash"),
+                                              ctypes.byref(params or default_params()), _stream()))
 
 
 def sph_backward(ctx: Context, grid: Grid, vel, u, h, rho, omega, g_acc, g_rho, g_pos, g_u, g_mass,

@@ -200,9 +200,10 @@ sph_status sph_grid_export(const sph_grid* g, int32_t* perm, uint64_t* keys, uin
     return SPH_OK;
 }
 
-sph_status sph_density(sph_ctx* ctx, const sph_grid* grid, float* h, const int32_t* active, int64_t n_active,
-                       float* rho, float* omega, int32_t* n_ngb, uint8_t* flags, uint64_t* hash,
-                       const sph_params* params, void* stream) {
+static sph_status density_call(sph_ctx* ctx, const sph_grid* grid, float* h, const int32_t* active,
+                               int64_t n_active, float* rho, float* omega, int32_t* n_ngb, uint8_t* flags,
+                               uint64_t* hash, const float* vel, float* divv, float* curlv,
+                               const sph_params* params, void* stream) {
     if (!ctx) return SPH_ERR_INVALID;
     if (!grid || grid->ctx != ctx) return fail(ctx, SPH_ERR_INVALID, "grid is NULL or from another context");
     if (!h || !rho || !omega || !n_ngb || !flags) return fail(ctx, SPH_ERR_INVALID, "h, rho, omega, n_ngb, flags are required");
@@ -234,6 +235,9 @@ sph_status sph_density(sph_ctx* ctx, const sph_grid* grid, float* h, const int32
     a.blocks_per_sm = params->blocks_per_sm;
     a.time_kernels = (params->flags & SPH_TIME_KERNELS) ? 1 : 0;
     a.buffered = (params->flags & SPH_DENSITY_BUFFERED) ? 1 : 0;
+    a.vel = vel;
+    a.divv = divv;
+    a.curlv = curlv;
     cudaError_t e = path == Path::Plain       ? run_density_plain(ctx, a, na, s)
                     : path == Path::WarpGroup ? launch_density(ctx, a, s)
                     : path == Path::Wpp       ? launch_density_wpp(ctx, a, na, s)
@@ -244,10 +248,29 @@ sph_status sph_density(sph_ctx* ctx, const sph_grid* grid, float* h, const int32
     return SPH_OK;
 }
 
-sph_status sph_hydro_force(sph_ctx* ctx, const sph_grid* grid, const float* vel, const float* u,
-                           const float* h, const float* rho, const float* omega, const int32_t* active,
-                           int64_t n_active, float* acc, float* dudt, float* vsig, uint64_t* hash,
-                           const sph_params* params, void* stream) {
+sph_status sph_density(sph_ctx* ctx, const sph_grid* grid, float* h, const int32_t* active, int64_t n_active,
+                       float* rho, float* omega, int32_t* n_ngb, uint8_t* flags, uint64_t* hash,
+                       const sph_params* params, void* stream) {
+    return density_call(ctx, grid, h, active, n_active, rho, omega, n_ngb, flags, hash, nullptr, nullptr, nullptr,
+                        params, stream);
+}
+
+sph_status sph_density_divcurl(sph_ctx* ctx, const sph_grid* grid, float* h, const int32_t* active,
+                               int64_t n_active, float* rho, float* omega, int32_t* n_ngb, uint8_t* flags,
+                               uint64_t* hash, const float* vel, float* divv, float* curlv,
+                               const sph_params* params, void* stream) {
+    if (!ctx) return SPH_ERR_INVALID;
+    if (!vel || !divv || !curlv) return fail(ctx, SPH_ERR_INVALID, "vel, divv and curlv are required");
+    if (params && pick_path(params->flags) != Path::Wpp)
+        return fail(ctx, SPH_ERR_INVALID, "velocity divergence and curl run on the default path only");
+    return density_call(ctx, grid, h, active, n_active, rho, omega, n_ngb, flags, hash, vel, divv, curlv, params,
+                        stream);
+}
+
+static sph_status force_call(sph_ctx* ctx, const sph_grid* grid, const float* vel, const float* u,
+                             const float* h, const float* rho, const float* omega, const float* divv,
+                             const float* curlv, const int32_t* active, int64_t n_active, float* acc, float* dudt,
+                             float* vsig, uint64_t* hash, const sph_params* params, void* stream) {
     if (!ctx) return SPH_ERR_INVALID;
     if (!grid || grid->ctx != ctx) return fail(ctx, SPH_ERR_INVALID, "grid is NULL or from another context");
     if (!vel || !u || !h || !rho || !omega || !acc || !dudt || !vsig)
@@ -280,6 +303,8 @@ sph_status sph_hydro_force(sph_ctx* ctx, const sph_grid* grid, const float* vel,
     a.fp64 = (params->flags & SPH_FP64) ? 1 : 0;
     a.blocks_per_sm = params->blocks_per_sm;
     a.time_kernels = (params->flags & SPH_TIME_KERNELS) ? 1 : 0;
+    a.divv = divv;
+    a.curlv = curlv;
     cudaError_t e = path == Path::Plain       ? launch_force_plain(ctx, a, na, s)
                     : path == Path::WarpGroup ? launch_force(ctx, a, s)
                     : path == Path::Wpp       ? launch_force_wpp(ctx, a, na, s)
@@ -288,6 +313,27 @@ sph_status sph_hydro_force(sph_ctx* ctx, const sph_grid* grid, const float* vel,
     if (!e) e = cudaGetLastError();
     if (e) return cuda_fail(ctx, e, "sph_hydro_force");
     return SPH_OK;
+}
+
+sph_status sph_hydro_force(sph_ctx* ctx, const sph_grid* grid, const float* vel, const float* u,
+                           const float* h, const float* rho, const float* omega, const int32_t* active,
+                           int64_t n_active, float* acc, float* dudt, float* vsig, uint64_t* hash,
+                           const sph_params* params, void* stream) {
+    return force_call(ctx, grid, vel, u, h, rho, omega, nullptr, nullptr, active, n_active, acc, dudt, vsig, hash,
+                      params, stream);
+}
+
+sph_status sph_hydro_force_balsara(sph_ctx* ctx, const sph_grid* grid, const float* vel, const float* u,
+                                   const float* h, const float* rho, const float* omega, const float* divv,
+                                   const float* curlv, const int32_t* active, int64_t n_active, float* acc,
+                                   float* dudt, float* vsig, uint64_t* hash, const sph_params* params,
+                                   void* stream) {
+    if (!ctx) return SPH_ERR_INVALID;
+    if (!divv || !curlv) return fail(ctx, SPH_ERR_INVALID, "divv and curlv are required");
+    if (params && pick_path(params->flags & ~SPH_DENSITY_BUFFERED) != Path::Wpp)
+        return fail(ctx, SPH_ERR_INVALID, "the Balsara switch runs on the default path only");
+    return force_call(ctx, grid, vel, u, h, rho, omega, divv, curlv, active, n_active, acc, dudt, vsig, hash,
+                      params, stream);
 }
 
 sph_status sph_backward(sph_ctx* ctx, const sph_grid* grid, const float* vel, const float* u, const float* h,

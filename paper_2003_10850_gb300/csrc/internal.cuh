@@ -50,6 +50,7 @@ struct sph_grid {
     float4* fthermo = nullptr;             // per force call, sorted: rho, A, c, 1/h
     float4* fposh = nullptr;               // per force call, sorted: leaf-relative position, h
     float4* fvm = nullptr;                 // per force call, sorted: v, m
+    float* fbal = nullptr;                 // per force call with the switch, sorted: Balsara factor
     // per-call scratch, sized at build so that calls never allocate
     int32_t* act = nullptr;                // active particles, sorted indices, sorted order
     uint8_t* flag = nullptr;               // n
@@ -142,6 +143,10 @@ struct DensityLaunch {
     int blocks_per_sm;
     int time_kernels;
     int buffered;
+    // velocity divergence and curl at the final h (default path only; NULL: not asked)
+    const float* vel = nullptr;
+    float* divv = nullptr;
+    float* curlv = nullptr;
 };
 cudaError_t launch_density(sph_ctx* ctx, const DensityLaunch& a, cudaStream_t s);
 cudaError_t run_density_plain(sph_ctx* ctx, const DensityLaunch& a, int64_t n_active,
@@ -163,6 +168,9 @@ struct ForceLaunch {
     int fp64;
     int blocks_per_sm;
     int time_kernels;
+    // Balsara's switch (default path only; NULL: no switch)
+    const float* divv = nullptr;
+    const float* curlv = nullptr;
 };
 cudaError_t launch_force(sph_ctx* ctx, const ForceLaunch& a, cudaStream_t s);
 cudaError_t launch_force_plain(sph_ctx* ctx, const ForceLaunch& a, int64_t n_active,
@@ -193,10 +201,11 @@ cudaError_t launch_density_wpp(sph_ctx* ctx, const DensityLaunch& a, int64_t n_a
 cudaError_t launch_force_wpp(sph_ctx* ctx, const ForceLaunch& a, int64_t n_active, cudaStream_t s);
 
 // tpp.cu (per-thread walks)
-// list_h / h_changed (optional): set *h_changed if some h differs from list_h
+// list_h / h_changed (optional): set *h_changed if some h differs from list_h;
+// divv / curlv (optional, caller order): Balsara factors into g->fbal
 void force_pack(const sph_grid* g, const float* vel, const float* u, const float* h, const float* rho,
                 const float* omega, float gamma, cudaStream_t s, const float* list_h = nullptr,
-                unsigned* h_changed = nullptr);
+                unsigned* h_changed = nullptr, const float* divv = nullptr, const float* curlv = nullptr);
 cudaError_t launch_density_tpp(sph_ctx* ctx, const DensityLaunch& a, int64_t n_active, cudaStream_t s);
 cudaError_t launch_force_tpp(sph_ctx* ctx, const ForceLaunch& a, int64_t n_active, cudaStream_t s);
 

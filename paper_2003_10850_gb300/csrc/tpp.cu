@@ -521,7 +521,9 @@ __global__ void k_force_pack(int n, const int32_t* __restrict__ perm, const floa
                              const float* __restrict__ u, const float* __restrict__ h, const float* __restrict__ rho,
                              const float* __restrict__ omega, float gam, const float4* __restrict__ posf,
                              float4* __restrict__ fvel, float4* __restrict__ fthermo, float4* __restrict__ fposh,
-                             float4* __restrict__ fvm, const float* __restrict__ list_h, unsigned* h_changed) {
+                             float4* __restrict__ fvm, const float* __restrict__ list_h, unsigned* h_changed,
+                             const float* __restrict__ divv, const float* __restrict__ curlv,
+                             float* __restrict__ fbal) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
     const int o = perm[p];
@@ -531,7 +533,13 @@ __global__ void k_force_pack(int n, const int32_t* __restrict__ perm, const floa
     const float vx = vel[3 * (size_t)o], vy = vel[3 * (size_t)o + 1], vz = vel[3 * (size_t)o + 2];
     fvel[p] = make_float4(vx, vy, vz, hh);
     fvm[p] = make_float4(vx, vy, vz, f.w);
-    fthermo[p] = make_float4(r, omega[o] * P / (r * r), sqrtf(gam * P / r), 1.f / hh);
+    const float cs = sqrtf(gam * P / r);
+    fthermo[p] = make_float4(r, omega[o] * P / (r * r), cs, 1.f / hh);
+    // Balsara's limiter f = |div v| / (|div v| + |curl v| + 1e-4 c/h)
+    if (fbal) {
+        const float ad = fabsf(divv[o]);
+        fbal[p] = ad / (ad + curlv[o] + 1e-4f * cs / hh);
+    }
     fposh[p] = make_float4(f.x, f.y, f.z, hh);
     // recorded neighbour lists are usable only if every h equals the one they were made with
     if (list_h && !(hh == list_h[p])) atomicOr(h_changed, 1u);
@@ -912,10 +920,12 @@ cudaError_t launch_density_tpp(sph_ctx* ctx, const DensityLaunch& a, int64_t n_a
 }
 
 void force_pack(const sph_grid* g, const float* vel, const float* u, const float* h, const float* rho,
-                const float* omega, float gamma, cudaStream_t s, const float* list_h, unsigned* h_changed) {
+                const float* omega, float gamma, cudaStream_t s, const float* list_h, unsigned* h_changed,
+                const float* divv, const float* curlv) {
     const int n = (int)g->n;
     k_force_pack<<<(n + 255) / 256, 256, 0, s>>>(n, g->perm, vel, u, h, rho, omega, gamma, g->posf, g->fvel, g->fthermo,
-                                                 g->fposh, g->fvm, list_h, h_changed);
+                                                 g->fposh, g->fvm, list_h, h_changed, divv, curlv,
+                                                 divv ? g->fbal : nullptr);
 }
 
 cudaError_t launch_force_tpp(sph_ctx* ctx, const ForceLaunch& a, int64_t n_active, cudaStream_t s) {

@@ -110,6 +110,12 @@ struct WppArgs {
     const uint32_t* ext_n;       // nonzero: the particle's extra partners are not usable
     float* list_h;
     unsigned* list_st;           // see kListSt
+    // density: velocity divergence and curl (NULL: not asked)
+    const float4* vpack;         // sorted (v, m)
+    float* divv;
+    float* curlv;
+    // force: Balsara factors (sorted order; NULL: no switch)
+    const float* fbal;
     int32_t* fb_list;
     long long list_pool;
     int list_chunk;              // pool entries a warp reserves at a time
@@ -505,13 +511,16 @@ __device__ __forceinline__ bool wpp_h_update(float& h, float f, float N, float d
 struct WppForceI {
     float vx, vy, vz;
     float hinv, rho, A, c, norm;   // norm = 8/(pi h^4)
+    float f;                       // Balsara factor (1 without the switch)
 };
 
 // One force pair term, Gadget-2 grad-h form with signal-velocity viscosity,
 // added to i's per-lane sums. (dx, dy, dz) = x_j - x_i; vj = (v_j, m_j);
-// thj = (rho_j, A_j, c_j, 1/h_j).
+// thj = (rho_j, A_j, c_j, 1/h_j); fj = j's Balsara factor (1 without the
+// switch: BAL = false leaves Pi_ij alone; BAL = true multiplies it by (f_i + f_j)/2).
+template <bool BAL>
 __device__ __forceinline__ void wpp_force_pair(const WppForceI& I, float dx, float dy, float dz, float4 vj, float4 thj,
-                                               float alpha, float& Sx, float& Sy, float& Sz, float& Su,
+                                               float fj, float alpha, float& Sx, float& Sy, float& Sz, float& Su,
                                                float& vsmax) {
     const float kNorm = (float)(8.0 / 3.141592653589793);
     const float r2 = dx * dx + dy * dy + dz * dz;
@@ -531,7 +540,8 @@ __device__ __forceinline__ void wpp_force_pair(const WppForceI& I, float dx, flo
     const float vs = I.c + thj.z - 3.f * wij;
     vsmax = fmaxf(vsmax, vs);
     // Pi_ij = -(alpha/2) v_sig w_ij / rho_bar, rho_bar = (rho_i + rho_j)/2
-    const float PI = wij < 0.f ? __fdividef(-alpha * vs * wij, I.rho + thj.x) : 0.f;
+    float PI = wij < 0.f ? __fdividef(-alpha * vs * wij, I.rho + thj.x) : 0.f;
+    if (BAL) PI *= 0.5f * (I.f + fj);
     const float Fbar = 0.5f * (Fi + Fj);
     const float mj = vj.w;
     const float coef = mj * (I.A * Fi + thj.y * Fj + PI * Fbar);
@@ -545,7 +555,7 @@ __device__ __forceinline__ void wpp_force_pair(const WppForceI& I, float dx, flo
 // Density
 // ---------------------------------------------------------------------------
 
-template <bool HASH, int MINB>
+template <bool HASH, int MINB, bool DIVCURL>
 __global__ void __launch_bounds__(kWppThreads, MINB) k_density_wpp(WppArgs a) {
     __shared__ WppSmem smem[kWppWarps];
     WppSmem& sm = smem[threadIdx.x >> 5];
@@ -765,46 +775,72 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_density_wpp(WppArgs a) {
                 wpp_fold2(Smw, Smdw, Smw, Cmw, Smdw, Cmdw);
                 nn = warp_sum(nn);
                 if (HASH) hs = warp_sum(hs);
-                if (a.nbr) {
-                    // Record the neighbour list {j != i : r_ij < h_i} at the final h for
-                    // the force pass: nn entries (the count of the final evaluation),
-                    // reserved from the warp's chunk of the pool, enumerated again with
-                    // the same exact predicate from the near list, the leaf list, or a
-                    // fresh walk, whichever the final evaluation could rely on.
+                if (a.nbr || DIVCURL) {
+                    // Enumerate the neighbour set {j != i : r_ij < h_i} at the final h
+                    // again, with the same exact predicate, from the near list, the leaf
+                    // list, or a fresh walk, whichever the final evaluation relied on:
+                    // - to record it for the force pass (nn entries, reserved from the
+                    //   warp's chunk of the list pool);
+                    // - to sum the velocity divergence and curl over it.
                     int loff = -1;
-                    if (nn > a.list_chunk) {
-                        unsigned long long o = 0;
-                        if (lane == 0) o = atomicAdd(reinterpret_cast<unsigned long long*>(a.list_st + 4),
-                                                     (unsigned long long)nn);
-                        o = __shfl_sync(0xffffffffu, o, 0);
-                        if ((long long)o + nn <= a.list_pool) loff = (int)o;
-                    } else {
-                        if (ch_next + nn > ch_end) {
+                    if (a.nbr) {
+                        if (nn > a.list_chunk) {
                             unsigned long long o = 0;
                             if (lane == 0) o = atomicAdd(reinterpret_cast<unsigned long long*>(a.list_st + 4),
-                                                         (unsigned long long)a.list_chunk);
+                                                         (unsigned long long)nn);
                             o = __shfl_sync(0xffffffffu, o, 0);
-                            ch_next = (long long)o;
-                            ch_end = ch_next + a.list_chunk;
+                            if ((long long)o + nn <= a.list_pool) loff = (int)o;
+                        } else {
+                            if (ch_next + nn > ch_end) {
+                                unsigned long long o = 0;
+                                if (lane == 0) o = atomicAdd(reinterpret_cast<unsigned long long*>(a.list_st + 4),
+                                                             (unsigned long long)a.list_chunk);
+                                o = __shfl_sync(0xffffffffu, o, 0);
+                                ch_next = (long long)o;
+                                ch_end = ch_next + a.list_chunk;
+                            }
+                            if (ch_next + nn <= a.list_pool) loff = (int)ch_next;
+                            ch_next += nn;
                         }
-                        if (ch_next + nn <= a.list_pool) loff = (int)ch_next;
-                        ch_next += nn;
                     }
-                    if (loff >= 0 && nn > 0) {
-                        int32_t* dst = a.nbr + loff;
+                    const bool rec = loff >= 0 && nn > 0;
+                    // per-lane sums of m_j w'(q)/r (v_ij . r_ij) and (v_ij x r_ij)
+                    float Dd = 0.f, Dx = 0.f, Dy = 0.f, Dz = 0.f;
+                    if (rec || DIVCURL) {
+                        int32_t* dst = rec ? a.nbr + loff : nullptr;
                         int pos = 0;
                         double HHf = -1.0;
+                        const float hinv = 1.f / h;
+                        const float4 vi = DIVCURL ? a.vpack[p] : make_float4(0.f, 0.f, 0.f, 0.f);
                         auto exact_f = [&](int q) {
                             if (HHf < 0.0) HHf = wpp_hh(h, B.L);
                             return exact_pred(exact_d2(Xi, a.posm[q]), HHf);
                         };
-                        auto put = [&](bool in, int q) {
-                            const unsigned hm = __ballot_sync(0xffffffffu, in);
-                            if (in) {
-                                const int k = pos + __popc(hm & lt);
-                                if (k < nn) dst[k] = q;
+                        // d = x_j - x_i; r_ij = -d, v_ij = v_i - v_j
+                        auto vterm = [&](float dx, float dy, float dz, int q) {
+                            const float r2 = dx * dx + dy * dy + dz * dz;
+                            if (!(r2 > 0.f)) return;   // coincident: no direction
+                            const float rinv = rsqrtf(r2);
+                            float w_, dw;
+                            spline<float>(r2 * rinv * hinv, w_, dw);
+                            const float4 vj = __ldg(a.vpack + q);
+                            const float g = vj.w * dw * rinv;
+                            const float vx = vi.x - vj.x, vy = vi.y - vj.y, vz = vi.z - vj.z;
+                            Dd -= g * (vx * dx + vy * dy + vz * dz);
+                            Dx -= g * (vy * dz - vz * dy);
+                            Dy -= g * (vz * dx - vx * dz);
+                            Dz -= g * (vx * dy - vy * dx);
+                        };
+                        auto put = [&](bool in, int q, float dx, float dy, float dz) {
+                            if (DIVCURL && in) vterm(dx, dy, dz, q);
+                            if (rec) {
+                                const unsigned hm = __ballot_sync(0xffffffffu, in);
+                                if (in) {
+                                    const int k = pos + __popc(hm & lt);
+                                    if (k < nn) dst[k] = q;
+                                }
+                                pos += __popc(hm);
                             }
-                            pos += __popc(hm);
                         };
                         if (near_ok) {
                             const float eL = ebmax + 2.f * rel * h;
@@ -814,12 +850,19 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_density_wpp(WppArgs a) {
                                 const int k = k0 + (int)lane;
                                 bool in = false;
                                 int q = p;
+                                float dx = 0.f, dy = 0.f, dz = 0.f;
                                 if (k < nnear) {
                                     const float r2 = sm.hit.n.d[k].x;
                                     q = sm.hit.n.j[k];
                                     in = q != p && r2 < hi2 && (r2 < lo2 || exact_f(q));
+                                    if (DIVCURL && in) {
+                                        const uint4 Xj = a.posm[q];
+                                        dx = (float)(int)(Xj.x - Xi.x) * sf;
+                                        dy = (float)(int)(Xj.y - Xi.y) * sf;
+                                        dz = (float)(int)(Xj.z - Xi.z) * sf;
+                                    }
                                 }
-                                put(in, q);
+                                put(in, q, dx, dy, dz);
                             }
                         } else {
                             // the candidates of the leaf list at h, as process(false) tests them
@@ -849,7 +892,7 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_density_wpp(WppArgs a) {
                                     if (__any_sync(0xffffffffu, band)) {
                                         if (band) in = exact_f(q);
                                     }
-                                    put(in, q);
+                                    put(in, q, dx, dy, dz);
                                 }
                             };
                             if (!complete) {
@@ -860,14 +903,30 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_density_wpp(WppArgs a) {
                             }
                             record();
                         }
-                        if (pos != nn) loff = -1;   // cannot happen: the same predicate counted nn
+                        if (rec && pos != nn) loff = -1;   // cannot happen: the same predicate counted nn
                     }
-                    if (lane == 0) {
-                        a.nbr_off[p] = loff >= 0 ? loff : 0;
-                        a.nbr_n[p] = loff >= 0 ? nn : -1;
-                        a.list_h[p] = h;
+                    if (a.nbr) {
+                        if (lane == 0) {
+                            a.nbr_off[p] = loff >= 0 ? loff : 0;
+                            a.nbr_n[p] = loff >= 0 ? nn : -1;
+                            a.list_h[p] = h;
+                        }
+                        ++c_lists;
                     }
-                    ++c_lists;
+                    if (DIVCURL) {
+                        // div = -(1/rho) sum m v_ij . grad W, curl = |(1/rho) sum m v_ij x grad W|,
+                        // grad_i W = 8/(pi h^4) w'(q) r_ij / r
+                        const float fs = wpp_fold4(Dd, Dx, Dy, Dz);
+                        const float sd = __shfl_sync(0xffffffffu, fs, 0), sx = __shfl_sync(0xffffffffu, fs, 8),
+                                    sy = __shfl_sync(0xffffffffu, fs, 16), sz = __shfl_sync(0xffffffffu, fs, 24);
+                        if (lane == 0) {
+                            const float hinv = 1.f / h;
+                            const float rho = 2.5464790894703255f * __fsub_rn(Smw, Cmw) * hinv_cube(h);
+                            const float nr = 2.5464790894703255f * hinv_cube(h) * hinv / rho;
+                            a.divv[oi] = -nr * sd;
+                            a.curlv[oi] = nr * sqrtf(sx * sx + sy * sy + sz * sz);
+                        }
+                    }
                 }
                 if (lane == 0) {
                     const float smw = __fsub_rn(Smw, Cmw), smdw = __fsub_rn(Smdw, Cmdw);
@@ -898,7 +957,7 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_density_wpp(WppArgs a) {
 // Force
 // ---------------------------------------------------------------------------
 
-template <bool HASH, int MINB>
+template <bool HASH, int MINB, bool BAL>
 __global__ void __launch_bounds__(kWppThreads, MINB) k_force_wpp(WppArgs a) {
     __shared__ WppSmem smem[kWppWarps];
     WppSmem& sm = smem[threadIdx.x >> 5];
@@ -952,7 +1011,7 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_force_wpp(WppArgs a) {
                 const float4 vi = a.fvm[p];
                 const float4 thi = a.fthermo[p];
                 const WppForceI I = {vi.x, vi.y, vi.z, thi.w, thi.x, thi.y, thi.z,
-                                     kNorm * thi.w * thi.w * thi.w * thi.w};
+                                     kNorm * thi.w * thi.w * thi.w * thi.w, BAL ? a.fbal[p] : 1.f};
                 // i side of the band test: h_i (1 +- 2^-19) (the leaf's rounding bound is added per leaf)
                 const float hiP = hi * (1.f + 2.f * rel), hiM = hi * (1.f - 2.f * rel);
                 double HHi = -1.0;
@@ -967,8 +1026,8 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_force_wpp(WppArgs a) {
                     if ((int)lane < k) {
                         const float4 e = sm.hit.f[lane];
                         const int q = __float_as_int(e.w);
-                        wpp_force_pair(I, e.x, e.y, e.z, __ldg(a.fvm + q), __ldg(a.fthermo + q), alpha, Sx, Sy, Sz, Su,
-                                       vsmax);
+                        wpp_force_pair<BAL>(I, e.x, e.y, e.z, __ldg(a.fvm + q), __ldg(a.fthermo + q),
+                                            BAL ? __ldg(a.fbal + q) : 1.f, alpha, Sx, Sy, Sz, Su, vsmax);
                     }
                     __syncwarp();
                 };
@@ -1204,7 +1263,7 @@ __global__ void __launch_bounds__(256) k_list_sort(int n, const uint32_t* __rest
 // fold as k_force_wpp. If the lists cannot serve the call at all the kernel
 // does nothing and the walk that follows takes the whole active set;
 // particles whose own lists did not fit go to fb_list for that walk.
-template <bool HASH>
+template <bool HASH, bool BAL>
 __global__ void __launch_bounds__(128) k_force_list(WppArgs a) {
     if (!wpp_lists_valid(a.list_st, a.n_total)) return;
     const unsigned lane = lane_id();
@@ -1226,19 +1285,32 @@ __global__ void __launch_bounds__(128) k_force_list(WppArgs a) {
         const int oi = a.perm[p];
         const float4 vi = a.fvm[p];
         const float4 thi = a.fthermo[p];
-        const WppForceI I = {vi.x, vi.y, vi.z, thi.w, thi.x, thi.y, thi.z, kNorm * thi.w * thi.w * thi.w * thi.w};
+        const WppForceI I = {vi.x, vi.y, vi.z, thi.w, thi.x, thi.y, thi.z, kNorm * thi.w * thi.w * thi.w * thi.w,
+                             BAL ? a.fbal[p] : 1.f};
         float Sx = 0.f, Sy = 0.f, Sz = 0.f, Su = 0.f, vsmax = 0.f;
         unsigned long long hs = 0;
         const int tot = cn + (int)(e1 - e0);
         const int32_t* ln = a.nbr + a.nbr_off[p];
         const int32_t* le = a.ext + e0;
-        for (int k = (int)lane; k < tot; k += 32) {
-            const int q = k < cn ? ln[k] : le[k - cn];
-            const uint4 Xj = a.posm[q];
-            const float dx = (float)(int)(Xj.x - Xi.x) * sf, dy = (float)(int)(Xj.y - Xi.y) * sf,
-                        dz = (float)(int)(Xj.z - Xi.z) * sf;
-            wpp_force_pair(I, dx, dy, dz, __ldg(a.fvm + q), __ldg(a.fthermo + q), a.alpha, Sx, Sy, Sz, Su, vsmax);
-            if (HASH) hs += splitmix64((unsigned long long)a.perm[q]);
+        // two pairs per lane per step (k and k + 32), their loads issued together;
+        // each lane still sums its pairs in the order k, k + 32, k + 64, ...
+        for (int k = (int)lane; k < tot; k += 64) {
+            const int k1 = k + 32;
+            const bool two = k1 < tot;
+            const int q0 = k < cn ? ln[k] : le[k - cn];
+            const int q1 = two ? (k1 < cn ? ln[k1] : le[k1 - cn]) : q0;
+            const uint4 X0 = a.posm[q0], X1 = a.posm[q1];
+            const float4 v0 = __ldg(a.fvm + q0), v1 = __ldg(a.fvm + q1);
+            const float4 t0 = __ldg(a.fthermo + q0), t1 = __ldg(a.fthermo + q1);
+            const float b0 = BAL ? __ldg(a.fbal + q0) : 1.f, b1 = BAL ? __ldg(a.fbal + q1) : 1.f;
+            wpp_force_pair<BAL>(I, (float)(int)(X0.x - Xi.x) * sf, (float)(int)(X0.y - Xi.y) * sf,
+                                (float)(int)(X0.z - Xi.z) * sf, v0, t0, b0, a.alpha, Sx, Sy, Sz, Su, vsmax);
+            if (HASH) hs += splitmix64((unsigned long long)a.perm[q0]);
+            if (two) {
+                wpp_force_pair<BAL>(I, (float)(int)(X1.x - Xi.x) * sf, (float)(int)(X1.y - Xi.y) * sf,
+                                    (float)(int)(X1.z - Xi.z) * sf, v1, t1, b1, a.alpha, Sx, Sy, Sz, Su, vsmax);
+                if (HASH) hs += splitmix64((unsigned long long)a.perm[q1]);
+            }
         }
         const float fs = wpp_fold4(Sx, Sy, Sz, Su);
         vsmax = warp_max(vsmax);
@@ -1315,6 +1387,15 @@ static WppArgs wpp_common(sph_ctx* ctx, const sph_grid* g, unsigned* queue) {
     return c;
 }
 
+// Sorted (v, m) for the density pass's velocity divergence and curl.
+__global__ void k_vel_pack(int n, const int32_t* __restrict__ perm, const float* __restrict__ vel,
+                           const float4* __restrict__ posf, float4* __restrict__ vm) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const size_t o = (size_t)perm[p];
+    vm[p] = make_float4(vel[3 * o], vel[3 * o + 1], vel[3 * o + 2], posf[p].w);
+}
+
 // Grid of a warp-per-particle helper kernel over n particles (256 threads).
 static int helper_blocks(sph_ctx* ctx, int64_t n) {
     return (int)std::max<long long>(1, std::min<long long>((long long)ctx->sm_count * 8, (n + 7) / 8));
@@ -1339,6 +1420,13 @@ cudaError_t launch_density_wpp(sph_ctx* ctx, const DensityLaunch& a, int64_t n_a
     c.max_iter = a.max_iter;
     c.guess_h = a.guess_h;
     c.fixed_h = a.fixed_h;
+    if (a.divv) {
+        k_vel_pack<<<(int)((g->n + 255) / 256), 256, 0, s>>>((int)g->n, g->perm, a.vel, g->posf, g->fvm);
+        ++ctx->launches;
+        c.vpack = g->fvm;
+        c.divv = a.divv;
+        c.curlv = a.curlv;
+    }
     // Neighbour lists: recorded for the active particles of every call. They
     // can serve a force call only if every particle was active (checked on the
     // device: lists written == n); the extra partners are built when the active
@@ -1359,13 +1447,12 @@ cudaError_t launch_density_wpp(sph_ctx* ctx, const DensityLaunch& a, int64_t n_a
     }
     WppSpan sp;
     if ((e = span_begin(ctx, a.time_kernels, 0, s, sp))) return e;
-    if (bps <= 6) {
-        if (a.hash) k_density_wpp<true, 6><<<blocks, kWppThreads, 0, s>>>(c);
-        else k_density_wpp<false, 6><<<blocks, kWppThreads, 0, s>>>(c);
-    } else {
-        if (a.hash) k_density_wpp<true, 8><<<blocks, kWppThreads, 0, s>>>(c);
-        else k_density_wpp<false, 8><<<blocks, kWppThreads, 0, s>>>(c);
-    }
+    const bool dc = a.divv != nullptr;
+    auto kd = bps <= 6 ? (a.hash ? (dc ? k_density_wpp<true, 6, true> : k_density_wpp<true, 6, false>)
+                                 : (dc ? k_density_wpp<false, 6, true> : k_density_wpp<false, 6, false>))
+                       : (a.hash ? (dc ? k_density_wpp<true, 8, true> : k_density_wpp<true, 8, false>)
+                                 : (dc ? k_density_wpp<false, 8, true> : k_density_wpp<false, 8, false>));
+    kd<<<blocks, kWppThreads, 0, s>>>(c);
     ++ctx->launches;
     // SPH_TIME_KERNELS times the density kernel alone; the list build follows
     if ((e = span_end(ctx, sp, s))) return e;
@@ -1391,7 +1478,7 @@ cudaError_t launch_force_wpp(sph_ctx* ctx, const ForceLaunch& a, int64_t n_activ
     const bool lists = g->nbr != nullptr && g->lists_full;
     if (lists && (e = cudaMemsetAsync(g->list_st + 2, 0, 2 * sizeof(unsigned), s))) return e;
     force_pack(g, a.vel, a.u, a.h, a.rho, a.omega, (float)a.gamma, s, lists ? g->list_h : nullptr,
-               lists ? g->list_st + 2 : nullptr);
+               lists ? g->list_st + 2 : nullptr, a.divv, a.curlv);
     ++ctx->launches;
     if ((e = cudaMemsetAsync(ctx->queue + 3, 0, sizeof(unsigned), s))) return e;
     WppArgs c = wpp_common(ctx, g, ctx->queue + 3);
@@ -1407,6 +1494,7 @@ cudaError_t launch_force_wpp(sph_ctx* ctx, const ForceLaunch& a, int64_t n_activ
     c.vsig = a.vsig;
     c.alpha = (float)a.alpha;
     c.hash = a.hash;
+    c.fbal = a.divv ? g->fbal : nullptr;
     WppSpan sp;
     if ((e = span_begin(ctx, a.time_kernels, 1, s, sp))) return e;
     if (lists) {
@@ -1424,19 +1512,20 @@ cudaError_t launch_force_wpp(sph_ctx* ctx, const ForceLaunch& a, int64_t n_activ
         c.fb_list = g->fb_list;
         const int lb = (int)std::max<long long>(
             1, std::min<long long>((long long)ctx->sm_count * 16, (n_active + 3) / 4));
-        if (a.hash) k_force_list<true><<<lb, 128, 0, s>>>(c);
-        else k_force_list<false><<<lb, 128, 0, s>>>(c);
+        const bool bal = c.fbal != nullptr;
+        auto kl = a.hash ? (bal ? k_force_list<true, true> : k_force_list<true, false>)
+                         : (bal ? k_force_list<false, true> : k_force_list<false, false>);
+        kl<<<lb, 128, 0, s>>>(c);
         ++ctx->launches;
         c.fb_act = g->fb_list;
         c.fb_count = g->list_st + 3;
     }
-    if (bps <= 6) {
-        if (a.hash) k_force_wpp<true, 6><<<blocks, kWppThreads, 0, s>>>(c);
-        else k_force_wpp<false, 6><<<blocks, kWppThreads, 0, s>>>(c);
-    } else {
-        if (a.hash) k_force_wpp<true, 8><<<blocks, kWppThreads, 0, s>>>(c);
-        else k_force_wpp<false, 8><<<blocks, kWppThreads, 0, s>>>(c);
-    }
+    const bool bw = c.fbal != nullptr;
+    auto kw = bps <= 6 ? (a.hash ? (bw ? k_force_wpp<true, 6, true> : k_force_wpp<true, 6, false>)
+                                 : (bw ? k_force_wpp<false, 6, true> : k_force_wpp<false, 6, false>))
+                       : (a.hash ? (bw ? k_force_wpp<true, 8, true> : k_force_wpp<true, 8, false>)
+                                 : (bw ? k_force_wpp<false, 8, true> : k_force_wpp<false, 8, false>));
+    kw<<<blocks, kWppThreads, 0, s>>>(c);
     ++ctx->launches;
     if ((e = span_end(ctx, sp, s))) return e;
     return cudaGetLastError();
