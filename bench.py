@@ -40,6 +40,10 @@ UNIT = "pairs/s"
 FLOPS_DENSITY_PAIR = 30.0   # FP32 flops per density pair (FMA = 2), one pass at the converged h
 FLOPS_FORCE_PAIR = 90.0     # FP32 flops per force pair
 FP32_LANES_PER_SM = 128
+# DRAM bytes (read + write) of one k_density_wpp launch per active particle: 592.06 MB measured by
+# ncu (dram__bytes_read.sum + dram__bytes_write.sum) on the 2,000,000-particle 100 % sub-step of
+# this benchmark's workload; scaled by the active particles of a launch
+DENSITY_DRAM_BYTES_PER_ACTIVE = 592.064768e6 / 2_000_000
 H_PERTURB = 0.02            # per-step log-normal scatter of the h guesses: the density change between steps
 
 
@@ -511,6 +515,7 @@ def main():
 
     ms_step = res_g["ms"] / args.steps
     pairs_step = res_g["pairs"] / args.steps
+    active_per_launch = sum(int(a.numel()) for a in wl["acts"]) / len(wl["acts"])
     if dist is not None:
         t = torch.tensor([ms_step, pairs_step], dtype=torch.float64, device=dev)
         mx = t.clone()
@@ -552,8 +557,12 @@ def main():
     else:
         kern, flops, kms, kl = fname, force_f, res["force_ms"], res["force_launches"]
     achieved = (flops / max(kl, 1)) / (kms / max(kl, 1) / 1e3) / 1e12 if kms > 0 else None
+    traffic = DENSITY_DRAM_BYTES_PER_ACTIVE * active_per_launch if kern == dname else None
     roofline = {"bound": "alu", "kernel": kern, "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
-                "frac": achieved / peak_tf if achieved else None, "traffic": None,
+                "frac": achieved / peak_tf if achieved else None, "traffic": traffic,
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the 2M 100 % density launch, "
+                                  "per active particle, times the mean active particles of a timed launch"
+                                  if traffic else None,
                 "peak_source": f"{sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
                                f"{pk.get('sm_max_mhz', 2070.0)} MHz ({src} max SM clock)",
                 "density_kernel_ms_per_step": res["dens_ms"] / args.steps,
