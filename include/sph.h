@@ -190,11 +190,12 @@ sph_status sph_grid_export(const sph_grid *grid, int32_t *perm, uint64_t *keys, 
  * With SPH_FIXED_H the sums are evaluated once at the given h.
  * Arithmetic: FP32 pair terms, per-batch compensated (Kahan) accumulation,
  * FP64 h update; SPH_FP64 computes everything in FP64.
- * Neighbour lists (default path, grid built without SPH_NO_LISTS): the call
- * records each active particle's set {j != i : r_ij < h_i} at its final h in
- * the grid. When every particle is active it also builds, for each i, the
- * partners j with h_i <= r_ij < h_j (the transpose), so that a following
- * sph_hydro_force can take its pairs from these lists (see there).
+ * Neighbour lists (default path, grid built without SPH_NO_LISTS): when every
+ * particle is active the call records each particle's set {j != i : r_ij <
+ * h_i} at its final h in the grid, and, for each i, the partners j with
+ * h_i <= r_ij < h_j (the transpose), so that a following sph_hydro_force can
+ * take its pairs from these lists (see there). A call on a smaller active set
+ * leaves the lists unusable.
  */
 sph_status sph_density(sph_ctx *ctx, const sph_grid *grid, float *h, const int32_t *active,
                        int64_t n_active, float *rho, float *omega, int32_t *n_ngb,

@@ -14,7 +14,7 @@
 // sums are folded across the warp with error-free (TwoSum) transformations,
 // so the result is deterministic and carries the compensation of the fold.
 //
-// Density keeps the pairs within 1.06 h of one walk (the "near list") across
+// Density keeps the pairs within 1.04 h of one walk (the "near list") across
 // the h iterations (safeguarded Newton on N^(1/3), FP32) and walks again only
 // when h leaves the walk radius. The neighbour predicate is the exact one,
 // (double)D2 < (h 2^32/L)^2, decided in FP64 only inside a thin band around
@@ -46,7 +46,7 @@ constexpr int kWppHits = 64;         // hit buffer per warp; drained at >= 32
 constexpr int kWppNear = 128;        // density: pairs within the walk radius, kept across h iterations
 constexpr int kWppGrpLeaves = 384;   // leaf list of a group walk, shared by the group's particles
 constexpr int kWppGrpSpan = 64;      // a group never leaves one leaf-parent node (kLeaf * kFan particles)
-constexpr float kWppWalkR = 1.06f;   // density walks at 1.06 h so that later iterations reuse the list
+constexpr float kWppWalkR = 1.04f;   // density walks at 1.04 h so that later iterations reuse the list
 
 // Stack bound: a pop-4 step starts from sp <= 96 and ends at sp <= 92 + 32 =
 // 124. Above that, in the pop-1 regime, the entries above the base form a
@@ -1168,18 +1168,31 @@ __global__ void __launch_bounds__(256) k_list_ext(const BoxDesc* __restrict__ bo
             const float Hs = (float)(4294967296.0 / B.L);   // integer units per box unit
             const uint4 Xj = posm[j];
             const float hj = list_h[j];
-            for (int k = (int)lane; k < cnt; k += 32) {
-                const int i = lj[k];
-                const float hi = list_h[i];
+            auto decide = [&](int i, float hi, uint4 Xi) {
                 bool x = false;
                 if (hi < hj) {
-                    const unsigned long long D2 = exact_d2(posm[i], Xj);
+                    const unsigned long long D2 = exact_d2(Xi, Xj);
                     const float d2 = __ull2float_rn(D2), Hi = hi * Hs, H2 = Hi * Hi;
                     if (d2 > H2 * (1.f + band)) x = true;
                     else if (!(d2 < H2 * (1.f - band))) x = !exact_pred(D2, wpp_hh(hi, B.L));
                 }
-                nbr_x[off + k] = x ? 1 : 0;
-                if (x) atomicAdd(&ext_n[i], 1u);
+                return x;
+            };
+            // two entries per lane per step (k and k + 32), their gathers issued together
+            for (int k = (int)lane; k < cnt; k += 64) {
+                const int k1 = k + 32;
+                const bool two = k1 < cnt;
+                const int i0 = lj[k], i1 = two ? lj[k1] : i0;
+                const float h0 = list_h[i0], h1 = list_h[i1];
+                const uint4 X0 = h0 < hj ? posm[i0] : Xj, X1 = (two && h1 < hj) ? posm[i1] : Xj;
+                const bool x0 = decide(i0, h0, X0);
+                nbr_x[off + k] = x0 ? 1 : 0;
+                if (x0) atomicAdd(&ext_n[i0], 1u);
+                if (two) {
+                    const bool x1 = decide(i1, h1, X1);
+                    nbr_x[off + k1] = x1 ? 1 : 0;
+                    if (x1) atomicAdd(&ext_n[i1], 1u);
+                }
             }
         } else {
             for (int k = (int)lane; k < cnt; k += 32) {
@@ -1427,13 +1440,12 @@ cudaError_t launch_density_wpp(sph_ctx* ctx, const DensityLaunch& a, int64_t n_a
         c.divv = a.divv;
         c.curlv = a.curlv;
     }
-    // Neighbour lists: recorded for the active particles of every call. They
-    // can serve a force call only if every particle was active (checked on the
-    // device: lists written == n); the extra partners are built when the active
-    // count can cover all particles.
-    const bool lists = g->nbr != nullptr;
-    const bool full = lists && n_active == g->n;
-    if (lists) {
+    // Neighbour lists: recorded when the active count can cover all particles.
+    // They serve a force call only if every particle was in fact active
+    // (checked on the device: lists written == n); a call on a smaller active
+    // set leaves them unusable.
+    const bool full = g->nbr != nullptr && n_active == g->n;
+    if (full) {
         c.nbr = g->nbr;
         c.nbr_off = g->nbr_off;
         c.nbr_n = g->nbr_n;
