@@ -58,6 +58,7 @@ def lib():
         L.orc_force.argtypes = [i32, P, P, i64, f64, P, P, P, P, P, P, f64, f64, P, P, P, i64, i32,
                                 P, P, P, P, P, P, P]
         L.orc_divcurl.argtypes = [i32, P, P, i64, f64, P, P, P, P, P, i64, i32, P, P, P, P]
+        L.orc_conduction.argtypes = [i32, P, P, i64, f64, P, P, P, P, P, P, i64, i32, P, P]
         L.orc_neighbours.argtypes = [i32, P, P, i64, f64, i64, f64, i32, P, i64]
         L.orc_neighbours.restype = i64
         L.orc_num_threads.restype = i32
@@ -165,6 +166,21 @@ def divcurl(X=None, vel=None, mass=None, h=None, rho=None, box=1.0, active=None,
     lib().orc_divcurl(mode, _p(Xc), _p(xcc), n, float(box), *[_p(a) for a in args], _p(act),
                       0 if act is None else act.size, int(bool(brute)), _p(divv), _p(curlv), _p(sd), _p(sc))
     return (divv, curlv, sd, sc) if scales else (divv, curlv)
+
+
+def conduction(X=None, mass=None, u=None, h=None, rho=None, kappa=None, box=1.0, active=None, brute=False,
+               xc=None):
+    """Conduction heating rate over the force pair set and its per-particle
+    scale (sum of the pair terms' magnitudes); inactive entries NaN."""
+    mode, Xc, xcc = _geom(X, xc, box)
+    n = Xc.shape[0]
+    args = [_c(a, np.float64) for a in (mass, u, h, rho, kappa)]
+    act = None if active is None else _c(active, np.int64)
+    du = np.full(n, np.nan)
+    sc = np.full(n, np.nan)
+    lib().orc_conduction(mode, _p(Xc), _p(xcc), n, float(box), *[_p(a) for a in args], _p(act),
+                         0 if act is None else act.size, int(bool(brute)), _p(du), _p(sc))
+    return du, sc
 
 
 def force(X=None, vel=None, mass=None, u=None, h=None, rho=None, omega=None, box=1.0,
