@@ -400,6 +400,47 @@ def balsara_line(S, ctx, wl, dparams, fparams, reps=3):
             "without_switch_ms_per_pass": out["plain"][1]}
 
 
+def conduction_line(S, ctx, wl, dparams, fparams, reps=3):
+    """Secondary line: the 100 % sub-step of the 10M clustered step with
+    thermal conduction in the force pass (conductivities log-uniform over a
+    decade, seeded), next to the same force pass without it."""
+    import torch
+    st, n, dev = wl["st"], wl["n"], wl["h"].device
+    act, h_in = wl["acts"][0], wl["h_ins"][0]
+    kappa = torch.from_numpy((10.0 ** np.random.default_rng(9).uniform(-1, 0, n)).astype(np.float32)).to(dev)
+    dc = torch.zeros(n, device=dev)
+    wl["h"].copy_(h_in)
+    S.sph_density(ctx, wl["grid"], wl["h"], act, st["rho"], st["omega"], st["n_ngb"], st["flags"], None, dparams)
+    S.sph_sync_status(ctx)
+
+    def cond():
+        S.sph_hydro_force_conduction(ctx, wl["grid"], wl["vel"], wl["u"], wl["h"], st["rho"], st["omega"], None,
+                                     None, kappa, act, st["acc"], st["dudt"], st["vsig"], dc, None, fparams)
+
+    def plain():
+        S.sph_hydro_force(ctx, wl["grid"], wl["vel"], wl["u"], wl["h"], st["rho"], st["omega"], act, st["acc"],
+                          st["dudt"], st["vsig"], None, fparams)
+
+    out = {}
+    for name, fn in (("cond", cond), ("plain", plain)):
+        fn()
+        S.sph_sync_status(ctx)
+        ms, pairs = 0.0, 0
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            _, stt = S.sph_sync_status(ctx)
+            ms += a.elapsed_time(b)
+            pairs += stt["force_pairs"]
+        out[name] = (pairs / (ms / 1e3), ms / reps)
+    return {"workload": "10M clustered, 100 % active sub-step: the force pass with thermal conduction "
+                        "(from the density pass's neighbour lists)",
+            "value": out["cond"][0], "unit": "force pairs/s", "ms_per_pass": out["cond"][1],
+            "without_conduction_ms_per_pass": out["plain"][1]}
+
+
 def batched_line(S, ctx, dev, reps=3):
     """Secondary line: 64 independent boxes (N log-uniform in [4096, 524288])
     in one grid, density (from 2%-scattered converged h) + force, one launch
@@ -540,6 +581,7 @@ def main():
     extra = {}
     if not args.no_extra and rank == 0:
         extra["balsara"] = balsara_line(S, ctx, wl, dpar, fpar)
+        extra["conduction"] = conduction_line(S, ctx, wl, dpar, fpar)
         del wl
         torch.cuda.empty_cache()
         extra["batched_boxes"] = batched_line(S, ctx, dev)

@@ -265,6 +265,30 @@ sph_status sph_hydro_force_balsara(sph_ctx *ctx, const sph_grid *grid, const flo
                                    void *stream);
 
 /*
+ * The force pass plus thermal conduction over the same pair set, in one
+ * traversal (default path only). The paper's code has a conduction module
+ * that loops over neighbours like the force module (Sec. 1); the paper
+ * states no formula, so this is the SPH conduction of Cleary & Monaghan
+ * (1999), as Jubelgas, Springel & Dolag (2004) used it in Gadget, for u with a
+ * conductivity kappa per particle (heat flux -kappa grad u):
+ *   dudt_cond_i = sum_j m_j/(rho_i rho_j) 4 kappa_i kappa_j/(kappa_i + kappa_j)
+ *                 (u_i - u_j) Fbar_ij,
+ *   Fbar_ij = (F(r_ij, h_i) + F(r_ij, h_j))/2,  F(r, h) = dW/dr(r, h)/r,
+ * over j != i with r_ij < max(h_i, h_j). The pair terms are antisymmetric, so
+ * sum_i m_i dudt_cond_i = 0 over an all-active pass.
+ *   kappa      device, n floats (>= 0, caller order, all particles);
+ *   dudt_cond  device, n floats: written for active particles (separate from
+ *              dudt, which stays the hydrodynamic rate);
+ *   divv, curlv  both NULL (no switch) or as in sph_hydro_force_balsara.
+ * Everything else as sph_hydro_force.
+ */
+sph_status sph_hydro_force_conduction(sph_ctx *ctx, const sph_grid *grid, const float *vel, const float *u,
+                                      const float *h, const float *rho, const float *omega, const float *divv,
+                                      const float *curlv, const float *kappa, const int32_t *active,
+                                      int64_t n_active, float *acc, float *dudt, float *vsig, float *dudt_cond,
+                                      uint64_t *hash, const sph_params *params, void *stream);
+
+/*
  * Adjoint of the density and force passes (an extension of the paper's hot
  * path, which has no gradients). All particles are active. Given the forward
  * state of the grid's particles -- vel, u (inputs of the force pass) and h,

@@ -16,7 +16,8 @@ from .abi import (SPH_FIXED_H, SPH_FP64, SPH_H_GUESS, SPH_PLAIN_FP32, SPH_TIME_K
                   default_params, sph_params, sph_stats)
 
 __all__ = ["Context", "Grid", "sph_create", "sph_build_grid", "sph_build_grid_batched", "sph_grid_update",
-           "sph_density", "sph_hydro_force", "sph_density_divcurl", "sph_hydro_force_balsara", "sph_backward", "sph_sync_status", "sph_grid_export", "sph_sort_keys_static", "density",
+           "sph_density", "sph_hydro_force", "sph_density_divcurl", "sph_hydro_force_balsara",
+           "sph_hydro_force_conduction", "sph_backward", "sph_sync_status", "sph_grid_export", "sph_sort_keys_static", "density",
            "hydro_force", "default_params", "sph_params", "sph_stats", "SPHError", "SPH_FP64",
            "SPH_PLAIN_FP32", "SPH_FIXED_H", "SPH_H_GUESS", "SPH_TIME_KERNELS", "SPH_WARP_GROUP", "SPH_DENSITY_BUFFERED", "SPH_PER_THREAD_WALK", "SPH_COOP_WALK", "SPH_WARP_WALK", "SPH_NO_LISTS"]
 
@@ -165,6 +166,19 @@ def sph_hydro_force_balsara(ctx: Context, grid: Grid, vel, u, h, rho, omega, div
                                               _ptr(dudt, f, "dudt"), _ptr(vsig, f, "vsig"),
                                               _ptr(hash, torch.int64, "hash"),
                                               ctypes.byref(params or default_params()), _stream()))
+
+
+def sph_hydro_force_conduction(ctx: Context, grid: Grid, vel, u, h, rho, omega, divv, curlv, kappa, active, acc,
+                               dudt, vsig, dudt_cond, hash=None, params: sph_params = None):
+    na = 0 if active is None else active.numel()
+    f = torch.float32
+    ctx.check(ctx.lib.sph_hydro_force_conduction(ctx.handle, grid.handle, _ptr(vel, f, "vel"), _ptr(u, f, "u"),
+                                                 _ptr(h, f, "h"), _ptr(rho, f, "rho"), _ptr(omega, f, "omega"),
+                                                 _ptr(divv, f, "divv"), _ptr(curlv, f, "curlv"),
+                                                 _ptr(kappa, f, "kappa"), _ptr(active, torch.int32, "active"), na,
+                                                 _ptr(acc, f, "acc"), _ptr(dudt, f, "dudt"), _ptr(vsig, f, "vsig"),
+                                                 _ptr(dudt_cond, f, "dudt_cond"), _ptr(hash, torch.int64, "hash"),
+                                                 ctypes.byref(params or default_params()), _stream()))
 
 
 def sph_backward(ctx: Context, grid: Grid, vel, u, h, rho, omega, g_acc, g_rho, g_pos, g_u, g_mass,

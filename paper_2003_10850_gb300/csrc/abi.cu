@@ -269,8 +269,9 @@ sph_status sph_density_divcurl(sph_ctx* ctx, const sph_grid* grid, float* h, con
 
 static sph_status force_call(sph_ctx* ctx, const sph_grid* grid, const float* vel, const float* u,
                              const float* h, const float* rho, const float* omega, const float* divv,
-                             const float* curlv, const int32_t* active, int64_t n_active, float* acc, float* dudt,
-                             float* vsig, uint64_t* hash, const sph_params* params, void* stream) {
+                             const float* curlv, const float* kappa, const int32_t* active, int64_t n_active,
+                             float* acc, float* dudt, float* vsig, float* dudt_cond, uint64_t* hash,
+                             const sph_params* params, void* stream) {
     if (!ctx) return SPH_ERR_INVALID;
     if (!grid || grid->ctx != ctx) return fail(ctx, SPH_ERR_INVALID, "grid is NULL or from another context");
     if (!vel || !u || !h || !rho || !omega || !acc || !dudt || !vsig)
@@ -305,6 +306,8 @@ static sph_status force_call(sph_ctx* ctx, const sph_grid* grid, const float* ve
     a.time_kernels = (params->flags & SPH_TIME_KERNELS) ? 1 : 0;
     a.divv = divv;
     a.curlv = curlv;
+    a.kappa = kappa;
+    a.dudt_cond = dudt_cond;
     cudaError_t e = path == Path::Plain       ? launch_force_plain(ctx, a, na, s)
                     : path == Path::WarpGroup ? launch_force(ctx, a, s)
                     : path == Path::Wpp       ? launch_force_wpp(ctx, a, na, s)
@@ -319,8 +322,8 @@ sph_status sph_hydro_force(sph_ctx* ctx, const sph_grid* grid, const float* vel,
                            const float* h, const float* rho, const float* omega, const int32_t* active,
                            int64_t n_active, float* acc, float* dudt, float* vsig, uint64_t* hash,
                            const sph_params* params, void* stream) {
-    return force_call(ctx, grid, vel, u, h, rho, omega, nullptr, nullptr, active, n_active, acc, dudt, vsig, hash,
-                      params, stream);
+    return force_call(ctx, grid, vel, u, h, rho, omega, nullptr, nullptr, nullptr, active, n_active, acc, dudt, vsig,
+                      nullptr, hash, params, stream);
 }
 
 sph_status sph_hydro_force_balsara(sph_ctx* ctx, const sph_grid* grid, const float* vel, const float* u,
@@ -332,8 +335,22 @@ sph_status sph_hydro_force_balsara(sph_ctx* ctx, const sph_grid* grid, const flo
     if (!divv || !curlv) return fail(ctx, SPH_ERR_INVALID, "divv and curlv are required");
     if (params && pick_path(params->flags & ~SPH_DENSITY_BUFFERED) != Path::Wpp)
         return fail(ctx, SPH_ERR_INVALID, "the Balsara switch runs on the default path only");
-    return force_call(ctx, grid, vel, u, h, rho, omega, divv, curlv, active, n_active, acc, dudt, vsig, hash,
-                      params, stream);
+    return force_call(ctx, grid, vel, u, h, rho, omega, divv, curlv, nullptr, active, n_active, acc, dudt, vsig,
+                      nullptr, hash, params, stream);
+}
+
+sph_status sph_hydro_force_conduction(sph_ctx* ctx, const sph_grid* grid, const float* vel, const float* u,
+                                      const float* h, const float* rho, const float* omega, const float* divv,
+                                      const float* curlv, const float* kappa, const int32_t* active,
+                                      int64_t n_active, float* acc, float* dudt, float* vsig, float* dudt_cond,
+                                      uint64_t* hash, const sph_params* params, void* stream) {
+    if (!ctx) return SPH_ERR_INVALID;
+    if (!kappa || !dudt_cond) return fail(ctx, SPH_ERR_INVALID, "kappa and dudt_cond are required");
+    if ((divv == nullptr) != (curlv == nullptr)) return fail(ctx, SPH_ERR_INVALID, "give both divv and curlv, or neither");
+    if (params && pick_path(params->flags & ~SPH_DENSITY_BUFFERED) != Path::Wpp)
+        return fail(ctx, SPH_ERR_INVALID, "conduction runs on the default path only");
+    return force_call(ctx, grid, vel, u, h, rho, omega, divv, curlv, kappa, active, n_active, acc, dudt, vsig,
+                      dudt_cond, hash, params, stream);
 }
 
 sph_status sph_backward(sph_ctx* ctx, const sph_grid* grid, const float* vel, const float* u, const float* h,

@@ -116,6 +116,9 @@ struct WppArgs {
     float* curlv;
     // force: Balsara factors (sorted order; NULL: no switch)
     const float* fbal;
+    // force: conduction (sorted (u, kappa); NULL: no conduction) and its output (caller order)
+    const float2* fcond;
+    float* dudt_cond;
     int32_t* fb_list;
     long long list_pool;
     int list_chunk;              // pool entries a warp reserves at a time
@@ -512,16 +515,19 @@ struct WppForceI {
     float vx, vy, vz;
     float hinv, rho, A, c, norm;   // norm = 8/(pi h^4)
     float f;                       // Balsara factor (1 without the switch)
+    float u, kap;                  // conduction: u and conductivity (unused without it)
 };
 
 // One force pair term, Gadget-2 grad-h form with signal-velocity viscosity,
 // added to i's per-lane sums. (dx, dy, dz) = x_j - x_i; vj = (v_j, m_j);
 // thj = (rho_j, A_j, c_j, 1/h_j); fj = j's Balsara factor (1 without the
 // switch: BAL = false leaves Pi_ij alone; BAL = true multiplies it by (f_i + f_j)/2).
-template <bool BAL>
+// COND adds the conduction term m_j/(rho_i rho_j) 4 k_i k_j/(k_i + k_j)
+// (u_i - u_j) Fbar_ij to Sc, with cj = (u_j, kappa_j).
+template <bool BAL, bool COND>
 __device__ __forceinline__ void wpp_force_pair(const WppForceI& I, float dx, float dy, float dz, float4 vj, float4 thj,
-                                               float fj, float alpha, float& Sx, float& Sy, float& Sz, float& Su,
-                                               float& vsmax) {
+                                               float fj, float2 cj, float alpha, float& Sx, float& Sy, float& Sz,
+                                               float& Su, float& Sc, float& vsmax) {
     const float kNorm = (float)(8.0 / 3.141592653589793);
     const float r2 = dx * dx + dy * dy + dz * dz;
     if (r2 <= 0.f) {  // coincident: no direction, no force
@@ -544,6 +550,11 @@ __device__ __forceinline__ void wpp_force_pair(const WppForceI& I, float dx, flo
     if (BAL) PI *= 0.5f * (I.f + fj);
     const float Fbar = 0.5f * (Fi + Fj);
     const float mj = vj.w;
+    if (COND) {
+        const float ks = I.kap + cj.y;
+        const float kij = ks > 0.f ? __fdividef(4.f * I.kap * cj.y, ks) : 0.f;
+        Sc += __fdividef(mj, I.rho * thj.x) * kij * (I.u - cj.x) * Fbar;
+    }
     const float coef = mj * (I.A * Fi + thj.y * Fj + PI * Fbar);
     Sx += coef * dx;
     Sy += coef * dy;
@@ -957,7 +968,7 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_density_wpp(WppArgs a) {
 // Force
 // ---------------------------------------------------------------------------
 
-template <bool HASH, int MINB, bool BAL>
+template <bool HASH, int MINB, bool BAL, bool COND>
 __global__ void __launch_bounds__(kWppThreads, MINB) k_force_wpp(WppArgs a) {
     __shared__ WppSmem smem[kWppWarps];
     WppSmem& sm = smem[threadIdx.x >> 5];
@@ -1010,12 +1021,13 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_force_wpp(WppArgs a) {
                 const int oi = a.perm[p];
                 const float4 vi = a.fvm[p];
                 const float4 thi = a.fthermo[p];
+                const float2 ci = COND ? a.fcond[p] : make_float2(0.f, 0.f);
                 const WppForceI I = {vi.x, vi.y, vi.z, thi.w, thi.x, thi.y, thi.z,
-                                     kNorm * thi.w * thi.w * thi.w * thi.w, BAL ? a.fbal[p] : 1.f};
+                                     kNorm * thi.w * thi.w * thi.w * thi.w, BAL ? a.fbal[p] : 1.f, ci.x, ci.y};
                 // i side of the band test: h_i (1 +- 2^-19) (the leaf's rounding bound is added per leaf)
                 const float hiP = hi * (1.f + 2.f * rel), hiM = hi * (1.f - 2.f * rel);
                 double HHi = -1.0;
-                float Sx = 0.f, Sy = 0.f, Sz = 0.f, Su = 0.f, vsmax = 0.f;   // per-lane partial sums
+                float Sx = 0.f, Sy = 0.f, Sz = 0.f, Su = 0.f, Sc = 0.f, vsmax = 0.f;   // per-lane partial sums
                 int np = 0, nh = 0, nlf = 0;
                 unsigned tests = 0;
                 bool complete = true;
@@ -1026,8 +1038,10 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_force_wpp(WppArgs a) {
                     if ((int)lane < k) {
                         const float4 e = sm.hit.f[lane];
                         const int q = __float_as_int(e.w);
-                        wpp_force_pair<BAL>(I, e.x, e.y, e.z, __ldg(a.fvm + q), __ldg(a.fthermo + q),
-                                            BAL ? __ldg(a.fbal + q) : 1.f, alpha, Sx, Sy, Sz, Su, vsmax);
+                        wpp_force_pair<BAL, COND>(I, e.x, e.y, e.z, __ldg(a.fvm + q), __ldg(a.fthermo + q),
+                                                  BAL ? __ldg(a.fbal + q) : 1.f,
+                                                  COND ? __ldg(a.fcond + q) : make_float2(0.f, 0.f), alpha, Sx, Sy,
+                                                  Sz, Su, Sc, vsmax);
                     }
                     __syncwarp();
                 };
@@ -1107,6 +1121,11 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_force_wpp(WppArgs a) {
                     const int comp = (int)(lane >> 3);
                     if (comp < 3) a.acc[3 * (size_t)oi + comp] = fs;
                     else a.dudt[oi] = fs;
+                }
+                if (COND) {
+                    float cs, cc, z0, z1;
+                    wpp_fold2(Sc, 0.f, cs, cc, z0, z1);
+                    if (lane == 0) a.dudt_cond[oi] = __fsub_rn(cs, cc);
                 }
                 if (lane == 0) {
                     a.vsig[oi] = vsmax;
@@ -1276,7 +1295,7 @@ __global__ void __launch_bounds__(256) k_list_sort(int n, const uint32_t* __rest
 // fold as k_force_wpp. If the lists cannot serve the call at all the kernel
 // does nothing and the walk that follows takes the whole active set;
 // particles whose own lists did not fit go to fb_list for that walk.
-template <bool HASH, bool BAL>
+template <bool HASH, bool BAL, bool COND>
 __global__ void __launch_bounds__(128) k_force_list(WppArgs a) {
     if (!wpp_lists_valid(a.list_st, a.n_total)) return;
     const unsigned lane = lane_id();
@@ -1298,9 +1317,10 @@ __global__ void __launch_bounds__(128) k_force_list(WppArgs a) {
         const int oi = a.perm[p];
         const float4 vi = a.fvm[p];
         const float4 thi = a.fthermo[p];
+        const float2 ci = COND ? a.fcond[p] : make_float2(0.f, 0.f);
         const WppForceI I = {vi.x, vi.y, vi.z, thi.w, thi.x, thi.y, thi.z, kNorm * thi.w * thi.w * thi.w * thi.w,
-                             BAL ? a.fbal[p] : 1.f};
-        float Sx = 0.f, Sy = 0.f, Sz = 0.f, Su = 0.f, vsmax = 0.f;
+                             BAL ? a.fbal[p] : 1.f, ci.x, ci.y};
+        float Sx = 0.f, Sy = 0.f, Sz = 0.f, Su = 0.f, Sc = 0.f, vsmax = 0.f;
         unsigned long long hs = 0;
         const int tot = cn + (int)(e1 - e0);
         const int32_t* ln = a.nbr + a.nbr_off[p];
@@ -1316,12 +1336,16 @@ __global__ void __launch_bounds__(128) k_force_list(WppArgs a) {
             const float4 v0 = __ldg(a.fvm + q0), v1 = __ldg(a.fvm + q1);
             const float4 t0 = __ldg(a.fthermo + q0), t1 = __ldg(a.fthermo + q1);
             const float b0 = BAL ? __ldg(a.fbal + q0) : 1.f, b1 = BAL ? __ldg(a.fbal + q1) : 1.f;
-            wpp_force_pair<BAL>(I, (float)(int)(X0.x - Xi.x) * sf, (float)(int)(X0.y - Xi.y) * sf,
-                                (float)(int)(X0.z - Xi.z) * sf, v0, t0, b0, a.alpha, Sx, Sy, Sz, Su, vsmax);
+            const float2 c0 = COND ? __ldg(a.fcond + q0) : make_float2(0.f, 0.f);
+            const float2 c1 = COND ? __ldg(a.fcond + q1) : make_float2(0.f, 0.f);
+            wpp_force_pair<BAL, COND>(I, (float)(int)(X0.x - Xi.x) * sf, (float)(int)(X0.y - Xi.y) * sf,
+                                      (float)(int)(X0.z - Xi.z) * sf, v0, t0, b0, c0, a.alpha, Sx, Sy, Sz, Su, Sc,
+                                      vsmax);
             if (HASH) hs += splitmix64((unsigned long long)a.perm[q0]);
             if (two) {
-                wpp_force_pair<BAL>(I, (float)(int)(X1.x - Xi.x) * sf, (float)(int)(X1.y - Xi.y) * sf,
-                                    (float)(int)(X1.z - Xi.z) * sf, v1, t1, b1, a.alpha, Sx, Sy, Sz, Su, vsmax);
+                wpp_force_pair<BAL, COND>(I, (float)(int)(X1.x - Xi.x) * sf, (float)(int)(X1.y - Xi.y) * sf,
+                                          (float)(int)(X1.z - Xi.z) * sf, v1, t1, b1, c1, a.alpha, Sx, Sy, Sz, Su, Sc,
+                                          vsmax);
                 if (HASH) hs += splitmix64((unsigned long long)a.perm[q1]);
             }
         }
@@ -1332,6 +1356,11 @@ __global__ void __launch_bounds__(128) k_force_list(WppArgs a) {
             const int comp = (int)(lane >> 3);
             if (comp < 3) a.acc[3 * (size_t)oi + comp] = fs;
             else a.dudt[oi] = fs;
+        }
+        if (COND) {
+            float cs, cc, z0, z1;
+            wpp_fold2(Sc, 0.f, cs, cc, z0, z1);
+            if (lane == 0) a.dudt_cond[oi] = __fsub_rn(cs, cc);
         }
         if (lane == 0) {
             a.vsig[oi] = vsmax;
@@ -1414,6 +1443,37 @@ static int helper_blocks(sph_ctx* ctx, int64_t n) {
     return (int)std::max<long long>(1, std::min<long long>((long long)ctx->sm_count * 8, (n + 7) / 8));
 }
 
+// Kernel variants of the force pass: hash output, register budget, Balsara's
+// switch, conduction.
+template <bool H, bool BAL, bool COND>
+static void launch_fl(int blocks, cudaStream_t s, const WppArgs& c) {
+    k_force_list<H, BAL, COND><<<blocks, 128, 0, s>>>(c);
+}
+static void launch_force_list(bool hash, bool bal, bool cond, int blocks, cudaStream_t s, const WppArgs& c) {
+    if (hash) {
+        if (bal) cond ? launch_fl<true, true, true>(blocks, s, c) : launch_fl<true, true, false>(blocks, s, c);
+        else cond ? launch_fl<true, false, true>(blocks, s, c) : launch_fl<true, false, false>(blocks, s, c);
+    } else {
+        if (bal) cond ? launch_fl<false, true, true>(blocks, s, c) : launch_fl<false, true, false>(blocks, s, c);
+        else cond ? launch_fl<false, false, true>(blocks, s, c) : launch_fl<false, false, false>(blocks, s, c);
+    }
+}
+template <bool H, int M>
+static void launch_fw(bool bal, bool cond, int blocks, cudaStream_t s, const WppArgs& c) {
+    if (bal) {
+        if (cond) k_force_wpp<H, M, true, true><<<blocks, kWppThreads, 0, s>>>(c);
+        else k_force_wpp<H, M, true, false><<<blocks, kWppThreads, 0, s>>>(c);
+    } else {
+        if (cond) k_force_wpp<H, M, false, true><<<blocks, kWppThreads, 0, s>>>(c);
+        else k_force_wpp<H, M, false, false><<<blocks, kWppThreads, 0, s>>>(c);
+    }
+}
+static void launch_force_walk(bool hash, bool six, bool bal, bool cond, int blocks, cudaStream_t s,
+                              const WppArgs& c) {
+    if (six) hash ? launch_fw<true, 6>(bal, cond, blocks, s, c) : launch_fw<false, 6>(bal, cond, blocks, s, c);
+    else hash ? launch_fw<true, 8>(bal, cond, blocks, s, c) : launch_fw<false, 8>(bal, cond, blocks, s, c);
+}
+
 cudaError_t launch_density_wpp(sph_ctx* ctx, const DensityLaunch& a, int64_t n_active, cudaStream_t s) {
     sph_grid* g = const_cast<sph_grid*>(a.g);
     cudaError_t e = cudaMemsetAsync(ctx->queue + 2, 0, sizeof(unsigned), s);
@@ -1490,7 +1550,7 @@ cudaError_t launch_force_wpp(sph_ctx* ctx, const ForceLaunch& a, int64_t n_activ
     const bool lists = g->nbr != nullptr && g->lists_full;
     if (lists && (e = cudaMemsetAsync(g->list_st + 2, 0, 2 * sizeof(unsigned), s))) return e;
     force_pack(g, a.vel, a.u, a.h, a.rho, a.omega, (float)a.gamma, s, lists ? g->list_h : nullptr,
-               lists ? g->list_st + 2 : nullptr, a.divv, a.curlv);
+               lists ? g->list_st + 2 : nullptr, a.divv, a.curlv, a.kappa);
     ++ctx->launches;
     if ((e = cudaMemsetAsync(ctx->queue + 3, 0, sizeof(unsigned), s))) return e;
     WppArgs c = wpp_common(ctx, g, ctx->queue + 3);
@@ -1507,6 +1567,8 @@ cudaError_t launch_force_wpp(sph_ctx* ctx, const ForceLaunch& a, int64_t n_activ
     c.alpha = (float)a.alpha;
     c.hash = a.hash;
     c.fbal = a.divv ? g->fbal : nullptr;
+    c.fcond = a.kappa ? g->fcond : nullptr;
+    c.dudt_cond = a.dudt_cond;
     WppSpan sp;
     if ((e = span_begin(ctx, a.time_kernels, 1, s, sp))) return e;
     if (lists) {
@@ -1524,20 +1586,12 @@ cudaError_t launch_force_wpp(sph_ctx* ctx, const ForceLaunch& a, int64_t n_activ
         c.fb_list = g->fb_list;
         const int lb = (int)std::max<long long>(
             1, std::min<long long>((long long)ctx->sm_count * 16, (n_active + 3) / 4));
-        const bool bal = c.fbal != nullptr;
-        auto kl = a.hash ? (bal ? k_force_list<true, true> : k_force_list<true, false>)
-                         : (bal ? k_force_list<false, true> : k_force_list<false, false>);
-        kl<<<lb, 128, 0, s>>>(c);
+        launch_force_list(a.hash != nullptr, c.fbal != nullptr, c.fcond != nullptr, lb, s, c);
         ++ctx->launches;
         c.fb_act = g->fb_list;
         c.fb_count = g->list_st + 3;
     }
-    const bool bw = c.fbal != nullptr;
-    auto kw = bps <= 6 ? (a.hash ? (bw ? k_force_wpp<true, 6, true> : k_force_wpp<true, 6, false>)
-                                 : (bw ? k_force_wpp<false, 6, true> : k_force_wpp<false, 6, false>))
-                       : (a.hash ? (bw ? k_force_wpp<true, 8, true> : k_force_wpp<true, 8, false>)
-                                 : (bw ? k_force_wpp<false, 8, true> : k_force_wpp<false, 8, false>));
-    kw<<<blocks, kWppThreads, 0, s>>>(c);
+    launch_force_walk(a.hash != nullptr, bps <= 6, c.fbal != nullptr, c.fcond != nullptr, blocks, s, c);
     ++ctx->launches;
     if ((e = span_end(ctx, sp, s))) return e;
     return cudaGetLastError();
