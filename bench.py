@@ -441,6 +441,41 @@ def conduction_line(S, ctx, wl, dparams, fparams, reps=3):
             "without_conduction_ms_per_pass": out["plain"][1]}
 
 
+def kdk_line(S, ctx, wl, max_ticks=64):
+    """Secondary line: one dt_max cycle of kick-drift-kick integration of the
+    10M clustered gas on Courant time bins: drift and prediction of every
+    particle, grid rebuild, density and force of the tick's active particles,
+    kicks and re-binning, all on the device. The finest bin holds the
+    smallest Courant step (no particle steps above its Courant limit);
+    max_bin is the number of halvings from the median Courant step down to
+    it, at most log2(max_ticks)."""
+    import math
+    import torch
+    from paper_2003_10850_gb300.kdk import KDK
+    st = wl["st"]
+    dt_c = 0.3 * wl["h"] / st["vsig"].clamp_min(1e-30)
+    dt_min = float(dt_c.min())
+    dt_med = float(torch.quantile(dt_c[torch.randperm(wl["n"], device=dt_c.device)[:1_000_000]], 0.5))
+    max_bin = max(1, min(int(math.log2(max_ticks)), math.ceil(math.log2(dt_med / dt_min))))
+    dt_max = 2 ** max_bin * dt_min * 0.999
+    g = KDK(ctx, wl["pos"].double(), wl["mass"], wl["vel"], wl["u"], dt_max, max_bin)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    pairs0 = g.pairs
+    a.record()
+    counts = [g.step() for _ in range(1 << max_bin)]
+    b.record()
+    b.synchronize()
+    ms = a.elapsed_time(b)
+    pairs = g.pairs - pairs0
+    g.grid.free()
+    return {"workload": f"10M clustered, kick-drift-kick on {max_bin + 1} Courant time bins, one dt_max cycle "
+                        f"({1 << max_bin} ticks): drift + prediction, grid rebuild, density and force of the "
+                        "active particles, kicks, re-binning",
+            "value": pairs / (ms / 1e3), "unit": UNIT, "ms_per_cycle": ms, "max_bin": max_bin,
+            "dt_max": dt_max, "active_per_tick": counts}
+
+
 def batched_line(S, ctx, dev, reps=3):
     """Secondary line: 64 independent boxes (N log-uniform in [4096, 524288])
     in one grid, density (from 2%-scattered converged h) + force, one launch
@@ -582,6 +617,7 @@ def main():
     if not args.no_extra and rank == 0:
         extra["balsara"] = balsara_line(S, ctx, wl, dpar, fpar)
         extra["conduction"] = conduction_line(S, ctx, wl, dpar, fpar)
+        extra["kdk"] = kdk_line(S, ctx, wl)
         del wl
         torch.cuda.empty_cache()
         extra["batched_boxes"] = batched_line(S, ctx, dev)

@@ -289,6 +289,44 @@ sph_status sph_hydro_force_conduction(sph_ctx *ctx, const sph_grid *grid, const 
                                       uint64_t *hash, const sph_params *params, void *stream);
 
 /*
+ * Time integration on individual power-of-two time steps (the paper's
+ * adaptive time bins, Sec. 2.2): kick-drift-kick with the bookkeeping on the
+ * device. The integer timeline counts steps of the smallest bin,
+ * dt_max / 2^max_bin ("ticks"); a particle in bin b has step dt_max / 2^b and
+ * ends a step at every tick that is a multiple of 2^(max_bin - b).
+ *
+ * sph_timebins: bins from the Courant step dt_i = courant * h_i / vsig_i (FP32,
+ * correctly rounded): the smallest b in [0, max_bin] with dt_max <= dt_i 2^b
+ * (max_bin if none; 0 if vsig_i <= 0), then raised until tick is a multiple of
+ * 2^(max_bin - b) (a new step starts on its bin's boundary). For the active
+ * particles (caller indices, device) or all (active = NULL). h, vsig device
+ * floats, bins device uint8 (n each, caller order).
+ */
+sph_status sph_timebins(sph_ctx *ctx, const float *h, const float *vsig, const int32_t *active, int64_t n_active,
+                        int64_t n, int64_t tick, double courant, double dt_max, int max_bin, uint8_t *bins,
+                        void *stream);
+/* The particles that end a step at `tick`, ascending (caller indices) into
+ * active (device, capacity n); their count into *n_active (device int32).
+ * Uses the grid's scratch (the grid fixes n). */
+sph_status sph_active_from_bins(sph_ctx *ctx, sph_grid *grid, const uint8_t *bins, int64_t tick, int max_bin,
+                                int32_t *active, int32_t *n_active, void *stream);
+/* Kick: for each active i, v_i += a_i dt_bin[bins_i] and u_i += dudt_i dt_bin[bins_i]
+ * (FP32 fused multiply-add). dt_bin is a HOST array of n_bins (<= 32) steps.
+ * vel_pred, u_pred (both or neither): also receive the kicked values (after a
+ * closing half kick these are the synchronized velocity and energy, the
+ * starting point of the next predictions). */
+sph_status sph_kick(sph_ctx *ctx, const int32_t *active, int64_t n_active, const uint8_t *bins,
+                    const double *dt_bin, int n_bins, const float *acc, const float *dudt, float *vel, float *u,
+                    float *vel_pred, float *u_pred, void *stream);
+/* Drift: x += v dt for all n particles, in FP64, wrapped into [0, box). pos is
+ * device n x 3 doubles, vel device n x 3 floats. With acc, dudt, vel_pred,
+ * u_pred (all four or none): also v_pred += a dt and u_pred += dudt dt, the
+ * predictions at the new time that the force evaluations take (the force
+ * depends on v through the viscosity and on u through the pressure). */
+sph_status sph_drift(sph_ctx *ctx, double *pos, const float *vel, int64_t n, double dt, double box,
+                     const float *acc, const float *dudt, float *vel_pred, float *u_pred, void *stream);
+
+/*
  * Adjoint of the density and force passes (an extension of the paper's hot
  * path, which has no gradients). All particles are active. Given the forward
  * state of the grid's particles -- vel, u (inputs of the force pass) and h,

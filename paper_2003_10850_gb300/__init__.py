@@ -17,7 +17,8 @@ from .abi import (SPH_FIXED_H, SPH_FP64, SPH_H_GUESS, SPH_PLAIN_FP32, SPH_TIME_K
 
 __all__ = ["Context", "Grid", "sph_create", "sph_build_grid", "sph_build_grid_batched", "sph_grid_update",
            "sph_density", "sph_hydro_force", "sph_density_divcurl", "sph_hydro_force_balsara",
-           "sph_hydro_force_conduction", "sph_backward", "sph_sync_status", "sph_grid_export", "sph_sort_keys_static", "density",
+           "sph_hydro_force_conduction", "sph_timebins", "sph_active_from_bins", "sph_kick", "sph_drift",
+           "sph_backward", "sph_sync_status", "sph_grid_export", "sph_sort_keys_static", "density",
            "hydro_force", "default_params", "sph_params", "sph_stats", "SPHError", "SPH_FP64",
            "SPH_PLAIN_FP32", "SPH_FIXED_H", "SPH_H_GUESS", "SPH_TIME_KERNELS", "SPH_WARP_GROUP", "SPH_DENSITY_BUFFERED", "SPH_PER_THREAD_WALK", "SPH_COOP_WALK", "SPH_WARP_WALK", "SPH_NO_LISTS"]
 
@@ -179,6 +180,36 @@ def sph_hydro_force_conduction(ctx: Context, grid: Grid, vel, u, h, rho, omega, 
                                                  _ptr(acc, f, "acc"), _ptr(dudt, f, "dudt"), _ptr(vsig, f, "vsig"),
                                                  _ptr(dudt_cond, f, "dudt_cond"), _ptr(hash, torch.int64, "hash"),
                                                  ctypes.byref(params or default_params()), _stream()))
+
+
+def sph_timebins(ctx: Context, h, vsig, active, tick, courant, dt_max, max_bin, bins):
+    na = 0 if active is None else active.numel()
+    f = torch.float32
+    ctx.check(ctx.lib.sph_timebins(ctx.handle, _ptr(h, f, "h"), _ptr(vsig, f, "vsig"),
+                                   _ptr(active, torch.int32, "active"), na, h.numel(), int(tick), float(courant),
+                                   float(dt_max), int(max_bin), _ptr(bins, torch.uint8, "bins"), _stream()))
+
+
+def sph_active_from_bins(ctx: Context, grid: Grid, bins, tick, max_bin, active, n_active):
+    ctx.check(ctx.lib.sph_active_from_bins(ctx.handle, grid.handle, _ptr(bins, torch.uint8, "bins"), int(tick),
+                                           int(max_bin), _ptr(active, torch.int32, "active"),
+                                           _ptr(n_active, torch.int32, "n_active"), _stream()))
+
+
+def sph_kick(ctx: Context, active, n_active, bins, dt_bin, acc, dudt, vel, u, vel_pred=None, u_pred=None):
+    dts = (ctypes.c_double * len(dt_bin))(*[float(x) for x in dt_bin])
+    f = torch.float32
+    ctx.check(ctx.lib.sph_kick(ctx.handle, _ptr(active, torch.int32, "active"), int(n_active),
+                               _ptr(bins, torch.uint8, "bins"), dts, len(dt_bin), _ptr(acc, f, "acc"),
+                               _ptr(dudt, f, "dudt"), _ptr(vel, f, "vel"), _ptr(u, f, "u"),
+                               _ptr(vel_pred, f, "vel_pred"), _ptr(u_pred, f, "u_pred"), _stream()))
+
+
+def sph_drift(ctx: Context, pos, vel, dt, box=1.0, acc=None, dudt=None, vel_pred=None, u_pred=None):
+    f = torch.float32
+    ctx.check(ctx.lib.sph_drift(ctx.handle, _ptr(pos, torch.float64, "pos"), _ptr(vel, f, "vel"),
+                                pos.shape[0], float(dt), float(box), _ptr(acc, f, "acc"), _ptr(dudt, f, "dudt"),
+                                _ptr(vel_pred, f, "vel_pred"), _ptr(u_pred, f, "u_pred"), _stream()))
 
 
 def sph_backward(ctx: Context, grid: Grid, vel, u, h, rho, omega, g_acc, g_rho, g_pos, g_u, g_mass,

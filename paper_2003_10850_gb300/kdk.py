@@ -1,0 +1,114 @@
+"""Kick-drift-kick integration on power-of-two time bins.
+
+The paper's code advances each particle on its own power-of-two time step
+(Sec. 2.2, adaptive time steps): at every tick of the smallest step only the
+particles whose step ends are active; every particle, inactive neighbours
+included, is drifted to the current time. `KDK` sequences the library calls
+of one tick; all arithmetic runs in the library's kernels:
+
+  drift and prediction (sph_drift) -> grid rebuild (sph_grid_update) ->
+  active set of the tick (sph_active_from_bins) -> density and force of that
+  set at the predicted velocities and energies -> closing half kick, which
+  resets the predictions to the synchronized values (sph_kick) -> new bins
+  (sph_timebins) -> opening half kick.
+
+Inactive particles keep the h, rho, Omega, a, du/dt of their last active
+step; their velocities and energies are predicted to the current time with
+those. The one value read back per tick is the active count, which the next
+calls take as their n_active.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import (default_params, sph_active_from_bins, sph_build_grid, sph_density, sph_drift, sph_grid_update,
+               sph_hydro_force, sph_kick, sph_sync_status, sph_timebins)
+
+
+class KDK:
+    """State of one periodic box: pos (n, 3) float64, vel (n, 3) float32,
+    mass, u float32 device tensors (copied). The time step of bin b is
+    dt_max / 2^b, b in [0, max_bin]. `bins` (uint8, n) fixes the bins (no
+    re-binning) if given; otherwise they come from the Courant step
+    courant * h / v_sig and are re-assigned at the end of every step. A
+    particle whose Courant step is below dt_max / 2^max_bin is held at
+    max_bin, above its Courant limit: choose dt_max and max_bin so that the
+    finest bin holds the smallest step."""
+
+    def __init__(self, ctx, pos, mass, vel, u, dt_max, max_bin, params=None, courant=0.3, bins=None):
+        self.ctx = ctx
+        self.params = params or default_params()
+        self.box = float(self.params.box)
+        self.dt_max = float(dt_max)
+        self.max_bin = int(max_bin)
+        self.courant = float(courant)
+        self.rebin = bins is None
+        dev = pos.device
+        self.pos = pos.to(torch.float64).contiguous().clone()
+        self.mass = mass.to(torch.float32).contiguous().clone()
+        self.vel = vel.to(torch.float32).contiguous().clone()
+        self.u = u.to(torch.float32).contiguous().clone()
+        self.vel_pred = self.vel.clone()
+        self.u_pred = self.u.clone()
+        n = self.n = self.pos.shape[0]
+        f = lambda: torch.zeros(n, device=dev)
+        self.h, self.rho, self.omega, self.dudt, self.vsig = f(), f(), f(), f(), f()
+        self.acc = torch.zeros(n, 3, device=dev)
+        self.n_ngb = torch.zeros(n, dtype=torch.int32, device=dev)
+        self.flags = torch.zeros(n, dtype=torch.uint8, device=dev)
+        self.active = torch.zeros(n, dtype=torch.int32, device=dev)
+        self.count = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.grid = sph_build_grid(ctx, self.pos, self.mass, self.params)
+        self.tick = 0
+        self.pairs = 0
+        everyone = torch.arange(n, dtype=torch.int32, device=dev)
+        self._forces(everyone)
+        if bins is None:
+            self.bins = torch.zeros(n, dtype=torch.uint8, device=dev)
+            sph_timebins(ctx, self.h, self.vsig, None, 0, self.courant, self.dt_max, self.max_bin, self.bins)
+        else:
+            self.bins = bins.to(torch.uint8).contiguous().clone()
+        self._kick(everyone, 0.5)          # opening half kick of every particle
+
+    def dt_bins(self, factor=1.0):
+        return [factor * self.dt_max / 2.0 ** b for b in range(self.max_bin + 1)]
+
+    def _forces(self, act):
+        sph_density(self.ctx, self.grid, self.h, act, self.rho, self.omega, self.n_ngb, self.flags, None,
+                    self.params)
+        sph_hydro_force(self.ctx, self.grid, self.vel_pred, self.u_pred, self.h, self.rho, self.omega, act, self.acc,
+                        self.dudt, self.vsig, None, self.params)
+        _, st = sph_sync_status(self.ctx)
+        self.pairs += st["density_pairs"] + st["force_pairs"]
+
+    def _kick(self, act, factor, sync=False):
+        sph_kick(self.ctx, act, act.numel(), self.bins, self.dt_bins(factor), self.acc, self.dudt, self.vel, self.u,
+                 self.vel_pred if sync else None, self.u_pred if sync else None)
+
+    def step(self):
+        """Advance one tick (dt_max / 2^max_bin). Returns the active count."""
+        ctx = self.ctx
+        sph_drift(ctx, self.pos, self.vel, self.dt_max / 2.0 ** self.max_bin, self.box, self.acc, self.dudt,
+                  self.vel_pred, self.u_pred)
+        self.tick += 1
+        sph_grid_update(ctx, self.grid, self.pos, self.mass)
+        sph_active_from_bins(ctx, self.grid, self.bins, self.tick, self.max_bin, self.active, self.count)
+        na = int(self.count.item())
+        if na:
+            act = self.active[:na]
+            self._forces(act)
+            self._kick(act, 0.5, sync=True)   # closing half kick: synchronized v, u become the predictions
+            if self.rebin:
+                sph_timebins(ctx, self.h, self.vsig, act, self.tick, self.courant, self.dt_max, self.max_bin,
+                             self.bins)
+            self._kick(act, 0.5)           # opening half kick of the next step
+        return na
+
+    def synchronized_velocity(self):
+        """Velocities at the current time: the half kick of every particle's
+        running step taken back (exact at the end of a dt_max cycle)."""
+        v = self.vel.clone()
+        u = self.u.clone()
+        everyone = torch.arange(self.n, dtype=torch.int32, device=self.vel.device)
+        sph_kick(self.ctx, everyone, self.n, self.bins, self.dt_bins(-0.5), self.acc, self.dudt, v, u)
+        return v, u
