@@ -200,7 +200,7 @@ cudaError_t run_backward(sph_ctx* ctx, sph_grid* g, const BackwardLaunch& b, cud
 cudaError_t launch_density_coop(sph_ctx* ctx, const DensityLaunch& a, cudaStream_t s);
 cudaError_t launch_force_coop(sph_ctx* ctx, const ForceLaunch& a, cudaStream_t s);
 
-// wpp.cu (one warp per particle)
+// wpp_density.cu, wpp_force.cu (one warp per particle)
 cudaError_t launch_density_wpp(sph_ctx* ctx, const DensityLaunch& a, int64_t n_active, cudaStream_t s);
 cudaError_t launch_force_wpp(sph_ctx* ctx, const ForceLaunch& a, int64_t n_active, cudaStream_t s);
 

@@ -1,0 +1,353 @@
+// wpp_force.cu -- the default force pass: pairs from the density pass's neighbour
+// lists (k_force_list), and the walk for what they cannot serve (k_force_wpp).
+#include "wpp.cuh"
+
+namespace sph {
+
+// ---------------------------------------------------------------------------
+// Force
+// ---------------------------------------------------------------------------
+
+template <bool HASH, int MINB, bool BAL, bool COND>
+__global__ void __launch_bounds__(kWppThreads, MINB) k_force_wpp(WppArgs a) {
+    __shared__ WppSmem smem[kWppWarps];
+    WppSmem& sm = smem[threadIdx.x >> 5];
+    const unsigned lane = lane_id();
+    const unsigned lt = (1u << lane) - 1u;
+    const float rel = 9.5367431640625e-07f;
+    const float elo = 1.f - 4.f * rel, ehi = 1.f + 4.f * rel;
+    const float kNorm = (float)(8.0 / 3.141592653589793);
+    const float alpha = a.alpha;
+    // after a list pass: only the particles the lists could not serve, one per
+    // queue grab (walked alone), unless the lists could not serve the call
+    const int32_t* act = a.act;
+    int cnt = (int)*a.count_ptr, chunk = a.chunk;
+    if (a.fb_act && wpp_lists_valid(a.list_st, a.n_total)) {
+        act = a.fb_act;
+        cnt = (int)*a.fb_count;
+        chunk = 1;
+    }
+    unsigned long long c_pairs = 0, c_tests = 0;   // lane 0's per-warp totals
+    for (;;) {
+        int t0 = 0;
+        if (lane == 0) t0 = (int)atomicAdd(a.queue, (unsigned)chunk);
+        t0 = __shfl_sync(0xffffffffu, t0, 0);
+        if (t0 >= cnt) break;
+        const int t1 = min(t0 + chunk, cnt);
+        for (int t = t0; t < t1;) {
+            const WppGroup G = wpp_group(a.boxes, a.n_boxes, act, t, t1);
+            t += G.n;
+            const BoxDesc& B = a.boxes[G.box];
+            const float sf = B.sf;
+            const int off = (int)B.off, pend = (int)(B.off + B.n);
+            // one shared walk for the group (radius: the largest member h)
+            uint4 Xl = make_uint4(0u, 0u, 0u, 0u);
+            float hl = 0.f;
+            if (G.p >= 0) {
+                Xl = a.posm[G.p];
+                hl = a.fvel[G.p].w;
+            }
+            int ngl = -1;
+            if (G.n >= 2 && B.nlev > 1) {
+                const float hg = warp_max(hl);
+                ngl = wpp_group_leaves(sm, B, a.node_c, a.node_e, Xl, G.p >= 0, sf,
+                                       [&](float4 e) { return fmaxf(hg, e.w); });
+            }
+            for (int m = 0; m < G.n; ++m) {
+                const int p = __shfl_sync(0xffffffffu, G.p, m);
+                const uint4 Xi = make_uint4(__shfl_sync(0xffffffffu, Xl.x, m), __shfl_sync(0xffffffffu, Xl.y, m),
+                                            __shfl_sync(0xffffffffu, Xl.z, m), __shfl_sync(0xffffffffu, Xl.w, m));
+                const float hi = __shfl_sync(0xffffffffu, hl, m);
+                const int oi = a.perm[p];
+                const float4 vi = a.fvm[p];
+                const float4 thi = a.fthermo[p];
+                const float2 ci = COND ? a.fcond[p] : make_float2(0.f, 0.f);
+                const WppForceI I = {vi.x, vi.y, vi.z, thi.w, thi.x, thi.y, thi.z,
+                                     kNorm * thi.w * thi.w * thi.w * thi.w, BAL ? a.fbal[p] : 1.f, ci.x, ci.y};
+                // i side of the band test: h_i (1 +- 2^-19) (the leaf's rounding bound is added per leaf)
+                const float hiP = hi * (1.f + 2.f * rel), hiM = hi * (1.f - 2.f * rel);
+                double HHi = -1.0;
+                float Sx = 0.f, Sy = 0.f, Sz = 0.f, Su = 0.f, Sc = 0.f, vsmax = 0.f;   // per-lane partial sums
+                int np = 0, nh = 0, nlf = 0;
+                unsigned tests = 0;
+                bool complete = true;
+                unsigned long long hs = 0;
+                // pair terms of hit-buffer entries [0, k), one per lane
+                auto drain = [&](int k) {
+                    __syncwarp();
+                    if ((int)lane < k) {
+                        const float4 e = sm.hit.f[lane];
+                        const int q = __float_as_int(e.w);
+                        wpp_force_pair<BAL, COND>(I, e.x, e.y, e.z, __ldg(a.fvm + q), __ldg(a.fthermo + q),
+                                                  BAL ? __ldg(a.fbal + q) : 1.f,
+                                                  COND ? __ldg(a.fcond + q) : make_float2(0.f, 0.f), alpha, Sx, Sy,
+                                                  Sz, Su, Sc, vsmax);
+                    }
+                    __syncwarp();
+                };
+                // Tests the candidates of leaf list entries [0, nlf), 32 per step
+                // (lanes 8k..8k+7: the particles of the step's k-th leaf). A pair
+                // is in the set when r < h_i or r < h_j; r^2 is tested in FP32
+                // against each radius widened and narrowed by the leaf's rounding
+                // bound, and only pairs inside that thin band take the exact
+                // integer/FP64 predicate.
+                auto process = [&]() {
+                    for (int base = 0; base < nlf; base += 4) {
+                        // li <= 127 < kWppLeaves: entries past nlf are stale but in
+                        // bounds; lanes without a candidate read particle p itself
+                        const int li = base + (int)(lane >> 3);
+                        const int id = sm.lid[li];
+                        const float4 o = sm.lof[li];
+                        const int qq = off + (id & 0x7fffffff) * kLeaf + (int)(lane & 7u);
+                        const bool cand = li < nlf && qq < pend;
+                        const int q = cand ? qq : p;
+                        const bool ok = cand && q != p;
+                        const float4 f = __ldg(a.fposh + q);
+                        float dx = o.x + f.x, dy = o.y + f.y, dz = o.z + f.z;
+                        if (__any_sync(0xffffffffu, ok && id < 0)) {
+                            if (ok && id < 0) {   // wide leaf: exact integer separations
+                                const uint4 Xj = a.posm[q];
+                                dx = (float)(int)(Xj.x - Xi.x) * sf;
+                                dy = (float)(int)(Xj.y - Xi.y) * sf;
+                                dz = (float)(int)(Xj.z - Xi.z) * sf;
+                            }
+                        }
+                        const float r2 = dx * dx + dy * dy + dz * dz;
+                        const float si = fmaxf(hiM - o.w, 0.f), sj = fmaxf(fmaf(f.w, 1.f - 2.f * rel, -o.w), 0.f);
+                        bool in = ok && (r2 < si * si * elo || r2 < sj * sj * elo);
+                        const float ti = hiP + o.w, tj = fmaf(f.w, 1.f + 2.f * rel, o.w);
+                        const bool mi = r2 < ti * ti * ehi, mj = r2 < tj * tj * ehi;
+                        const bool band = ok && !in && (mi || mj);
+                        if (__any_sync(0xffffffffu, band)) {
+                            if (band) {
+                                const unsigned long long D2 = exact_d2(Xi, a.posm[q]);
+                                if (mi) {
+                                    if (HHi < 0.0) HHi = wpp_hh(hi, B.L);
+                                    in = exact_pred(D2, HHi);
+                                }
+                                if (!in && mj) in = exact_pred(D2, wpp_hh(f.w, B.L));
+                            }
+                        }
+                        tests += __popc(__ballot_sync(0xffffffffu, cand));
+                        const unsigned hm = __ballot_sync(0xffffffffu, in);
+                        if (in) {
+                            sm.hit.f[nh + __popc(hm & lt)] = make_float4(dx, dy, dz, __int_as_float(q));
+                            if (HASH) hs += splitmix64((unsigned long long)a.perm[q]);
+                        }
+                        np += __popc(hm);
+                        nh += __popc(hm);
+                        if (nh >= 32) {
+                            drain(32);
+                            nh -= 32;
+                            if ((int)lane < nh) sm.hit.f[lane] = sm.hit.f[32 + lane];
+                            __syncwarp();
+                        }
+                    }
+                };
+                if (ngl >= 0)
+                    wpp_filter(sm, ngl, B, a.node_c, a.node_e, Xi, sf, nlf, complete,
+                               [&](float4 e) { return fmaxf(hi, e.w); }, [&]() { process(); nlf = 0; });
+                else
+                    wpp_walk(sm, B, a.node_c, a.node_e, Xi, sf, nlf, complete, [&](float4 e) { return fmaxf(hi, e.w); },
+                             [&]() { process(); nlf = 0; });
+                process();
+                drain(nh);
+                // fold the per-lane sums: lanes 0-7 end with acc.x, 8-15 acc.y,
+                // 16-23 acc.z, 24-31 du/dt
+                const float fs = wpp_fold4(Sx, Sy, Sz, Su);
+                vsmax = warp_max(vsmax);
+                if (HASH) hs = warp_sum(hs);
+                if ((lane & 7u) == 0u) {
+                    const int comp = (int)(lane >> 3);
+                    if (comp < 3) a.acc[3 * (size_t)oi + comp] = fs;
+                    else a.dudt[oi] = fs;
+                }
+                if (COND) {
+                    float cs, cc, z0, z1;
+                    wpp_fold2(Sc, 0.f, cs, cc, z0, z1);
+                    if (lane == 0) a.dudt_cond[oi] = __fsub_rn(cs, cc);
+                }
+                if (lane == 0) {
+                    a.vsig[oi] = vsmax;
+                    if (HASH) a.hash[oi] = hs;
+                    c_pairs += (unsigned long long)np;
+                    c_tests += tests;
+                }
+                __syncwarp();
+            }
+        }
+    }
+    if (lane == 0) {
+        atomicAdd(&a.ctr->force_pairs, c_pairs);
+        atomicAdd(&a.ctr->pair_tests, c_tests);
+    }
+}
+
+// Force pass from the recorded lists: warp per active particle, pairs 32 at a
+// time (the neighbour list, then the extra partners), the same pair terms and
+// fold as k_force_wpp. If the lists cannot serve the call at all the kernel
+// does nothing and the walk that follows takes the whole active set;
+// particles whose own lists did not fit go to fb_list for that walk.
+template <bool HASH, bool BAL, bool COND>
+__global__ void __launch_bounds__(128) k_force_list(WppArgs a) {
+    if (!wpp_lists_valid(a.list_st, a.n_total)) return;
+    const unsigned lane = lane_id();
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    const int cnt = (int)*a.count_ptr;
+    const float kNorm = (float)(8.0 / 3.141592653589793);
+    unsigned long long c_pairs = 0;   // per warp, lane-uniform
+    for (int t = blockIdx.x * (blockDim.x >> 5) + (int)(threadIdx.x >> 5); t < cnt; t += warps) {
+        const int p = a.act[t];
+        const int cn = a.nbr_n[p];
+        const unsigned e0 = a.ext_off[p], e1 = a.ext_off[p + 1];
+        if (cn < 0 || e1 > a.ext_pool || a.ext_n[p] != 0u) {
+            if (lane == 0) a.fb_list[atomicAdd(&a.list_st[3], 1u)] = p;
+            continue;
+        }
+        const BoxDesc& B = a.boxes[a.n_boxes == 1 ? 0 : wpp_box(a.boxes, a.n_boxes, p)];
+        const float sf = B.sf;
+        const uint4 Xi = a.posm[p];
+        const int oi = a.perm[p];
+        const float4 vi = a.fvm[p];
+        const float4 thi = a.fthermo[p];
+        const float2 ci = COND ? a.fcond[p] : make_float2(0.f, 0.f);
+        const WppForceI I = {vi.x, vi.y, vi.z, thi.w, thi.x, thi.y, thi.z, kNorm * thi.w * thi.w * thi.w * thi.w,
+                             BAL ? a.fbal[p] : 1.f, ci.x, ci.y};
+        float Sx = 0.f, Sy = 0.f, Sz = 0.f, Su = 0.f, Sc = 0.f, vsmax = 0.f;
+        unsigned long long hs = 0;
+        const int tot = cn + (int)(e1 - e0);
+        const int32_t* ln = a.nbr + a.nbr_off[p];
+        const int32_t* le = a.ext + e0;
+        // two pairs per lane per step (k and k + 32), their loads issued together;
+        // each lane still sums its pairs in the order k, k + 32, k + 64, ...
+        for (int k = (int)lane; k < tot; k += 64) {
+            const int k1 = k + 32;
+            const bool two = k1 < tot;
+            const int q0 = k < cn ? ln[k] : le[k - cn];
+            const int q1 = two ? (k1 < cn ? ln[k1] : le[k1 - cn]) : q0;
+            const uint4 X0 = a.posm[q0], X1 = a.posm[q1];
+            const float4 v0 = __ldg(a.fvm + q0), v1 = __ldg(a.fvm + q1);
+            const float4 t0 = __ldg(a.fthermo + q0), t1 = __ldg(a.fthermo + q1);
+            const float b0 = BAL ? __ldg(a.fbal + q0) : 1.f, b1 = BAL ? __ldg(a.fbal + q1) : 1.f;
+            const float2 c0 = COND ? __ldg(a.fcond + q0) : make_float2(0.f, 0.f);
+            const float2 c1 = COND ? __ldg(a.fcond + q1) : make_float2(0.f, 0.f);
+            wpp_force_pair<BAL, COND>(I, (float)(int)(X0.x - Xi.x) * sf, (float)(int)(X0.y - Xi.y) * sf,
+                                      (float)(int)(X0.z - Xi.z) * sf, v0, t0, b0, c0, a.alpha, Sx, Sy, Sz, Su, Sc,
+                                      vsmax);
+            if (HASH) hs += splitmix64((unsigned long long)a.perm[q0]);
+            if (two) {
+                wpp_force_pair<BAL, COND>(I, (float)(int)(X1.x - Xi.x) * sf, (float)(int)(X1.y - Xi.y) * sf,
+                                          (float)(int)(X1.z - Xi.z) * sf, v1, t1, b1, c1, a.alpha, Sx, Sy, Sz, Su, Sc,
+                                          vsmax);
+                if (HASH) hs += splitmix64((unsigned long long)a.perm[q1]);
+            }
+        }
+        const float fs = wpp_fold4(Sx, Sy, Sz, Su);
+        vsmax = warp_max(vsmax);
+        if (HASH) hs = warp_sum(hs);
+        if ((lane & 7u) == 0u) {
+            const int comp = (int)(lane >> 3);
+            if (comp < 3) a.acc[3 * (size_t)oi + comp] = fs;
+            else a.dudt[oi] = fs;
+        }
+        if (COND) {
+            float cs, cc, z0, z1;
+            wpp_fold2(Sc, 0.f, cs, cc, z0, z1);
+            if (lane == 0) a.dudt_cond[oi] = __fsub_rn(cs, cc);
+        }
+        if (lane == 0) {
+            a.vsig[oi] = vsmax;
+            if (HASH) a.hash[oi] = hs;
+        }
+        c_pairs += (unsigned long long)tot;
+    }
+    if (lane == 0 && c_pairs) atomicAdd(&a.ctr->force_pairs, c_pairs);
+}
+
+
+// Kernel variants of the force pass: hash output, register budget, Balsara's
+// switch, conduction.
+template <bool H, bool BAL, bool COND>
+static void launch_fl(int blocks, cudaStream_t s, const WppArgs& c) {
+    k_force_list<H, BAL, COND><<<blocks, 128, 0, s>>>(c);
+}
+static void launch_force_list(bool hash, bool bal, bool cond, int blocks, cudaStream_t s, const WppArgs& c) {
+    if (hash) {
+        if (bal) cond ? launch_fl<true, true, true>(blocks, s, c) : launch_fl<true, true, false>(blocks, s, c);
+        else cond ? launch_fl<true, false, true>(blocks, s, c) : launch_fl<true, false, false>(blocks, s, c);
+    } else {
+        if (bal) cond ? launch_fl<false, true, true>(blocks, s, c) : launch_fl<false, true, false>(blocks, s, c);
+        else cond ? launch_fl<false, false, true>(blocks, s, c) : launch_fl<false, false, false>(blocks, s, c);
+    }
+}
+template <bool H, int M>
+static void launch_fw(bool bal, bool cond, int blocks, cudaStream_t s, const WppArgs& c) {
+    if (bal) {
+        if (cond) k_force_wpp<H, M, true, true><<<blocks, kWppThreads, 0, s>>>(c);
+        else k_force_wpp<H, M, true, false><<<blocks, kWppThreads, 0, s>>>(c);
+    } else {
+        if (cond) k_force_wpp<H, M, false, true><<<blocks, kWppThreads, 0, s>>>(c);
+        else k_force_wpp<H, M, false, false><<<blocks, kWppThreads, 0, s>>>(c);
+    }
+}
+static void launch_force_walk(bool hash, bool six, bool bal, bool cond, int blocks, cudaStream_t s,
+                              const WppArgs& c) {
+    if (six) hash ? launch_fw<true, 6>(bal, cond, blocks, s, c) : launch_fw<false, 6>(bal, cond, blocks, s, c);
+    else hash ? launch_fw<true, 8>(bal, cond, blocks, s, c) : launch_fw<false, 8>(bal, cond, blocks, s, c);
+}
+
+
+cudaError_t launch_force_wpp(sph_ctx* ctx, const ForceLaunch& a, int64_t n_active, cudaStream_t s) {
+    sph_grid* g = const_cast<sph_grid*>(a.g);
+    cudaError_t e;
+    const bool lists = g->nbr != nullptr && g->lists_full;
+    if (lists && (e = cudaMemsetAsync(g->list_st + 2, 0, 2 * sizeof(unsigned), s))) return e;
+    force_pack(g, a.vel, a.u, a.h, a.rho, a.omega, (float)a.gamma, s, lists ? g->list_h : nullptr,
+               lists ? g->list_st + 2 : nullptr, a.divv, a.curlv, a.kappa);
+    ++ctx->launches;
+    if ((e = cudaMemsetAsync(ctx->queue + 3, 0, sizeof(unsigned), s))) return e;
+    WppArgs c = wpp_common(ctx, g, ctx->queue + 3);
+    int blocks = 0;
+    const int bps = a.blocks_per_sm > 0 ? a.blocks_per_sm : kWppForceBps;
+    wpp_shape(ctx, bps, n_active, blocks, c.chunk);
+    c.fvel = g->fvel;
+    c.fthermo = g->fthermo;
+    c.fposh = g->fposh;
+    c.fvm = g->fvm;
+    c.acc = a.acc;
+    c.dudt = a.dudt;
+    c.vsig = a.vsig;
+    c.alpha = (float)a.alpha;
+    c.hash = a.hash;
+    c.fbal = a.divv ? g->fbal : nullptr;
+    c.fcond = a.kappa ? g->fcond : nullptr;
+    c.dudt_cond = a.dudt_cond;
+    WppSpan sp;
+    if ((e = span_begin(ctx, a.time_kernels, 1, s, sp))) return e;
+    if (lists) {
+        // pairs from the recorded lists; the walk that follows takes the
+        // particles they cannot serve (usually none), or every active particle
+        // if the lists cannot serve this call
+        c.nbr = g->nbr;
+        c.nbr_off = g->nbr_off;
+        c.nbr_n = g->nbr_n;
+        c.ext = g->ext;
+        c.ext_off = g->ext_off;
+        c.ext_n = g->ext_n;
+        c.ext_pool = (unsigned)g->ext_pool;
+        c.list_st = g->list_st;
+        c.fb_list = g->fb_list;
+        const int lb = (int)std::max<long long>(
+            1, std::min<long long>((long long)ctx->sm_count * 16, (n_active + 3) / 4));
+        launch_force_list(a.hash != nullptr, c.fbal != nullptr, c.fcond != nullptr, lb, s, c);
+        ++ctx->launches;
+        c.fb_act = g->fb_list;
+        c.fb_count = g->list_st + 3;
+    }
+    launch_force_walk(a.hash != nullptr, bps <= 6, c.fbal != nullptr, c.fcond != nullptr, blocks, s, c);
+    ++ctx->launches;
+    if ((e = span_end(ctx, sp, s))) return e;
+    return cudaGetLastError();
+}
+
+}  // namespace sph
