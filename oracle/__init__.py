@@ -55,7 +55,7 @@ def lib():
         L.orc_density.argtypes = [i32, P, P, i64, f64, P, P, f64, f64, i32, P, i64, i32, i32,
                                   P, P, P, P, P, P, P, P]
         L.orc_density.restype = i32
-        L.orc_force.argtypes = [i32, P, P, i64, f64, P, P, P, P, P, P, f64, f64, P, P, P, i64, i32,
+        L.orc_force.argtypes = [i32, P, P, i64, f64, P, P, P, P, P, P, f64, P, f64, P, P, P, i64, i32,
                                 P, P, P, P, P, P, P]
         L.orc_divcurl.argtypes = [i32, P, P, i64, f64, P, P, P, P, P, i64, i32, P, P, P, P]
         L.orc_conduction.argtypes = [i32, P, P, i64, f64, P, P, P, P, P, P, i64, i32, P, P]
@@ -187,8 +187,12 @@ def force(X=None, vel=None, mass=None, u=None, h=None, rho=None, omega=None, box
           alpha=1.0, gamma=5.0 / 3.0, active=None, brute=False, xc=None, divv=None, curlv=None):
     """Hydro-force pass. Returns acc (N,3), dudt, vsig, scale_a, scale_u,
     n_pairs, hash (entries of inactive particles NaN / -1). With divv and
-    curlv, Balsara's switch limits the viscosity."""
+    curlv, Balsara's switch limits the viscosity. alpha: a number, or one
+    value per particle (the pair taking the mean of its two)."""
     mode, Xc, xcc = _geom(X, xc, box)
+    alpha_p = None
+    if np.ndim(alpha) > 0:
+        alpha_p, alpha = _c(alpha, np.float64), 0.0
     n = Xc.shape[0]
     args = [_c(a, np.float64) for a in (vel, mass, u, h, rho, omega)]
     sw = [None, None] if divv is None else [_c(divv, np.float64), _c(curlv, np.float64)]
@@ -198,11 +202,24 @@ def force(X=None, vel=None, mass=None, u=None, h=None, rho=None, omega=None, box
         out[k] = np.full(n, np.nan)
     out["n_pairs"] = np.full(n, -1, dtype=np.int64)
     out["hash"] = np.zeros(n, dtype=np.uint64)
-    lib().orc_force(mode, _p(Xc), _p(xcc), n, float(box), *[_p(a) for a in args], float(alpha),
+    lib().orc_force(mode, _p(Xc), _p(xcc), n, float(box), *[_p(a) for a in args], float(alpha), _p(alpha_p),
                     float(gamma), _p(sw[0]), _p(sw[1]), _p(act), 0 if act is None else act.size, int(bool(brute)),
                     _p(out["acc"]), _p(out["dudt"]), _p(out["vsig"]), _p(out["scale_a"]),
                     _p(out["scale_u"]), _p(out["n_pairs"]), _p(out["hash"]))
     return out
+
+
+def visc_rate(h, u, divv, alpha, alpha_min=0.1, alpha_max=1.0, ell=0.2, gamma=5.0 / 3.0):
+    """Rate of change of the viscosity parameter (Morris & Monaghan 1997):
+    d alpha/dt = -(alpha - alpha_min) / tau + S, with the decay time
+    tau = h / (ell c) (h the kernel's support radius, c = sqrt(gamma (gamma - 1) u)
+    the sound speed) and the source S = max(-div v, 0) (alpha_max - alpha),
+    which raises alpha only where the flow converges."""
+    h, u, divv, alpha = (np.asarray(a, np.float64) for a in (h, u, divv, alpha))
+    c = np.sqrt(gamma * (gamma - 1.0) * u)
+    tau = h / (ell * c)
+    source = np.maximum(-divv, 0.0) * (alpha_max - alpha)
+    return -(alpha - alpha_min) / tau + source
 
 
 def neighbours(X=None, i=0, h=0.1, box=1.0, brute=True, xc=None) -> np.ndarray:

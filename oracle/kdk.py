@@ -20,12 +20,18 @@ Inactive particles keep the h, rho, Omega, a, du/dt of their last step. The
 prediction keeps the scheme second order although the force depends on v
 (viscosity, du/dt) and u (pressure). Bins are given (the same bins for both
 sides of a comparison).
+
+Options: balsara=True limits the viscosity with Balsara's switch (div v and
+curl v from the density pass's neighbours); visc=dict(alpha0, alpha_min,
+alpha_max, ell) gives every particle its own viscosity parameter alpha, with
+the rate of Morris & Monaghan (1997) (oracle.visc_rate) evaluated with the
+force and integrated like u: kicked, predicted, reset at the closing kick.
 """
 from __future__ import annotations
 
 import numpy as np
 
-from . import density, force, quantize
+from . import density, divcurl, force, quantize, visc_rate
 
 
 def timebins(h, vsig, courant, dt_max, max_bin, tick=0):
@@ -50,7 +56,7 @@ def timebins(h, vsig, courant, dt_max, max_bin, tick=0):
 
 class KDK:
     def __init__(self, pos, vel, mass, u, bins, dt_max, max_bin, box=1.0, n_target=64.0, alpha=1.0,
-                 gamma=5.0 / 3.0):
+                 gamma=5.0 / 3.0, balsara=False, visc=None):
         self.pos = np.array(pos, np.float64)
         self.vel = np.array(vel, np.float64)
         self.mass = np.array(mass, np.float64)
@@ -58,6 +64,7 @@ class KDK:
         self.bins = np.array(bins, np.int64)
         self.dt_max, self.max_bin, self.box = float(dt_max), int(max_bin), float(box)
         self.n_target, self.alpha, self.gamma = n_target, alpha, gamma
+        self.balsara, self.visc = bool(balsara), visc
         n = self.pos.shape[0]
         self.h = np.zeros(n)
         self.rho = np.zeros(n)
@@ -70,6 +77,12 @@ class KDK:
         self.tick = 0
         self.vel_pred = self.vel.copy()
         self.u_pred = self.u.copy()
+        self.divv = np.zeros(n)
+        self.curlv = np.zeros(n)
+        if visc is not None:
+            self.av = np.full(n, float(visc["alpha0"]))   # the viscosity parameter, kicked like u
+            self.av_pred = self.av.copy()
+            self.dav = np.zeros(n)
         self._forces(np.arange(n))
         self._kick(np.arange(n), 0.5)
 
@@ -81,8 +94,19 @@ class KDK:
         d = density(X, self.mass, self.h, box=self.box, n_target=self.n_target, tol=1e-10, active=act)
         for k in ("h", "rho", "omega"):
             getattr(self, k)[act] = d[k][act]
+        sw = {}
+        if self.balsara or self.visc is not None:
+            dv, cv = divcurl(X, self.vel_pred, self.mass, self.h, self.rho, box=self.box, active=act)
+            self.divv[act], self.curlv[act] = dv[act], cv[act]
+            if self.balsara:
+                sw = {"divv": self.divv, "curlv": self.curlv}
+        alpha = self.alpha if self.visc is None else self.av_pred
         f = force(X, self.vel_pred, self.mass, self.u_pred, self.h, self.rho, self.omega, box=self.box,
-                  alpha=self.alpha, gamma=self.gamma, active=act)
+                  alpha=alpha, gamma=self.gamma, active=act, **sw)
+        if self.visc is not None:
+            v = self.visc
+            self.dav[act] = visc_rate(self.h[act], self.u_pred[act], self.divv[act], self.av_pred[act],
+                                      v["alpha_min"], v["alpha_max"], v["ell"], self.gamma)
         self.acc[act] = f["acc"][act]
         self.dudt[act] = f["dudt"][act]
         self.vsig[act] = f["vsig"][act]
@@ -94,9 +118,13 @@ class KDK:
         self.u[act] += self.dudt[act] * dt
         self.scale_a[act] += self._sa[act] * np.abs(dt)
         self.scale_u[act] += self._su[act] * np.abs(dt)
+        if self.visc is not None:
+            self.av[act] += self.dav[act] * dt
         if sync:   # the kicked values are the synchronized ones: the new predictions
             self.vel_pred[act] = self.vel[act]
             self.u_pred[act] = self.u[act]
+            if self.visc is not None:
+                self.av_pred[act] = self.av[act]
 
     def step(self):
         dt = self.dt_max / 2.0 ** self.max_bin
@@ -104,6 +132,8 @@ class KDK:
         self.pos[self.pos >= self.box] -= self.box
         self.vel_pred += self.acc * dt
         self.u_pred += self.dudt * dt
+        if self.visc is not None:
+            self.av_pred += self.dav * dt
         self.tick += 1
         act = np.nonzero(self.tick % (1 << (self.max_bin - self.bins)) == 0)[0]
         if act.size:
@@ -115,3 +145,6 @@ class KDK:
     def synchronized_velocity(self):
         dt = -0.5 * self.dt_bin(np.arange(self.pos.shape[0]))
         return self.vel + self.acc * dt[:, None], self.u + self.dudt * dt
+
+    def synchronized_alpha(self):
+        return self.av - 0.5 * self.dav * self.dt_bin(np.arange(self.pos.shape[0]))

@@ -531,10 +531,13 @@ static double orc_balsara(double div, double curl, double cs, double h)
  * magnitude of each pair's term (the per-particle absolute scale used for
  * tolerances); n_pairs = |pair set|; hash = neighbour-set checksum.
  * divv / curlv (both NULL or both given): Balsara's switch on Pi_ij.
+ * alpha_p (NULL: alpha for every pair): a viscosity parameter per particle,
+ * the pair taking alpha_ij = (alpha_i + alpha_j) / 2 (time-dependent
+ * viscosity, Morris & Monaghan 1997), symmetric in i and j.
  */
 void orc_force(int mode, const uint32_t *X, const double *xc, int64_t n, double L,
                const double *v, const double *m, const double *u, const double *h,
-               const double *rho, const double *omega, double alpha, double gamma,
+               const double *rho, const double *omega, double alpha, const double *alpha_p, double gamma,
                const double *divv, const double *curlv,
                const int64_t *active, int64_t n_active, int brute,
                double *acc, double *dudt, double *vsig, double *scale_a, double *scale_u,
@@ -601,7 +604,8 @@ void orc_force(int mode, const uint32_t *X, const double *xc, int64_t n, double 
                 double Fj = orc_dWdr(r, h[j]) / r;
                 double Fbar = 0.5 * (Fi + Fj);
                 double PIij = 0.0;
-                if (wij < 0.0) PIij = -0.5 * alpha * vsg * wij / (0.5 * (rho[i] + rho[j]));
+                double aij = alpha_p ? 0.5 * (alpha_p[i] + alpha_p[j]) : alpha;
+                if (wij < 0.0) PIij = -0.5 * aij * vsg * wij / (0.5 * (rho[i] + rho[j]));
                 if (divv) PIij *= 0.5 * (fi + orc_balsara(divv[j], curlv[j], cj, h[j]));
                 double coef = m[j] * (Ai * Fi + Aj * Fj + PIij * Fbar);
                 ax -= coef * rij[0];
