@@ -361,11 +361,16 @@ def e2e_steps(S, ctx, wl, dparams, fparams, steps):
 def balsara_line(S, ctx, wl, dparams, fparams, reps=3):
     """Secondary line: the 100 % sub-step of the 10M clustered step with
     Balsara's switch (density + velocity divergence and curl, then the
-    switched force), next to the same sub-step without it."""
+    switched force), next to the same sub-step without it and with the
+    time-dependent viscosity (per-particle alpha, seeded uniform in [0.1, 1],
+    with the switch, plus the alpha rate)."""
     import torch
     st, n, dev = wl["st"], wl["n"], wl["h"].device
     act, h_in = wl["acts"][0], wl["h_ins"][0]
     dv, cv = torch.zeros(n, device=dev), torch.zeros(n, device=dev)
+    gen = torch.Generator(device=dev).manual_seed(41)
+    alpha = 0.1 + 0.9 * torch.rand(n, device=dev, generator=gen)
+    dalpha = torch.zeros(n, device=dev)
 
     def switched():
         S.sph_density_divcurl(ctx, wl["grid"], wl["h"], act, st["rho"], st["omega"], st["n_ngb"], st["flags"], None,
@@ -378,8 +383,15 @@ def balsara_line(S, ctx, wl, dparams, fparams, reps=3):
         S.sph_hydro_force(ctx, wl["grid"], wl["vel"], wl["u"], wl["h"], st["rho"], st["omega"], act, st["acc"],
                           st["dudt"], st["vsig"], None, fparams)
 
+    def visc():
+        S.sph_density_divcurl(ctx, wl["grid"], wl["h"], act, st["rho"], st["omega"], st["n_ngb"], st["flags"], None,
+                              wl["vel"], dv, cv, dparams)
+        S.sph_hydro_force_visc(ctx, wl["grid"], wl["vel"], wl["u"], wl["h"], st["rho"], st["omega"], alpha, dv, cv,
+                               act, st["acc"], st["dudt"], st["vsig"], None, fparams)
+        S.sph_visc_rate(ctx, act, wl["h"], wl["u"], dv, alpha, dalpha)
+
     out = {}
-    for name, fn in (("switched", switched), ("plain", plain)):
+    for name, fn in (("switched", switched), ("plain", plain), ("visc", visc)):
         wl["h"].copy_(h_in)
         fn()
         S.sph_sync_status(ctx)
@@ -397,7 +409,8 @@ def balsara_line(S, ctx, wl, dparams, fparams, reps=3):
     return {"workload": "10M clustered, 100 % active sub-step: density + velocity divergence and curl, "
                         "then the force with Balsara's switch",
             "value": out["switched"][0], "unit": UNIT, "ms_per_pass": out["switched"][1],
-            "without_switch_ms_per_pass": out["plain"][1]}
+            "without_switch_ms_per_pass": out["plain"][1],
+            "time_dependent_alpha_ms_per_pass": out["visc"][1]}
 
 
 def conduction_line(S, ctx, wl, dparams, fparams, reps=3):

@@ -265,6 +265,23 @@ sph_status sph_hydro_force_balsara(sph_ctx *ctx, const sph_grid *grid, const flo
                                    void *stream);
 
 /*
+ * sph_hydro_force with a viscosity parameter per particle (time-dependent
+ * artificial viscosity, the "improved SPH" viscosity of the paper's code,
+ * Sec. 1; default path only): the pair takes alpha_ij = (alpha_i + alpha_j)/2
+ * in place of params->alpha_visc,
+ *   Pi_ij = -(alpha_ij/2) v_sig w_ij / rho_bar [(f_i + f_j)/2],
+ * the bracket (Balsara's switch) when divv and curlv are given.
+ *   alpha_v      device, n floats (caller order, all particles);
+ *   divv, curlv  both NULL (no switch) or as in sph_hydro_force_balsara.
+ * Everything else as sph_hydro_force. alpha_v usually evolves with
+ * sph_visc_rate, sph_kick_scalar and sph_predict_scalar.
+ */
+sph_status sph_hydro_force_visc(sph_ctx *ctx, const sph_grid *grid, const float *vel, const float *u, const float *h,
+                                const float *rho, const float *omega, const float *alpha_v, const float *divv,
+                                const float *curlv, const int32_t *active, int64_t n_active, float *acc, float *dudt,
+                                float *vsig, uint64_t *hash, const sph_params *params, void *stream);
+
+/*
  * The force pass plus thermal conduction over the same pair set, in one
  * traversal (default path only). The paper's code has a conduction module
  * that loops over neighbours like the force module (Sec. 1); the paper
@@ -325,6 +342,26 @@ sph_status sph_kick(sph_ctx *ctx, const int32_t *active, int64_t n_active, const
  * depends on v through the viscosity and on u through the pressure). */
 sph_status sph_drift(sph_ctx *ctx, double *pos, const float *vel, int64_t n, double dt, double box,
                      const float *acc, const float *dudt, float *vel_pred, float *u_pred, void *stream);
+
+/* Rate of the per-particle viscosity parameter (Morris & Monaghan 1997), for
+ * the active particles (caller indices, device) or all (active = NULL):
+ *   dalpha_i = -(alpha_i - alpha_min) ell c_i / h_i + max(-divv_i, 0) (alpha_max - alpha_i),
+ *   c_i = sqrt(gamma (gamma - 1) u_i),
+ * a decay to alpha_min over tau = h/(ell c) (h the support radius) and a
+ * source where the flow converges. h, u, divv, alpha_v, dalpha: device, n
+ * floats, caller order. SPH_ERR_INVALID unless gamma > 1, ell > 0 and
+ * 0 <= alpha_min <= alpha_max. */
+sph_status sph_visc_rate(sph_ctx *ctx, const int32_t *active, int64_t n_active, const float *h, const float *u,
+                         const float *divv, const float *alpha_v, double gamma, double alpha_min, double alpha_max,
+                         double ell, float *dalpha, void *stream);
+/* sph_kick for one per-particle quantity: value_i += rate_i dt_bin[bins_i]
+ * for the active particles; value_pred (or NULL) also receives the result. */
+sph_status sph_kick_scalar(sph_ctx *ctx, const int32_t *active, int64_t n_active, const uint8_t *bins,
+                           const double *dt_bin, int n_bins, const float *rate, float *value, float *value_pred,
+                           void *stream);
+/* The prediction of sph_drift for one quantity: value_pred += rate dt, all n. */
+sph_status sph_predict_scalar(sph_ctx *ctx, int64_t n, double dt, const float *rate, float *value_pred,
+                              void *stream);
 
 /*
  * Adjoint of the density and force passes (an extension of the paper's hot

@@ -17,7 +17,8 @@ from .abi import (SPH_FIXED_H, SPH_FP64, SPH_H_GUESS, SPH_PLAIN_FP32, SPH_TIME_K
 
 __all__ = ["Context", "Grid", "sph_create", "sph_build_grid", "sph_build_grid_batched", "sph_grid_update",
            "sph_density", "sph_hydro_force", "sph_density_divcurl", "sph_hydro_force_balsara",
-           "sph_hydro_force_conduction", "sph_timebins", "sph_active_from_bins", "sph_kick", "sph_drift",
+           "sph_hydro_force_conduction", "sph_hydro_force_visc", "sph_visc_rate", "sph_kick_scalar",
+           "sph_predict_scalar", "sph_timebins", "sph_active_from_bins", "sph_kick", "sph_drift",
            "sph_backward", "sph_sync_status", "sph_grid_export", "sph_sort_keys_static", "density",
            "hydro_force", "default_params", "sph_params", "sph_stats", "SPHError", "SPH_FP64",
            "SPH_PLAIN_FP32", "SPH_FIXED_H", "SPH_H_GUESS", "SPH_TIME_KERNELS", "SPH_WARP_GROUP", "SPH_DENSITY_BUFFERED", "SPH_PER_THREAD_WALK", "SPH_COOP_WALK", "SPH_WARP_WALK", "SPH_NO_LISTS"]
@@ -180,6 +181,43 @@ def sph_hydro_force_conduction(ctx: Context, grid: Grid, vel, u, h, rho, omega, 
                                                  _ptr(acc, f, "acc"), _ptr(dudt, f, "dudt"), _ptr(vsig, f, "vsig"),
                                                  _ptr(dudt_cond, f, "dudt_cond"), _ptr(hash, torch.int64, "hash"),
                                                  ctypes.byref(params or default_params()), _stream()))
+
+
+def sph_hydro_force_visc(ctx: Context, grid: Grid, vel, u, h, rho, omega, alpha_v, divv, curlv, active, acc, dudt,
+                         vsig, hash=None, params: sph_params = None):
+    na = 0 if active is None else active.numel()
+    f = torch.float32
+    ctx.check(ctx.lib.sph_hydro_force_visc(ctx.handle, grid.handle, _ptr(vel, f, "vel"), _ptr(u, f, "u"),
+                                           _ptr(h, f, "h"), _ptr(rho, f, "rho"), _ptr(omega, f, "omega"),
+                                           _ptr(alpha_v, f, "alpha_v"), _ptr(divv, f, "divv"), _ptr(curlv, f, "curlv"),
+                                           _ptr(active, torch.int32, "active"), na, _ptr(acc, f, "acc"),
+                                           _ptr(dudt, f, "dudt"), _ptr(vsig, f, "vsig"),
+                                           _ptr(hash, torch.int64, "hash"),
+                                           ctypes.byref(params or default_params()), _stream()))
+
+
+def sph_visc_rate(ctx: Context, active, h, u, divv, alpha_v, dalpha, gamma=5.0 / 3.0, alpha_min=0.1, alpha_max=1.0,
+                  ell=0.2):
+    na = h.numel() if active is None else active.numel()
+    f = torch.float32
+    ctx.check(ctx.lib.sph_visc_rate(ctx.handle, _ptr(active, torch.int32, "active"), na, _ptr(h, f, "h"),
+                                    _ptr(u, f, "u"), _ptr(divv, f, "divv"), _ptr(alpha_v, f, "alpha_v"),
+                                    float(gamma), float(alpha_min), float(alpha_max), float(ell),
+                                    _ptr(dalpha, f, "dalpha"), _stream()))
+
+
+def sph_kick_scalar(ctx: Context, active, n_active, bins, dt_bin, rate, value, value_pred=None):
+    dts = (ctypes.c_double * len(dt_bin))(*[float(x) for x in dt_bin])
+    f = torch.float32
+    ctx.check(ctx.lib.sph_kick_scalar(ctx.handle, _ptr(active, torch.int32, "active"), int(n_active),
+                                      _ptr(bins, torch.uint8, "bins"), dts, len(dt_bin), _ptr(rate, f, "rate"),
+                                      _ptr(value, f, "value"), _ptr(value_pred, f, "value_pred"), _stream()))
+
+
+def sph_predict_scalar(ctx: Context, dt, rate, value_pred):
+    f = torch.float32
+    ctx.check(ctx.lib.sph_predict_scalar(ctx.handle, value_pred.numel(), float(dt), _ptr(rate, f, "rate"),
+                                         _ptr(value_pred, f, "value_pred"), _stream()))
 
 
 def sph_timebins(ctx: Context, h, vsig, active, tick, courant, dt_max, max_bin, bins):

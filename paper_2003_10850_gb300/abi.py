@@ -44,8 +44,8 @@ SPH_ST_INVALID = 0x08
 EXPORTED = ["sph_default_params", "sph_create", "sph_destroy", "sph_last_error", "sph_build_grid",
             "sph_build_grid_batched", "sph_grid_update", "sph_grid_free", "sph_grid_size", "sph_grid_export",
             "sph_density", "sph_hydro_force", "sph_density_divcurl", "sph_hydro_force_balsara",
-            "sph_hydro_force_conduction", "sph_timebins", "sph_active_from_bins", "sph_kick", "sph_drift",
-            "sph_backward",
+            "sph_hydro_force_conduction", "sph_hydro_force_visc", "sph_timebins", "sph_active_from_bins",
+            "sph_kick", "sph_drift", "sph_visc_rate", "sph_kick_scalar", "sph_predict_scalar", "sph_backward",
             "sph_sync_status", "sph_sort_keys_static"]
 SPH_SORT_STATIC_MAX_KEYS = 1 << 20
 
@@ -121,6 +121,16 @@ def load(path: str | None = None):
     L.sph_hydro_force_conduction.argtypes = [P, P, P, P, P, P, P, P, P, P, P, i64, P, P, P, P, P,
                                              ctypes.POINTER(sph_params), P]
     L.sph_hydro_force_conduction.restype = i32
+    L.sph_hydro_force_visc.argtypes = [P, P, P, P, P, P, P, P, P, P, P, i64, P, P, P, P,
+                                       ctypes.POINTER(sph_params), P]
+    L.sph_hydro_force_visc.restype = i32
+    L.sph_visc_rate.argtypes = [P, P, i64, P, P, P, P, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                ctypes.c_double, P, P]
+    L.sph_visc_rate.restype = i32
+    L.sph_kick_scalar.argtypes = [P, P, i64, P, P, i32, P, P, P, P]
+    L.sph_kick_scalar.restype = i32
+    L.sph_predict_scalar.argtypes = [P, i64, ctypes.c_double, P, P, P]
+    L.sph_predict_scalar.restype = i32
     L.sph_timebins.argtypes = [P, P, P, P, i64, i64, i64, ctypes.c_double, ctypes.c_double, i32, P, P]
     L.sph_timebins.restype = i32
     L.sph_active_from_bins.argtypes = [P, P, P, i64, i32, P, P, P]

@@ -271,7 +271,7 @@ static sph_status force_call(sph_ctx* ctx, const sph_grid* grid, const float* ve
                              const float* h, const float* rho, const float* omega, const float* divv,
                              const float* curlv, const float* kappa, const int32_t* active, int64_t n_active,
                              float* acc, float* dudt, float* vsig, float* dudt_cond, uint64_t* hash,
-                             const sph_params* params, void* stream) {
+                             const sph_params* params, void* stream, const float* alpha_v = nullptr) {
     if (!ctx) return SPH_ERR_INVALID;
     if (!grid || grid->ctx != ctx) return fail(ctx, SPH_ERR_INVALID, "grid is NULL or from another context");
     if (!vel || !u || !h || !rho || !omega || !acc || !dudt || !vsig)
@@ -308,6 +308,7 @@ static sph_status force_call(sph_ctx* ctx, const sph_grid* grid, const float* ve
     a.curlv = curlv;
     a.kappa = kappa;
     a.dudt_cond = dudt_cond;
+    a.alpha_v = alpha_v;
     cudaError_t e = path == Path::Plain       ? launch_force_plain(ctx, a, na, s)
                     : path == Path::WarpGroup ? launch_force(ctx, a, s)
                     : path == Path::Wpp       ? launch_force_wpp(ctx, a, na, s)
@@ -337,6 +338,19 @@ sph_status sph_hydro_force_balsara(sph_ctx* ctx, const sph_grid* grid, const flo
         return fail(ctx, SPH_ERR_INVALID, "the Balsara switch runs on the default path only");
     return force_call(ctx, grid, vel, u, h, rho, omega, divv, curlv, nullptr, active, n_active, acc, dudt, vsig,
                       nullptr, hash, params, stream);
+}
+
+sph_status sph_hydro_force_visc(sph_ctx* ctx, const sph_grid* grid, const float* vel, const float* u, const float* h,
+                                const float* rho, const float* omega, const float* alpha_v, const float* divv,
+                                const float* curlv, const int32_t* active, int64_t n_active, float* acc, float* dudt,
+                                float* vsig, uint64_t* hash, const sph_params* params, void* stream) {
+    if (!ctx) return SPH_ERR_INVALID;
+    if (!alpha_v) return fail(ctx, SPH_ERR_INVALID, "alpha_v is required");
+    if ((divv == nullptr) != (curlv == nullptr)) return fail(ctx, SPH_ERR_INVALID, "give both divv and curlv, or neither");
+    if (params && pick_path(params->flags & ~SPH_DENSITY_BUFFERED) != Path::Wpp)
+        return fail(ctx, SPH_ERR_INVALID, "per-particle viscosity runs on the default path only");
+    return force_call(ctx, grid, vel, u, h, rho, omega, divv, curlv, nullptr, active, n_active, acc, dudt, vsig,
+                      nullptr, hash, params, stream, alpha_v);
 }
 
 sph_status sph_hydro_force_conduction(sph_ctx* ctx, const sph_grid* grid, const float* vel, const float* u,

@@ -52,6 +52,7 @@ struct sph_grid {
     float4* fvm = nullptr;                 // per force call, sorted: v, m
     float* fbal = nullptr;                 // per force call with the switch, sorted: Balsara factor
     float2* fcond = nullptr;               // per force call with conduction, sorted: u, kappa
+    float2* fvisc = nullptr;               // per force call with per-particle viscosity, sorted: factor, alpha
     // per-call scratch, sized at build so that calls never allocate
     int32_t* act = nullptr;                // active particles, sorted indices, sorted order
     uint8_t* flag = nullptr;               // n
@@ -175,6 +176,8 @@ struct ForceLaunch {
     // thermal conduction (default path only; NULL: none): conductivity in, heating rate out
     const float* kappa = nullptr;
     float* dudt_cond = nullptr;
+    // per-particle viscosity parameter (default path only; NULL: alpha for every pair)
+    const float* alpha_v = nullptr;
 };
 cudaError_t launch_force(sph_ctx* ctx, const ForceLaunch& a, cudaStream_t s);
 cudaError_t launch_force_plain(sph_ctx* ctx, const ForceLaunch& a, int64_t n_active,
@@ -207,11 +210,12 @@ cudaError_t launch_force_wpp(sph_ctx* ctx, const ForceLaunch& a, int64_t n_activ
 // tpp.cu (per-thread walks)
 // list_h / h_changed (optional): set *h_changed if some h differs from list_h;
 // divv / curlv (optional, caller order): Balsara factors into g->fbal;
-// kappa (optional, caller order): (u, kappa) into g->fcond
+// kappa (optional, caller order): (u, kappa) into g->fcond;
+// alpha_v (optional, caller order): (Balsara factor or 1, alpha) into g->fvisc
 void force_pack(const sph_grid* g, const float* vel, const float* u, const float* h, const float* rho,
                 const float* omega, float gamma, cudaStream_t s, const float* list_h = nullptr,
                 unsigned* h_changed = nullptr, const float* divv = nullptr, const float* curlv = nullptr,
-                const float* kappa = nullptr);
+                const float* kappa = nullptr, const float* alpha_v = nullptr);
 cudaError_t launch_density_tpp(sph_ctx* ctx, const DensityLaunch& a, int64_t n_active, cudaStream_t s);
 cudaError_t launch_force_tpp(sph_ctx* ctx, const ForceLaunch& a, int64_t n_active, cudaStream_t s);
 

@@ -11,6 +11,9 @@
 //   k_drift         x += v dt for every particle (FP64 positions, periodic), and
 //                   the predictions v_pred += a dt, u_pred += du/dt dt that the
 //                   next force evaluations use
+//   k_visc_rate     d alpha/dt of the time-dependent viscosity (Morris & Monaghan)
+//   k_kick_scalar,  the same kick and prediction for one more per-particle
+//   k_predict_scalar  quantity (the viscosity parameter)
 // The integer timeline counts steps of the smallest bin, dt_max / 2^max_bin;
 // a particle in bin b has step dt_max / 2^b and ends a step at every tick that
 // is a multiple of 2^(max_bin - b).
@@ -98,6 +101,37 @@ __global__ void k_drift(int n, double* __restrict__ pos, const float* __restrict
     }
 }
 
+// d alpha/dt = -(alpha - alpha_min) ell c / h + max(-div v, 0) (alpha_max - alpha),
+// c = sqrt(gamma (gamma - 1) u): decay to alpha_min over tau = h / (ell c),
+// growth towards alpha_max where the flow converges (Morris & Monaghan 1997).
+__global__ void k_visc_rate(int na, const int32_t* __restrict__ active, const float* __restrict__ h,
+                            const float* __restrict__ u, const float* __restrict__ divv,
+                            const float* __restrict__ alpha, float gg1, float amin, float amax, float ell,
+                            float* __restrict__ dalpha) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= na) return;
+    const int i = active ? active[t] : t;
+    const float c = sqrtf(gg1 * u[i]);
+    const float a = alpha[i];
+    dalpha[i] = fmaxf(-divv[i], 0.f) * (amax - a) - (a - amin) * (ell * c / h[i]);
+}
+
+__global__ void k_kick_scalar(int na, const int32_t* __restrict__ active, const uint8_t* __restrict__ bins,
+                              KickSteps ks, int n_bins, const float* __restrict__ rate, float* __restrict__ value,
+                              float* __restrict__ value_pred) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= na) return;
+    const int i = active[t];
+    const float v = fmaf(rate[i], ks.dt[min((int)bins[i], n_bins - 1)], value[i]);
+    value[i] = v;
+    if (value_pred) value_pred[i] = v;
+}
+
+__global__ void k_predict_scalar(int n, float dt, const float* __restrict__ rate, float* __restrict__ value_pred) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) value_pred[i] = fmaf(rate[i], dt, value_pred[i]);
+}
+
 }  // namespace sph
 
 using namespace sph;
@@ -176,4 +210,52 @@ sph_status sph_drift(sph_ctx* ctx, double* pos, const float* vel, int64_t n, dou
     k_drift<<<(m + 255) / 256, 256, 0, s>>>((int)n, pos, vel, dt, box, acc, dudt, vel_pred, u_pred);
     ++ctx->launches;
     return cudaGetLastError() ? kdk_fail(ctx, SPH_ERR_CUDA, "sph_drift launch failed") : SPH_OK;
+}
+
+sph_status sph_visc_rate(sph_ctx* ctx, const int32_t* active, int64_t n_active, const float* h, const float* u,
+                         const float* divv, const float* alpha_v, double gamma, double alpha_min, double alpha_max,
+                         double ell, float* dalpha, void* stream) {
+    if (!ctx) return SPH_ERR_INVALID;
+    if (!h || !u || !divv || !alpha_v || !dalpha || n_active < 0 || n_active >= (int64_t(1) << 31))
+        return kdk_fail(ctx, SPH_ERR_INVALID, "sph_visc_rate: bad pointers or n_active");
+    if (!(gamma > 1.0) || !(ell > 0.0) || !(alpha_min >= 0.0) || !(alpha_max >= alpha_min))
+        return kdk_fail(ctx, SPH_ERR_INVALID, "sph_visc_rate: gamma > 1, ell > 0, 0 <= alpha_min <= alpha_max");
+    if (cudaSetDevice(ctx->device)) return kdk_fail(ctx, SPH_ERR_CUDA, "cudaSetDevice failed");
+    if (n_active == 0) return SPH_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    k_visc_rate<<<(int)((n_active + 255) / 256), 256, 0, s>>>((int)n_active, active, h, u, divv, alpha_v,
+                                                              (float)(gamma * (gamma - 1.0)), (float)alpha_min,
+                                                              (float)alpha_max, (float)ell, dalpha);
+    ++ctx->launches;
+    return cudaGetLastError() ? kdk_fail(ctx, SPH_ERR_CUDA, "sph_visc_rate launch failed") : SPH_OK;
+}
+
+sph_status sph_kick_scalar(sph_ctx* ctx, const int32_t* active, int64_t n_active, const uint8_t* bins,
+                           const double* dt_bin, int n_bins, const float* rate, float* value, float* value_pred,
+                           void* stream) {
+    if (!ctx) return SPH_ERR_INVALID;
+    if (!active || !bins || !dt_bin || !rate || !value || n_bins < 1 || n_bins > 32 || n_active < 0 ||
+        n_active >= (int64_t(1) << 31))
+        return kdk_fail(ctx, SPH_ERR_INVALID, "sph_kick_scalar: bad pointers or sizes (1 <= n_bins <= 32)");
+    if (cudaSetDevice(ctx->device)) return kdk_fail(ctx, SPH_ERR_CUDA, "cudaSetDevice failed");
+    if (n_active == 0) return SPH_OK;
+    KickSteps ks = {};
+    for (int b = 0; b < n_bins; ++b) ks.dt[b] = (float)dt_bin[b];
+    cudaStream_t s = (cudaStream_t)stream;
+    k_kick_scalar<<<(int)((n_active + 255) / 256), 256, 0, s>>>((int)n_active, active, bins, ks, n_bins, rate, value,
+                                                                value_pred);
+    ++ctx->launches;
+    return cudaGetLastError() ? kdk_fail(ctx, SPH_ERR_CUDA, "sph_kick_scalar launch failed") : SPH_OK;
+}
+
+sph_status sph_predict_scalar(sph_ctx* ctx, int64_t n, double dt, const float* rate, float* value_pred,
+                              void* stream) {
+    if (!ctx) return SPH_ERR_INVALID;
+    if (!rate || !value_pred || n < 1 || n >= (int64_t(1) << 31) || !std::isfinite(dt))
+        return kdk_fail(ctx, SPH_ERR_INVALID, "sph_predict_scalar: bad pointers, n or dt");
+    if (cudaSetDevice(ctx->device)) return kdk_fail(ctx, SPH_ERR_CUDA, "cudaSetDevice failed");
+    cudaStream_t s = (cudaStream_t)stream;
+    k_predict_scalar<<<(int)((n + 255) / 256), 256, 0, s>>>((int)n, (float)dt, rate, value_pred);
+    ++ctx->launches;
+    return cudaGetLastError() ? kdk_fail(ctx, SPH_ERR_CUDA, "sph_predict_scalar launch failed") : SPH_OK;
 }

@@ -523,7 +523,8 @@ __global__ void k_force_pack(int n, const int32_t* __restrict__ perm, const floa
                              float4* __restrict__ fvel, float4* __restrict__ fthermo, float4* __restrict__ fposh,
                              float4* __restrict__ fvm, const float* __restrict__ list_h, unsigned* h_changed,
                              const float* __restrict__ divv, const float* __restrict__ curlv,
-                             float* __restrict__ fbal, const float* __restrict__ kappa, float2* __restrict__ fcond) {
+                             float* __restrict__ fbal, const float* __restrict__ kappa, float2* __restrict__ fcond,
+                             const float* __restrict__ alpha_v, float2* __restrict__ fvisc) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
     const int o = perm[p];
@@ -536,10 +537,13 @@ __global__ void k_force_pack(int n, const int32_t* __restrict__ perm, const floa
     const float cs = sqrtf(gam * P / r);
     fthermo[p] = make_float4(r, omega[o] * P / (r * r), cs, 1.f / hh);
     // Balsara's limiter f = |div v| / (|div v| + |curl v| + 1e-4 c/h)
-    if (fbal) {
+    float fb = 1.f;
+    if (divv) {
         const float ad = fabsf(divv[o]);
-        fbal[p] = ad / (ad + curlv[o] + 1e-4f * cs / hh);
+        fb = ad / (ad + curlv[o] + 1e-4f * cs / hh);
     }
+    if (fbal) fbal[p] = fb;
+    if (fvisc) fvisc[p] = make_float2(fb, alpha_v[o]);
     if (fcond) fcond[p] = make_float2(u[o], kappa[o]);
     fposh[p] = make_float4(f.x, f.y, f.z, hh);
     // recorded neighbour lists are usable only if every h equals the one they were made with
@@ -922,11 +926,13 @@ cudaError_t launch_density_tpp(sph_ctx* ctx, const DensityLaunch& a, int64_t n_a
 
 void force_pack(const sph_grid* g, const float* vel, const float* u, const float* h, const float* rho,
                 const float* omega, float gamma, cudaStream_t s, const float* list_h, unsigned* h_changed,
-                const float* divv, const float* curlv, const float* kappa) {
+                const float* divv, const float* curlv, const float* kappa, const float* alpha_v) {
     const int n = (int)g->n;
     k_force_pack<<<(n + 255) / 256, 256, 0, s>>>(n, g->perm, vel, u, h, rho, omega, gamma, g->posf, g->fvel, g->fthermo,
                                                  g->fposh, g->fvm, list_h, h_changed, divv, curlv,
-                                                 divv ? g->fbal : nullptr, kappa, kappa ? g->fcond : nullptr);
+                                                 divv && !alpha_v ? g->fbal : nullptr, kappa,
+                                                 kappa ? g->fcond : nullptr, alpha_v,
+                                                 alpha_v ? g->fvisc : nullptr);
 }
 
 cudaError_t launch_force_tpp(sph_ctx* ctx, const ForceLaunch& a, int64_t n_active, cudaStream_t s) {

@@ -115,8 +115,10 @@ struct WppArgs {
     const float4* vpack;         // sorted (v, m)
     float* divv;
     float* curlv;
-    // force: Balsara factors (sorted order; NULL: no switch)
+    // force: Balsara factors (sorted order; NULL: no switch), or (factor,
+    // viscosity parameter) pairs for per-particle viscosity
     const float* fbal;
+    const float2* fvisc;
     // force: conduction (sorted (u, kappa); NULL: no conduction) and its output (caller order)
     const float2* fcond;
     float* dudt_cond;
@@ -517,17 +519,23 @@ struct WppForceI {
     float hinv, rho, A, c, norm;   // norm = 8/(pi h^4)
     float f;                       // Balsara factor (1 without the switch)
     float u, kap;                  // conduction: u and conductivity (unused without it)
+    float al;                      // own viscosity parameter (VISC = 2 only)
 };
+
+// Viscosity variants of the force pair term: kViscScalar, one alpha for every
+// pair; kViscBalsara, alpha (f_i + f_j)/2; kViscPerParticle, per-particle
+// alpha, (alpha_i + alpha_j)/2 (f_i + f_j)/2, f = 1 without the switch.
+constexpr int kViscScalar = 0, kViscBalsara = 1, kViscPerParticle = 2;
 
 // One force pair term, Gadget-2 grad-h form with signal-velocity viscosity,
 // added to i's per-lane sums. (dx, dy, dz) = x_j - x_i; vj = (v_j, m_j);
-// thj = (rho_j, A_j, c_j, 1/h_j); fj = j's Balsara factor (1 without the
-// switch: BAL = false leaves Pi_ij alone; BAL = true multiplies it by (f_i + f_j)/2).
+// thj = (rho_j, A_j, c_j, 1/h_j); bj = (f_j, alpha_j): j's Balsara factor
+// (VISC >= 1) and viscosity parameter (VISC = 2), see kViscScalar.
 // COND adds the conduction term m_j/(rho_i rho_j) 4 k_i k_j/(k_i + k_j)
 // (u_i - u_j) Fbar_ij to Sc, with cj = (u_j, kappa_j).
-template <bool BAL, bool COND>
+template <int VISC, bool COND>
 __device__ __forceinline__ void wpp_force_pair(const WppForceI& I, float dx, float dy, float dz, float4 vj, float4 thj,
-                                               float fj, float2 cj, float alpha, float& Sx, float& Sy, float& Sz,
+                                               float2 bj, float2 cj, float alpha, float& Sx, float& Sy, float& Sz,
                                                float& Su, float& Sc, float& vsmax) {
     const float kNorm = (float)(8.0 / 3.141592653589793);
     const float r2 = dx * dx + dy * dy + dz * dz;
@@ -547,8 +555,9 @@ __device__ __forceinline__ void wpp_force_pair(const WppForceI& I, float dx, flo
     const float vs = I.c + thj.z - 3.f * wij;
     vsmax = fmaxf(vsmax, vs);
     // Pi_ij = -(alpha/2) v_sig w_ij / rho_bar, rho_bar = (rho_i + rho_j)/2
-    float PI = wij < 0.f ? __fdividef(-alpha * vs * wij, I.rho + thj.x) : 0.f;
-    if (BAL) PI *= 0.5f * (I.f + fj);
+    const float aij = VISC == kViscPerParticle ? 0.5f * (I.al + bj.y) : alpha;
+    float PI = wij < 0.f ? __fdividef(-aij * vs * wij, I.rho + thj.x) : 0.f;
+    if (VISC != kViscScalar) PI *= 0.5f * (I.f + bj.x);
     const float Fbar = 0.5f * (Fi + Fj);
     const float mj = vj.w;
     if (COND) {

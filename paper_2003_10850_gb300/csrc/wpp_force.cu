@@ -8,7 +8,18 @@ namespace sph {
 // Force
 // ---------------------------------------------------------------------------
 
-template <bool HASH, int MINB, bool BAL, bool COND>
+// Particle i's Balsara factor and viscosity parameter, and the pair partner's.
+template <int VISC>
+__device__ __forceinline__ float2 wpp_visc_i(const WppArgs& a, int p) {
+    return VISC == kViscPerParticle ? a.fvisc[p] : make_float2(VISC == kViscBalsara ? a.fbal[p] : 1.f, 0.f);
+}
+template <int VISC>
+__device__ __forceinline__ float2 wpp_visc_j(const WppArgs& a, int q) {
+    return VISC == kViscPerParticle ? __ldg(a.fvisc + q)
+                                    : make_float2(VISC == kViscBalsara ? __ldg(a.fbal + q) : 1.f, 0.f);
+}
+
+template <bool HASH, int MINB, int VISC, bool COND>
 __global__ void __launch_bounds__(kWppThreads, MINB) k_force_wpp(WppArgs a) {
     __shared__ WppSmem smem[kWppWarps];
     WppSmem& sm = smem[threadIdx.x >> 5];
@@ -62,8 +73,9 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_force_wpp(WppArgs a) {
                 const float4 vi = a.fvm[p];
                 const float4 thi = a.fthermo[p];
                 const float2 ci = COND ? a.fcond[p] : make_float2(0.f, 0.f);
+                const float2 bi = wpp_visc_i<VISC>(a, p);
                 const WppForceI I = {vi.x, vi.y, vi.z, thi.w, thi.x, thi.y, thi.z,
-                                     kNorm * thi.w * thi.w * thi.w * thi.w, BAL ? a.fbal[p] : 1.f, ci.x, ci.y};
+                                     kNorm * thi.w * thi.w * thi.w * thi.w, bi.x, ci.x, ci.y, bi.y};
                 // i side of the band test: h_i (1 +- 2^-19) (the leaf's rounding bound is added per leaf)
                 const float hiP = hi * (1.f + 2.f * rel), hiM = hi * (1.f - 2.f * rel);
                 double HHi = -1.0;
@@ -78,8 +90,8 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_force_wpp(WppArgs a) {
                     if ((int)lane < k) {
                         const float4 e = sm.hit.f[lane];
                         const int q = __float_as_int(e.w);
-                        wpp_force_pair<BAL, COND>(I, e.x, e.y, e.z, __ldg(a.fvm + q), __ldg(a.fthermo + q),
-                                                  BAL ? __ldg(a.fbal + q) : 1.f,
+                        wpp_force_pair<VISC, COND>(I, e.x, e.y, e.z, __ldg(a.fvm + q), __ldg(a.fthermo + q),
+                                                   wpp_visc_j<VISC>(a, q),
                                                   COND ? __ldg(a.fcond + q) : make_float2(0.f, 0.f), alpha, Sx, Sy,
                                                   Sz, Su, Sc, vsmax);
                     }
@@ -188,7 +200,7 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_force_wpp(WppArgs a) {
 // fold as k_force_wpp. If the lists cannot serve the call at all the kernel
 // does nothing and the walk that follows takes the whole active set;
 // particles whose own lists did not fit go to fb_list for that walk.
-template <bool HASH, bool BAL, bool COND>
+template <bool HASH, int VISC, bool COND>
 __global__ void __launch_bounds__(128) k_force_list(WppArgs a) {
     if (!wpp_lists_valid(a.list_st, a.n_total)) return;
     const unsigned lane = lane_id();
@@ -211,8 +223,9 @@ __global__ void __launch_bounds__(128) k_force_list(WppArgs a) {
         const float4 vi = a.fvm[p];
         const float4 thi = a.fthermo[p];
         const float2 ci = COND ? a.fcond[p] : make_float2(0.f, 0.f);
+        const float2 bi = wpp_visc_i<VISC>(a, p);
         const WppForceI I = {vi.x, vi.y, vi.z, thi.w, thi.x, thi.y, thi.z, kNorm * thi.w * thi.w * thi.w * thi.w,
-                             BAL ? a.fbal[p] : 1.f, ci.x, ci.y};
+                             bi.x, ci.x, ci.y, bi.y};
         float Sx = 0.f, Sy = 0.f, Sz = 0.f, Su = 0.f, Sc = 0.f, vsmax = 0.f;
         unsigned long long hs = 0;
         const int tot = cn + (int)(e1 - e0);
@@ -228,15 +241,15 @@ __global__ void __launch_bounds__(128) k_force_list(WppArgs a) {
             const uint4 X0 = a.posm[q0], X1 = a.posm[q1];
             const float4 v0 = __ldg(a.fvm + q0), v1 = __ldg(a.fvm + q1);
             const float4 t0 = __ldg(a.fthermo + q0), t1 = __ldg(a.fthermo + q1);
-            const float b0 = BAL ? __ldg(a.fbal + q0) : 1.f, b1 = BAL ? __ldg(a.fbal + q1) : 1.f;
+            const float2 b0 = wpp_visc_j<VISC>(a, q0), b1 = wpp_visc_j<VISC>(a, q1);
             const float2 c0 = COND ? __ldg(a.fcond + q0) : make_float2(0.f, 0.f);
             const float2 c1 = COND ? __ldg(a.fcond + q1) : make_float2(0.f, 0.f);
-            wpp_force_pair<BAL, COND>(I, (float)(int)(X0.x - Xi.x) * sf, (float)(int)(X0.y - Xi.y) * sf,
+            wpp_force_pair<VISC, COND>(I, (float)(int)(X0.x - Xi.x) * sf, (float)(int)(X0.y - Xi.y) * sf,
                                       (float)(int)(X0.z - Xi.z) * sf, v0, t0, b0, c0, a.alpha, Sx, Sy, Sz, Su, Sc,
                                       vsmax);
             if (HASH) hs += splitmix64((unsigned long long)a.perm[q0]);
             if (two) {
-                wpp_force_pair<BAL, COND>(I, (float)(int)(X1.x - Xi.x) * sf, (float)(int)(X1.y - Xi.y) * sf,
+                wpp_force_pair<VISC, COND>(I, (float)(int)(X1.x - Xi.x) * sf, (float)(int)(X1.y - Xi.y) * sf,
                                           (float)(int)(X1.z - Xi.z) * sf, v1, t1, b1, c1, a.alpha, Sx, Sy, Sz, Su, Sc,
                                           vsmax);
                 if (HASH) hs += splitmix64((unsigned long long)a.perm[q1]);
@@ -265,37 +278,39 @@ __global__ void __launch_bounds__(128) k_force_list(WppArgs a) {
 }
 
 
-// Kernel variants of the force pass: hash output, register budget, Balsara's
-// switch, conduction.
-template <bool H, bool BAL, bool COND>
+// Kernel variants of the force pass: hash output, register budget,
+// viscosity (kViscScalar ...), conduction. Per-particle viscosity comes
+// without conduction (no entry point asks for both).
+template <bool H, int V, bool C>
 static void launch_fl(int blocks, cudaStream_t s, const WppArgs& c) {
-    k_force_list<H, BAL, COND><<<blocks, 128, 0, s>>>(c);
+    k_force_list<H, V, C><<<blocks, 128, 0, s>>>(c);
 }
-static void launch_force_list(bool hash, bool bal, bool cond, int blocks, cudaStream_t s, const WppArgs& c) {
-    if (hash) {
-        if (bal) cond ? launch_fl<true, true, true>(blocks, s, c) : launch_fl<true, true, false>(blocks, s, c);
-        else cond ? launch_fl<true, false, true>(blocks, s, c) : launch_fl<true, false, false>(blocks, s, c);
-    } else {
-        if (bal) cond ? launch_fl<false, true, true>(blocks, s, c) : launch_fl<false, true, false>(blocks, s, c);
-        else cond ? launch_fl<false, false, true>(blocks, s, c) : launch_fl<false, false, false>(blocks, s, c);
-    }
+template <bool H>
+static void launch_fl_v(int visc, bool cond, int blocks, cudaStream_t s, const WppArgs& c) {
+    if (visc == kViscPerParticle) launch_fl<H, kViscPerParticle, false>(blocks, s, c);
+    else if (visc == kViscBalsara) cond ? launch_fl<H, kViscBalsara, true>(blocks, s, c)
+                                        : launch_fl<H, kViscBalsara, false>(blocks, s, c);
+    else cond ? launch_fl<H, kViscScalar, true>(blocks, s, c) : launch_fl<H, kViscScalar, false>(blocks, s, c);
+}
+static void launch_force_list(bool hash, int visc, bool cond, int blocks, cudaStream_t s, const WppArgs& c) {
+    hash ? launch_fl_v<true>(visc, cond, blocks, s, c) : launch_fl_v<false>(visc, cond, blocks, s, c);
 }
 template <bool H, int M>
-static void launch_fw(bool bal, bool cond, int blocks, cudaStream_t s, const WppArgs& c) {
-    if (bal) {
-        if (cond) k_force_wpp<H, M, true, true><<<blocks, kWppThreads, 0, s>>>(c);
-        else k_force_wpp<H, M, true, false><<<blocks, kWppThreads, 0, s>>>(c);
+static void launch_fw(int visc, bool cond, int blocks, cudaStream_t s, const WppArgs& c) {
+    if (visc == kViscPerParticle) k_force_wpp<H, M, kViscPerParticle, false><<<blocks, kWppThreads, 0, s>>>(c);
+    else if (visc == kViscBalsara) {
+        if (cond) k_force_wpp<H, M, kViscBalsara, true><<<blocks, kWppThreads, 0, s>>>(c);
+        else k_force_wpp<H, M, kViscBalsara, false><<<blocks, kWppThreads, 0, s>>>(c);
     } else {
-        if (cond) k_force_wpp<H, M, false, true><<<blocks, kWppThreads, 0, s>>>(c);
-        else k_force_wpp<H, M, false, false><<<blocks, kWppThreads, 0, s>>>(c);
+        if (cond) k_force_wpp<H, M, kViscScalar, true><<<blocks, kWppThreads, 0, s>>>(c);
+        else k_force_wpp<H, M, kViscScalar, false><<<blocks, kWppThreads, 0, s>>>(c);
     }
 }
-static void launch_force_walk(bool hash, bool six, bool bal, bool cond, int blocks, cudaStream_t s,
+static void launch_force_walk(bool hash, bool six, int visc, bool cond, int blocks, cudaStream_t s,
                               const WppArgs& c) {
-    if (six) hash ? launch_fw<true, 6>(bal, cond, blocks, s, c) : launch_fw<false, 6>(bal, cond, blocks, s, c);
-    else hash ? launch_fw<true, 8>(bal, cond, blocks, s, c) : launch_fw<false, 8>(bal, cond, blocks, s, c);
+    if (six) hash ? launch_fw<true, 6>(visc, cond, blocks, s, c) : launch_fw<false, 6>(visc, cond, blocks, s, c);
+    else hash ? launch_fw<true, 8>(visc, cond, blocks, s, c) : launch_fw<false, 8>(visc, cond, blocks, s, c);
 }
-
 
 cudaError_t launch_force_wpp(sph_ctx* ctx, const ForceLaunch& a, int64_t n_active, cudaStream_t s) {
     sph_grid* g = const_cast<sph_grid*>(a.g);
@@ -303,7 +318,7 @@ cudaError_t launch_force_wpp(sph_ctx* ctx, const ForceLaunch& a, int64_t n_activ
     const bool lists = g->nbr != nullptr && g->lists_full;
     if (lists && (e = cudaMemsetAsync(g->list_st + 2, 0, 2 * sizeof(unsigned), s))) return e;
     force_pack(g, a.vel, a.u, a.h, a.rho, a.omega, (float)a.gamma, s, lists ? g->list_h : nullptr,
-               lists ? g->list_st + 2 : nullptr, a.divv, a.curlv, a.kappa);
+               lists ? g->list_st + 2 : nullptr, a.divv, a.curlv, a.kappa, a.alpha_v);
     ++ctx->launches;
     if ((e = cudaMemsetAsync(ctx->queue + 3, 0, sizeof(unsigned), s))) return e;
     WppArgs c = wpp_common(ctx, g, ctx->queue + 3);
@@ -319,7 +334,9 @@ cudaError_t launch_force_wpp(sph_ctx* ctx, const ForceLaunch& a, int64_t n_activ
     c.vsig = a.vsig;
     c.alpha = (float)a.alpha;
     c.hash = a.hash;
-    c.fbal = a.divv ? g->fbal : nullptr;
+    const int visc = a.alpha_v ? kViscPerParticle : a.divv ? kViscBalsara : kViscScalar;
+    c.fbal = visc == kViscBalsara ? g->fbal : nullptr;
+    c.fvisc = visc == kViscPerParticle ? g->fvisc : nullptr;
     c.fcond = a.kappa ? g->fcond : nullptr;
     c.dudt_cond = a.dudt_cond;
     WppSpan sp;
@@ -339,12 +356,12 @@ cudaError_t launch_force_wpp(sph_ctx* ctx, const ForceLaunch& a, int64_t n_activ
         c.fb_list = g->fb_list;
         const int lb = (int)std::max<long long>(
             1, std::min<long long>((long long)ctx->sm_count * 16, (n_active + 3) / 4));
-        launch_force_list(a.hash != nullptr, c.fbal != nullptr, c.fcond != nullptr, lb, s, c);
+        launch_force_list(a.hash != nullptr, visc, c.fcond != nullptr, lb, s, c);
         ++ctx->launches;
         c.fb_act = g->fb_list;
         c.fb_count = g->list_st + 3;
     }
-    launch_force_walk(a.hash != nullptr, bps <= 6, c.fbal != nullptr, c.fcond != nullptr, blocks, s, c);
+    launch_force_walk(a.hash != nullptr, bps <= 6, visc, c.fcond != nullptr, blocks, s, c);
     ++ctx->launches;
     if ((e = span_end(ctx, sp, s))) return e;
     return cudaGetLastError();

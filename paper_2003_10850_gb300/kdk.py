@@ -16,13 +16,20 @@ Inactive particles keep the h, rho, Omega, a, du/dt of their last active
 step; their velocities and energies are predicted to the current time with
 those. The one value read back per tick is the active count, which the next
 calls take as their n_active.
+
+Options: balsara=True limits the viscosity with Balsara's switch (div v and
+curl v from sph_density_divcurl); visc=dict(alpha0, alpha_min, alpha_max,
+ell) gives each particle its own viscosity parameter (sph_hydro_force_visc),
+whose rate (sph_visc_rate, Morris & Monaghan) is kicked and predicted like
+du/dt (sph_kick_scalar, sph_predict_scalar).
 """
 from __future__ import annotations
 
 import torch
 
-from . import (default_params, sph_active_from_bins, sph_build_grid, sph_density, sph_drift, sph_grid_update,
-               sph_hydro_force, sph_kick, sph_sync_status, sph_timebins)
+from . import (default_params, sph_active_from_bins, sph_build_grid, sph_density, sph_density_divcurl, sph_drift,
+               sph_grid_update, sph_hydro_force, sph_hydro_force_balsara, sph_hydro_force_visc, sph_kick,
+               sph_kick_scalar, sph_predict_scalar, sph_sync_status, sph_timebins, sph_visc_rate)
 
 
 class KDK:
@@ -35,7 +42,8 @@ class KDK:
     max_bin, above its Courant limit: choose dt_max and max_bin so that the
     finest bin holds the smallest step."""
 
-    def __init__(self, ctx, pos, mass, vel, u, dt_max, max_bin, params=None, courant=0.3, bins=None):
+    def __init__(self, ctx, pos, mass, vel, u, dt_max, max_bin, params=None, courant=0.3, bins=None, balsara=False,
+                 visc=None):
         self.ctx = ctx
         self.params = params or default_params()
         self.box = float(self.params.box)
@@ -55,6 +63,13 @@ class KDK:
         self.h, self.rho, self.omega, self.dudt, self.vsig = f(), f(), f(), f(), f()
         self.acc = torch.zeros(n, 3, device=dev)
         self.n_ngb = torch.zeros(n, dtype=torch.int32, device=dev)
+        self.balsara, self.visc = bool(balsara), visc
+        if self.balsara or visc is not None:
+            self.divv, self.curlv = f(), f()
+        if visc is not None:
+            self.alpha = torch.full((n,), float(visc["alpha0"]), device=dev)
+            self.alpha_pred = self.alpha.clone()
+            self.dalpha = f()
         self.flags = torch.zeros(n, dtype=torch.uint8, device=dev)
         self.active = torch.zeros(n, dtype=torch.int32, device=dev)
         self.count = torch.zeros(1, dtype=torch.int32, device=dev)
@@ -74,22 +89,42 @@ class KDK:
         return [factor * self.dt_max / 2.0 ** b for b in range(self.max_bin + 1)]
 
     def _forces(self, act):
-        sph_density(self.ctx, self.grid, self.h, act, self.rho, self.omega, self.n_ngb, self.flags, None,
-                    self.params)
-        sph_hydro_force(self.ctx, self.grid, self.vel_pred, self.u_pred, self.h, self.rho, self.omega, act, self.acc,
-                        self.dudt, self.vsig, None, self.params)
+        ctx, g = self.ctx, self.grid
+        if self.balsara or self.visc is not None:
+            sph_density_divcurl(ctx, g, self.h, act, self.rho, self.omega, self.n_ngb, self.flags, None,
+                                self.vel_pred, self.divv, self.curlv, self.params)
+        else:
+            sph_density(ctx, g, self.h, act, self.rho, self.omega, self.n_ngb, self.flags, None, self.params)
+        if self.visc is not None:
+            sw = (self.divv, self.curlv) if self.balsara else (None, None)
+            sph_hydro_force_visc(ctx, g, self.vel_pred, self.u_pred, self.h, self.rho, self.omega, self.alpha_pred,
+                                 *sw, act, self.acc, self.dudt, self.vsig, None, self.params)
+            v = self.visc
+            sph_visc_rate(ctx, act, self.h, self.u_pred, self.divv, self.alpha_pred, self.dalpha, self.params.gamma,
+                          v["alpha_min"], v["alpha_max"], v["ell"])
+        elif self.balsara:
+            sph_hydro_force_balsara(ctx, g, self.vel_pred, self.u_pred, self.h, self.rho, self.omega, self.divv,
+                                    self.curlv, act, self.acc, self.dudt, self.vsig, None, self.params)
+        else:
+            sph_hydro_force(ctx, g, self.vel_pred, self.u_pred, self.h, self.rho, self.omega, act, self.acc,
+                            self.dudt, self.vsig, None, self.params)
         _, st = sph_sync_status(self.ctx)
         self.pairs += st["density_pairs"] + st["force_pairs"]
 
     def _kick(self, act, factor, sync=False):
         sph_kick(self.ctx, act, act.numel(), self.bins, self.dt_bins(factor), self.acc, self.dudt, self.vel, self.u,
                  self.vel_pred if sync else None, self.u_pred if sync else None)
+        if self.visc is not None:
+            sph_kick_scalar(self.ctx, act, act.numel(), self.bins, self.dt_bins(factor), self.dalpha, self.alpha,
+                            self.alpha_pred if sync else None)
 
     def step(self):
         """Advance one tick (dt_max / 2^max_bin). Returns the active count."""
         ctx = self.ctx
-        sph_drift(ctx, self.pos, self.vel, self.dt_max / 2.0 ** self.max_bin, self.box, self.acc, self.dudt,
-                  self.vel_pred, self.u_pred)
+        dt = self.dt_max / 2.0 ** self.max_bin
+        sph_drift(ctx, self.pos, self.vel, dt, self.box, self.acc, self.dudt, self.vel_pred, self.u_pred)
+        if self.visc is not None:
+            sph_predict_scalar(ctx, dt, self.dalpha, self.alpha_pred)
         self.tick += 1
         sph_grid_update(ctx, self.grid, self.pos, self.mass)
         sph_active_from_bins(ctx, self.grid, self.bins, self.tick, self.max_bin, self.active, self.count)
@@ -112,3 +147,10 @@ class KDK:
         everyone = torch.arange(self.n, dtype=torch.int32, device=self.vel.device)
         sph_kick(self.ctx, everyone, self.n, self.bins, self.dt_bins(-0.5), self.acc, self.dudt, v, u)
         return v, u
+
+    def synchronized_alpha(self):
+        """Viscosity parameters at the current time (as synchronized_velocity)."""
+        a = self.alpha.clone()
+        everyone = torch.arange(self.n, dtype=torch.int32, device=a.device)
+        sph_kick_scalar(self.ctx, everyone, self.n, self.bins, self.dt_bins(-0.5), self.dalpha, a)
+        return a
