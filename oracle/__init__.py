@@ -1,4 +1,5 @@
-"""FP64 CPU oracle for the SPH density and hydro-force passes.
+"""FP64 CPU oracle for the SPH density and hydro-force passes and the
+short-range gravity pass.
 
 TEST INFRASTRUCTURE ONLY. Only ``tests/``, ``__graft_entry__.smoke()`` and the
 CPU-baseline leg of ``bench.py`` may import this package. It shares no code
@@ -62,6 +63,9 @@ def lib():
         L.orc_neighbours.argtypes = [i32, P, P, i64, f64, i64, f64, i32, P, i64]
         L.orc_neighbours.restype = i64
         L.orc_num_threads.restype = i32
+        L.orc_gravity.argtypes = [P, i64, f64, P, f64, f64, f64, f64, f64, P, i64, P, P, P, P]
+        L.orc_soft_mass.argtypes = [f64]
+        L.orc_soft_mass.restype = f64
         L.orc_pair_list.argtypes = [i32, P, P, i64, f64, P, i32, P, P, i64]
         L.orc_pair_list.restype = i64
         _lib = L
@@ -220,6 +224,28 @@ def visc_rate(h, u, divv, alpha, alpha_min=0.1, alpha_max=1.0, ell=0.2, gamma=5.
     tau = h / (ell * c)
     source = np.maximum(-divv, 0.0) * (alpha_max - alpha)
     return -(alpha - alpha_min) / tau + source
+
+
+def gravity(X, mass, box=1.0, G=1.0, theta=0.5, r_split=0.0, r_cut=0.25, h_soft=0.0, active=None):
+    """Short-range gravity (TreePM split) by the Barnes-Hut walk of
+    orc_gravity. X: integer positions (N, 3). Returns acc (N, 3), scale (sum
+    of |term|), n_nodes, n_pairs; inactive entries NaN / -1."""
+    Xc = _c(X, np.uint32)
+    n = Xc.shape[0]
+    if not (0.0 < r_cut <= 0.25 * box) or not (0.0 <= theta <= 1.0):
+        raise ValueError("need 0 < r_cut <= box/4 and 0 <= theta <= 1")
+    act = None if active is None else _c(active, np.int64)
+    out = {"acc": np.full((n, 3), np.nan), "scale": np.full(n, np.nan),
+           "n_nodes": np.full(n, -1, np.int64), "n_pairs": np.full(n, -1, np.int64)}
+    lib().orc_gravity(_p(Xc), n, float(box), _p(_c(mass, np.float64)), float(G), float(theta), float(r_split),
+                      float(r_cut), float(h_soft), _p(act), 0 if act is None else act.size, _p(out["acc"]),
+                      _p(out["scale"]), _p(out["n_nodes"]), _p(out["n_pairs"]))
+    return out
+
+
+def soft_mass(q) -> float:
+    """Mass fraction of the cubic spline (support 1) inside radius q."""
+    return lib().orc_soft_mass(float(q))
 
 
 def neighbours(X=None, i=0, h=0.1, box=1.0, brute=True, xc=None) -> np.ndarray:

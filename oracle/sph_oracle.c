@@ -1,6 +1,6 @@
 /*
  * sph_oracle.c -- plain FP64 CPU oracle for the SPH density and hydro-force
- * passes. TEST INFRASTRUCTURE ONLY: it is loaded by tests/, by the
+ * passes and the short-range gravity pass. TEST INFRASTRUCTURE ONLY: it is loaded by tests/, by the
  * __graft_entry__ smoke check and by the CPU-baseline leg of bench.py, and by
  * nothing else. It shares no code, header or constant with the CUDA library.
  *
@@ -40,6 +40,8 @@
  *               du_i^cond = sum_j m_j/(rho_i rho_j) 4 kappa_i kappa_j/(kappa_i + kappa_j)
  *                           (u_i - u_j) Fbar_ij,  Fbar_ij = (F(h_i) + F(h_j))/2,
  *               F(h) = dW/dr(r_ij, h) / r_ij.
+ *   gravity     (separate pass) short-range TreePM gravity by a Barnes-Hut
+ *               walk over a tree fixed by definition; see orc_gravity.
  *
  * Everything is a direct sum in FP64 over an explicit candidate set: either
  * every particle (brute force) or the particles of the cells around i in a
@@ -779,4 +781,252 @@ int64_t orc_pair_list(int mode, const uint32_t *X, const double *xc, int64_t n, 
     orc_hindex_free(Hx);
     orc_index_free(I);
     return k;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Gravity: short-range part of the TreePM split by a Barnes-Hut walk        */
+/* ------------------------------------------------------------------------- */
+
+/*
+ * The paper's code computes short-range gravity by Barnes-Hut (particles
+ * interact with distant tree nodes as point masses, chosen by an opening
+ * criterion; the interactions happen inside the walk) and long-range gravity
+ * by a particle mesh (Sec. 1, Sec. 3). This is the short-range part, in the
+ * form of Gadget's TreePM split (Springel 2005), on a tree fixed by
+ * definition so that the approximation itself is reproducible:
+ *
+ *   tree     particles sorted by Morton key (ties by index); a leaf is 8
+ *            consecutive sorted particles, a level-k node is 8 consecutive
+ *            level-(k-1) nodes, up to a single root. A node's box is the
+ *            min/max of its particles' integer coordinates, its mass and
+ *            centre of mass the plain sums.
+ *   decisions in coarse integer units (integer coordinates >> 8, i.e.
+ *            2^-24 L): for particle i and a node, G_a = periodic gap between
+ *            X_i and the node's box on axis a, D2 = sum G_a^2, l = largest side,
+ *            L2 = l^2; F2 = sum of the squared far distances to the box,
+ *            F_a = (periodic distance from X_i to the far side of the box +
+ *            255) >> 8 (rounded up); RC2 = (r_cut 2^24 / L)^2 and
+ *            theta2 = theta^2 in FP64. The root is always opened. A child of
+ *            an opened node is
+ *              skipped   if D2 >= RC2 (the box lies beyond the cutoff),
+ *              accepted  (monopole) if theta2 > 0, D2 > 0, F2 < RC2 (the box
+ *                        lies inside the cutoff, so that every member would
+ *                        interact) and theta2 * D2 >= L2 (opening angle),
+ *              opened    otherwise (a leaf: its particles one by one).
+ *            A particle j != i of an opened leaf interacts if its coarse
+ *            distance, sum_a (|(int32)(X_j - X_i)| >> 8)^2, is below RC2.
+ *   pair     a_i += G m_j K(r) (x_j - x_i), minimum image, with
+ *            K(r) = M(r/h_s) / r^3 * g(r): M the mass fraction of the cubic
+ *            spline of support h_s inside r (1 for r >= h_s; Gadget's
+ *            softening), g(r) = erfc(r / (2 r_s)) + r / (r_s sqrt(pi))
+ *            exp(-r^2 / (4 r_s^2)) the short-range factor (1 without a
+ *            split, r_s <= 0). A node acts as its mass at its centre of mass.
+ *            Coincident pairs (r = 0) exert nothing.
+ */
+
+/* Fraction of a cubic-spline (support 1) mass inside radius q:
+ * 32 int_0^q w(s) s^2 ds, piece by piece. */
+double orc_soft_mass(double q)
+{
+    if (q >= 1.0) return 1.0;
+    double a = q < 0.5 ? q : 0.5;
+    double inner = a * a * a / 3.0 - 6.0 * pow(a, 5) / 5.0 + pow(a, 6);
+    if (q <= 0.5) return 32.0 * inner;
+#define ORC_F2(s) (2.0 * ((s) * (s) * (s) / 3.0 - 3.0 * pow((s), 4) / 4.0 + 3.0 * pow((s), 5) / 5.0 - pow((s), 6) / 6.0))
+    double outer = ORC_F2(q) - ORC_F2(0.5);
+#undef ORC_F2
+    return 32.0 * (inner + outer);
+}
+
+/* K(r): the acceleration per unit mass and unit separation vector. */
+static double orc_grav_K(double r, double hs, double rs)
+{
+    double Mq = hs > 0.0 ? orc_soft_mass(r / hs) : 1.0;
+    double g = 1.0;
+    if (rs > 0.0) g = erfc(r / (2.0 * rs)) + r / (rs * sqrt(ORC_PI)) * exp(-r * r / (4.0 * rs * rs));
+    return Mq / (r * r * r) * g;
+}
+
+typedef struct {
+    int nlev;
+    int64_t cnt[32], off[32];   /* nodes per level, first node of the level */
+    uint32_t *lo, *hi;          /* 3 per node */
+    double *mass, *com;         /* com: 3 per node, integer units */
+} orc_tree;
+
+static void orc_tree_build(const uint32_t *X, const double *m, const int64_t *sorted, int64_t n, orc_tree *T)
+{
+    int64_t c = (n + 7) / 8, total = 0;
+    T->nlev = 0;
+    for (;;) {
+        T->cnt[T->nlev] = c;
+        T->off[T->nlev] = total;
+        total += c;
+        T->nlev++;
+        if (c == 1) break;
+        c = (c + 7) / 8;
+    }
+    T->lo = (uint32_t *)malloc(sizeof(uint32_t) * 3 * total);
+    T->hi = (uint32_t *)malloc(sizeof(uint32_t) * 3 * total);
+    T->mass = (double *)malloc(sizeof(double) * total);
+    T->com = (double *)malloc(sizeof(double) * 3 * total);
+    for (int k = 0; k < T->nlev; ++k) {
+        for (int64_t t = 0; t < T->cnt[k]; ++t) {
+            int64_t nd = T->off[k] + t;
+            uint32_t lo[3] = {0xffffffffu, 0xffffffffu, 0xffffffffu}, hi[3] = {0, 0, 0};
+            double M = 0.0, S[3] = {0.0, 0.0, 0.0};
+            /* members: particles (leaf) or child nodes */
+            int64_t a = 8 * t, b = a + 8, lim = k == 0 ? n : T->cnt[k - 1];
+            if (b > lim) b = lim;
+            for (int64_t e = a; e < b; ++e) {
+                for (int d = 0; d < 3; ++d) {
+                    uint32_t l, h;
+                    if (k == 0) {
+                        l = h = X[3 * sorted[e] + d];
+                    } else {
+                        l = T->lo[3 * (T->off[k - 1] + e) + d];
+                        h = T->hi[3 * (T->off[k - 1] + e) + d];
+                    }
+                    if (l < lo[d]) lo[d] = l;
+                    if (h > hi[d]) hi[d] = h;
+                }
+                double me = k == 0 ? m[sorted[e]] : T->mass[T->off[k - 1] + e];
+                for (int d = 0; d < 3; ++d) {
+                    double xe = k == 0 ? (double)X[3 * sorted[e] + d] : T->com[3 * (T->off[k - 1] + e) + d];
+                    S[d] += me * xe;
+                }
+                M += me;
+            }
+            for (int d = 0; d < 3; ++d) {
+                T->lo[3 * nd + d] = lo[d];
+                T->hi[3 * nd + d] = hi[d];
+                T->com[3 * nd + d] = M > 0.0 ? S[d] / M : 0.5 * ((double)lo[d] + (double)hi[d]);
+            }
+            T->mass[nd] = M;
+        }
+    }
+}
+
+static void orc_tree_free(orc_tree *T)
+{
+    free(T->lo);
+    free(T->hi);
+    free(T->mass);
+    free(T->com);
+}
+
+/*
+ * Short-range gravity of the active particles (NULL = all) on all n
+ * (single periodic box of side L, r_cut <= L/4, theta <= 1). Outputs for
+ * active i: acc (n x 3), scale = sum of |term| (the per-particle absolute
+ * scale for tolerances), n_nodes / n_pairs = node and particle interactions.
+ */
+void orc_gravity(const uint32_t *X, int64_t n, double L, const double *m, double G, double theta,
+                 double r_split, double r_cut, double h_soft, const int64_t *active, int64_t n_active,
+                 double *acc, double *scale, int64_t *n_nodes, int64_t *n_pairs)
+{
+    uint64_t *key = (uint64_t *)malloc(sizeof(uint64_t) * n);
+    int64_t *sorted = (int64_t *)malloc(sizeof(int64_t) * n);
+    orc_keys(X, n, 0, 0, key);
+    orc_sort_keys(key, n, sorted);
+    free(key);
+    orc_tree T;
+    orc_tree_build(X, m, sorted, n, &T);
+    const double u = L / ORC_TWO32;           /* physical length of one integer unit */
+    const double rcu = r_cut / L * 16777216.0; /* r_cut in coarse units (2^-24 L) */
+    const double RC2 = rcu * rcu, theta2 = theta * theta;
+    int64_t na = active ? n_active : n;
+#pragma omp parallel
+    {
+        int64_t *stack = (int64_t *)malloc(sizeof(int64_t) * 4096);
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t a = 0; a < na; ++a) {
+            int64_t i = active ? active[a] : a;
+            const uint32_t *Xi = X + 3 * i;
+            double ax = 0.0, ay = 0.0, az = 0.0, sc = 0.0;
+            int64_t nn = 0, np = 0;
+            /* stack entries: level * 2^40 + node index within the level */
+            int sp = 0;
+            stack[sp++] = (int64_t)(T.nlev - 1) << 40;
+            while (sp > 0) {
+                int64_t e = stack[--sp];
+                int k = (int)(e >> 40);
+                int64_t t = e & (((int64_t)1 << 40) - 1);
+                if (k == 0) {
+                    /* an opened leaf: its particles one by one */
+                    int64_t p0 = 8 * t, p1 = p0 + 8 < n ? p0 + 8 : n;
+                    for (int64_t p = p0; p < p1; ++p) {
+                        int64_t j = sorted[p];
+                        if (j == i) continue;
+                        int32_t d[3];
+                        uint64_t D2 = 0;
+                        for (int q = 0; q < 3; ++q) {
+                            d[q] = (int32_t)(X[3 * j + q] - Xi[q]);
+                            uint64_t g = (uint64_t)(d[q] < 0 ? -(int64_t)d[q] : (int64_t)d[q]) >> 8;
+                            D2 += g * g;
+                        }
+                        if (!((double)D2 < RC2)) continue;
+                        ++np;
+                        double rx = d[0] * u, ry = d[1] * u, rz = d[2] * u;
+                        double r = sqrt(rx * rx + ry * ry + rz * rz);
+                        if (r == 0.0) continue;
+                        double f = G * m[j] * orc_grav_K(r, h_soft, r_split);
+                        ax += f * rx;
+                        ay += f * ry;
+                        az += f * rz;
+                        sc += fabs(f) * r;
+                    }
+                    continue;
+                }
+                /* an opened internal node: test its children */
+                int64_t c0 = 8 * t, c1 = c0 + 8 < T.cnt[k - 1] ? c0 + 8 : T.cnt[k - 1];
+                for (int64_t c = c0; c < c1; ++c) {
+                    int64_t nd = T.off[k - 1] + c;
+                    uint64_t D2 = 0, F2 = 0, l = 0;
+                    for (int q = 0; q < 3; ++q) {
+                        uint32_t lo = T.lo[3 * nd + q], hi = T.hi[3 * nd + q], x = Xi[q], gap = 0, far;
+                        if (x < lo || x > hi) {
+                            uint32_t g1 = lo - x, g2 = x - hi;   /* both ways round the periodic axis */
+                            gap = g1 < g2 ? g1 : g2;
+                            far = gap + (hi - lo);
+                        } else {
+                            far = x - lo > hi - x ? x - lo : hi - x;
+                        }
+                        uint64_t g = gap >> 8, f = ((uint64_t)far + 255) >> 8, s = (uint64_t)((hi - lo) >> 8);
+                        D2 += g * g;
+                        F2 += f * f;
+                        if (s > l) l = s;
+                    }
+                    if ((double)D2 >= RC2) continue;
+                    if (theta2 > 0.0 && D2 > 0 && (double)F2 < RC2 && theta2 * (double)D2 >= (double)(l * l)) {
+                        ++nn;
+                        double v[3];
+                        for (int q = 0; q < 3; ++q) {
+                            double dd = T.com[3 * nd + q] - (double)Xi[q];
+                            dd -= ORC_TWO32 * rint(dd / ORC_TWO32);
+                            v[q] = dd * u;
+                        }
+                        double r = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+                        if (r == 0.0) continue;
+                        double f = G * T.mass[nd] * orc_grav_K(r, h_soft, r_split);
+                        ax += f * v[0];
+                        ay += f * v[1];
+                        az += f * v[2];
+                        sc += fabs(f) * r;
+                        continue;
+                    }
+                    stack[sp++] = ((int64_t)(k - 1) << 40) | c;
+                }
+            }
+            acc[3 * i] = ax;
+            acc[3 * i + 1] = ay;
+            acc[3 * i + 2] = az;
+            if (scale) scale[i] = sc;
+            if (n_nodes) n_nodes[i] = nn;
+            if (n_pairs) n_pairs[i] = np;
+        }
+        free(stack);
+    }
+    orc_tree_free(&T);
+    free(sorted);
 }
