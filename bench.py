@@ -526,6 +526,34 @@ def batched_line(S, ctx, dev, reps=3):
             "value": pairs / (ms / 1e3), "unit": UNIT, "ms_per_pass": ms / reps}
 
 
+def gravity_line(S, ctx, wl, reps=3):
+    """Secondary line: the short-range gravity pass (Barnes-Hut walk,
+    theta = 0.5) over the 10M clustered particles, all active, with the TreePM
+    split of a mesh of one cell per mean particle spacing: r_s = 1.25 cells,
+    r_cut = 4.5 r_s, spline softening 2.8 / 30 cells."""
+    import torch
+    n = wl["n"]
+    cell = 1.0 / round(n ** (1.0 / 3.0))
+    gp = S.gravity_params(G=1.0, theta=0.5, r_split=1.25 * cell, r_cut=4.5 * 1.25 * cell, h_soft=2.8 * cell / 30)
+    acc = torch.zeros(n, 3, device=wl["h"].device)
+    S.sph_gravity(ctx, wl["grid"], None, gp, acc)
+    S.sph_sync_status(ctx)
+    ms, nodes, pairs = 0.0, 0, 0
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        S.sph_gravity(ctx, wl["grid"], None, gp, acc)
+        b.record()
+        _, st = S.sph_sync_status(ctx)
+        ms += a.elapsed_time(b)
+        nodes += st["grav_nodes"]
+        pairs += st["grav_pairs"]
+    return {"workload": "10M clustered, all active: short-range gravity (TreePM split, r_s = 1.25 mean spacings, "
+                        "r_cut = 4.5 r_s), Barnes-Hut walk at theta = 0.5, node moments included",
+            "value": (nodes + pairs) / (ms / 1e3), "unit": "interactions/s", "ms_per_pass": ms / reps,
+            "node_interactions_per_particle": nodes / reps / n, "pair_interactions_per_particle": pairs / reps / n}
+
+
 def adjoint_line(S, ctx, dev, reps=3):
     """Secondary line: the differentiation workload (262,144 clustered
     particles): forward density + force, then sph_backward for the loss
@@ -630,6 +658,7 @@ def main():
     if not args.no_extra and rank == 0:
         extra["balsara"] = balsara_line(S, ctx, wl, dpar, fpar)
         extra["conduction"] = conduction_line(S, ctx, wl, dpar, fpar)
+        extra["gravity"] = gravity_line(S, ctx, wl)
         extra["kdk"] = kdk_line(S, ctx, wl)
         del wl
         torch.cuda.empty_cache()

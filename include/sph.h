@@ -104,6 +104,8 @@ typedef struct {
     double force_kernel_ms;   /* SPH_TIME_KERNELS: summed time of the force kernels */
     uint32_t density_launches; /* SPH_TIME_KERNELS: timed density kernel launches */
     uint32_t force_launches;   /* SPH_TIME_KERNELS: timed force kernel launches */
+    uint64_t grav_nodes;      /* sph_gravity: node (monopole) interactions */
+    uint64_t grav_pairs;      /* sph_gravity: particle interactions inside the cutoff */
 } sph_stats;
 
 /* Fills *p with the library defaults: L = 1, N_t = 64, n_tol = 1e-6 N_t,
@@ -362,6 +364,49 @@ sph_status sph_kick_scalar(sph_ctx *ctx, const int32_t *active, int64_t n_active
 /* The prediction of sph_drift for one quantity: value_pred += rate dt, all n. */
 sph_status sph_predict_scalar(sph_ctx *ctx, int64_t n, double dt, const float *rate, float *value_pred,
                               void *stream);
+
+/*
+ * Short-range gravity of the TreePM split by a Barnes-Hut walk (the paper's
+ * gravity module: particles interact with distant tree nodes as point masses
+ * chosen by an opening criterion, inside the walk; Sec. 1, Sec. 3). The long-
+ * range particle-mesh part is not computed here.
+ *   tree      the grid's hierarchy: a leaf is 8 consecutive Morton-sorted
+ *             particles, a node 8 consecutive nodes of the level below; node
+ *             boxes are the min/max integer coordinates of their particles,
+ *             node masses and centres of mass the sums (computed by the call).
+ *   decisions exact integer comparisons in coarse units (integer
+ *             coordinates >> 8): with D2 the squared periodic gap between X_i
+ *             and a node's box, F2 the squared distance to its far side
+ *             (rounded up), L2 its squared largest side, RCi =
+ *             ceil((r_cut 2^24 / L)^2) and P = rint(theta^2 2^16), the root is
+ *             opened and a child of an opened node is skipped if D2 >= RCi,
+ *             taken as its monopole if P > 0, D2 > 0, F2 < RCi, L2 <= D2 and
+ *             2^16 L2 <= P D2, else opened; a particle j != i of an opened leaf
+ *             interacts if sum_a (|(int32)(X_j - X_i)| >> 8)^2 < RCi.
+ *   term      a_i += G m_j K(r) (x_j - x_i) (minimum image; a node: its mass at
+ *             its centre of mass), K(r) = M(r/h_soft) g(r) / r^3 with M the mass
+ *             fraction of the cubic spline (support h_soft) inside r (1 beyond,
+ *             or with h_soft = 0) and g(r) = erfc(r/(2 r_split)) +
+ *             r/(r_split sqrt(pi)) exp(-r^2/(4 r_split^2)) (1 with r_split = 0).
+ *             Coincident pairs exert nothing.
+ *   active    device int32 caller indices (NULL: all), as sph_density;
+ *   acc       device, n x 3 floats: written for active particles (FP32 sums
+ *             folded with error-free transformations);
+ *   n_nodes, n_pairs  device, n int32 each, or NULL: per active particle the
+ *             node and particle interactions.
+ * SPH_ERR_INVALID unless 0 <= theta <= 1, r_split >= 0, h_soft >= 0, G
+ * finite and 0 < r_cut <= L/4 for every box of the grid. The totals are in
+ * sph_stats.grav_nodes / grav_pairs.
+ */
+typedef struct {
+    double G;        /* gravitational constant */
+    double theta;    /* opening angle (0: never accept a node) */
+    double r_split;  /* TreePM split scale r_s (0: no split) */
+    double r_cut;    /* cutoff radius, <= L/4 */
+    double h_soft;   /* spline softening radius (support; 0: none) */
+} sph_gravity_params;
+sph_status sph_gravity(sph_ctx *ctx, const sph_grid *grid, const int32_t *active, int64_t n_active,
+                       const sph_gravity_params *gp, float *acc, int32_t *n_nodes, int32_t *n_pairs, void *stream);
 
 /*
  * Adjoint of the density and force passes (an extension of the paper's hot

@@ -805,16 +805,19 @@ int64_t orc_pair_list(int mode, const uint32_t *X, const double *xc, int64_t n, 
  *            X_i and the node's box on axis a, D2 = sum G_a^2, l = largest side,
  *            L2 = l^2; F2 = sum of the squared far distances to the box,
  *            F_a = (periodic distance from X_i to the far side of the box +
- *            255) >> 8 (rounded up); RC2 = (r_cut 2^24 / L)^2 and
- *            theta2 = theta^2 in FP64. The root is always opened. A child of
- *            an opened node is
- *              skipped   if D2 >= RC2 (the box lies beyond the cutoff),
- *              accepted  (monopole) if theta2 > 0, D2 > 0, F2 < RC2 (the box
- *                        lies inside the cutoff, so that every member would
- *                        interact) and theta2 * D2 >= L2 (opening angle),
+ *            255) >> 8 (rounded up). All tests are integer comparisons:
+ *            RCi = ceil((r_cut 2^24 / L)^2) (FP64, then exact), so that
+ *            "D2 < RCi" is "coarse distance below r_cut"; the opening angle
+ *            enters as P = rint(theta^2 2^16). The root is always opened. A
+ *            child of an opened node is
+ *              skipped   if D2 >= RCi (the box lies beyond the cutoff),
+ *              accepted  (monopole) if P > 0, D2 > 0, F2 < RCi (the box lies
+ *                        inside the cutoff, so that every member would
+ *                        interact), L2 <= D2 and 2^16 L2 <= P D2 (opening
+ *                        angle: l <= theta D),
  *              opened    otherwise (a leaf: its particles one by one).
  *            A particle j != i of an opened leaf interacts if its coarse
- *            distance, sum_a (|(int32)(X_j - X_i)| >> 8)^2, is below RC2.
+ *            distance, sum_a (|(int32)(X_j - X_i)| >> 8)^2, is below RCi.
  *   pair     a_i += G m_j K(r) (x_j - x_i), minimum image, with
  *            K(r) = M(r/h_s) / r^3 * g(r): M the mass fraction of the cubic
  *            spline of support h_s inside r (1 for r >= h_s; Gadget's
@@ -934,7 +937,8 @@ void orc_gravity(const uint32_t *X, int64_t n, double L, const double *m, double
     orc_tree_build(X, m, sorted, n, &T);
     const double u = L / ORC_TWO32;           /* physical length of one integer unit */
     const double rcu = r_cut / L * 16777216.0; /* r_cut in coarse units (2^-24 L) */
-    const double RC2 = rcu * rcu, theta2 = theta * theta;
+    const uint64_t RCi = (uint64_t)ceil(rcu * rcu);
+    const uint64_t P = (uint64_t)rint(theta * theta * 65536.0);
     int64_t na = active ? n_active : n;
 #pragma omp parallel
     {
@@ -965,7 +969,7 @@ void orc_gravity(const uint32_t *X, int64_t n, double L, const double *m, double
                             uint64_t g = (uint64_t)(d[q] < 0 ? -(int64_t)d[q] : (int64_t)d[q]) >> 8;
                             D2 += g * g;
                         }
-                        if (!((double)D2 < RC2)) continue;
+                        if (!(D2 < RCi)) continue;
                         ++np;
                         double rx = d[0] * u, ry = d[1] * u, rz = d[2] * u;
                         double r = sqrt(rx * rx + ry * ry + rz * rz);
@@ -997,8 +1001,9 @@ void orc_gravity(const uint32_t *X, int64_t n, double L, const double *m, double
                         F2 += f * f;
                         if (s > l) l = s;
                     }
-                    if ((double)D2 >= RC2) continue;
-                    if (theta2 > 0.0 && D2 > 0 && (double)F2 < RC2 && theta2 * (double)D2 >= (double)(l * l)) {
+                    if (D2 >= RCi) continue;
+                    uint64_t L2 = l * l;
+                    if (P > 0 && D2 > 0 && F2 < RCi && L2 <= D2 && (L2 << 16) <= P * D2) {
                         ++nn;
                         double v[3];
                         for (int q = 0; q < 3; ++q) {

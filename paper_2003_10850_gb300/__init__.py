@@ -13,12 +13,12 @@ import torch
 
 from . import abi
 from .abi import (SPH_FIXED_H, SPH_FP64, SPH_H_GUESS, SPH_PLAIN_FP32, SPH_TIME_KERNELS, SPH_WARP_GROUP, SPH_DENSITY_BUFFERED, SPH_PER_THREAD_WALK, SPH_COOP_WALK, SPH_WARP_WALK, SPH_NO_LISTS, SPHError,
-                  default_params, sph_params, sph_stats)
+                  default_params, sph_gravity_params, sph_params, sph_stats)
 
 __all__ = ["Context", "Grid", "sph_create", "sph_build_grid", "sph_build_grid_batched", "sph_grid_update",
            "sph_density", "sph_hydro_force", "sph_density_divcurl", "sph_hydro_force_balsara",
            "sph_hydro_force_conduction", "sph_hydro_force_visc", "sph_visc_rate", "sph_kick_scalar",
-           "sph_predict_scalar", "sph_timebins", "sph_active_from_bins", "sph_kick", "sph_drift",
+           "sph_predict_scalar", "sph_gravity", "gravity_params", "sph_gravity_params", "sph_timebins", "sph_active_from_bins", "sph_kick", "sph_drift",
            "sph_backward", "sph_sync_status", "sph_grid_export", "sph_sort_keys_static", "density",
            "hydro_force", "default_params", "sph_params", "sph_stats", "SPHError", "SPH_FP64",
            "SPH_PLAIN_FP32", "SPH_FIXED_H", "SPH_H_GUESS", "SPH_TIME_KERNELS", "SPH_WARP_GROUP", "SPH_DENSITY_BUFFERED", "SPH_PER_THREAD_WALK", "SPH_COOP_WALK", "SPH_WARP_WALK", "SPH_NO_LISTS"]
@@ -218,6 +218,18 @@ def sph_predict_scalar(ctx: Context, dt, rate, value_pred):
     f = torch.float32
     ctx.check(ctx.lib.sph_predict_scalar(ctx.handle, value_pred.numel(), float(dt), _ptr(rate, f, "rate"),
                                          _ptr(value_pred, f, "value_pred"), _stream()))
+
+
+def gravity_params(G=1.0, theta=0.5, r_split=0.0, r_cut=0.25, h_soft=0.0) -> sph_gravity_params:
+    return sph_gravity_params(float(G), float(theta), float(r_split), float(r_cut), float(h_soft))
+
+
+def sph_gravity(ctx: Context, grid: Grid, active, gp: sph_gravity_params, acc, n_nodes=None, n_pairs=None):
+    na = 0 if active is None else active.numel()
+    i32 = torch.int32
+    ctx.check(ctx.lib.sph_gravity(ctx.handle, grid.handle, _ptr(active, i32, "active"), na, ctypes.byref(gp),
+                                  _ptr(acc, torch.float32, "acc"), _ptr(n_nodes, i32, "n_nodes"),
+                                  _ptr(n_pairs, i32, "n_pairs"), _stream()))
 
 
 def sph_timebins(ctx: Context, h, vsig, active, tick, courant, dt_max, max_bin, bins):

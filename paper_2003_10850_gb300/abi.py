@@ -45,7 +45,7 @@ EXPORTED = ["sph_default_params", "sph_create", "sph_destroy", "sph_last_error",
             "sph_build_grid_batched", "sph_grid_update", "sph_grid_free", "sph_grid_size", "sph_grid_export",
             "sph_density", "sph_hydro_force", "sph_density_divcurl", "sph_hydro_force_balsara",
             "sph_hydro_force_conduction", "sph_hydro_force_visc", "sph_timebins", "sph_active_from_bins",
-            "sph_kick", "sph_drift", "sph_visc_rate", "sph_kick_scalar", "sph_predict_scalar", "sph_backward",
+            "sph_kick", "sph_drift", "sph_visc_rate", "sph_kick_scalar", "sph_predict_scalar", "sph_gravity", "sph_backward",
             "sph_sync_status", "sph_sort_keys_static"]
 SPH_SORT_STATIC_MAX_KEYS = 1 << 20
 
@@ -62,10 +62,16 @@ class sph_stats(ctypes.Structure):
                 ("density_evals", ctypes.c_uint64), ("pair_tests", ctypes.c_uint64),
                 ("groups", ctypes.c_uint64), ("density_kernel_ms", ctypes.c_double),
                 ("force_kernel_ms", ctypes.c_double), ("density_launches", ctypes.c_uint32),
-                ("force_launches", ctypes.c_uint32)]
+                ("force_launches", ctypes.c_uint32), ("grav_nodes", ctypes.c_uint64),
+                ("grav_pairs", ctypes.c_uint64)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class sph_gravity_params(ctypes.Structure):
+    _fields_ = [("G", ctypes.c_double), ("theta", ctypes.c_double), ("r_split", ctypes.c_double),
+                ("r_cut", ctypes.c_double), ("h_soft", ctypes.c_double)]
 
 
 class SPHError(RuntimeError):
@@ -131,6 +137,8 @@ def load(path: str | None = None):
     L.sph_kick_scalar.restype = i32
     L.sph_predict_scalar.argtypes = [P, i64, ctypes.c_double, P, P, P]
     L.sph_predict_scalar.restype = i32
+    L.sph_gravity.argtypes = [P, P, P, i64, ctypes.POINTER(sph_gravity_params), P, P, P, P]
+    L.sph_gravity.restype = i32
     L.sph_timebins.argtypes = [P, P, P, P, i64, i64, i64, ctypes.c_double, ctypes.c_double, i32, P, P]
     L.sph_timebins.restype = i32
     L.sph_active_from_bins.argtypes = [P, P, P, i64, i32, P, P, P]

@@ -367,6 +367,39 @@ sph_status sph_hydro_force_conduction(sph_ctx* ctx, const sph_grid* grid, const 
                       dudt_cond, hash, params, stream);
 }
 
+sph_status sph_gravity(sph_ctx* ctx, const sph_grid* grid, const int32_t* active, int64_t n_active,
+                       const sph_gravity_params* gp, float* acc, int32_t* n_nodes, int32_t* n_pairs, void* stream) {
+    if (!ctx) return SPH_ERR_INVALID;
+    if (!grid || grid->ctx != ctx) return fail(ctx, SPH_ERR_INVALID, "grid is NULL or from another context");
+    if (!gp || !acc) return fail(ctx, SPH_ERR_INVALID, "gp and acc are required");
+    if (!(gp->theta >= 0.0 && gp->theta <= 1.0) || !(gp->r_split >= 0.0) || !(gp->h_soft >= 0.0) ||
+        !std::isfinite(gp->G) || !std::isfinite(gp->r_split) || !std::isfinite(gp->h_soft) || !(gp->r_cut > 0.0))
+        return fail(ctx, SPH_ERR_INVALID, "gravity: need 0 <= theta <= 1, r_split >= 0, h_soft >= 0, r_cut > 0");
+    for (const auto& B : grid->boxes_h)
+        if (!(gp->r_cut <= 0.25 * B.L)) return fail(ctx, SPH_ERR_INVALID, "gravity: r_cut must be <= L/4");
+    sph_status st = check_active(ctx, grid, active, n_active);
+    if (st) return st;
+    const int64_t na = active ? n_active : grid->n;
+    if (na == 0) return SPH_OK;
+    if (cudaSetDevice(ctx->device)) return fail(ctx, SPH_ERR_CUDA, "cudaSetDevice failed");
+    cudaStream_t s = (cudaStream_t)stream;
+    sph_grid* g = const_cast<sph_grid*>(grid);
+    grid_active(g, active, n_active, 32, false, s);
+    GravityLaunch L;
+    L.g = g;
+    L.G = gp->G;
+    L.theta = gp->theta;
+    L.r_split = gp->r_split;
+    L.r_cut = gp->r_cut;
+    L.h_soft = gp->h_soft;
+    L.acc = acc;
+    L.n_nodes = n_nodes;
+    L.n_pairs = n_pairs;
+    cudaError_t e = launch_gravity(ctx, L, na, s);
+    if (e) return cuda_fail(ctx, e, "sph_gravity");
+    return SPH_OK;
+}
+
 sph_status sph_backward(sph_ctx* ctx, const sph_grid* grid, const float* vel, const float* u, const float* h,
                         const float* rho, const float* omega, const float* g_acc, const float* g_rho,
                         float* g_pos, float* g_u, float* g_mass, const sph_params* params, void* stream) {
@@ -432,6 +465,8 @@ sph_status sph_sync_status(sph_ctx* ctx, void* stream, sph_stats* stats) {
         stats->density_evals = c.density_evals;
         stats->pair_tests = c.pair_tests;
         stats->groups = c.groups;
+        stats->grav_nodes = c.grav_nodes;
+        stats->grav_pairs = c.grav_pairs;
     }
     if (c.status & ST_INVALID) return fail(ctx, SPH_ERR_INVALID, "device: non-finite or out-of-range input");
     if (c.status & ST_TIMEOUT) return fail(ctx, SPH_ERR_TIMEOUT, "device: a bounded wait ran out");

@@ -61,6 +61,8 @@ struct Counters {
     unsigned long long density_evals;
     unsigned long long pair_tests;
     unsigned long long groups;
+    unsigned long long grav_nodes;
+    unsigned long long grav_pairs;
 };
 
 // -------------------------------------------------------------------------

@@ -439,7 +439,7 @@ void grid_free(sph_grid* g) {
                     g->node_hmax, g->act, g->flag, g->scan, g->scan_tmp, g->box_act, g->n_groups,
                     g->groups, g->list_a, g->list_b, g->st_lo, g->st_hi, g->list_n, g->d_off, g->d_L,
                     g->k2, g->v1, g->v2, g->counts, g->cscan, g->node_c, g->node_e, g->posf,
-                    g->fvel, g->fthermo, g->fposh, g->fvm, g->fbal, g->fcond, g->fvisc, g->nbr, g->nbr_off, g->nbr_x, g->nbr_n, g->ext_n, g->ext_off, g->ext_raw, g->ext, g->list_h, g->list_st, g->fb_list, g->bw_ga, g->bw_xbar, g->bw_rd, g->bw_f, g->lcache};
+                    g->fvel, g->fthermo, g->fposh, g->fvm, g->fbal, g->fcond, g->fvisc, g->node_m, g->box_rci, g->nbr, g->nbr_off, g->nbr_x, g->nbr_n, g->ext_n, g->ext_off, g->ext_raw, g->ext, g->list_h, g->list_st, g->fb_list, g->bw_ga, g->bw_xbar, g->bw_rd, g->bw_f, g->lcache};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete g;
@@ -547,6 +547,8 @@ sph_status grid_build(sph_ctx* ctx, const void* pos, int f64, const float* mass,
     GRID_CHECK(cudaMalloc(&g->fbal, sizeof(float) * n));
     GRID_CHECK(cudaMalloc(&g->fcond, sizeof(float2) * n));
     GRID_CHECK(cudaMalloc(&g->fvisc, sizeof(float2) * n));
+    GRID_CHECK(cudaMalloc(&g->node_m, sizeof(float4) * node));
+    GRID_CHECK(cudaMalloc(&g->box_rci, sizeof(unsigned long long) * nb));
     // a 64 x 32 leaf list per persistent warp of the cooperative density
     // kernel (<= 16 blocks of 3 warps per SM)
     GRID_CHECK(cudaMalloc(&g->lcache, sizeof(int) * (size_t)ctx->sm_count * 16 * 3 * 64 * 32));

@@ -53,6 +53,8 @@ struct sph_grid {
     float* fbal = nullptr;                 // per force call with the switch, sorted: Balsara factor
     float2* fcond = nullptr;               // per force call with conduction, sorted: u, kappa
     float2* fvisc = nullptr;               // per force call with per-particle viscosity, sorted: factor, alpha
+    float4* node_m = nullptr;              // per gravity call, per node: centre of mass - node centre, mass
+    unsigned long long* box_rci = nullptr; // per gravity call, per box: coarse squared cutoff
     // per-call scratch, sized at build so that calls never allocate
     int32_t* act = nullptr;                // active particles, sorted indices, sorted order
     uint8_t* flag = nullptr;               // n
@@ -102,7 +104,7 @@ struct sph_grid {
 
 namespace sph {
 
-constexpr int kQueues = 4;
+constexpr int kQueues = 5;
 constexpr int kListPool = 128;  // neighbour-list pool entries per particle (lists vary in length)
 constexpr int kExtPool = 64;    // extra-partner pool entries per particle
 constexpr int kListChunk = 2048; // pool entries a warp reserves at a time for its particles' lists
@@ -202,6 +204,16 @@ cudaError_t run_backward(sph_ctx* ctx, sph_grid* g, const BackwardLaunch& b, cud
 // coop.cu (default path)
 cudaError_t launch_density_coop(sph_ctx* ctx, const DensityLaunch& a, cudaStream_t s);
 cudaError_t launch_force_coop(sph_ctx* ctx, const ForceLaunch& a, cudaStream_t s);
+
+// gravity.cu
+struct GravityLaunch {
+    const sph_grid* g;
+    double G, theta, r_split, r_cut, h_soft;
+    float* acc;
+    int32_t* n_nodes;   // optional
+    int32_t* n_pairs;   // optional
+};
+cudaError_t launch_gravity(sph_ctx* ctx, const GravityLaunch& L, int64_t n_active, cudaStream_t s);
 
 // wpp_density.cu, wpp_force.cu (one warp per particle)
 cudaError_t launch_density_wpp(sph_ctx* ctx, const DensityLaunch& a, int64_t n_active, cudaStream_t s);
