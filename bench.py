@@ -321,35 +321,61 @@ def graph_steps(S, ctx, wl, dparams, fparams, steps, warmup, dist=None):
 
 def e2e_steps(S, ctx, wl, dparams, fparams, steps):
     """Same step through the public API from pinned HOST buffers: H2D of the
-    step's inputs and D2H of its results inside the timed region."""
+    step's inputs and D2H of its results inside the timed region. The inputs
+    travel on a copy stream in the order the step needs them (positions and
+    masses, the first h guesses, then velocities, energies and the later
+    guesses), so that only the first ones delay the grid rebuild; each
+    sub-step waits for its own h guesses, the first force pass for v and u."""
     import torch
     n = wl["n"]
     hst = {k: wl[k].cpu().pin_memory() for k in ("pos", "mass", "vel", "u")}
     h_ins = [h.cpu().pin_memory() for h in wl["h_ins"]]
+    h_dev = [torch.empty_like(wl["h"]) for _ in h_ins]
     outs = {k: torch.empty(wl["st"][k].shape, dtype=wl["st"][k].dtype).pin_memory()
             for k in ("rho", "omega", "acc", "dudt", "vsig")}
     h_out = torch.empty(n).pin_memory()
     st = wl["st"]
     h2d = sum(t.numel() * t.element_size() for t in hst.values()) + sum(t.numel() * 4 for t in h_ins)
     d2h = sum(t.numel() * t.element_size() for t in outs.values()) + n * 4
+    main = torch.cuda.current_stream()
+    cs = torch.cuda.Stream()
     pairs = 0
     torch.cuda.synchronize()
     t_ms = 0.0
     for _ in range(steps):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
-        for k in hst:
-            wl[k].copy_(hst[k], non_blocking=True)
+        cs.wait_stream(main)   # the previous step is done with the input buffers
+        with torch.cuda.stream(cs):
+            wl["pos"].copy_(hst["pos"], non_blocking=True)
+            wl["mass"].copy_(hst["mass"], non_blocking=True)
+            e_pos = torch.cuda.Event()
+            e_pos.record()
+            e_h = []
+            h_dev[0].copy_(h_ins[0], non_blocking=True)
+            e_h.append(torch.cuda.Event())
+            e_h[-1].record()
+            wl["vel"].copy_(hst["vel"], non_blocking=True)
+            wl["u"].copy_(hst["u"], non_blocking=True)
+            e_vu = torch.cuda.Event()
+            e_vu.record()
+            for k in range(1, len(h_ins)):
+                h_dev[k].copy_(h_ins[k], non_blocking=True)
+                e_h.append(torch.cuda.Event())
+                e_h[-1].record()
+        main.wait_event(e_pos)
         S.sph_grid_update(ctx, wl["grid"], wl["pos"], wl["mass"])
-        for act, h_in in zip(wl["acts"], h_ins):
-            wl["h"].copy_(h_in, non_blocking=True)
-            S.sph_density(ctx, wl["grid"], wl["h"], act, st["rho"], st["omega"], st["n_ngb"], st["flags"], None,
+        for k, act in enumerate(wl["acts"]):
+            main.wait_event(e_h[k])
+            S.sph_density(ctx, wl["grid"], h_dev[k], act, st["rho"], st["omega"], st["n_ngb"], st["flags"], None,
                           dparams)
-            S.sph_hydro_force(ctx, wl["grid"], wl["vel"], wl["u"], wl["h"], st["rho"], st["omega"], act,
+            if k == 0:
+                main.wait_event(e_vu)
+            S.sph_hydro_force(ctx, wl["grid"], wl["vel"], wl["u"], h_dev[k], st["rho"], st["omega"], act,
                               st["acc"], st["dudt"], st["vsig"], None, fparams)
         for k in outs:
             outs[k].copy_(st[k], non_blocking=True)
-        h_out.copy_(wl["h"], non_blocking=True)
+        h_out.copy_(h_dev[-1], non_blocking=True)
         b.record()
         _, stt = S.sph_sync_status(ctx)
         t_ms += a.elapsed_time(b)

@@ -223,7 +223,8 @@ sph_status sph_density(sph_ctx *ctx, const sph_grid *grid, float *h, const int32
  * equals the h that call ended with (checked on the device), the pairs come
  * from the neighbour lists that call recorded -- no hierarchy walk, no
  * candidate test. Otherwise, and for any particle whose lists did not fit
- * (more than 128 neighbours or 64 extra partners), the hierarchy is walked.
+ * (the neighbour pool full, or more than 128 extra partners), the hierarchy is
+ * walked.
  * Both give the same pair set.
  */
 sph_status sph_hydro_force(sph_ctx *ctx, const sph_grid *grid, const float *vel, const float *u,

@@ -439,7 +439,7 @@ void grid_free(sph_grid* g) {
                     g->node_hmax, g->act, g->flag, g->scan, g->scan_tmp, g->box_act, g->n_groups,
                     g->groups, g->list_a, g->list_b, g->st_lo, g->st_hi, g->list_n, g->d_off, g->d_L,
                     g->k2, g->v1, g->v2, g->counts, g->cscan, g->node_c, g->node_e, g->posf,
-                    g->fvel, g->fthermo, g->fposh, g->fvm, g->fbal, g->fcond, g->fvisc, g->node_m, g->box_rci, g->nbr, g->nbr_off, g->nbr_x, g->nbr_n, g->ext_n, g->ext_off, g->ext_raw, g->ext, g->list_h, g->list_st, g->fb_list, g->bw_ga, g->bw_xbar, g->bw_rd, g->bw_f, g->lcache};
+                    g->fvel, g->fthermo, g->fposh, g->fvm, g->fbal, g->fcond, g->fvisc, g->node_m, g->box_rci, g->nbr, g->nbr_off, g->nbr_n, g->ext_n, g->ext, g->list_h, g->list_st, g->fb_list, g->bw_ga, g->bw_xbar, g->bw_rd, g->bw_f, g->lcache};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete g;
@@ -558,16 +558,13 @@ sph_status grid_build(sph_ctx* ctx, const void* pos, int f64, const float* mass,
         // built without them and the force pass walks.
         const long long lim = (1ll << 31) - (1ll << 12);
         g->list_pool = (int64_t)std::min<long long>((long long)n * kListPool, lim);
-        g->ext_pool = (int64_t)std::min<long long>((long long)n * kExtPool, lim);
         void** lp[] = {(void**)&g->nbr, (void**)&g->nbr_off, (void**)&g->nbr_n, (void**)&g->ext_n,
-                       (void**)&g->ext_off, (void**)&g->ext_raw, (void**)&g->ext, (void**)&g->list_h,
-                       (void**)&g->list_st, (void**)&g->fb_list, (void**)&g->nbr_x};
+                       (void**)&g->ext, (void**)&g->list_h, (void**)&g->list_st, (void**)&g->fb_list};
         const size_t sz[] = {sizeof(int32_t) * (size_t)g->list_pool, sizeof(int32_t) * n, sizeof(int32_t) * n,
-                             sizeof(uint32_t) * n, sizeof(uint32_t) * (n + 1), sizeof(int32_t) * (size_t)g->ext_pool,
-                             sizeof(int32_t) * (size_t)g->ext_pool, sizeof(float) * n, sizeof(unsigned) * kListSt,
-                             sizeof(int32_t) * n, (size_t)g->list_pool};
+                             sizeof(uint32_t) * n, sizeof(int32_t) * (size_t)n * kExtCap, sizeof(float) * n,
+                             sizeof(unsigned) * kListSt, sizeof(int32_t) * n};
         bool ok = true;
-        for (int k = 0; k < 11 && ok; ++k) ok = cudaMalloc(lp[k], sz[k]) == cudaSuccess;
+        for (int k = 0; k < 8 && ok; ++k) ok = cudaMalloc(lp[k], sz[k]) == cudaSuccess;
         if (ok) ok = cudaMemset(g->list_st, 0, sizeof(unsigned) * kListSt) == cudaSuccess;
         if (!ok) {
             (void)cudaGetLastError();

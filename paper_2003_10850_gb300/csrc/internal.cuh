@@ -83,18 +83,15 @@ struct sph_grid {
     // reused by the force pass (NULL when the grid was built with SPH_NO_LISTS)
     int32_t* nbr = nullptr;                // pool of kListPool * n entries: the lists {j != i : r_ij < h_i}
     int32_t* nbr_off = nullptr;            // n: start of i's list in the pool
-    uint8_t* nbr_x = nullptr;              // pool-sized: 1 where the entry (j on i's list) makes i an extra partner of j
     int32_t* nbr_n = nullptr;              // n: length of i's list, -1 if the pool was full
-    uint32_t* ext_n = nullptr;             // n: extra partners of i (j with h_i <= r_ij < h_j)
-    uint32_t* ext_off = nullptr;           // n + 1: exclusive scan of ext_n
-    int32_t* ext_raw = nullptr;            // pool of kExtPool * n entries: extra partners, scatter order
-    int32_t* ext = nullptr;                // the same, ascending within each particle
+    uint32_t* ext_n = nullptr;             // n: extra partners of i (j with h_i <= r_ij < h_j); after
+                                           // the sort, kExtUnusable if they overflowed their segment
+    int32_t* ext = nullptr;                // n segments of kExtCap: i's extra partners, ascending
     float* list_h = nullptr;               // n: the h the lists were made with (sorted order)
     unsigned* list_st = nullptr;           // device, kListSt words (see kListSt)
     int32_t* fb_list = nullptr;            // n: active particles the list force pass hands to the walk
     bool lists_full = false;               // host: the last density call recorded every particle's list
     int64_t list_pool = 0;                 // entries of the nbr pool
-    int64_t ext_pool = 0;                  // entries of the ext pools
     // adjoint scratch (allocated by the first sph_backward on the grid)
     float4* bw_ga = nullptr;
     float4* bw_xbar = nullptr;
@@ -106,7 +103,9 @@ namespace sph {
 
 constexpr int kQueues = 5;
 constexpr int kListPool = 128;  // neighbour-list pool entries per particle (lists vary in length)
-constexpr int kExtPool = 64;    // extra-partner pool entries per particle
+constexpr int kExtCap = 128;    // extra-partner segment per particle (262k clustered: mean 24, max 106)
+constexpr unsigned kExtUnusable = 0xffffffffu;
+static_assert((kExtCap & (kExtCap - 1)) == 0 && kExtCap >= 64, "kExtCap: a power of two >= 64 (the segment sort)");
 constexpr int kListChunk = 2048; // pool entries a warp reserves at a time for its particles' lists
 // list_st words: [0] lists written, [1] a list missing (pool full), [2] h
 // changed since the lists were made, [3] fallback count, [4..5] pool entries

@@ -106,9 +106,8 @@ struct WppArgs {
     int32_t* nbr;                // pool of list_pool entries
     int32_t* nbr_off;
     int32_t* nbr_n;
-    const int32_t* ext;          // pool of ext_pool entries, ascending per particle
-    const uint32_t* ext_off;     // n + 1
-    const uint32_t* ext_n;       // nonzero: the particle's extra partners are not usable
+    const int32_t* ext;          // n segments of kExtCap entries, ascending per particle
+    const uint32_t* ext_n;       // extra partners per particle; kExtUnusable: not usable
     float* list_h;
     unsigned* list_st;           // see kListSt
     // density: velocity divergence and curl (NULL: not asked)
@@ -125,7 +124,6 @@ struct WppArgs {
     int32_t* fb_list;
     long long list_pool;
     int list_chunk;              // pool entries a warp reserves at a time
-    unsigned ext_pool;
     int n_total;                 // particles in the grid
     // force walk after a list pass: the particles the lists could not serve
     // (fb_act, *fb_count) when the lists are valid, else the whole active set

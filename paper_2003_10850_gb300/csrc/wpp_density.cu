@@ -422,96 +422,77 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_density_wpp(WppArgs a) {
 // Warp per particle j: every i on j's list with r_ij >= h_i gets j as an
 // extra partner (possible only if h_i < h_j, which is tested first). "r_ij <
 // h_i" is the exact predicate, decided in FP32 outside a band of 2^-20 around
-// h_i^2 and in FP64 inside it. COUNT = true counts each i's extra partners in
-// ext_n and marks the list entries that make one in nbr_x; COUNT = false
-// places the marked pairs in i's segment [ext_off[i], ext_off[i+1]) of
-// ext_raw (scatter order; ext_n counts down to 0).
-template <bool COUNT>
+// h_i^2 and in FP64 inside it. The pair goes straight into i's fixed segment
+// of kExtCap entries at the slot its counter hands out (scatter order); a
+// count beyond kExtCap leaves the segment incomplete, which the sort marks.
 __global__ void __launch_bounds__(256) k_list_ext(const BoxDesc* __restrict__ boxes, int nb, int n,
                                                   const uint4* __restrict__ posm, const int32_t* __restrict__ nbr,
                                                   const int32_t* __restrict__ nbr_off,
-                                                  const int32_t* __restrict__ nbr_n, uint8_t* __restrict__ nbr_x,
-                                                  const float* __restrict__ list_h, uint32_t* __restrict__ ext_n,
-                                                  const uint32_t* __restrict__ ext_off, int32_t* __restrict__ ext_raw,
-                                                  unsigned ext_pool, unsigned* list_st) {
+                                                  const int32_t* __restrict__ nbr_n, const float* __restrict__ list_h,
+                                                  uint32_t* __restrict__ ext_n, int32_t* __restrict__ ext,
+                                                  unsigned* list_st) {
     const unsigned lane = lane_id();
     const int warps = gridDim.x * (blockDim.x >> 5);
     const float band = 9.5367431640625e-07f;  // 2^-20
     for (int j = blockIdx.x * (blockDim.x >> 5) + (int)(threadIdx.x >> 5); j < n; j += warps) {
         const int cnt = nbr_n[j];
         if (cnt < 0) {   // j's list is missing: the extra lists cannot be completed
-            if (COUNT && lane == 0) atomicOr(&list_st[1], 1u);
+            if (lane == 0) atomicOr(&list_st[1], 1u);
             continue;
         }
-        const int off = nbr_off[j];
-        const int32_t* lj = nbr + off;
-        if (COUNT) {
-            const BoxDesc& B = boxes[nb == 1 ? 0 : wpp_box(boxes, nb, j)];
-            const float Hs = (float)(4294967296.0 / B.L);   // integer units per box unit
-            const uint4 Xj = posm[j];
-            const float hj = list_h[j];
-            auto decide = [&](int i, float hi, uint4 Xi) {
-                bool x = false;
-                if (hi < hj) {
-                    const unsigned long long D2 = exact_d2(Xi, Xj);
-                    const float d2 = __ull2float_rn(D2), Hi = hi * Hs, H2 = Hi * Hi;
-                    if (d2 > H2 * (1.f + band)) x = true;
-                    else if (!(d2 < H2 * (1.f - band))) x = !exact_pred(D2, wpp_hh(hi, B.L));
-                }
-                return x;
-            };
-            // two entries per lane per step (k and k + 32), their gathers issued together
-            for (int k = (int)lane; k < cnt; k += 64) {
-                const int k1 = k + 32;
-                const bool two = k1 < cnt;
-                const int i0 = lj[k], i1 = two ? lj[k1] : i0;
-                const float h0 = list_h[i0], h1 = list_h[i1];
-                const uint4 X0 = h0 < hj ? posm[i0] : Xj, X1 = (two && h1 < hj) ? posm[i1] : Xj;
-                const bool x0 = decide(i0, h0, X0);
-                nbr_x[off + k] = x0 ? 1 : 0;
-                if (x0) atomicAdd(&ext_n[i0], 1u);
-                if (two) {
-                    const bool x1 = decide(i1, h1, X1);
-                    nbr_x[off + k1] = x1 ? 1 : 0;
-                    if (x1) atomicAdd(&ext_n[i1], 1u);
-                }
+        const int32_t* lj = nbr + nbr_off[j];
+        const BoxDesc& B = boxes[nb == 1 ? 0 : wpp_box(boxes, nb, j)];
+        const float Hs = (float)(4294967296.0 / B.L);   // integer units per box unit
+        const uint4 Xj = posm[j];
+        const float hj = list_h[j];
+        auto decide = [&](float hi, uint4 Xi) {
+            bool x = false;
+            if (hi < hj) {
+                const unsigned long long D2 = exact_d2(Xi, Xj);
+                const float d2 = __ull2float_rn(D2), Hi = hi * Hs, H2 = Hi * Hi;
+                if (d2 > H2 * (1.f + band)) x = true;
+                else if (!(d2 < H2 * (1.f - band))) x = !exact_pred(D2, wpp_hh(hi, B.L));
             }
-        } else {
-            for (int k = (int)lane; k < cnt; k += 32) {
-                if (!nbr_x[off + k]) continue;
-                const int i = lj[k];
-                if (ext_off[i + 1] <= ext_pool) {
-                    const unsigned pos = atomicSub(&ext_n[i], 1u) - 1u;
-                    ext_raw[ext_off[i] + pos] = j;
-                }
-            }
+            return x;
+        };
+        auto place = [&](int i) {
+            const unsigned slot = atomicAdd(&ext_n[i], 1u);
+            if (slot < (unsigned)kExtCap) ext[(size_t)i * kExtCap + slot] = j;
+        };
+        // two entries per lane per step (k and k + 32), their gathers issued together
+        for (int k = (int)lane; k < cnt; k += 64) {
+            const int k1 = k + 32;
+            const bool two = k1 < cnt;
+            const int i0 = lj[k], i1 = two ? lj[k1] : i0;
+            const float h0 = list_h[i0], h1 = list_h[i1];
+            const uint4 X0 = h0 < hj ? posm[i0] : Xj, X1 = (two && h1 < hj) ? posm[i1] : Xj;
+            if (decide(h0, X0)) place(i0);
+            if (two && decide(h1, X1)) place(i1);
         }
     }
 }
 
-// Warp per particle: its extra partners (distinct indices) in ascending
-// order. Up to 64 entries: each placed at its rank (registers); up to
-// kSortMax: a bitonic sort in shared memory; longer segments (and segments
-// that did not fit the pool) are marked in ext_n (nonzero), and the force
-// pass walks for those particles.
-constexpr int kSortMax = 1024;
-
-__global__ void __launch_bounds__(256) k_list_sort(int n, const uint32_t* __restrict__ ext_off, unsigned ext_pool,
-                                                   const int32_t* __restrict__ ext_raw, int32_t* __restrict__ ext,
-                                                   uint32_t* __restrict__ ext_n) {
-    __shared__ int buf[8][kSortMax];
+// Warp per particle: its extra partners (distinct indices) in ascending order,
+// in place in its segment: up to 64 entries each goes to its rank (registers),
+// up to kExtCap through a bitonic sort in shared memory. A segment that
+// overflowed is marked kExtUnusable, and the force pass walks for that particle.
+__global__ void __launch_bounds__(256) k_list_sort(int n, int32_t* __restrict__ ext, uint32_t* __restrict__ ext_n) {
+    __shared__ int buf[8][kExtCap];
     int* sb = buf[threadIdx.x >> 5];
     const unsigned lane = lane_id();
     const int warps = gridDim.x * (blockDim.x >> 5);
     for (int i = blockIdx.x * (blockDim.x >> 5) + (int)(threadIdx.x >> 5); i < n; i += warps) {
-        const unsigned b = ext_off[i], e = ext_off[i + 1];
-        if (e > ext_pool || e == b) continue;
-        const int c = (int)(e - b);
-        const int32_t* src = ext_raw + b;
-        int32_t* dst = ext + b;
+        const unsigned cu = ext_n[i];
+        if (cu > (unsigned)kExtCap) {
+            if (lane == 0) ext_n[i] = kExtUnusable;
+            continue;
+        }
+        const int c = (int)cu;
+        if (c < 2) continue;
+        int32_t* seg = ext + (size_t)i * kExtCap;
         if (c <= 64) {
-            const int v0 = (int)lane < c ? src[lane] : 0x7fffffff;
-            const int v1 = (int)lane + 32 < c ? src[lane + 32] : 0x7fffffff;
+            const int v0 = (int)lane < c ? seg[lane] : 0x7fffffff;
+            const int v1 = (int)lane + 32 < c ? seg[lane + 32] : 0x7fffffff;
             int r0 = 0, r1 = 0;
             const int c0 = min(c, 32);
             for (int k = 0; k < c0; ++k) {
@@ -524,12 +505,12 @@ __global__ void __launch_bounds__(256) k_list_sort(int n, const uint32_t* __rest
                 r0 += x < v0;
                 r1 += x < v1;
             }
-            if ((int)lane < c) dst[r0] = v0;
-            if ((int)lane + 32 < c) dst[r1] = v1;
-        } else if (c <= kSortMax) {
-            int P = 128;
-            while (P < c) P <<= 1;
-            for (int k = (int)lane; k < P; k += 32) sb[k] = k < c ? src[k] : 0x7fffffff;
+            __syncwarp();   // every lane has read the segment before it is overwritten
+            if ((int)lane < c) seg[r0] = v0;
+            if ((int)lane + 32 < c) seg[r1] = v1;
+        } else {
+            constexpr int P = kExtCap;   // a power of two
+            for (int k = (int)lane; k < P; k += 32) sb[k] = k < c ? seg[k] : 0x7fffffff;
             __syncwarp();
             for (int size = 2; size <= P; size <<= 1) {
                 for (int stride = size >> 1; stride > 0; stride >>= 1) {
@@ -545,11 +526,9 @@ __global__ void __launch_bounds__(256) k_list_sort(int n, const uint32_t* __rest
                     __syncwarp();
                 }
             }
-            for (int k = (int)lane; k < c; k += 32) dst[k] = sb[k];
-            __syncwarp();
-        } else if (lane == 0) {
-            ext_n[i] = 1u;   // too long to sort here: walked by the force pass
+            for (int k = (int)lane; k < c; k += 32) seg[k] = sb[k];
         }
+        __syncwarp();
     }
 }
 
@@ -618,15 +597,11 @@ cudaError_t launch_density_wpp(sph_ctx* ctx, const DensityLaunch& a, int64_t n_a
     if ((e = span_end(ctx, sp, s))) return e;
     if (full) {
         const int n = (int)g->n, hb = helper_blocks(ctx, n);
-        const unsigned ep = (unsigned)g->ext_pool;
         if ((e = cudaMemsetAsync(g->ext_n, 0, sizeof(uint32_t) * n, s))) return e;
-        k_list_ext<true><<<hb, 256, 0, s>>>(g->boxes, g->n_boxes, n, g->posm, g->nbr, g->nbr_off, g->nbr_n, g->nbr_x,
-                                            g->list_h, g->ext_n, g->ext_off, g->ext_raw, ep, g->list_st);
-        scan_exclusive<uint32_t>(g->ext_n, n, g->ext_off, g->scan_tmp, s, &ctx->launches);
-        k_list_ext<false><<<hb, 256, 0, s>>>(g->boxes, g->n_boxes, n, g->posm, g->nbr, g->nbr_off, g->nbr_n, g->nbr_x,
-                                             g->list_h, g->ext_n, g->ext_off, g->ext_raw, ep, g->list_st);
-        k_list_sort<<<hb, 256, 0, s>>>(n, g->ext_off, ep, g->ext_raw, g->ext, g->ext_n);
-        ctx->launches += 3;
+        k_list_ext<<<hb, 256, 0, s>>>(g->boxes, g->n_boxes, n, g->posm, g->nbr, g->nbr_off, g->nbr_n, g->list_h,
+                                      g->ext_n, g->ext, g->list_st);
+        k_list_sort<<<hb, 256, 0, s>>>(n, g->ext, g->ext_n);
+        ctx->launches += 2;
     }
     g->lists_full = full;
     return cudaGetLastError();

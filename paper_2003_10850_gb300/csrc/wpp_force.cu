@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_force_wpp(WppArgs a) {
 // does nothing and the walk that follows takes the whole active set;
 // particles whose own lists did not fit go to fb_list for that walk.
 template <bool HASH, int VISC, bool COND>
-__global__ void __launch_bounds__(128) k_force_list(WppArgs a) {
+__global__ void __launch_bounds__(128, 8) k_force_list(WppArgs a) {
     if (!wpp_lists_valid(a.list_st, a.n_total)) return;
     const unsigned lane = lane_id();
     const int warps = gridDim.x * (blockDim.x >> 5);
@@ -211,8 +211,8 @@ __global__ void __launch_bounds__(128) k_force_list(WppArgs a) {
     for (int t = blockIdx.x * (blockDim.x >> 5) + (int)(threadIdx.x >> 5); t < cnt; t += warps) {
         const int p = a.act[t];
         const int cn = a.nbr_n[p];
-        const unsigned e0 = a.ext_off[p], e1 = a.ext_off[p + 1];
-        if (cn < 0 || e1 > a.ext_pool || a.ext_n[p] != 0u) {
+        const unsigned ec = a.ext_n[p];
+        if (cn < 0 || ec > (unsigned)kExtCap) {   // (kExtUnusable included)
             if (lane == 0) a.fb_list[atomicAdd(&a.list_st[3], 1u)] = p;
             continue;
         }
@@ -228,9 +228,9 @@ __global__ void __launch_bounds__(128) k_force_list(WppArgs a) {
                              bi.x, ci.x, ci.y, bi.y};
         float Sx = 0.f, Sy = 0.f, Sz = 0.f, Su = 0.f, Sc = 0.f, vsmax = 0.f;
         unsigned long long hs = 0;
-        const int tot = cn + (int)(e1 - e0);
+        const int tot = cn + (int)ec;
         const int32_t* ln = a.nbr + a.nbr_off[p];
-        const int32_t* le = a.ext + e0;
+        const int32_t* le = a.ext + (size_t)p * kExtCap;
         // two pairs per lane per step (k and k + 32), their loads issued together;
         // each lane still sums its pairs in the order k, k + 32, k + 64, ...
         for (int k = (int)lane; k < tot; k += 64) {
@@ -349,9 +349,7 @@ cudaError_t launch_force_wpp(sph_ctx* ctx, const ForceLaunch& a, int64_t n_activ
         c.nbr_off = g->nbr_off;
         c.nbr_n = g->nbr_n;
         c.ext = g->ext;
-        c.ext_off = g->ext_off;
         c.ext_n = g->ext_n;
-        c.ext_pool = (unsigned)g->ext_pool;
         c.list_st = g->list_st;
         c.fb_list = g->fb_list;
         const int lb = (int)std::max<long long>(
