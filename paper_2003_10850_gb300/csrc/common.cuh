@@ -33,7 +33,7 @@ struct BoxDesc {
     long long n;            // particles in the box
     double L;               // box side
     int nlev;               // number of levels; level nlev-1 is the single root
-    int pad;
+    int pow2;               // L is a power of two: h 2^32 / L = h S exactly
     int lvl_off[kMaxLev];   // global node index of the box's first node on level k
     int lvl_n[kMaxLev];     // nodes of the box on level k
     // FP32 forms for kernels that keep FP64 off their per-particle path
@@ -41,6 +41,8 @@ struct BoxDesc {
     float Lf;               // L rounded to FP32
     float wideL;            // 0.45 L: a leaf whose extent plus radius reaches it takes exact separations
     float capu;             // smallest float >= 0.5 L (1 - 1e-9), the bound h must stay below
+    float Hs;               // 2^32 / L (integer steps per box unit), rounded to FP32
+    double S;               // 2^32 / L in FP64 (correctly rounded; exact when pow2)
 };
 
 // Active groups of one call: group g covers active-list entries

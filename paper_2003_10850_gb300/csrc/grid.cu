@@ -501,6 +501,10 @@ sph_status grid_build(sph_ctx* ctx, const void* pos, int f64, const float* mass,
         }
         B.nlev = lev;
         B.sf = (float)std::ldexp(B.L, -32);
+        B.S = 4294967296.0 / B.L;
+        B.Hs = (float)B.S;
+        int ex = 0;
+        B.pow2 = std::frexp(B.L, &ex) == 0.5 ? 1 : 0;
         B.Lf = (float)B.L;
         B.wideL = 0.45f * B.Lf;
         const double cap = 0.5 * B.L * (1.0 - 1e-9);

@@ -218,8 +218,11 @@ __device__ __forceinline__ float wpp_fold4(float x, float y, float z, float u) {
 // predicate. Out of line so that the compiler cannot hoist the FP64 division
 // out of the rare band branches onto every evaluation: with one particle per
 // warp each FP64 instruction costs a full warp slot of the narrow FP64 pipe.
-static __device__ __noinline__ double wpp_hh(float h, double L) {
-    const double Hd = (double)h * 4294967296.0 / L;
+// Without the division when L is a power of two: then h 2^32 / L = h S
+// exactly (S = 2^32 / L is a power of two), a product in place of a
+// division's instruction sequence; the value is the same.
+static __device__ __noinline__ double wpp_hh(float h, const BoxDesc& B) {
+    const double Hd = B.pow2 ? (double)h * B.S : (double)h * 4294967296.0 / B.L;
     return Hd * Hd;
 }
 

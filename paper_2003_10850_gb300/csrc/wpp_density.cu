@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_density_wpp(WppArgs a) {
                     double HH = -1.0;
                     int nh = 0;
                     auto exact_in = [&](int q) {
-                        if (HH < 0.0) HH = wpp_hh(h, B.L);
+                        if (HH < 0.0) HH = wpp_hh(h, B);
                         return exact_pred(exact_d2(Xi, a.posm[q]), HH);
                     };
                     auto term = [&](float r2, float m) {
@@ -266,7 +266,7 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_density_wpp(WppArgs a) {
                         const float hinv = 1.f / h;
                         const float4 vi = DIVCURL ? a.vpack[p] : make_float4(0.f, 0.f, 0.f, 0.f);
                         auto exact_f = [&](int q) {
-                            if (HHf < 0.0) HHf = wpp_hh(h, B.L);
+                            if (HHf < 0.0) HHf = wpp_hh(h, B);
                             return exact_pred(exact_d2(Xi, a.posm[q]), HHf);
                         };
                         // d = x_j - x_i; r_ij = -d, v_ij = v_i - v_j
@@ -442,7 +442,7 @@ __global__ void __launch_bounds__(256) k_list_ext(const BoxDesc* __restrict__ bo
         }
         const int32_t* lj = nbr + nbr_off[j];
         const BoxDesc& B = boxes[nb == 1 ? 0 : wpp_box(boxes, nb, j)];
-        const float Hs = (float)(4294967296.0 / B.L);   // integer units per box unit
+        const float Hs = B.Hs;   // integer units per box unit
         const uint4 Xj = posm[j];
         const float hj = list_h[j];
         auto decide = [&](float hi, uint4 Xi) {
@@ -451,7 +451,7 @@ __global__ void __launch_bounds__(256) k_list_ext(const BoxDesc* __restrict__ bo
                 const unsigned long long D2 = exact_d2(Xi, Xj);
                 const float d2 = __ull2float_rn(D2), Hi = hi * Hs, H2 = Hi * Hi;
                 if (d2 > H2 * (1.f + band)) x = true;
-                else if (!(d2 < H2 * (1.f - band))) x = !exact_pred(D2, wpp_hh(hi, B.L));
+                else if (!(d2 < H2 * (1.f - band))) x = !exact_pred(D2, wpp_hh(hi, B));
             }
             return x;
         };

@@ -134,10 +134,10 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_force_wpp(WppArgs a) {
                             if (band) {
                                 const unsigned long long D2 = exact_d2(Xi, a.posm[q]);
                                 if (mi) {
-                                    if (HHi < 0.0) HHi = wpp_hh(hi, B.L);
+                                    if (HHi < 0.0) HHi = wpp_hh(hi, B);
                                     in = exact_pred(D2, HHi);
                                 }
-                                if (!in && mj) in = exact_pred(D2, wpp_hh(f.w, B.L));
+                                if (!in && mj) in = exact_pred(D2, wpp_hh(f.w, B));
                             }
                         }
                         tests += __popc(__ballot_sync(0xffffffffu, cand));

@@ -213,6 +213,49 @@ def test_force_lists_that_do_not_fit(S, ctx):
     check_force(g, f, np.arange(p.n), 1e-4)
 
 
+def _sparse_shell_around_clump(seed=12):
+    """64 particles within ~0.001 of the centre, 160 in a sparse shell at
+    0.05-0.15 around them, a uniform background beyond 0.3: every shell
+    particle's h reaches the clump, so clump particles have more than 128
+    extra partners (j with h_i <= r_ij < h_j)."""
+    rng = np.random.default_rng(seed)
+    c = np.array([0.5, 0.5, 0.5])
+    clump = c + 0.001 * rng.standard_normal((64, 3))
+    v = rng.standard_normal((160, 3))
+    v /= np.linalg.norm(v, axis=1)[:, None]
+    shell = c + v * rng.uniform(0.05, 0.15, (160, 1))
+    bg = rng.uniform(0, 1, (20000, 3))
+    bg = bg[np.linalg.norm(bg - c, axis=1) > 0.3]
+    pos = np.concatenate([clump, shell, bg])
+    n = len(pos)
+    return as_f32(W.Particles(pos, rng.normal(0, 0.1, (n, 3)), np.full(n, 1.0 / n), rng.uniform(0.5, 1.5, n), 1.0))
+
+
+def test_extra_partner_segments_that_overflow(S, ctx):
+    """Particles with more than 128 extra partners overflow their fixed
+    segments: the force pass walks for them and reads the lists for the
+    rest, with the oracle's results."""
+    p = _sparse_shell_around_clump()
+    X, d, _ = oracle_all(p)
+    h, rho, om = _oracle_inputs32(d)
+    oi, oj = oracle.pair_list(X, h.astype(np.float64))
+    xu = X.astype(np.int64)
+    dd = (xu[oj] - xu[oi] + 2**31) % 2**32 - 2**31
+    r = np.sqrt((dd.astype(np.float64) ** 2).sum(1)) / 2**32
+    n_ext = np.bincount(oi[r >= h[oi]], minlength=p.n)
+    assert (n_ext > 128).sum() >= 8            # the input overflows some segments
+    params = S.default_params(box=p.box)
+    grid = gpu_grid(S, ctx, p, params)
+    gd = gpu_density(S, ctx, grid, h, S.default_params(box=p.box, flags=S.SPH_FIXED_H))
+    assert gd["rc"] == 0
+    f = oracle.force(X, p.vel, p.mass, p.u, h, rho, om, box=p.box)
+    g = gpu_force(S, ctx, grid, p, h, rho, om, params)
+    # a changed h makes every particle walk: the candidate tests of a full walk
+    walk = gpu_force(S, ctx, grid, p, (h * np.float32(1.0001)).astype(np.float32), rho, om, params)
+    assert g["rc"] == 0 and 0 < g["stats"]["pair_tests"] < walk["stats"]["pair_tests"] // 10
+    check_force(g, f, np.arange(p.n), 1e-4)
+
+
 def test_no_lists_grid(S, ctx, clustered50k):
     """A grid built with SPH_NO_LISTS records nothing; the force pass walks."""
     p, (X, d, _) = clustered50k
