@@ -35,8 +35,9 @@ namespace sph {
 constexpr int kWppWarps = 4;
 constexpr int kWppThreads = kWppWarps * 32;
 // Register budgets: 8 resident blocks (32 warps, 64 registers) or 6 (24 warps,
-// 80 registers); the launch takes the one matching blocks_per_sm. The
-// autotuner picks between them per pass.
+// 80 registers), and for the density pass also 7 (28 warps, 72 registers);
+// the launch takes the one matching blocks_per_sm. The autotuner picks
+// between them per pass.
 constexpr int kWppDensityBps = 8;
 constexpr int kWppForceBps = 8;
 constexpr int kWppMaxBps = 16;

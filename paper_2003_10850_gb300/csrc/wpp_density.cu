@@ -589,8 +589,10 @@ cudaError_t launch_density_wpp(sph_ctx* ctx, const DensityLaunch& a, int64_t n_a
     const bool dc = a.divv != nullptr;
     auto kd = bps <= 6 ? (a.hash ? (dc ? k_density_wpp<true, 6, true> : k_density_wpp<true, 6, false>)
                                  : (dc ? k_density_wpp<false, 6, true> : k_density_wpp<false, 6, false>))
-                       : (a.hash ? (dc ? k_density_wpp<true, 8, true> : k_density_wpp<true, 8, false>)
-                                 : (dc ? k_density_wpp<false, 8, true> : k_density_wpp<false, 8, false>));
+              : bps == 7 ? (a.hash ? (dc ? k_density_wpp<true, 7, true> : k_density_wpp<true, 7, false>)
+                                   : (dc ? k_density_wpp<false, 7, true> : k_density_wpp<false, 7, false>))
+                         : (a.hash ? (dc ? k_density_wpp<true, 8, true> : k_density_wpp<true, 8, false>)
+                                   : (dc ? k_density_wpp<false, 8, true> : k_density_wpp<false, 8, false>));
     kd<<<blocks, kWppThreads, 0, s>>>(c);
     ++ctx->launches;
     // SPH_TIME_KERNELS times the density kernel alone; the list build follows

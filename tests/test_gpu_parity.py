@@ -133,6 +133,23 @@ def test_density_converged(S, ctx, kind, fp64, path, lattice32, clustered50k):
     assert rel(g2["h"], d["h"]).max() <= 1e-5
 
 
+@pytest.mark.parametrize("bps", [6, 7, 8])
+def test_register_budgets_agree(S, ctx, bps, clustered50k):
+    """The default path's kernels at each register budget the autotuner can
+    pick (blocks per SM 6, 7, 8): converged density and the force from the
+    recorded lists against the oracle, pair sets exact."""
+    p, (X, d, _) = clustered50k
+    params = S.default_params(box=p.box, blocks_per_sm=bps)
+    grid = gpu_grid(S, ctx, p, params)
+    g = gpu_density(S, ctx, grid, W.perturb(d["h"], 0.02, seed=4).astype(np.float32), params)
+    _density_converged_checks(g, p, X, d, False)
+    h, rho, om = (g[k].astype(np.float32) for k in ("h", "rho", "omega"))
+    f = oracle.force(X, p.vel, p.mass, p.u, h, rho, om, box=p.box)
+    gf = gpu_force(S, ctx, grid, p, h, rho, om, params)
+    assert gf["rc"] == 0 and gf["stats"]["pair_tests"] == 0
+    check_force(gf, f, np.arange(p.n), 1e-4)
+
+
 def test_density_plain_fp32(S, ctx, clustered50k):
     p, (X, d, _) = clustered50k
     params = S.default_params(box=p.box, flags=S.SPH_PLAIN_FP32)
