@@ -47,7 +47,7 @@ DENSITY_DRAM_BYTES_PER_ACTIVE = 592.064768e6 / 2_000_000
 H_PERTURB = 0.02            # per-step log-normal scatter of the h guesses: the density change between steps
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -59,7 +59,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the batched-boxes and adjoint lines")
     ap.add_argument("--cpu-n", type=int, default=1 << 20, help="particles of the CPU-baseline sample")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 def peaks():
@@ -617,6 +617,21 @@ def adjoint_line(S, ctx, dev, reps=3):
             "pair_visits_per_s": 3 * stt["force_pairs"] / (ms / reps / 1e3)}
 
 
+def over_ranks(ms_step, pairs_step, dist, device):
+    """Whole-job figures of a run of independent replicas, one per rank: the
+    slowest rank's time per step and the pairs of all ranks (no data moves
+    between ranks but these two numbers)."""
+    if dist is None:
+        return ms_step, pairs_step
+    import torch
+    t = torch.tensor([ms_step, pairs_step], dtype=torch.float64, device=device)
+    mx = t.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    sm = t.clone()
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return float(mx[0]), float(sm[1])
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -659,15 +674,7 @@ def main():
     ms_step = res_g["ms"] / args.steps
     pairs_step = res_g["pairs"] / args.steps
     active_per_launch = sum(int(a.numel()) for a in wl["acts"]) / len(wl["acts"])
-    if dist is not None:
-        t = torch.tensor([ms_step, pairs_step], dtype=torch.float64, device=dev)
-        mx = t.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm = t.clone()
-        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-        ms_step, pairs_total = float(mx[0]), float(sm[1])
-    else:
-        pairs_total = pairs_step
+    ms_step, pairs_total = over_ranks(ms_step, pairs_step, dist, dev)
     value = pairs_total / (ms_step / 1e3)
 
     plain = None
