@@ -28,7 +28,7 @@
 // so the pair terms run with every lane busy. The pair term is
 //   a_i += G m_j K(r) (x_j - x_i),  K(r) = M(r/h_s) g(r) / r^3,
 // M the spline softening's mass fraction, g(r) = erfc(r/2r_s) + r/(r_s sqrt(pi))
-// exp(-r^2/4r_s^2) the short-range factor.
+// exp(-r^2/4r_s^2) the short-range factor (erfc to 1.5e-7, see grav_K).
 #include <cmath>
 
 #include "wpp.cuh"
@@ -64,7 +64,7 @@ struct GravArgs {
     float G;
     unsigned long long P;    // rint(theta^2 2^16)
     float hs, inv_hs;        // softening radius (0: none)
-    float inv2rs, c_rs;      // 1 / (2 r_s), 1 / (r_s sqrt(pi)); r_s <= 0: inv2rs = 0
+    float inv2rs;            // 1 / (2 r_s); r_s <= 0: 0
 };
 
 // Leaf moments: mass and centre of mass relative to the node centre.
@@ -123,9 +123,13 @@ __global__ void k_grav_box_rc(const BoxDesc* __restrict__ boxes, int nb, double 
     rci[b] = (unsigned long long)ceil(rcu * rcu);
 }
 
-// M(q) g(r) / r^3 for r^2 = r2 > 0.
-__device__ __forceinline__ float grav_K(const GravArgs& a, float r2) {
-    const float r = sqrtf(r2);
+// M(q) g(r) / r^3 for r^2 = r2 > 0, and r.
+// The split factor g = erfc(x) + (2/sqrt(pi)) x e^{-x^2}, x = r / (2 r_s), takes
+// erfc from Abramowitz & Stegun 7.1.26 (Hastings' rational approximation,
+// |error| <= 1.5e-7): erfc(x) = t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) e^{-x^2},
+// t = 1 / (1 + p x), so that both terms share one exponential.
+__device__ __forceinline__ float grav_K(const GravArgs& a, float r2, float& r) {
+    r = r2 * rsqrtf(r2);
     float Mq = 1.f;
     if (r < a.hs) {   // mass fraction of the cubic spline (support 1) inside q
         const float q = r * a.inv_hs, q2 = q * q, q3 = q2 * q;
@@ -136,7 +140,11 @@ __device__ __forceinline__ float grav_K(const GravArgs& a, float r2) {
     float g = 1.f;
     if (a.inv2rs > 0.f) {
         const float x = r * a.inv2rs;
-        g = fmaf(r * a.c_rs, expf(-x * x), erfcf(x));
+        const float t = __fdividef(1.f, fmaf(0.3275911f, x, 1.f));
+        const float poly =
+            t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f),
+                     0.254829592f);
+        g = __expf(-x * x) * fmaf(1.1283791671f, x, poly);   // 2 / sqrt(pi) = 1.1283791671
     }
     return __fdividef(Mq * g, r2 * r);   // r^3 stays far inside the normal range
 }
@@ -221,11 +229,12 @@ __global__ void __launch_bounds__(kWppThreads) k_gravity(GravArgs a) {
                     const float4 h = hb[lane];
                     const float r2 = h.x * h.x + h.y * h.y + h.z * h.z;
                     if (r2 > 0.f) {
-                        const float f = a.G * h.w * grav_K(a, r2);
+                        float r;
+                        const float f = a.G * h.w * grav_K(a, r2, r);
                         ax = fmaf(f, h.x, ax);
                         ay = fmaf(f, h.y, ay);
                         az = fmaf(f, h.z, az);
-                        sc = fmaf(fabsf(f), sqrtf(r2), sc);
+                        sc = fmaf(fabsf(f), r, sc);
                     }
                 }
                 nh -= k;   // <= 31 left: move hb[32..nh+32) down
@@ -366,7 +375,6 @@ cudaError_t launch_gravity(sph_ctx* ctx, const GravityLaunch& L, int64_t n_activ
     a.hs = (float)L.h_soft;
     a.inv_hs = L.h_soft > 0.0 ? (float)(1.0 / L.h_soft) : 0.f;
     a.inv2rs = L.r_split > 0.0 ? (float)(0.5 / L.r_split) : 0.f;
-    a.c_rs = L.r_split > 0.0 ? (float)(1.0 / (L.r_split * std::sqrt(3.141592653589793))) : 0.f;
     const long long want = (n_active + kWppWarps - 1) / kWppWarps;
     const int blocks = (int)std::max<long long>(1, std::min<long long>((long long)ctx->sm_count * 8, want));
     k_gravity<<<blocks, kWppThreads, 0, s>>>(a);
