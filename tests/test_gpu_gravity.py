@@ -3,9 +3,10 @@ oracle, through the C ABI.
 
 Every decision of the walk (skip, monopole, open; pair inside the cutoff) is
 exact integer arithmetic on both sides, so the per-particle node and pair
-counts must agree exactly. The accelerations differ only by FP32 rounding
-(pair terms, node centres of mass, sums): within 2e-5 of the per-particle
-scale sum |G m K(r) r| (about 300 FP32 roundings of the largest terms).
+counts must agree exactly. The accelerations differ by FP32 rounding (pair
+terms, node centres of mass, sums) and by the kernel's erfc approximation
+(Abramowitz & Stegun 7.1.26: at most 1.2e-5 of a term's split factor, in
+FP32): within 2e-5 of the per-particle scale sum |G m K(r) r|.
 """
 import numpy as np
 import pytest
