@@ -31,9 +31,12 @@ __device__ __forceinline__ unsigned long long spread3(unsigned v) {
     return x;
 }
 
-__device__ __forceinline__ unsigned quantize1(double x, double L, bool& bad) {
+// x / L is a product when L is a power of two: x * (S 2^-32) with S = 2^32 / L
+// exact, so the value is the division's (FP64 division is a long sequence on
+// the narrow FP64 pipe).
+__device__ __forceinline__ unsigned quantize1(double x, const BoxDesc& B, bool& bad) {
     if (!isfinite(x)) { bad = true; return 0u; }
-    double t = x / L;
+    double t = B.pow2 ? x * (B.S * 2.3283064365386962890625e-10) : x / B.L;
     t = t - floor(t);
     double v = rint(t * 4294967296.0);
     if (v >= 4294967296.0) v -= 4294967296.0;
@@ -42,7 +45,7 @@ __device__ __forceinline__ unsigned quantize1(double x, double L, bool& bad) {
 
 template <typename P>
 __global__ void k_quantize(const P* __restrict__ pos, const float* __restrict__ mass, int n,
-                           const long long* __restrict__ box_off, const double* __restrict__ box_L,
+                           const long long* __restrict__ box_off, const BoxDesc* __restrict__ boxes,
                            int nb, int bb, uint4* __restrict__ xq, unsigned long long* __restrict__ keys,
                            unsigned* __restrict__ vals, Counters* ctr) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -52,11 +55,11 @@ __global__ void k_quantize(const P* __restrict__ pos, const float* __restrict__ 
         int mid = (lo + hi + 1) >> 1;
         if (box_off[mid] <= i) lo = mid; else hi = mid - 1;
     }
-    double L = box_L[lo];
+    const BoxDesc& B = boxes[lo];
     bool bad = false;
-    unsigned X = quantize1((double)pos[3 * (size_t)i], L, bad);
-    unsigned Y = quantize1((double)pos[3 * (size_t)i + 1], L, bad);
-    unsigned Z = quantize1((double)pos[3 * (size_t)i + 2], L, bad);
+    unsigned X = quantize1((double)pos[3 * (size_t)i], B, bad);
+    unsigned Y = quantize1((double)pos[3 * (size_t)i + 1], B, bad);
+    unsigned Z = quantize1((double)pos[3 * (size_t)i + 2], B, bad);
     float m = mass[i];
     if (!(m > 0.f) || !isfinite(m)) bad = true;
     if (bad) atomicOr(&ctr->status, ST_INVALID);
@@ -450,10 +453,10 @@ static void grid_fill(sph_grid* g, const void* pos, int f64, const float* mass, 
     const int n = (int)g->n, nb = g->n_boxes;
     const int blocks = (n + 255) / 256;
     if (f64)
-        k_quantize<double><<<blocks, 256, 0, s>>>((const double*)pos, mass, n, g->d_off, g->d_L, nb, g->box_bits,
+        k_quantize<double><<<blocks, 256, 0, s>>>((const double*)pos, mass, n, g->d_off, g->boxes, nb, g->box_bits,
                                                   g->xq, (unsigned long long*)g->keys, g->v1, ctx->counters);
     else
-        k_quantize<float><<<blocks, 256, 0, s>>>((const float*)pos, mass, n, g->d_off, g->d_L, nb, g->box_bits,
+        k_quantize<float><<<blocks, 256, 0, s>>>((const float*)pos, mass, n, g->d_off, g->boxes, nb, g->box_bits,
                                                  g->xq, (unsigned long long*)g->keys, g->v1, ctx->counters);
     ++ctx->launches;
     radix_sort((unsigned long long*)g->keys, g->v1, g->k2, g->v2, n, 63, g->counts, g->cscan, g->scan_tmp, s,

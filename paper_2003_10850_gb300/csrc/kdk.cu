@@ -84,14 +84,16 @@ __global__ void k_kick(int na, const int32_t* __restrict__ active, const uint8_t
     }
 }
 
-// x += v dt in FP64, wrapped into [0, L); v_pred += a dt, u_pred += du/dt dt
+// x += v dt in FP64, wrapped into [0, L); v_pred += a dt, u_pred += du/dt dt.
+// invL > 0: L is a power of two and invL = 1/L exactly, so x * invL is x / L
+// without the FP64 division.
 __global__ void k_drift(int n, double* __restrict__ pos, const float* __restrict__ vel, double dt, double L,
-                        const float* __restrict__ acc, const float* __restrict__ dudt, float* __restrict__ vel_pred,
-                        float* __restrict__ u_pred) {
+                        double invL, const float* __restrict__ acc, const float* __restrict__ dudt,
+                        float* __restrict__ vel_pred, float* __restrict__ u_pred) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= 3 * n) return;
     double x = fma((double)vel[t], dt, pos[t]);
-    x -= L * floor(x / L);
+    x -= L * floor(invL > 0.0 ? x * invL : x / L);
     if (x >= L) x -= L;
     pos[t] = x;
     if (vel_pred) {
@@ -207,7 +209,9 @@ sph_status sph_drift(sph_ctx* ctx, double* pos, const float* vel, int64_t n, dou
     if (cudaSetDevice(ctx->device)) return kdk_fail(ctx, SPH_ERR_CUDA, "cudaSetDevice failed");
     cudaStream_t s = (cudaStream_t)stream;
     const int m = (int)(3 * n);
-    k_drift<<<(m + 255) / 256, 256, 0, s>>>((int)n, pos, vel, dt, box, acc, dudt, vel_pred, u_pred);
+    int ex = 0;
+    const double invL = std::frexp(box, &ex) == 0.5 ? 1.0 / box : 0.0;
+    k_drift<<<(m + 255) / 256, 256, 0, s>>>((int)n, pos, vel, dt, box, invL, acc, dudt, vel_pred, u_pred);
     ++ctx->launches;
     return cudaGetLastError() ? kdk_fail(ctx, SPH_ERR_CUDA, "sph_drift launch failed") : SPH_OK;
 }
