@@ -39,6 +39,7 @@ METRIC = "SPH pair-interactions/s (density+force) at 10M particles, vs plain FP3
 UNIT = "pairs/s"
 FLOPS_DENSITY_PAIR = 30.0   # FP32 flops per density pair (FMA = 2), one pass at the converged h
 FLOPS_FORCE_PAIR = 90.0     # FP32 flops per force pair
+FLOPS_GRAV_INTERACTION = 40.0   # FP32 flops per gravity interaction (softened, split pair or node term)
 FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) of one k_density_wpp launch per active particle: 592.06 MB measured by
 # ncu (dram__bytes_read.sum + dram__bytes_write.sum) on the 2,000,000-particle 100 % sub-step of
@@ -577,6 +578,7 @@ def gravity_line(S, ctx, wl, reps=3):
     return {"workload": "10M clustered, all active: short-range gravity (TreePM split, r_s = 1.25 mean spacings, "
                         "r_cut = 4.5 r_s), Barnes-Hut walk at theta = 0.5, node moments included",
             "value": (nodes + pairs) / (ms / 1e3), "unit": "interactions/s", "ms_per_pass": ms / reps,
+            "achieved_tflops": FLOPS_GRAV_INTERACTION * (nodes + pairs) / (ms / 1e3) / 1e12,
             "node_interactions_per_particle": nodes / reps / n, "pair_interactions_per_particle": pairs / reps / n}
 
 
