@@ -740,6 +740,14 @@ def main():
         cpu = {"value": pr / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
                "sample": f"same generator at N={args.cpu_n} (blobs ~ sqrt N), all active, density from "
                          f"perturbed converged h + force, one step, {dt:.1f} s"}
+        # the same step on one core, on a sixteenth of the sample
+        n1 = max(4096, args.cpu_n // 16)
+        s1 = oracle_sample(n1)
+        prev = oracle.set_threads(1)
+        pr1, dt1 = oracle_step(s1)
+        oracle.set_threads(prev)
+        cpu["one_core"] = {"value": pr1 / dt1, "unit": UNIT, "cores": 1,
+                           "sample": f"same generator at N={n1}, one step, {dt1:.1f} s"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

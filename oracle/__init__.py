@@ -63,6 +63,8 @@ def lib():
         L.orc_neighbours.argtypes = [i32, P, P, i64, f64, i64, f64, i32, P, i64]
         L.orc_neighbours.restype = i64
         L.orc_num_threads.restype = i32
+        L.orc_set_threads.argtypes = [i32]
+        L.orc_set_threads.restype = i32
         L.orc_gravity.argtypes = [P, i64, f64, P, f64, f64, f64, f64, f64, P, i64, P, P, P, P]
         L.orc_soft_mass.argtypes = [f64]
         L.orc_soft_mass.restype = f64
@@ -82,6 +84,11 @@ def _c(a, dt):
 
 def num_threads() -> int:
     return int(lib().orc_num_threads())
+
+
+def set_threads(t: int) -> int:
+    """Threads of the oracle's later parallel regions; returns the previous count."""
+    return int(lib().orc_set_threads(int(t)))
 
 
 def quantize(pos, box: float = 1.0) -> np.ndarray:

@@ -730,6 +730,17 @@ int orc_num_threads(void)
 #endif
 }
 
+/* Threads of the following parallel regions (the 1-core timing of the CPU
+ * baseline); returns the previous count. */
+int orc_set_threads(int t)
+{
+    int old = orc_num_threads();
+#ifdef _OPENMP
+    if (t > 0) omp_set_num_threads(t);
+#endif
+    return old;
+}
+
 /* Vectorised kernel evaluation for the pins (w, dw/dq at each q). */
 void orc_kernel_array(const double *q, int64_t n, double *w, double *dw)
 {
