@@ -58,3 +58,21 @@ def test_host_validation_without_gpu(lib):
         == abi.SPH_ERR_INVALID
     assert lib.sph_sync_status(None, None, None) == abi.SPH_ERR_INVALID
     assert lib.sph_last_error(None) == b"context is NULL"
+
+
+def test_later_entry_points_reject_a_null_context_without_gpu(lib):
+    """The time-integration, viscosity and gravity entry points check their
+    context before any CUDA call."""
+    from paper_2003_10850_gb300 import abi
+    gp = abi.sph_gravity_params(1.0, 0.5, 0.0, 0.1, 0.0)
+    dts = (ctypes.c_double * 1)(0.1)
+    assert lib.sph_gravity(None, None, None, 0, ctypes.byref(gp), None, None, None, None) == abi.SPH_ERR_INVALID
+    assert lib.sph_visc_rate(None, None, 0, None, None, None, None, 5 / 3, 0.1, 1.0, 0.2, None, None) \
+        == abi.SPH_ERR_INVALID
+    assert lib.sph_kick_scalar(None, None, 0, None, dts, 1, None, None, None, None) == abi.SPH_ERR_INVALID
+    assert lib.sph_predict_scalar(None, 1, 0.1, None, None, None) == abi.SPH_ERR_INVALID
+    assert lib.sph_timebins(None, None, None, None, 0, 1, 0, 0.3, 1.0, 2, None, None) == abi.SPH_ERR_INVALID
+    assert lib.sph_drift(None, None, None, 1, 0.1, 1.0, None, None, None, None, None) == abi.SPH_ERR_INVALID
+    p = abi.default_params()
+    assert lib.sph_hydro_force_visc(None, None, None, None, None, None, None, None, None, None, None, 0, None,
+                                    None, None, None, ctypes.byref(p), None) == abi.SPH_ERR_INVALID
