@@ -68,7 +68,7 @@ typedef enum {
                                      compacted leaf lists and hit buffers */
 #define SPH_NO_LISTS 0x400        /* sph_build_grid: do not allocate the neighbour lists that the
                                      default path records in an all-active density pass and reuses
-                                     in the force pass (saves ~790 bytes per particle) */
+                                     in the force pass (saves ~1,040 bytes per particle) */
 
 /* Device status bits returned in sph_stats.status */
 #define SPH_ST_NOT_CONVERGED 0x01
