@@ -139,3 +139,19 @@ def test_barnes_hut_error_falls_with_theta():
             assert np.median(err / an) < 3e-3
     assert q99[0] < q99[1] < q99[2] and q99[0] < 0.02
     assert nodes[0] < nodes[1] < nodes[2] and pairs[0] > pairs[1] > pairs[2]
+
+
+def test_relabelling_the_particles_changes_nothing():
+    """The tree is built from the positions (ties of equal keys by index), so a
+    relabelling of particles with distinct keys gives the same walk for every
+    particle: results equal, bit for bit, after undoing the relabelling.
+    Catches index mix-ups between sorted and caller order."""
+    p = W.clustered(5000, 6, seed=21)
+    X = oracle.quantize(p.pos)
+    assert len(np.unique(oracle.morton_keys(X))) == p.n
+    g = oracle.gravity(X, p.mass, theta=0.6, **SPLIT)
+    perm = np.random.default_rng(4).permutation(p.n)
+    gp = oracle.gravity(X[perm], p.mass[perm], theta=0.6, **SPLIT)
+    inv = np.argsort(perm)
+    for k in ("acc", "scale", "n_nodes", "n_pairs"):
+        assert np.array_equal(gp[k][inv], g[k])
