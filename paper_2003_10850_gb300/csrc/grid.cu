@@ -43,6 +43,21 @@ __device__ __forceinline__ unsigned quantize1(double x, const BoxDesc& B, bool& 
     return (unsigned)(unsigned long long)v;
 }
 
+// FP32 positions inside [0, L) of a power-of-two box take an FP32 path with
+// the same result: t = x / L is in [0, 1), so frac(t) = t, and t 2^32 = x Hs
+// (Hs = 2^32 / L, a power of two) is exact in FP32; rint of that float is the
+// FP64 rint of the same value. Everything else takes the FP64 definition.
+__device__ __forceinline__ unsigned quantize_p(float x, const BoxDesc& B, bool& bad) {
+    if (B.pow2 && x >= 0.f && x < B.Lf && (double)B.Lf == B.L) {
+        const float v = rintf(x * B.Hs);
+        return v >= 4294967296.0f ? 0u : (unsigned)(unsigned long long)v;
+    }
+    return quantize1((double)x, B, bad);
+}
+__device__ __forceinline__ unsigned quantize_p(double x, const BoxDesc& B, bool& bad) {
+    return quantize1(x, B, bad);
+}
+
 template <typename P>
 __global__ void k_quantize(const P* __restrict__ pos, const float* __restrict__ mass, int n,
                            const long long* __restrict__ box_off, const BoxDesc* __restrict__ boxes,
@@ -57,9 +72,9 @@ __global__ void k_quantize(const P* __restrict__ pos, const float* __restrict__ 
     }
     const BoxDesc& B = boxes[lo];
     bool bad = false;
-    unsigned X = quantize1((double)pos[3 * (size_t)i], B, bad);
-    unsigned Y = quantize1((double)pos[3 * (size_t)i + 1], B, bad);
-    unsigned Z = quantize1((double)pos[3 * (size_t)i + 2], B, bad);
+    unsigned X = quantize_p(pos[3 * (size_t)i], B, bad);
+    unsigned Y = quantize_p(pos[3 * (size_t)i + 1], B, bad);
+    unsigned Z = quantize_p(pos[3 * (size_t)i + 2], B, bad);
     float m = mass[i];
     if (!(m > 0.f) || !isfinite(m)) bad = true;
     if (bad) atomicOr(&ctr->status, ST_INVALID);

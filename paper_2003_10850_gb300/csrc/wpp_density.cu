@@ -490,7 +490,13 @@ __global__ void __launch_bounds__(256) k_list_sort(int n, int32_t* __restrict__ 
         const int c = (int)cu;
         if (c < 2) continue;
         int32_t* seg = ext + (size_t)i * kExtCap;
-        if (c <= 64) {
+        if (c <= 32) {   // one entry per lane: its rank among the c
+            const int v0 = (int)lane < c ? seg[lane] : 0x7fffffff;
+            int r0 = 0;
+            for (int k = 0; k < c; ++k) r0 += __shfl_sync(0xffffffffu, v0, k) < v0;
+            __syncwarp();   // every lane has read the segment before it is overwritten
+            if ((int)lane < c) seg[r0] = v0;
+        } else if (c <= 64) {
             const int v0 = (int)lane < c ? seg[lane] : 0x7fffffff;
             const int v1 = (int)lane + 32 < c ? seg[lane + 32] : 0x7fffffff;
             int r0 = 0, r1 = 0;
