@@ -100,3 +100,26 @@ def test_courant_bin_rule():
     # a tick off a bin's boundary raises the bin
     b5 = K.timebins(h, vs, 0.3, 0.08, 4, tick=2)
     assert np.all(b5 >= 3) and np.all((2 % (1 << (4 - b5.astype(int)))) == 0)
+
+
+def test_energy_second_order_with_time_dependent_viscosity_and_switch():
+    """With per-particle alpha (integrated like u) and Balsara's switch the pair
+    terms stay symmetric, so total energy is still conserved to second order in
+    dt and momentum exactly on one shared step."""
+    p = _gas(seed=5)
+    n = p.n
+    bins = np.zeros(n, np.uint8)
+    visc = {"alpha0": 0.6, "alpha_min": 0.1, "alpha_max": 1.0, "ell": 0.2}
+    T = 0.04
+    e0 = (p.mass * (0.5 * (p.vel * p.vel).sum(1) + p.u)).sum()
+    mom0 = (p.mass[:, None] * p.vel).sum(0)
+    errs = []
+    for k in (4, 8):
+        r = K.KDK(p.pos, p.vel, p.mass, p.u, bins, T / k, 0, balsara=True, visc=visc)
+        for _ in range(k):
+            r.step()
+        e, mom = _energy(r)
+        errs.append(abs(e - e0))
+        assert np.abs(mom - mom0).max() <= 1e-14 * np.abs(p.mass[:, None] * p.vel).sum()
+        assert np.ptp(r.synchronized_alpha()) > 1e-3          # the alphas evolved apart
+    assert errs[1] < errs[0] and 2.5 < errs[0] / errs[1] < 6.0
