@@ -180,8 +180,10 @@ sph_status sph_grid_export(const sph_grid *grid, int32_t *perm, uint64_t *keys, 
  * For each active i (the caller indices in `active[0..n_active)`, device
  * int32, no duplicates; active = NULL means all particles):
  *   h_i solves N_eff(h) = (4 pi/3) h^3 sum_j W(r_ij, h) = N_t (self included,
- *   W = M4 cubic spline with support h) to |N_eff - N_t| <= n_tol, by
- *   bracketed Newton/bisection in FP64, starting from h[i] (in/out, box units);
+ *   W = M4 cubic spline with support h) to |N_eff - N_t| <= n_tol (or until
+ *   the bracket is one float wide: h is stored in FP32), by a bracketed,
+ *   bisection-safeguarded Newton iteration on N_eff^(1/3), starting from h[i]
+ *   (in/out, box units);
  *   rho_i   = sum_j m_j W(r_ij, h_i)                (self included)
  *   omega_i = [1 + h_i/(3 rho_i) d rho_i/d h_i]^-1  (grad-h factor)
  *   n_ngb_i = #{j != i : r_ij < h_i} under the exact predicate
@@ -190,8 +192,12 @@ sph_status sph_grid_export(const sph_grid *grid, int32_t *perm, uint64_t *keys, 
  *   hash_i  = optional (NULL to skip) checksum of the neighbour set:
  *             sum over j of splitmix64(caller index j), mod 2^64.
  * With SPH_FIXED_H the sums are evaluated once at the given h.
- * Arithmetic: FP32 pair terms, per-batch compensated (Kahan) accumulation,
- * FP64 h update; SPH_FP64 computes everything in FP64.
+ * Arithmetic (default path): FP32 pair terms; per-lane FP32 partial sums
+ * folded across the lanes that share a particle by error-free (TwoSum)
+ * transformations and rounded once; the h update in FP32 on the compensated
+ * N_eff; FP64 only in the exact neighbour predicate, for the rare pairs
+ * within 2^-20 of the radius. SPH_PER_THREAD_WALK keeps an FP64 bracket and
+ * h update; SPH_FP64 computes everything in FP64.
  * Neighbour lists (default path, grid built without SPH_NO_LISTS): when every
  * particle is active the call records each particle's set {j != i : r_ij <
  * h_i} at its final h in the grid, and, for each i, the partners j with
@@ -444,11 +450,19 @@ sph_status sph_backward(sph_ctx *ctx, const sph_grid *grid, const float *vel, co
  *   pointers); SPH_ERR_CUDA if a CUDA call fails.
  * Runs asynchronously on `stream` on the current device. Its scratch is a
  * fixed device array of about 12.6 MB inside the library, which every GPU
- * that loads the library holds until the process exits. The first call on a
- * device looks up that array's address (set-up); make that first call before
- * any stream capture. All calls on a device share the array: calls whose
+ * that uses it holds until the process exits. Every call looks up that
+ * array's address in the current context (no allocation), so a context that
+ * was reset and created again is handled. Set-up: under lazy module loading
+ * (CUDA_MODULE_LOADING=LAZY, CUDA's default) the array is created when this
+ * module is first used on a device -- by the first call, unless another
+ * kernel of the library ran there before -- which allocates and may
+ * synchronise; make that first call before any stream capture and outside
+ * any memory budget. All calls on a device share the array: calls whose
  * kernels overlap on the GPU (different streams, or different host threads)
- * race and corrupt each other's results -- serialise them.
+ * race and corrupt each other's results -- serialise them. Nothing needs
+ * clearing between calls: every scratch word a call reads it wrote itself.
+ * SPH_ERR_CUDA, without launching, if a CUDA error is already pending on the
+ * calling thread (it is left pending for its owner).
  */
 #define SPH_SORT_STATIC_MAX_KEYS (1 << 20)
 sph_status sph_sort_keys_static(const uint64_t *keys, int64_t n, uint64_t *sorted_keys,

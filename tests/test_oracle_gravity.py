@@ -155,3 +155,90 @@ def test_relabelling_the_particles_changes_nothing():
     inv = np.argsort(perm)
     for k in ("acc", "scale", "n_nodes", "n_pairs"):
         assert np.array_equal(gp[k][inv], g[k])
+
+
+def _real_criterion_counts(X, theta, r_cut):
+    """Per-particle node and particle interaction counts of the Barnes-Hut walk
+    with the opening criterion in real-valued form, decided in exact rational
+    arithmetic (no 2^16 fixed point, no ceil of the cutoff): in coarse units
+    (integer coordinates / 2^8, gaps rounded down, far distances up) a child of
+    an opened node is skipped if D^2 >= rc^2, taken as its monopole if
+    theta > 0, D > 0, F^2 < rc^2, l <= D and l <= theta D, else opened; a
+    particle of an opened leaf interacts if its coarse distance is below rc.
+    rc = r_cut 2^24 / L. The tree is the one the definition fixes, built here
+    independently: Morton order of the top 21 bits per axis (x most
+    significant), ties by index; leaves of 8; nodes of 8 children; boxes the
+    min/max integer coordinates."""
+    from fractions import Fraction
+    n = X.shape[0]
+    top = (X >> 11).astype(np.uint64)
+    key = np.zeros(n, np.uint64)
+    for b in range(21):
+        for a in range(3):
+            key |= ((top[:, a] >> np.uint64(b)) & np.uint64(1)) << np.uint64(3 * b + 2 - a)
+    order = np.lexsort((np.arange(n), key))
+    levels = []                                   # per level: list of (lo, hi) integer boxes
+    Xs = X[order].astype(np.int64)
+    leaves = [(Xs[p:p + 8].min(0), Xs[p:p + 8].max(0)) for p in range(0, n, 8)]
+    levels.append(leaves)
+    while len(levels[-1]) > 1:
+        prev = levels[-1]
+        levels.append([(np.min([b[0] for b in prev[c:c + 8]], 0), np.max([b[1] for b in prev[c:c + 8]], 0))
+                       for c in range(0, len(prev), 8)])
+    th2 = Fraction(theta) ** 2
+    rc2 = (Fraction(r_cut) * 2**24) ** 2
+    two32 = 1 << 32
+    nodes = np.zeros(n, np.int64)
+    pairs = np.zeros(n, np.int64)
+    for i in range(n):
+        xi = X[i].astype(np.int64)
+        stack = [(len(levels) - 1, 0)]
+        while stack:
+            k, t = stack.pop()
+            if k == 0:
+                for p in range(8 * t, min(8 * t + 8, n)):
+                    j = order[p]
+                    if j == i:
+                        continue
+                    d = (X[j].astype(np.int64) - xi + two32 // 2) % two32 - two32 // 2
+                    if sum((abs(int(c)) >> 8) ** 2 for c in d) < rc2:
+                        pairs[i] += 1
+                continue
+            for c in range(8 * t, min(8 * t + 8, len(levels[k - 1]))):
+                lo, hi = levels[k - 1][c]
+                D2 = F2 = 0
+                l = 0
+                for a in range(3):
+                    x, lo_a, hi_a = int(xi[a]), int(lo[a]), int(hi[a])
+                    if x < lo_a or x > hi_a:
+                        gap = min((lo_a - x) % two32, (x - hi_a) % two32)
+                        far = gap + (hi_a - lo_a)
+                    else:
+                        gap, far = 0, max(x - lo_a, hi_a - x)
+                    D2 += (gap >> 8) ** 2
+                    F2 += (-(-far // 256)) ** 2
+                    l = max(l, (hi_a - lo_a) >> 8)
+                if D2 >= rc2:
+                    continue
+                if theta > 0 and D2 > 0 and F2 < rc2 and l * l <= D2 and l * l <= th2 * D2:
+                    nodes[i] += 1
+                    continue
+                stack.append((k - 1, c))
+    return nodes, pairs
+
+
+@pytest.mark.parametrize("theta", [0.25, 0.5, 0.75, 1.0])
+def test_integer_criterion_is_the_real_one(theta):
+    """Whenever theta^2 2^16 is an integer (theta = 1/4, 1/2, 3/4, 1) the
+    oracle's fixed-point decisions (2^16 l^2 <= rint(theta^2 2^16) D^2 and
+    D^2 < ceil(rc^2)) are the real-valued Barnes-Hut criterion l <= theta D and
+    the cutoff D < rc: node and particle interaction counts of every particle
+    match a walk that decides in exact rational arithmetic."""
+    p = W.clustered(700, 4, seed=77)
+    X = oracle.quantize(np.asarray(p.pos, np.float32).astype(np.float64))
+    r_cut = 0.23
+    g = oracle.gravity(X, p.mass, theta=theta, r_cut=r_cut)
+    nodes, pairs = _real_criterion_counts(X, theta, r_cut)
+    assert nodes.sum() > 0 and pairs.sum() > 0
+    np.testing.assert_array_equal(g["n_nodes"], nodes)
+    np.testing.assert_array_equal(g["n_pairs"], pairs)

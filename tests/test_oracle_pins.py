@@ -375,3 +375,39 @@ def test_active_subset_matches_full():
     assert np.all(np.isnan(np.delete(da["h"], act)))
     fa = oracle.force(X, p.vel, p.mass, p.u, d["h"], d["rho"], d["omega"], active=act)
     np.testing.assert_array_equal(fa["acc"][act], f["acc"][act])
+
+
+def _golden_visc():
+    rows = {}
+    path = os.path.join(os.path.dirname(__file__), "golden", "viscosity_pair.txt")
+    with open(path) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                c, *v = line.split()
+                rows[c] = [float(x) for x in v]
+    return rows
+
+
+@pytest.mark.parametrize("case", ["A", "B", "C"])
+def test_viscosity_pair_hand_values(case):
+    """Magnitude of the artificial viscosity: two isolated particles whose a,
+    du/dt and v_sig are worked by hand from the published Gadget-2 / Monaghan
+    (1997) forms (tests/golden/viscosity_pair.txt). A wrong factor (alpha in
+    place of alpha/2, a 2 in place of the 3 in v_sig, the mean density in the
+    wrong place) changes these values."""
+    want = _golden_visc()[case]
+    pos = np.array([[7 / 16, 0.5, 0.5], [9 / 16, 0.5, 0.5]])
+    if case == "A":
+        m, h, rho, om, u, al = [1, 1], [0.25, 0.25], [1, 1], [1, 1], [0.6, 0.6], 1.0
+        v = [[1, 0, 0], [-1, 0, 0]]
+    else:
+        m, h, rho, om, u, al = [1, 2], [0.25, 0.2], [1, 3], [0.9, 1.1], [0.6, 0.2], 0.8
+        v = [[0.5, 0.3, 0], [-1, 0.3, 0.2]] if case == "B" else [[-0.5, 0.3, 0], [1, 0.3, 0.2]]
+    X = oracle.quantize(pos)
+    arr = lambda a: np.asarray(a, np.float64)
+    for brute in (True, False):
+        f = oracle.force(X, arr(v), arr(m), arr(u), arr(h), arr(rho), arr(om), alpha=al, brute=brute)
+        got = [f["acc"][0, 0], f["acc"][1, 0], f["dudt"][0], f["dudt"][1], f["vsig"][0], f["vsig"][1]]
+        np.testing.assert_allclose(got, want, rtol=1e-13, atol=1e-12)
+        np.testing.assert_array_equal(f["acc"][:, 1:], 0.0)
+        np.testing.assert_array_equal(f["n_pairs"], [1, 1])
