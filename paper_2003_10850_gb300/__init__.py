@@ -280,9 +280,25 @@ def sph_sync_status(ctx: Context, raise_on_error: bool = True):
     return rc, st.as_dict()
 
 
+def _check_sort_static(keys, sorted_keys, perm, device):
+    """Host-side checks of sph_sort_keys_static's tensors, made before any
+    launch: the outputs hold exactly as many elements as the keys (a shorter
+    one would be written past its end), and all three live on `device`, the
+    device whose scratch array the call uses."""
+    for name, t in (("keys", keys), ("sorted_keys", sorted_keys), ("perm", perm)):
+        if not isinstance(t, torch.Tensor):
+            raise TypeError(f"{name} must be a tensor")
+        if t.device != device:
+            raise ValueError(f"{name} is on {t.device}, the call runs on {device}")
+    if not (sorted_keys.numel() == perm.numel() == keys.numel()):
+        raise ValueError(f"sorted_keys ({sorted_keys.numel()}) and perm ({perm.numel()}) must hold as many "
+                         f"elements as keys ({keys.numel()})")
+
+
 def sph_sort_keys_static(keys, sorted_keys, perm):
     """Stable sort of int64-viewed uint64 keys without any allocation (see
     include/sph.h): fills sorted_keys and perm. Needs no Context."""
+    _check_sort_static(keys, sorted_keys, perm, torch.device("cuda", torch.cuda.current_device()))
     lib = abi.load()
     rc = lib.sph_sort_keys_static(_ptr(keys, torch.int64, "keys"), keys.numel(),
                                   _ptr(sorted_keys, torch.int64, "sorted_keys"), _ptr(perm, torch.int32, "perm"),

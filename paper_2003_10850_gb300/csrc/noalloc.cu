@@ -9,8 +9,6 @@
 // second key/index buffer and the digit histograms of the radix passes -- is
 // the file-scope device array below, of a fixed size, which every GPU that
 // loads the library holds until the process exits.
-#include <mutex>
-
 #include "internal.cuh"
 
 namespace sph {
@@ -39,24 +37,21 @@ constexpr size_t kScratchBytes = align256(kOffTmp + sizeof(unsigned) * 64);
 
 // The scratch itself. Host code must not use this name as a device address:
 // on the host it names a stand-in object; the device address comes from
-// cudaGetSymbolAddress below.
+// cudaGetSymbolAddress below. Device code could name it directly; the radix
+// kernels are shared with the grid build and take plain pointers instead.
 static __device__ __align__(256) unsigned char g_sort_scratch[kScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_setup_mutex;
-unsigned char* g_scratch_dev[kMaxDevices] = {};
-
-// Once per device, with that device current: look up the array's device address.
+// The array's device address in the current device's context. Looked up on
+// every call (cudaGetSymbolAddress allocates nothing), so a context that was
+// destroyed and created again (cudaDeviceReset) never leaves a stale address
+// behind. Under lazy module loading (CUDA_MODULE_LOADING=LAZY, the default) the
+// first lookup on a device loads this module, which creates the array: that
+// first call is the set-up, and it should come before any stream capture and
+// outside any memory budget.
 sph_status scratch_for_current_device(unsigned char** out) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SPH_ERR_CUDA;
-    std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_dev[dev]) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_sort_scratch) != cudaSuccess || !p) return SPH_ERR_CUDA;
-        g_scratch_dev[dev] = static_cast<unsigned char*>(p);
-    }
-    *out = g_scratch_dev[dev];
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_sort_scratch) != cudaSuccess || !p) return SPH_ERR_CUDA;
+    *out = static_cast<unsigned char*>(p);
     return SPH_OK;
 }
 
@@ -66,6 +61,9 @@ extern "C" sph_status sph_sort_keys_static(const uint64_t* keys, int64_t n, uint
                                            int32_t* perm, void* stream) {
     if (!keys || !sorted_keys || !perm) return SPH_ERR_INVALID;
     if (n < 1 || n > kMaxKeys) return SPH_ERR_INVALID;
+    // An error left pending by earlier, unrelated work on this thread is not
+    // this sort's: report it without launching, and without clearing it.
+    if (cudaPeekAtLastError() != cudaSuccess) return SPH_ERR_CUDA;
     unsigned char* base = nullptr;
     sph_status st = scratch_for_current_device(&base);
     if (st != SPH_OK) return st;
@@ -85,16 +83,20 @@ extern "C" sph_status sph_sort_keys_static(const uint64_t* keys, int64_t n, uint
     if (cudaMemcpyAsync(ka, keys, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
         return SPH_ERR_CUDA;
     sph::k_iota<<<(nn + 255) / 256, 256, 0, s>>>(perm, nn);
+    if (cudaGetLastError() != cudaSuccess) return SPH_ERR_CUDA;
     unsigned launches = 0;
-    // 8 passes of 8 bits over the 63 key bits: an even count, so the result
-    // ends in the caller's buffers
-    for (int shift = 0; shift < 63; shift += 8) {
+    // 8 passes of 8 bits over all 64 key bits: an even count, so the result
+    // ends in the caller's buffers. Each launch is checked as it is queued, and
+    // the first failure stops the sort.
+    for (int shift = 0; shift < 64; shift += 8) {
         sph::k_rs_hist<<<nblk, 256, 0, s>>>(ka, nn, shift, counts, nblk);
+        if (cudaGetLastError() != cudaSuccess) return SPH_ERR_CUDA;
         sph::scan_exclusive<uint32_t>(counts, 256 * nblk, cscan, tmp, s, &launches);
+        if (cudaGetLastError() != cudaSuccess) return SPH_ERR_CUDA;
         sph::k_rs_scatter<<<nblk, 256, 0, s>>>(ka, va, kb, vb, nn, shift, cscan, nblk);
+        if (cudaGetLastError() != cudaSuccess) return SPH_ERR_CUDA;
         std::swap(ka, kb);
         std::swap(va, vb);
     }
-    if (cudaGetLastError() != cudaSuccess) return SPH_ERR_CUDA;
     return SPH_OK;
 }

@@ -50,6 +50,27 @@ def test_static_sort_matches_grid_sort_twice():
     ctx.close()
 
 
+def test_static_sort_full_width_keys_with_duplicates():
+    """Keys over all 64 bits (bit 63 set in about half of them) drawn from
+    1000 values, so that most keys repeat: sorted keys and permutation must
+    equal numpy's stable argsort of the unsigned keys, on two calls in a row
+    (the second reuses the scratch the first left behind)."""
+    import paper_2003_10850_gb300 as S
+    rng = np.random.default_rng(43)
+    for n in (100_003, 65_536):
+        vals = rng.integers(0, 2**64, size=1000, dtype=np.uint64)
+        keys_u = vals[rng.integers(0, 1000, size=n)]
+        assert (keys_u >> np.uint64(63)).any() and not (keys_u >> np.uint64(63)).all()
+        order = np.argsort(keys_u, kind="stable")
+        keys = torch.from_numpy(keys_u.view(np.int64)).cuda()
+        out_keys = torch.full_like(keys, -1)
+        out_perm = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+        S.sph_sort_keys_static(keys, out_keys, out_perm)
+        torch.cuda.synchronize()
+        assert np.array_equal(out_keys.cpu().numpy().view(np.uint64), keys_u[order])
+        assert np.array_equal(out_perm.cpu().numpy(), order.astype(np.int32))
+
+
 def test_static_sort_rejects_oversize():
     import paper_2003_10850_gb300 as S
     from paper_2003_10850_gb300 import abi
