@@ -178,7 +178,10 @@ sph_status sph_grid_export(const sph_grid *grid, int32_t *perm, uint64_t *keys, 
  * Density pass with on-device smoothing-length iteration (paper Sec. 1: the
  * first of the two SPH modules, which iterates until each h settles).
  * For each active i (the caller indices in `active[0..n_active)`, device
- * int32, no duplicates; active = NULL means all particles):
+ * int32; a repeated index counts once and negative entries are skipped, so a
+ * list padded with -1 up to a fixed capacity -- as sph_active_from_bins
+ * writes it -- can be passed whole without reading its count on the host;
+ * active = NULL means all particles):
  *   h_i solves N_eff(h) = (4 pi/3) h^3 sum_j W(r_ij, h) = N_t (self included,
  *   W = M4 cubic spline with support h) to |N_eff - N_t| <= n_tol (or until
  *   the bracket is one float wide: h is stored in FP32), by a bracketed,
@@ -332,11 +335,16 @@ sph_status sph_timebins(sph_ctx *ctx, const float *h, const float *vsig, const i
                         int64_t n, int64_t tick, double courant, double dt_max, int max_bin, uint8_t *bins,
                         void *stream);
 /* The particles that end a step at `tick`, ascending (caller indices) into
- * active (device, capacity n); their count into *n_active (device int32).
- * Uses the grid's scratch (the grid fixes n). */
+ * active[0, count) (device, capacity n), then -1 in every later entry up to n;
+ * the count into *n_active (device int32). The padded list can be passed
+ * whole (n_active = n) to the density, force and kick calls, which skip
+ * negative entries: a time-stepping loop then never reads the count on the
+ * host and can be captured in a CUDA graph. Uses the grid's scratch (the
+ * grid fixes n). */
 sph_status sph_active_from_bins(sph_ctx *ctx, sph_grid *grid, const uint8_t *bins, int64_t tick, int max_bin,
                                 int32_t *active, int32_t *n_active, void *stream);
-/* Kick: for each active i, v_i += a_i dt_bin[bins_i] and u_i += dudt_i dt_bin[bins_i]
+/* Kick: for each active i (negative entries of active skipped),
+ * v_i += a_i dt_bin[bins_i] and u_i += dudt_i dt_bin[bins_i]
  * (FP32 fused multiply-add). dt_bin is a HOST array of n_bins (<= 32) steps.
  * vel_pred, u_pred (both or neither): also receive the kicked values (after a
  * closing half kick these are the synchronized velocity and energy, the

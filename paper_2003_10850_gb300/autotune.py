@@ -20,9 +20,9 @@ from . import (SPH_COOP_WALK, SPH_PER_THREAD_WALK, SPH_WARP_GROUP, default_param
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
 
 # warp-per-particle walks (the default path, flags 0) at several register
-# budgets (density: 80, 72 or 64 registers), the warp-cooperative walks and
+# budgets (density: 128 or 96 registers), the warp-cooperative walks and
 # the per-thread walks
-DENSITY_CANDIDATES = ([dict(flags=0, blocks_per_sm=b) for b in (6, 7, 8)] +
+DENSITY_CANDIDATES = ([dict(flags=0, blocks_per_sm=b) for b in (4, 5)] +
                       [dict(flags=SPH_COOP_WALK, blocks_per_sm=10),
                        dict(flags=SPH_PER_THREAD_WALK, blocks_per_sm=16)])
 FORCE_CANDIDATES = ([dict(flags=0, blocks_per_sm=b) for b in (6, 8)] +

@@ -395,7 +395,8 @@ __global__ void k_mark(const int32_t* __restrict__ active, int na, const int32_t
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= na) return;
     int i = active[k];
-    if (i < 0 || i >= n) { atomicOr(&ctr->status, ST_INVALID); return; }
+    if (i < 0) return;   // a padding entry (a list of fixed capacity whose count lives on the device)
+    if (i >= n) { atomicOr(&ctr->status, ST_INVALID); return; }
     flag[rank[i]] = 1;
 }
 
@@ -457,7 +458,7 @@ void grid_free(sph_grid* g) {
                     g->node_hmax, g->act, g->flag, g->scan, g->scan_tmp, g->box_act, g->n_groups,
                     g->groups, g->list_a, g->list_b, g->st_lo, g->st_hi, g->list_n, g->d_off, g->d_L,
                     g->k2, g->v1, g->v2, g->counts, g->cscan, g->node_c, g->node_e, g->posf,
-                    g->fvel, g->fthermo, g->fposh, g->fvm, g->fbal, g->fcond, g->fvisc, g->node_m, g->box_rci, g->nbr, g->nbr_off, g->nbr_n, g->ext_n, g->ext, g->list_h, g->list_st, g->fb_list, g->bw_ga, g->bw_xbar, g->bw_rd, g->bw_f, g->lcache};
+                    g->fvel, g->fthermo, g->fposh, g->fvm, g->fbal, g->fcond, g->fvisc, g->node_m, g->box_rci, g->nbr, g->nbr_off, g->nbr_n, g->ext_n, g->ext, g->list_h, g->list_st, g->fb_list, g->bw_ga, g->bw_xbar, g->bw_rd, g->bw_f, g->lcache, g->mp_j, g->den_left};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete g;
@@ -574,6 +575,10 @@ sph_status grid_build(sph_ctx* ctx, const void* pos, int f64, const float* mass,
     // a 64 x 32 leaf list per persistent warp of the cooperative density
     // kernel (<= 16 blocks of 3 warps per SM)
     GRID_CHECK(cudaMalloc(&g->lcache, sizeof(int) * (size_t)ctx->sm_count * 16 * 3 * 64 * 32));
+    // the near-list indices of the density pass's member-parallel path, one
+    // block of kMpMembers x kMpCap per persistent warp
+    GRID_CHECK(cudaMalloc(&g->mp_j, sizeof(int32_t) * (size_t)ctx->sm_count * kMpWarpsPerSm * kMpMembers * kMpCap));
+    GRID_CHECK(cudaMalloc(&g->den_left, sizeof(int32_t) * n));
     if (lists) {
         // Neighbour-list pools (int32 offsets: at most 2^31 - 2^12 entries each).
         // Lists are an optimisation: if they cannot be allocated the grid is

@@ -79,6 +79,8 @@ struct sph_grid {
     unsigned* counts = nullptr;
     unsigned* cscan = nullptr;
     int* lcache = nullptr;                 // cooperative density: leaf lists reused across iterations
+    int32_t* mp_j = nullptr;               // density, member-parallel path: near-list indices per persistent warp
+    int32_t* den_left = nullptr;           // density: particles left to the one-particle kernel (n)
     // neighbour lists recorded by an all-active density call on the default path and
     // reused by the force pass (NULL when the grid was built with SPH_NO_LISTS)
     int32_t* nbr = nullptr;                // pool of kListPool * n entries: the lists {j != i : r_ij < h_i}
@@ -101,12 +103,17 @@ struct sph_grid {
 
 namespace sph {
 
-constexpr int kQueues = 5;
+constexpr int kQueues = 8;
 constexpr int kListPool = 128;  // neighbour-list pool entries per particle (lists vary in length)
 constexpr int kExtCap = 128;    // extra-partner segment per particle (262k clustered: mean 24, max 106)
 constexpr unsigned kExtUnusable = 0xffffffffu;
 static_assert((kExtCap & (kExtCap - 1)) == 0 && kExtCap >= 64, "kExtCap: a power of two >= 64 (the segment sort)");
 constexpr int kListChunk = 2048; // pool entries a warp reserves at a time for its particles' lists
+// density, member-parallel path: members per group (the largest work chunk),
+// near-list entries per member, resident warps per SM at most
+constexpr int kMpMembers = 8;
+constexpr int kMpCap = 128;
+constexpr int kMpWarpsPerSm = 64;
 // list_st words: [0] lists written, [1] a list missing (pool full), [2] h
 // changed since the lists were made, [3] fallback count, [4..5] pool entries
 // reserved (64-bit)

@@ -32,6 +32,7 @@ __global__ void k_timebins(int n, const float* __restrict__ h, const float* __re
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (active ? na : n)) return;
     const int i = active ? active[t] : t;
+    if (i < 0 || i >= n) return;   // padding entry of a fixed-capacity list
     const float vs = vsig[i];
     int b = 0;
     if (vs > 0.f) {
@@ -50,10 +51,16 @@ __global__ void k_active_flags(int n, const uint8_t* __restrict__ bins, long lon
     flag[i] = (tick & ((1ll << (max_bin - b)) - 1)) == 0 ? 1 : 0;
 }
 
+// The active particles ascending in active[0, count), then -1 in every entry
+// of active[count, n): the whole array can be passed on with n_active = n,
+// without reading the count on the host (negative entries are skipped).
 __global__ void k_flags_to_list(int n, const uint8_t* __restrict__ flag, const uint32_t* __restrict__ scan,
                                 int32_t* __restrict__ active, int32_t* __restrict__ count) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n && flag[i]) active[scan[i]] = i;
+    if (i < n) {
+        if (flag[i]) active[scan[i]] = i;
+        else active[scan[n] + (i - scan[i])] = -1;
+    }
     if (i == 0) *count = (int32_t)scan[n];
 }
 
@@ -68,6 +75,7 @@ __global__ void k_kick(int na, const int32_t* __restrict__ active, const uint8_t
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= na) return;
     const int i = active[t];
+    if (i < 0) return;   // padding entry of a fixed-capacity list
     const float dt = ks.dt[min((int)bins[i], n_bins - 1)];
     const size_t k = 3 * (size_t)i;
     const float vx = fmaf(acc[k], dt, vel[k]), vy = fmaf(acc[k + 1], dt, vel[k + 1]),
@@ -113,6 +121,7 @@ __global__ void k_visc_rate(int na, const int32_t* __restrict__ active, const fl
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= na) return;
     const int i = active ? active[t] : t;
+    if (i < 0) return;   // padding entry of a fixed-capacity list
     const float c = sqrtf(gg1 * u[i]);
     const float a = alpha[i];
     dalpha[i] = fmaxf(-divv[i], 0.f) * (amax - a) - (a - amin) * (ell * c / h[i]);
@@ -124,6 +133,7 @@ __global__ void k_kick_scalar(int na, const int32_t* __restrict__ active, const 
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= na) return;
     const int i = active[t];
+    if (i < 0) return;   // padding entry of a fixed-capacity list
     const float v = fmaf(rate[i], ks.dt[min((int)bins[i], n_bins - 1)], value[i]);
     value[i] = v;
     if (value_pred) value_pred[i] = v;

@@ -34,11 +34,13 @@ namespace sph {
 
 constexpr int kWppWarps = 4;
 constexpr int kWppThreads = kWppWarps * 32;
-// Register budgets: 8 resident blocks (32 warps, 64 registers) or 6 (24 warps,
-// 80 registers), and for the density pass also 7 (28 warps, 72 registers);
-// the launch takes the one matching blocks_per_sm. The autotuner picks
-// between them per pass.
-constexpr int kWppDensityBps = 8;
+// Register budgets: force, 8 resident blocks (32 warps, 64 registers) or 6 (24
+// warps, 80 registers); density, 5 (20 warps, 96 registers: its shared memory
+// holds 5 blocks per SM) or 4 (16 warps, 128 registers). The launch takes the
+// one matching blocks_per_sm; the autotuner picks between them per pass.
+constexpr int kWppDensityBps = 5;
+constexpr int kWppDensityMaxBps = 5;
+constexpr int kWppLeftBps = 6;   // the one-particle density kernel over the leftovers: 80 registers
 constexpr int kWppForceBps = 8;
 constexpr int kWppMaxBps = 16;
 constexpr int kWppStack = 256;       // see the bound below
@@ -56,8 +58,9 @@ constexpr float kWppWalkR = 1.04f;   // density walks at 1.04 h so that later it
 // below 124 + 8 * kMaxLev = 220 < kWppStack.
 
 struct WppSmem {
-    int stk[kWppStack];
     int glf[kWppGrpLeaves];  // group walk: leaves within reach of at least one particle of the group
+                             // (bit 31: "wide" for the group, see WppGroupGeom)
+    int stk[kWppStack];
     int lid[kWppLeaves];     // leaf index within the box; bit 31 = "wide" (exact separations)
     float4 lof[kWppLeaves];  // leaf centre - particle (box units), h-independent rounding bound
     union {
@@ -130,6 +133,11 @@ struct WppArgs {
     // (fb_act, *fb_count) when the lists are valid, else the whole active set
     const int32_t* fb_act;
     const unsigned* fb_count;
+    // density, member-parallel path: near-list indices, kMpMembers x kMpCap per persistent warp
+    int32_t* mp_j;
+    // density: the particles the member-parallel kernel leaves to the one-particle kernel
+    int32_t* left;
+    unsigned* left_n;
 };
 
 // The recorded lists can serve this force call: every particle's list was
@@ -348,13 +356,29 @@ __device__ __forceinline__ WppGroup wpp_group(const BoxDesc* boxes, int nb, cons
 // (2^-14 of R plus 2^-20 of the offsets and extents) covers the FP32 rounding
 // of both tests. Leaves go to sm.glf; returns their number, or -1 when they
 // would not fit (the members then walk alone).
+// Geometry of a group and of its leaf list: the integer centre Gc, the
+// half-extents eg (box units, rounded up) of the members' box around it, and,
+// over the listed leaves, the largest bound eb on the FP32 rounding error of
+// a separation (leaf centre - Gc) + (particle - leaf centre) - (member - Gc);
+// a listed leaf is marked wide (bit 31) when that form may not be the minimum
+// image for every member.
+struct WppGroupGeom {
+    uint4 Gc;
+    float egx, egy, egz;
+    float eb;
+};
+
 template <class Radius>
 __device__ __forceinline__ int wpp_group_walk(WppSmem& sm, const BoxDesc& B, const uint4* __restrict__ node_c,
-                                              const float4* __restrict__ node_e, uint4 Gc, float egx, float egy,
-                                              float egz, float sf, Radius&& radius) {
+                                              const float4* __restrict__ node_e, WppGroupGeom& gg, float sf,
+                                              Radius&& radius) {
     const unsigned lane = lane_id();
     const unsigned lt = (1u << lane) - 1u;
+    const uint4 Gc = gg.Gc;
+    const float egx = gg.egx, egy = gg.egy, egz = gg.egz;
     const float egs = egx + egy + egz;
+    const float rel = 9.5367431640625e-07f;  // 2^-20
+    float eb = 0.f;
     int ngl = 0;
     if (lane == 0) sm.stk[0] = (B.nlev - 1) << 27;
     int sp = 1;
@@ -367,7 +391,8 @@ __device__ __forceinline__ int wpp_group_walk(WppSmem& sm, const BoxDesc& B, con
         __syncwarp();
         sp -= npop;
         const int lev = enc >> 27, t = enc & ((1 << 27) - 1);
-        const int cl = lev - 1, ct = t * kFan + c;
+        const int cl = lev - 1;
+        int ct = t * kFan + c;
         const bool ok = slot < npop && ct < B.lvl_n[max(cl, 0)];
         bool pass = false;
         if (ok) {
@@ -381,6 +406,12 @@ __device__ __forceinline__ int wpp_group_walk(WppSmem& sm, const BoxDesc& B, con
             const float Rt = radius(E) * (1.f + 6.103515625e-05f) +
                              9.5367431640625e-07f * (fabsf(dx) + fabsf(dy) + fabsf(dz) + E.x + E.y + E.z + egs);
             pass = gx * gx + gy * gy + gz * gz < Rt * Rt;
+            if (pass && cl == 0) {
+                const bool wide = 2.f * (E.x + E.y + E.z + egs) + radius(E) >= B.wideL;
+                ct |= wide ? (int)0x80000000u : 0;
+                if (!wide)
+                    eb = fmaxf(eb, rel * (4.f * (E.x + E.y + E.z) + 2.f * (fabsf(dx) + fabsf(dy) + fabsf(dz))));
+            }
         }
         const bool isleaf = pass && cl == 0, isint = pass && cl > 0;
         const unsigned ml = __ballot_sync(0xffffffffu, isleaf);
@@ -391,6 +422,7 @@ __device__ __forceinline__ int wpp_group_walk(WppSmem& sm, const BoxDesc& B, con
         sp += __popc(mi);
         __syncwarp();
     }
+    gg.eb = warp_max(eb) + rel * 2.f * egs;
     return ngl;
 }
 
@@ -400,7 +432,7 @@ __device__ __forceinline__ int wpp_group_walk(WppSmem& sm, const BoxDesc& B, con
 template <class Radius>
 __device__ __forceinline__ int wpp_group_leaves(WppSmem& sm, const BoxDesc& B, const uint4* __restrict__ node_c,
                                                 const float4* __restrict__ node_e, uint4 Xl, bool valid, float sf,
-                                                Radius&& radius) {
+                                                Radius&& radius, WppGroupGeom& gg) {
     const unsigned X0x = __shfl_sync(0xffffffffu, Xl.x, 0), X0y = __shfl_sync(0xffffffffu, Xl.y, 0),
                    X0z = __shfl_sync(0xffffffffu, Xl.z, 0);
     const int dx = valid ? (int)(Xl.x - X0x) : 0, dy = valid ? (int)(Xl.y - X0y) : 0,
@@ -409,15 +441,22 @@ __device__ __forceinline__ int wpp_group_leaves(WppSmem& sm, const BoxDesc& B, c
     const long long ex = (long long)warp_max(dx) - lox, ey = (long long)warp_max(dy) - loy,
                     ez = (long long)warp_max(dz) - loz;
     if (ex >= (1ll << 30) || ey >= (1ll << 30) || ez >= (1ll << 30)) return -1;
-    uint4 Gc;
-    Gc.x = X0x + (unsigned)(lox + (int)(ex >> 1));
-    Gc.y = X0y + (unsigned)(loy + (int)(ey >> 1));
-    Gc.z = X0z + (unsigned)(loz + (int)(ez >> 1));
-    Gc.w = 0u;
+    gg.Gc.x = X0x + (unsigned)(lox + (int)(ex >> 1));
+    gg.Gc.y = X0y + (unsigned)(loy + (int)(ey >> 1));
+    gg.Gc.z = X0z + (unsigned)(loz + (int)(ez >> 1));
+    gg.Gc.w = 0u;
     const float up = 1.f + 9.5367431640625e-07f;
-    const float egx = (float)((ex + 1) >> 1) * sf * up, egy = (float)((ey + 1) >> 1) * sf * up,
-                egz = (float)((ez + 1) >> 1) * sf * up;
-    return wpp_group_walk(sm, B, node_c, node_e, Gc, egx, egy, egz, sf, radius);
+    gg.egx = (float)((ex + 1) >> 1) * sf * up;
+    gg.egy = (float)((ey + 1) >> 1) * sf * up;
+    gg.egz = (float)((ez + 1) >> 1) * sf * up;
+    return wpp_group_walk(sm, B, node_c, node_e, gg, sf, radius);
+}
+template <class Radius>
+__device__ __forceinline__ int wpp_group_leaves(WppSmem& sm, const BoxDesc& B, const uint4* __restrict__ node_c,
+                                                const float4* __restrict__ node_e, uint4 Xl, bool valid, float sf,
+                                                Radius&& radius) {
+    WppGroupGeom gg;
+    return wpp_group_leaves(sm, B, node_c, node_e, Xl, valid, sf, radius, gg);
 }
 
 // A member's own leaf list from the group's: the leaves of sm.glf that pass
@@ -442,7 +481,7 @@ __device__ __forceinline__ void wpp_filter(WppSmem& sm, int ngl, const BoxDesc& 
         float dx = 0.f, dy = 0.f, dz = 0.f;
         float4 E = make_float4(0.f, 0.f, 0.f, 0.f);
         if (k < ngl) {
-            ct = sm.glf[k];
+            ct = sm.glf[k] & 0x7fffffff;
             const int nd = B.lvl_off[0] + ct;
             const uint4 C = node_c[nd];
             E = node_e[nd];
@@ -605,12 +644,12 @@ static inline cudaError_t span_end(sph_ctx* ctx, const WppSpan& sp, cudaStream_t
 // per queue grab (several for locality in L1, fewer when the set is small so
 // that every warp gets work).
 static inline void wpp_shape(sph_ctx* ctx, int bps, int64_t n_active, int& blocks, int& chunk) {
-    const int b = std::min(bps, kWppMaxBps);
+    const int b = std::min(bps, std::min(kWppMaxBps, kMpWarpsPerSm / kWppWarps));
     const long long warps_needed = std::max<long long>(1, n_active);
     const long long want_blocks = (warps_needed + kWppWarps - 1) / kWppWarps;
     blocks = (int)std::max<long long>(1, std::min<long long>((long long)ctx->sm_count * b, want_blocks));
     const long long warps = (long long)blocks * kWppWarps;
-    chunk = (int)std::max<long long>(1, std::min<long long>(8, n_active / (warps * 4)));
+    chunk = (int)std::max<long long>(1, std::min<long long>(kMpMembers, n_active / (warps * 4)));
 }
 
 static inline WppArgs wpp_common(sph_ctx* ctx, const sph_grid* g, unsigned* queue) {

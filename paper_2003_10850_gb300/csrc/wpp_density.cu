@@ -8,6 +8,449 @@ namespace sph {
 // Density
 // ---------------------------------------------------------------------------
 
+// Member-parallel path of the density pass (groups of >= 2 members that have a
+// group leaf list; at full activity a group is one leaf of 8 particles):
+// - candidates: the group's leaf list is swept once, one candidate per lane
+//   (lanes 8k..8k+7 on one leaf), each candidate load tested against every
+//   member; the pairs within a member's walk radius go to that member's near
+//   list in shared memory ((r^2, m)) and global scratch (the index);
+// - h iteration: lanes 4m..4m+3 serve member m, each summing every fourth
+//   entry of its near list; the four partial sums are folded error-free and
+//   the safeguarded Newton step runs for all members at once;
+// - a last sweep at the final h records the neighbour lists (and sums the
+//   velocity divergence and curl, and the set checksums).
+// A member whose near list overflows or whose h leaves its walk radius takes
+// the whole-warp path of one particle afterwards.
+constexpr int kMpStride = kMpCap + 4;   // float2 entries per member row: rows start 32 bytes apart mod 128
+struct WppMpSmem {
+    float2 d[kMpMembers][kMpStride];    // (r^2, m_j) of each member's near list
+    float4 mem[kMpMembers];             // member offset from the group centre (box units), inclusive threshold
+    uint4 X[kMpMembers];                // member integer positions (and mass bits)
+};
+constexpr int kGlfBytes = (int)sizeof(int) * kWppGrpLeaves;   // WppSmem starts with glf
+constexpr int kDenSmemWarp = (int)(sizeof(WppSmem) > kGlfBytes + sizeof(WppMpSmem) ? sizeof(WppSmem)
+                                                                                      : kGlfBytes + sizeof(WppMpSmem));
+static_assert(kWppWarps * kDenSmemWarp <= 48 * 1024, "static shared memory of the density block");
+
+// Error-free (TwoSum) fold of two per-lane sums over aligned quads of lanes:
+// every lane of the quad ends with both totals as (s, c), value s - c.
+__device__ __forceinline__ void wpp_fold_quad2(float& s1, float& c1, float& s2, float& c2) {
+    auto two_sum = [](float& s, float& c, float s2_, float c2_) {
+        const float t = __fadd_rn(s, s2_);
+        const float bp = __fsub_rn(t, s);
+        const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(s2_, bp));
+        s = t;
+        c = __fsub_rn(__fadd_rn(c, c2_), e);
+    };
+    c1 = 0.f;
+    c2 = 0.f;
+#pragma unroll
+    for (int o = 1; o <= 2; o <<= 1) {
+        const float a1 = __shfl_xor_sync(0xffffffffu, s1, o), b1 = __shfl_xor_sync(0xffffffffu, c1, o);
+        const float a2 = __shfl_xor_sync(0xffffffffu, s2, o), b2 = __shfl_xor_sync(0xffffffffu, c2, o);
+        two_sum(s1, c1, a1, b1);
+        two_sum(s2, c2, a2, b2);
+    }
+}
+
+template <bool HASH, int MINB, bool DIVCURL>
+__global__ void __launch_bounds__(kWppThreads, MINB) k_density_mp(WppArgs a) {
+    __shared__ __align__(16) unsigned char sraw[kWppWarps][kDenSmemWarp];
+    const int wib = (int)(threadIdx.x >> 5);
+    WppSmem& sm = *reinterpret_cast<WppSmem*>(sraw[wib]);
+    WppMpSmem& mp = *reinterpret_cast<WppMpSmem*>(sraw[wib] + kGlfBytes);
+    int32_t* mpj = a.mp_j ? a.mp_j + ((size_t)blockIdx.x * kWppWarps + wib) * (kMpMembers * kMpCap) : nullptr;
+    const unsigned lane = lane_id();
+    const unsigned lt = (1u << lane) - 1u;
+    const float rel = 9.5367431640625e-07f;  // 2^-20
+    const float nt = (float)a.n_target, nt3 = 3.f * nt, tol3 = 3.f * (float)a.n_tol;
+    const int cnt = (int)*a.count_ptr;
+    // per-lane counters, summed over the warp at the end
+    unsigned c_pairs = 0, c_evals = 0, c_status = 0, c_lists = 0;
+    unsigned long long c_tests = 0;
+    long long ch_next = 0, ch_end = 0;   // the warp's current chunk of the neighbour-list pool
+    // Space for n list entries from the warp's chunk of the pool (warp-uniform
+    // n); returns the first entry, or -1 if the pool is full.
+    auto reserve = [&](int n) -> long long {
+        if (n > a.list_chunk) {
+            unsigned long long o = 0;
+            if (lane == 0) o = atomicAdd(reinterpret_cast<unsigned long long*>(a.list_st + 4), (unsigned long long)n);
+            o = __shfl_sync(0xffffffffu, o, 0);
+            return (long long)o + n <= a.list_pool ? (long long)o : -1;
+        }
+        if (ch_next + n > ch_end) {
+            unsigned long long o = 0;
+            if (lane == 0)
+                o = atomicAdd(reinterpret_cast<unsigned long long*>(a.list_st + 4), (unsigned long long)a.list_chunk);
+            o = __shfl_sync(0xffffffffu, o, 0);
+            ch_next = (long long)o;
+            ch_end = ch_next + a.list_chunk;
+        }
+        const long long r = ch_next + n <= a.list_pool ? ch_next : -1;
+        ch_next += n;
+        return r;
+    };
+    for (;;) {
+        int t0 = 0;
+        if (lane == 0) t0 = (int)atomicAdd(a.queue, (unsigned)a.chunk);
+        t0 = __shfl_sync(0xffffffffu, t0, 0);
+        if (t0 >= cnt) break;
+        const int t1 = min(t0 + a.chunk, cnt);
+        for (int t = t0; t < t1;) {
+            const WppGroup G = wpp_group(a.boxes, a.n_boxes, a.act, t, t1);
+            t += G.n;
+            const BoxDesc& B = a.boxes[G.box];
+            const float sf = B.sf;
+            const int off = (int)B.off, pend = (int)(B.off + B.n);
+            // members' start h, one per lane, then one shared walk for the group
+            // (radius: the largest first walk radius of its members)
+            uint4 Xl = make_uint4(0u, 0u, 0u, 0u);
+            int ol = 0;
+            float hl = 0.f;
+            if (G.p >= 0) {
+                Xl = a.posm[G.p];
+                ol = a.perm[G.p];
+                hl = a.h[ol];
+                if (a.guess_h || !(hl > 0.f) || !isfinite(hl))
+                    hl = wpp_guess_h(B, a.node_lo, a.node_hi, G.p, ldexp(B.L, -32), a.n_target);
+            }
+            int ngl = -1;
+            float Rg = 0.f;
+            WppGroupGeom gg;
+            if (G.n >= 2 && B.nlev > 1) {
+                Rg = warp_max(a.fixed_h ? hl : hl * kWppWalkR);
+                ngl = wpp_group_leaves(sm, B, a.node_c, a.node_e, Xl, G.p >= 0, sf, [&](float4) { return Rg; }, gg);
+            }
+            unsigned todo = (1u << G.n) - 1u;   // members left for the one-particle path
+            if (ngl >= 0 && mpj && G.n >= 2) {
+                // ---------------- candidates: one sweep of the group's leaves ----------------
+                // Every member tests every candidate of a step without a branch (a
+                // member slot past G.n has a negative threshold), so the eight
+                // members' dependent chains interleave; the next step's candidates
+                // are loaded while this step's are tested.
+                const float eT = gg.eb;   // rounding bound of a computed separation (non-wide leaves)
+                if ((int)lane < kMpMembers) {
+                    float4 mem = make_float4(0.f, 0.f, 0.f, -1.f);
+                    if ((int)lane < G.n) {
+                        const float Rw = a.fixed_h ? hl : hl * kWppWalkR;
+                        const float tR = Rw + eT + 2.f * rel * Rw;
+                        mem = make_float4((float)(int)(Xl.x - gg.Gc.x) * sf, (float)(int)(Xl.y - gg.Gc.y) * sf,
+                                          (float)(int)(Xl.z - gg.Gc.z) * sf, tR * tR * (1.f + 4.f * rel));
+                    }
+                    mp.mem[lane] = mem;
+                    mp.X[lane] = Xl;
+                }
+                __syncwarp();
+                int cntm[kMpMembers], pmv[kMpMembers];
+#pragma unroll
+                for (int k = 0; k < kMpMembers; ++k) {
+                    cntm[k] = 0;
+                    pmv[k] = __shfl_sync(0xffffffffu, G.p, k);   // -1 past G.n
+                }
+                unsigned ctest = 0;
+                const int lvl0 = B.lvl_off[0];
+                // the candidate of this lane in step `base`: leaf entry, index, centre, (offset, mass)
+                auto fetch = [&](int base, int& e, int& q, bool& cand, uint4& C, float4& f) {
+                    const int li = base + (int)(lane >> 3);
+                    e = li < ngl ? sm.glf[li] : 0;
+                    const int qq = off + (e & 0x7fffffff) * kLeaf + (int)(lane & 7u);
+                    cand = li < ngl && qq < pend;
+                    q = cand ? qq : off;
+                    C = a.node_c[lvl0 + (e & 0x7fffffff)];
+                    f = __ldg(a.posf + q);
+                };
+                int e_n, q_n;
+                bool cand_n;
+                uint4 C_n;
+                float4 f_n;
+                fetch(0, e_n, q_n, cand_n, C_n, f_n);
+                for (int base = 0; base < ngl; base += 4) {
+                    const int e = e_n, q = q_n;
+                    const bool cand = cand_n;
+                    const uint4 C = C_n;
+                    const float4 f = f_n;
+                    if (base + 4 < ngl) fetch(base + 4, e_n, q_n, cand_n, C_n, f_n);
+                    const float px = (float)(int)(C.x - gg.Gc.x) * sf + f.x, py = (float)(int)(C.y - gg.Gc.y) * sf + f.y,
+                                pz = (float)(int)(C.z - gg.Gc.z) * sf + f.z;
+                    const bool wide = cand && e < 0;
+                    ctest += __popc(__ballot_sync(0xffffffffu, cand));
+                    if (!__any_sync(0xffffffffu, wide)) {
+#pragma unroll
+                        for (int m = 0; m < kMpMembers; ++m) {
+                            const float4 g = mp.mem[m];
+                            const float dx = px - g.x, dy = py - g.y, dz = pz - g.z;
+                            const float r2 = dx * dx + dy * dy + dz * dz;
+                            const bool in = cand && q != pmv[m] && r2 < g.w;
+                            const unsigned msk = __ballot_sync(0xffffffffu, in);
+                            const int k = cntm[m] + __popc(msk & lt);
+                            if (in && k < kMpCap) {
+                                mp.d[m][k] = make_float2(r2, f.w);
+                                mpj[m * kMpCap + k] = q;
+                            }
+                            cntm[m] += __popc(msk);
+                        }
+                    } else {
+                        // a wide leaf in the step: exact integer separations from each member there
+                        const uint4 Xq = wide ? a.posm[q] : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+                        for (int m = 0; m < kMpMembers; ++m) {
+                            const float4 g = mp.mem[m];
+                            float dx = px - g.x, dy = py - g.y, dz = pz - g.z;
+                            if (wide) {
+                                const uint4 Xm = mp.X[m];
+                                dx = (float)(int)(Xq.x - Xm.x) * sf;
+                                dy = (float)(int)(Xq.y - Xm.y) * sf;
+                                dz = (float)(int)(Xq.z - Xm.z) * sf;
+                            }
+                            const float r2 = dx * dx + dy * dy + dz * dz;
+                            const bool in = cand && q != pmv[m] && r2 < g.w;
+                            const unsigned msk = __ballot_sync(0xffffffffu, in);
+                            const int k = cntm[m] + __popc(msk & lt);
+                            if (in && k < kMpCap) {
+                                mp.d[m][k] = make_float2(r2, f.w);
+                                mpj[m * kMpCap + k] = q;
+                            }
+                            cntm[m] += __popc(msk);
+                        }
+                    }
+                }
+                if (lane == 0) c_tests += (unsigned long long)ctest * (unsigned)G.n;
+                __syncwarp();
+                // ---------------- h iteration: lanes 4m..4m+3 serve member m ----------------
+                const int mm = (int)(lane >> 2), sub = (int)(lane & 3u);
+                int cm = 0;
+#pragma unroll
+                for (int k = 0; k < kMpMembers; ++k) cm = mm == k ? cntm[k] : cm;
+                const bool mval = mm < G.n;
+                float h = __shfl_sync(0xffffffffu, hl, mm);
+                const int pm = __shfl_sync(0xffffffffu, G.p, mm);
+                const int oim = __shfl_sync(0xffffffffu, ol, mm);
+                const uint4 Xm = mp.X[mm];
+                const int32_t* jm = mpj + mm * kMpCap;
+                const float Rwm = a.fixed_h ? h : h * kWppWalkR;
+                bool run = mval && cm <= kMpCap;
+                bool rew = mval && cm > kMpCap;   // near list overflowed: one-particle path
+                float blo = 0.f, bhi = INFINITY, dold = INFINITY;
+                unsigned st = 0;
+                float fSmw = 0.f, fSmdw = 0.f;   // the final evaluation's per-lane mass sums
+                int fnn = 0;
+                for (int it = 0;; ++it) {
+                    if (!__any_sync(0xffffffffu, run)) break;
+                    const float hinv = 1.f / h;
+                    const float eL = eT + 2.f * rel * h;
+                    const float hi2 = (h + eL) * (h + eL) * (1.f + 4.f * rel);
+                    const float lo2 = h > eL ? (h - eL) * (h - eL) * (1.f - 4.f * rel) : 0.f;
+                    double HH = -1.0;
+                    const bool self = run && sub == 0;   // the self term: w(0) = 1, q w'(0) = 0
+                    float Sw = self ? 1.f : 0.f, Sdw = 0.f, Smw = self ? __uint_as_float(Xm.w) : 0.f, Smdw = 0.f;
+                    int nn = 0;
+                    const int kend = run ? cm : 0;
+                    // two entries per lane per step (k and k + 4), independent until the sums
+                    auto take = [&](int k) {
+                        const float2 e = mp.d[mm][k];
+                        bool in = e.x < lo2;
+                        if (!in && e.x < hi2) {   // the thin band: the exact predicate
+                            if (HH < 0.0) HH = wpp_hh(h, B);
+                            in = exact_pred(exact_d2(Xm, a.posm[jm[k]]), HH);
+                        }
+                        return in ? e : make_float2(-1.f, 0.f);
+                    };
+                    auto term = [&](float2 e) {
+                        if (e.x < 0.f) return;
+                        const float qq = (e.x > 0.f ? e.x * rsqrtf(e.x) : 0.f) * hinv;
+                        float w, dw;
+                        spline<float>(qq, w, dw);
+                        const float qdw = qq * dw;
+                        Sw += w;
+                        Sdw += qdw;
+                        Smw += e.y * w;
+                        Smdw += e.y * qdw;
+                        ++nn;
+                    };
+                    for (int k = sub; __any_sync(0xffffffffu, k < kend); k += 8) {
+                        const float2 e0 = k < kend ? take(k) : make_float2(-1.f, 0.f);
+                        const float2 e1 = k + 4 < kend ? take(k + 4) : make_float2(-1.f, 0.f);
+                        term(e0);
+                        term(e1);
+                    }
+                    float Cw, Cdw;
+                    wpp_fold_quad2(Sw, Cw, Sdw, Cdw);
+                    if (run) {
+                        if (sub == 0) ++c_evals;
+                        // 3 (N_eff - N_t) = (32 S - 3 N_t) - 32 C: the scalings by 32 are exact
+                        const float f3 = __fsub_rn(__fsub_rn(32.f * Sw, nt3), 32.f * Cw);
+                        bool done = false;
+                        if (a.fixed_h || fabsf(f3) <= tol3) {
+                            done = true;
+                        } else if (it >= a.max_iter) {
+                            done = true;
+                            st |= ST_NOT_CONVERGED;
+                        } else {
+                            const float N = (32.f / 3.f) * __fsub_rn(Sw, Cw);
+                            const float dN = -(32.f / 3.f) * __fsub_rn(Sdw, Cdw) / h;
+                            if (!wpp_h_update(h, f3, N, dN, nt, B.capu, blo, bhi, dold, st)) done = true;
+                        }
+                        if (done) {
+                            run = false;
+                            fSmw = Smw;
+                            fSmdw = Smdw;
+                            fnn = nn;
+                        } else if (!(h <= Rwm * 0.99999f)) {
+                            run = false;   // h left the walk radius: one-particle path from this h
+                            rew = true;
+                        }
+                    }
+                }
+                // ---------------- final: outputs, lists, div/curl, checksums ----------------
+                const bool okm = mval && !rew;
+                float Cmw, Cmdw;
+                wpp_fold_quad2(fSmw, Cmw, fSmdw, Cmdw);
+                int nnm = fnn + __shfl_xor_sync(0xffffffffu, fnn, 1);
+                nnm += __shfl_xor_sync(0xffffffffu, nnm, 2);
+                if (!okm) nnm = 0;
+                long long loff = -1;
+                if (a.nbr) {
+                    int pre = 0, tot = 0;
+#pragma unroll
+                    for (int k = 0; k < kMpMembers; ++k) {
+                        const int v = __shfl_sync(0xffffffffu, nnm, 4 * k);
+                        pre += k < mm ? v : 0;
+                        tot += v;
+                    }
+                    const long long gb = tot > 0 ? reserve(tot) : -1;
+                    loff = gb >= 0 ? gb + pre : -1;
+                }
+                const bool rec = loff >= 0 && nnm > 0;
+                unsigned long long hs = 0;
+                float Dd = 0.f, Dx = 0.f, Dy = 0.f, Dz = 0.f;   // per-lane div/curl sums
+                if (a.nbr || DIVCURL || HASH) {
+                    const float hinv = 1.f / h;
+                    const float eL = eT + 2.f * rel * h;
+                    const float hi2 = (h + eL) * (h + eL) * (1.f + 4.f * rel);
+                    const float lo2 = h > eL ? (h - eL) * (h - eL) * (1.f - 4.f * rel) : 0.f;
+                    double HH = -1.0;
+                    const float4 vi = DIVCURL && okm ? a.vpack[pm] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    const int kend = okm ? cm : 0;
+                    int pos = 0;
+                    for (int k = sub; __any_sync(0xffffffffu, k < kend); k += 4) {
+                        bool in = false;
+                        int q = 0;
+                        if (k < kend) {
+                            const float x2 = mp.d[mm][k].x;
+                            if (x2 < hi2) {
+                                q = jm[k];
+                                in = x2 < lo2;
+                                if (!in) {
+                                    if (HH < 0.0) HH = wpp_hh(h, B);
+                                    in = exact_pred(exact_d2(Xm, a.posm[q]), HH);
+                                }
+                            }
+                        }
+                        const unsigned nib = (__ballot_sync(0xffffffffu, in) >> (4 * mm)) & 0xfu;
+                        if (in) {
+                            const int kk = pos + __popc(nib & ((1u << sub) - 1u));
+                            if (rec && kk < nnm) a.nbr[loff + kk] = q;
+                            if (HASH) hs += splitmix64((unsigned long long)a.perm[q]);
+                            if (DIVCURL) {
+                                // d = x_j - x_i; r_ij = -d, v_ij = v_i - v_j
+                                const uint4 Xj = a.posm[q];
+                                const float dx = (float)(int)(Xj.x - Xm.x) * sf, dy = (float)(int)(Xj.y - Xm.y) * sf,
+                                            dz = (float)(int)(Xj.z - Xm.z) * sf;
+                                const float r2 = dx * dx + dy * dy + dz * dz;
+                                if (r2 > 0.f) {   // coincident: no direction
+                                    const float rinv = rsqrtf(r2);
+                                    float w_, dw;
+                                    spline<float>(r2 * rinv * hinv, w_, dw);
+                                    const float4 vj = __ldg(a.vpack + q);
+                                    const float gsc = vj.w * dw * rinv;
+                                    const float vx = vi.x - vj.x, vy = vi.y - vj.y, vz = vi.z - vj.z;
+                                    Dd -= gsc * (vx * dx + vy * dy + vz * dz);
+                                    Dx -= gsc * (vy * dz - vz * dy);
+                                    Dy -= gsc * (vz * dx - vx * dz);
+                                    Dz -= gsc * (vx * dy - vy * dx);
+                                }
+                            }
+                        }
+                        pos += __popc(nib);
+                    }
+                    if (rec && pos != nnm) loff = -1;   // cannot happen: the same predicate counted nnm
+                    if (HASH) {
+                        hs += __shfl_xor_sync(0xffffffffu, hs, 1);
+                        hs += __shfl_xor_sync(0xffffffffu, hs, 2);
+                    }
+                }
+                if (DIVCURL) {
+                    float cd, cx, cy, cz;
+                    wpp_fold_quad2(Dd, cd, Dx, cx);
+                    wpp_fold_quad2(Dy, cy, Dz, cz);
+                    Dd = __fsub_rn(Dd, cd);
+                    Dx = __fsub_rn(Dx, cx);
+                    Dy = __fsub_rn(Dy, cy);
+                    Dz = __fsub_rn(Dz, cz);
+                }
+                if (okm && sub == 0) {
+                    const float smw = __fsub_rn(fSmw, Cmw), smdw = __fsub_rn(fSmdw, Cmdw);
+                    const float rho = 2.5464790894703255f * smw * hinv_cube(h);   // 8/(pi h^3) sum m w
+                    a.h[oim] = h;
+                    a.rho[oim] = rho;
+                    a.omega[oim] = smdw != 0.f ? -3.f * smw / smdw : 1.f;
+                    a.n_ngb[oim] = nnm;
+                    a.flags[oim] = (uint8_t)st;
+                    if (HASH) a.hash[oim] = hs;
+                    if (a.nbr) {
+                        a.nbr_off[pm] = loff >= 0 ? (int)loff : 0;
+                        a.nbr_n[pm] = loff >= 0 ? nnm : -1;
+                        a.list_h[pm] = h;
+                        ++c_lists;
+                    }
+                    if (DIVCURL) {
+                        // div = -(1/rho) sum m v_ij . grad W, curl = |(1/rho) sum m v_ij x grad W|,
+                        // grad_i W = 8/(pi h^4) w'(q) r_ij / r
+                        const float nr = 2.5464790894703255f * hinv_cube(h) / h / rho;
+                        a.divv[oim] = -nr * Dd;
+                        a.curlv[oim] = nr * sqrtf(Dx * Dx + Dy * Dy + Dz * Dz);
+                    }
+                    c_pairs += (unsigned)nnm;
+                    c_status |= st;
+                }
+                // members for the one-particle path, from the h they reached
+                const unsigned rb = __ballot_sync(0xffffffffu, rew && sub == 0);
+                todo = 0;
+#pragma unroll
+                for (int k = 0; k < kMpMembers; ++k) todo |= ((rb >> (4 * k)) & 1u) << k;
+                const float hnow = __shfl_sync(0xffffffffu, h, (int)(lane & 7u) * 4);
+                if ((int)lane < G.n && ((todo >> lane) & 1u)) hl = hnow;
+                __syncwarp();
+            }
+            // the members left over go to the one-particle kernel, each with the h
+            // it should start from
+            if (todo) {
+                const int nl = __popc(todo);
+                unsigned o = 0;
+                if (lane == 0) o = atomicAdd(a.left_n, (unsigned)nl);
+                o = __shfl_sync(0xffffffffu, o, 0);
+                if ((int)lane < G.n && ((todo >> lane) & 1u)) {
+                    a.left[o + __popc(todo & lt)] = G.p;
+                    a.h[ol] = hl;
+                }
+            }
+        }
+    }
+    // per-lane counters: lanes 4m hold the members', lane 0 the candidate tests
+    c_pairs = warp_sum(c_pairs);
+    c_evals = warp_sum(c_evals);
+    c_lists = warp_sum(c_lists);
+    c_tests = warp_sum(c_tests);
+    c_status = __reduce_or_sync(0xffffffffu, c_status);
+    if (lane == 0) {
+        if (a.nbr && c_lists) atomicAdd(&a.list_st[0], c_lists);
+        atomicAdd(&a.ctr->density_pairs, (unsigned long long)c_pairs);
+        atomicAdd(&a.ctr->density_evals, (unsigned long long)c_evals);
+        atomicAdd(&a.ctr->pair_tests, c_tests);
+        if (c_status) atomicOr(&a.ctr->status, c_status);
+    }
+}
+
 template <bool HASH, int MINB, bool DIVCURL>
 __global__ void __launch_bounds__(kWppThreads, MINB) k_density_wpp(WppArgs a) {
     __shared__ WppSmem smem[kWppWarps];
@@ -431,6 +874,9 @@ __global__ void __launch_bounds__(256) k_list_ext(const BoxDesc* __restrict__ bo
                                                   const int32_t* __restrict__ nbr_n, const float* __restrict__ list_h,
                                                   uint32_t* __restrict__ ext_n, int32_t* __restrict__ ext,
                                                   unsigned* list_st) {
+    // the lists serve a force call only if every particle's was written: when
+    // the density call had a smaller active set there is nothing to complete
+    if (list_st[0] != (unsigned)n) return;
     const unsigned lane = lane_id();
     const int warps = gridDim.x * (blockDim.x >> 5);
     const float band = 9.5367431640625e-07f;  // 2^-20
@@ -476,7 +922,9 @@ __global__ void __launch_bounds__(256) k_list_ext(const BoxDesc* __restrict__ bo
 // in place in its segment: up to 64 entries each goes to its rank (registers),
 // up to kExtCap through a bitonic sort in shared memory. A segment that
 // overflowed is marked kExtUnusable, and the force pass walks for that particle.
-__global__ void __launch_bounds__(256) k_list_sort(int n, int32_t* __restrict__ ext, uint32_t* __restrict__ ext_n) {
+__global__ void __launch_bounds__(256) k_list_sort(int n, int32_t* __restrict__ ext, uint32_t* __restrict__ ext_n,
+                                                   const unsigned* __restrict__ list_st) {
+    if (list_st[0] != (unsigned)n) return;   // as k_list_ext
     __shared__ int buf[8][kExtCap];
     int* sb = buf[threadIdx.x >> 5];
     const unsigned lane = lane_id();
@@ -553,7 +1001,7 @@ cudaError_t launch_density_wpp(sph_ctx* ctx, const DensityLaunch& a, int64_t n_a
     if (e) return e;
     WppArgs c = wpp_common(ctx, g, ctx->queue + 2);
     int blocks = 0;
-    const int bps = a.blocks_per_sm > 0 ? a.blocks_per_sm : kWppDensityBps;
+    const int bps = std::min(a.blocks_per_sm > 0 ? a.blocks_per_sm : kWppDensityBps, kWppDensityMaxBps);
     wpp_shape(ctx, bps, n_active, blocks, c.chunk);
     c.h = a.h;
     c.rho = a.rho;
@@ -566,6 +1014,8 @@ cudaError_t launch_density_wpp(sph_ctx* ctx, const DensityLaunch& a, int64_t n_a
     c.max_iter = a.max_iter;
     c.guess_h = a.guess_h;
     c.fixed_h = a.fixed_h;
+    // the scratch holds kMpWarpsPerSm warps per SM of the device the grid was built on
+    c.mp_j = g->ctx->sm_count >= ctx->sm_count ? g->mp_j : nullptr;
     if (a.divv) {
         k_vel_pack<<<(int)((g->n + 255) / 256), 256, 0, s>>>((int)g->n, g->perm, a.vel, g->posf, g->fvm);
         ++ctx->launches;
@@ -590,17 +1040,35 @@ cudaError_t launch_density_wpp(sph_ctx* ctx, const DensityLaunch& a, int64_t n_a
         c.list_chunk = (int)std::max<long long>(32, std::min<long long>(kListChunk, g->list_pool / (4 * warps)));
         if ((e = cudaMemsetAsync(g->list_st, 0, sizeof(unsigned) * kListSt, s))) return e;
     }
+    // leftovers of the member-parallel kernel: list g->den_left, count queue[6],
+    // work queue queue[5]
+    if ((e = cudaMemsetAsync(ctx->queue + 5, 0, 2 * sizeof(unsigned), s))) return e;
+    c.left = g->den_left;
+    c.left_n = ctx->queue + 6;
     WppSpan sp;
     if ((e = span_begin(ctx, a.time_kernels, 0, s, sp))) return e;
     const bool dc = a.divv != nullptr;
-    auto kd = bps <= 6 ? (a.hash ? (dc ? k_density_wpp<true, 6, true> : k_density_wpp<true, 6, false>)
-                                 : (dc ? k_density_wpp<false, 6, true> : k_density_wpp<false, 6, false>))
-              : bps == 7 ? (a.hash ? (dc ? k_density_wpp<true, 7, true> : k_density_wpp<true, 7, false>)
-                                   : (dc ? k_density_wpp<false, 7, true> : k_density_wpp<false, 7, false>))
-                         : (a.hash ? (dc ? k_density_wpp<true, 8, true> : k_density_wpp<true, 8, false>)
-                                   : (dc ? k_density_wpp<false, 8, true> : k_density_wpp<false, 8, false>));
+    // 4 or 5 resident blocks (the shared memory of a block holds the member
+    // near lists: 5 blocks fill an SM), 128 or 96 registers
+    auto kd = bps <= 4 ? (a.hash ? (dc ? k_density_mp<true, 4, true> : k_density_mp<true, 4, false>)
+                                 : (dc ? k_density_mp<false, 4, true> : k_density_mp<false, 4, false>))
+                       : (a.hash ? (dc ? k_density_mp<true, 5, true> : k_density_mp<true, 5, false>)
+                                 : (dc ? k_density_mp<false, 5, true> : k_density_mp<false, 5, false>));
     kd<<<blocks, kWppThreads, 0, s>>>(c);
-    ++ctx->launches;
+    // the leftovers, one particle per warp (count on the device), from the h the
+    // member-parallel kernel left for them
+    WppArgs cl = c;
+    cl.act = g->den_left;
+    cl.count_ptr = ctx->queue + 6;
+    cl.queue = ctx->queue + 5;
+    cl.chunk = 1;
+    cl.guess_h = 0;
+    int lblocks = 0, lchunk = 0;
+    wpp_shape(ctx, kWppLeftBps, n_active, lblocks, lchunk);
+    auto kl = a.hash ? (dc ? k_density_wpp<true, kWppLeftBps, true> : k_density_wpp<true, kWppLeftBps, false>)
+                     : (dc ? k_density_wpp<false, kWppLeftBps, true> : k_density_wpp<false, kWppLeftBps, false>);
+    kl<<<lblocks, kWppThreads, 0, s>>>(cl);
+    ctx->launches += 2;
     // SPH_TIME_KERNELS times the density kernel alone; the list build follows
     if ((e = span_end(ctx, sp, s))) return e;
     if (full) {
@@ -608,7 +1076,7 @@ cudaError_t launch_density_wpp(sph_ctx* ctx, const DensityLaunch& a, int64_t n_a
         if ((e = cudaMemsetAsync(g->ext_n, 0, sizeof(uint32_t) * n, s))) return e;
         k_list_ext<<<hb, 256, 0, s>>>(g->boxes, g->n_boxes, n, g->posm, g->nbr, g->nbr_off, g->nbr_n, g->list_h,
                                       g->ext_n, g->ext, g->list_st);
-        k_list_sort<<<hb, 256, 0, s>>>(n, g->ext, g->ext_n);
+        k_list_sort<<<hb, 256, 0, s>>>(n, g->ext, g->ext_n, g->list_st);
         ctx->launches += 2;
     }
     g->lists_full = full;

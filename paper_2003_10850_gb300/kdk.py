@@ -14,8 +14,10 @@ of one tick; all arithmetic runs in the library's kernels:
 
 Inactive particles keep the h, rho, Omega, a, du/dt of their last active
 step; their velocities and energies are predicted to the current time with
-those. The one value read back per tick is the active count, which the next
-calls take as their n_active.
+those. Nothing is read back per tick: sph_active_from_bins pads the active
+list with -1 to its capacity n, and every call takes the whole list
+(n_active = n), skipping the padding on the device. So a whole dt_max cycle
+can be captured as one CUDA graph (capture_cycle) and replayed (run_cycle).
 
 Options: balsara=True limits the viscosity with Balsara's switch (div v and
 curl v from sph_density_divcurl); visc=dict(alpha0, alpha_min, alpha_max,
@@ -73,11 +75,15 @@ class KDK:
         self.flags = torch.zeros(n, dtype=torch.uint8, device=dev)
         self.active = torch.zeros(n, dtype=torch.int32, device=dev)
         self.count = torch.zeros(1, dtype=torch.int32, device=dev)
+        # active count of each tick of a cycle (device; tick k at k mod 2^max_bin)
+        self.tick_counts = torch.zeros(1 << self.max_bin, dtype=torch.int32, device=dev)
         self.grid = sph_build_grid(ctx, self.pos, self.mass, self.params)
         self.tick = 0
         self.pairs = 0
+        self.graph = None
         everyone = torch.arange(n, dtype=torch.int32, device=dev)
         self._forces(everyone)
+        self.collect()
         if bins is None:
             self.bins = torch.zeros(n, dtype=torch.uint8, device=dev)
             sph_timebins(ctx, self.h, self.vsig, None, 0, self.courant, self.dt_max, self.max_bin, self.bins)
@@ -108,6 +114,10 @@ class KDK:
         else:
             sph_hydro_force(ctx, g, self.vel_pred, self.u_pred, self.h, self.rho, self.omega, act, self.acc,
                             self.dudt, self.vsig, None, self.params)
+
+    def collect(self):
+        """Reads and clears the context's device counters (a host
+        synchronisation); adds the pairs they counted to self.pairs."""
         _, st = sph_sync_status(self.ctx)
         self.pairs += st["density_pairs"] + st["force_pairs"]
 
@@ -118,8 +128,11 @@ class KDK:
             sph_kick_scalar(self.ctx, act, act.numel(), self.bins, self.dt_bins(factor), self.dalpha, self.alpha,
                             self.alpha_pred if sync else None)
 
-    def step(self):
-        """Advance one tick (dt_max / 2^max_bin). Returns the active count."""
+    def step(self, sync=True):
+        """Advance one tick (dt_max / 2^max_bin). With sync (a host round
+        trip) the device counters are collected and the active count is
+        returned; without, nothing is read back and the count stays in
+        self.count and self.tick_counts."""
         ctx = self.ctx
         dt = self.dt_max / 2.0 ** self.max_bin
         sph_drift(ctx, self.pos, self.vel, dt, self.box, self.acc, self.dudt, self.vel_pred, self.u_pred)
@@ -127,17 +140,44 @@ class KDK:
             sph_predict_scalar(ctx, dt, self.dalpha, self.alpha_pred)
         self.tick += 1
         sph_grid_update(ctx, self.grid, self.pos, self.mass)
+        # the active particles, then -1 up to n: every call below takes the whole list
         sph_active_from_bins(ctx, self.grid, self.bins, self.tick, self.max_bin, self.active, self.count)
-        na = int(self.count.item())
-        if na:
-            act = self.active[:na]
-            self._forces(act)
-            self._kick(act, 0.5, sync=True)   # closing half kick: synchronized v, u become the predictions
-            if self.rebin:
-                sph_timebins(ctx, self.h, self.vsig, act, self.tick, self.courant, self.dt_max, self.max_bin,
-                             self.bins)
-            self._kick(act, 0.5)           # opening half kick of the next step
-        return na
+        act = self.active
+        self._forces(act)
+        self._kick(act, 0.5, sync=True)   # closing half kick: synchronized v, u become the predictions
+        if self.rebin:
+            sph_timebins(ctx, self.h, self.vsig, act, self.tick, self.courant, self.dt_max, self.max_bin, self.bins)
+        self._kick(act, 0.5)           # opening half kick of the next step
+        self.tick_counts[self.tick % (1 << self.max_bin)].copy_(self.count[0])
+        if sync:
+            self.collect()
+            return int(self.count.item())
+        return None
+
+    def capture_cycle(self):
+        """Captures the ticks of one dt_max cycle (2^max_bin of them) as a CUDA
+        graph, at a cycle boundary. The decisions depend on the tick only
+        modulo 2^max_bin, so run_cycle may replay it at every later boundary.
+        Capturing runs nothing."""
+        if self.tick % (1 << self.max_bin):
+            raise RuntimeError("capture_cycle: not at a cycle boundary")
+        t0 = self.tick
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(side):
+            with torch.cuda.graph(self.graph, stream=side):
+                for _ in range(1 << self.max_bin):
+                    self.step(sync=False)
+        torch.cuda.current_stream().wait_stream(side)
+        self.tick = t0
+
+    def run_cycle(self):
+        """Replays the captured cycle (no host round trip)."""
+        if self.graph is None or self.tick % (1 << self.max_bin):
+            raise RuntimeError("run_cycle: capture_cycle first, at a cycle boundary")
+        self.graph.replay()
+        self.tick += 1 << self.max_bin
 
     def synchronized_velocity(self):
         """Velocities at the current time: the half kick of every particle's

@@ -116,3 +116,45 @@ def test_kdk_rebinning_follows_the_rule(S, ctx):
         expect = OK.timebins(host(g.h)[act], host(g.vsig)[act], 0.3, dt_max, 3, tick=g.tick)
         assert np.array_equal(host(g.bins)[act], expect)
     assert torch.isfinite(g.u).all() and bool((g.u > 0).all())
+
+
+def test_kdk_cycle_graph_replays_eager(S, ctx):
+    """A dt_max cycle captured as one CUDA graph (nothing read back per tick:
+    the active list is padded with -1 up to its capacity and every call takes
+    the whole list) ends in bit for bit the state of the same cycle run
+    eagerly, tick by tick, and records the same active counts."""
+    from paper_2003_10850_gb300.kdk import KDK
+    p = as_f32(W.clustered(8192, 8, seed=23))
+    state = (ctx, dev(p.pos, torch.float64), dev(p.mass), dev(p.vel), dev(p.u))
+    probe = KDK(*state, 1e-3, 2)
+    dt_max = _dt_max(host(probe.h), host(probe.vsig), 2)
+    a = KDK(*state, dt_max, 2)
+    b = KDK(*state, dt_max, 2)
+    counts = [a.step() for _ in range(4)]
+    assert counts[3] == p.n and 0 < min(counts)
+    b.capture_cycle()
+    b.run_cycle()
+    torch.cuda.synchronize()
+    for k in ("pos", "vel", "u", "vel_pred", "u_pred", "h", "rho", "omega", "acc", "dudt", "vsig", "bins"):
+        assert torch.equal(getattr(a, k), getattr(b, k)), k
+    assert host(b.tick_counts).tolist() == [counts[3], counts[0], counts[1], counts[2]]
+    # the graph replays at every later cycle boundary
+    for _ in range(4):
+        a.step(sync=False)
+    b.run_cycle()
+    torch.cuda.synchronize()
+    assert torch.equal(a.pos, b.pos) and torch.equal(a.vel, b.vel)
+
+
+def test_active_from_bins_pads_with_minus_one(S, ctx):
+    n = 5000
+    p = as_f32(W.clustered(n, 4, seed=29))
+    grid = S.sph_build_grid(ctx, dev(p.pos), dev(p.mass), S.default_params())
+    b = np.random.default_rng(3).integers(0, 4, n).astype(np.uint8)
+    out = torch.full((n,), 7, dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+    S.sph_active_from_bins(ctx, grid, dev(b, torch.uint8), 2, 3, out, cnt)
+    k = int(cnt.item())
+    expect = np.nonzero(2 % (1 << (3 - b.astype(np.int64))) == 0)[0]
+    o = host(out)
+    assert k == expect.size and np.array_equal(o[:k], expect) and np.all(o[k:] == -1)

@@ -133,11 +133,11 @@ def test_density_converged(S, ctx, kind, fp64, path, lattice32, clustered50k):
     assert rel(g2["h"], d["h"]).max() <= 1e-5
 
 
-@pytest.mark.parametrize("bps", [6, 7, 8])
+@pytest.mark.parametrize("bps", [4, 5, 6, 8])
 def test_register_budgets_agree(S, ctx, bps, clustered50k):
     """The default path's kernels at each register budget the autotuner can
-    pick (blocks per SM 6, 7, 8): converged density and the force from the
-    recorded lists against the oracle, pair sets exact."""
+    pick (blocks per SM: density 4 or 5, force 6 or 8): converged density and
+    the force from the recorded lists against the oracle, pair sets exact."""
     p, (X, d, _) = clustered50k
     params = S.default_params(box=p.box, blocks_per_sm=bps)
     grid = gpu_grid(S, ctx, p, params)
@@ -322,6 +322,19 @@ def test_active_subset(S, ctx, path, clustered50k):
     dup = np.concatenate([act, act[:100]])
     g2 = gpu_density(S, ctx, grid, h0, params, active=dup)
     assert np.array_equal(g2["n_ngb"][act], g["n_ngb"][act])
+    # so are negative entries: the list padded with -1 to capacity n (the
+    # launch shape then follows the capacity, so the sums may round
+    # differently; the results meet the same bounds)
+    pad = np.full(p.n, -1, np.int32)
+    pad[:act.size] = act
+    g3 = gpu_density(S, ctx, grid, h0, params, active=pad)
+    assert g3["rc"] == 0
+    assert rel(g3["h"][act], d["h"][act]).max() <= 1e-5
+    assert rel(g3["rho"][act], d["rho"][act]).max() <= 1e-5
+    assert np.all(g3["h"][inact] == -7.0) and np.all(g3["n_ngb"][inact] == -1)
+    gf3 = gpu_force(S, ctx, grid, p, h, rho, om, params, active=pad)
+    check_force(gf3, f, act, 1e-4)
+    assert np.all(gf3["acc"][inact] == 0)
 
 
 @pytest.mark.parametrize("path", PATHS)
