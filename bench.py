@@ -246,15 +246,11 @@ def kernel_names(S, dflags, fflags):
     def pick(fl, names):
         if fl & S.SPH_PLAIN_FP32:
             return names[0]
-        if fl & S.SPH_WARP_GROUP:
-            return names[1]
-        if fl & S.SPH_COOP_WALK:
-            return names[2]
         if fl & (S.SPH_PER_THREAD_WALK | S.SPH_DENSITY_BUFFERED | S.SPH_FP64):
-            return names[3] if not (fl & S.SPH_DENSITY_BUFFERED) else "k_density_buf"
-        return names[4]
-    return (pick(dflags, ("k_density_plain", "k_density", "k_density_coop", "k_density_tpp<float>", "k_density_wpp")),
-            pick(fflags, ("k_force_plain", "k_force", "k_force_coop", "k_force_mask", "k_force_wpp")))
+            return names[1] if not (fl & S.SPH_DENSITY_BUFFERED) else "k_density_buf"
+        return names[2]
+    return (pick(dflags, ("k_density_plain", "k_density_tpp<float>", "k_density_mp + k_density_wpp")),
+            pick(fflags, ("k_force_plain", "k_force_mask", "k_force_list + k_force_mp + k_force_wpp")))
 
 
 def timed_steps(S, ctx, wl, dparams, fparams, steps, warmup, dist=None):
@@ -697,9 +693,9 @@ def main():
     dpar, fpar, tuned = autotune.tune(ctx, wl["grid"], wl["st"], wl["vel"], wl["u"], wl["h"], wl["h_ins"][0],
                                       tag="clustered-100pct")
     dtime = S.default_params(flags=dpar.flags | S.SPH_TIME_KERNELS, blocks_per_sm=dpar.blocks_per_sm,
-                             group_size=dpar.group_size)
+                             walk_radius=dpar.walk_radius)
     ftime = S.default_params(flags=fpar.flags | S.SPH_TIME_KERNELS, blocks_per_sm=fpar.blocks_per_sm,
-                             group_size=fpar.group_size)
+                             walk_radius=fpar.walk_radius)
 
     clocks = Clocks(local)
     res_g = graph_steps(S, ctx, wl, dpar, fpar, args.steps, args.warmup, dist)

@@ -52,9 +52,7 @@ typedef enum {
                                 estimate made from the grid's leaf-parent boxes */
 #define SPH_TIME_KERNELS 0x10 /* record CUDA events around the main density/force kernel on
                                  the launching stream; sph_sync_status sums their durations */
-#define SPH_WARP_GROUP 0x20   /* alternative path: one warp per group of <= group_size
-                                 Morton-consecutive particles sharing one walk against the
-                                 group's bounding box (a common candidate set) */
+#define SPH_WARP_GROUP 0x20   /* reserved: names a path that is no longer built (SPH_ERR_INVALID) */
 #define SPH_DENSITY_BUFFERED 0x40 /* density, per-thread walks: iterate h on a per-thread buffer
                                      of the candidates found by one walk at 1.06 h */
 #define SPH_PER_THREAD_WALK 0x80  /* force one thread per particle walking alone */
@@ -63,9 +61,7 @@ typedef enum {
                                      nodes per step, one child per lane), keeps the leaf list in
                                      shared memory across h iterations, tests 32 candidates per step
                                      and evaluates the pair terms from a warp-wide hit buffer */
-#define SPH_COOP_WALK 0x100       /* alternative path: one warp per 32 Morton-consecutive active
-                                     particles, per-lane spheres, shared node tests, per-lane
-                                     compacted leaf lists and hit buffers */
+#define SPH_COOP_WALK 0x100       /* reserved: names a path that is no longer built (SPH_ERR_INVALID) */
 #define SPH_NO_LISTS 0x400        /* sph_build_grid: do not allocate the neighbour lists that the
                                      default path records in an all-active density pass and reuses
                                      in the force pass (saves ~1,040 bytes per particle) */
@@ -87,8 +83,12 @@ typedef struct {
     double alpha_visc;  /* artificial-viscosity alpha */
     double gamma;       /* adiabatic index */
     int    flags;       /* SPH_* flags above */
-    int    group_size;  /* particles per warp group: 0 (= 32), 16 or 32 */
+    int    group_size;  /* unused (the warp-group path is no longer built): 0, 16 or 32 */
     int    blocks_per_sm; /* persistent CTAs per SM: 0 = library default */
+    double walk_radius; /* density, default path: radius of a particle's candidate (near) list
+                           as a multiple of its starting h, in [1, 2]; 0 = library default
+                           (1.04). Larger radii keep more candidates but walk again less
+                           often when h grows during the iteration. */
 } sph_params;
 
 /* Counters accumulated by the device since the last sph_sync_status(). */
@@ -99,7 +99,7 @@ typedef struct {
     uint64_t force_pairs;     /* sum over active i of |{j != i : r_ij < max(h_i, h_j)}| */
     uint64_t density_evals;   /* particle-evaluations of the density sums (all iterations) */
     uint64_t pair_tests;      /* candidate pairs tested (work including rejected ones) */
-    uint64_t groups;          /* warp groups processed */
+    uint64_t groups;          /* reserved (0) */
     double density_kernel_ms; /* SPH_TIME_KERNELS: summed time of the density kernels */
     double force_kernel_ms;   /* SPH_TIME_KERNELS: summed time of the force kernels */
     uint32_t density_launches; /* SPH_TIME_KERNELS: timed density kernel launches */

@@ -53,6 +53,8 @@ def lib():
         L.orc_kernel_array.argtypes = [P, i64, P, P]
         L.orc_splitmix64.argtypes = [ctypes.c_uint64]
         L.orc_splitmix64.restype = ctypes.c_uint64
+        L.orc_set_hash_offset.argtypes = [i64]
+        L.orc_set_hash_offset.restype = None
         L.orc_density.argtypes = [i32, P, P, i64, f64, P, P, f64, f64, i32, P, i64, i32, i32,
                                   P, P, P, P, P, P, P, P]
         L.orc_density.restype = i32
@@ -136,12 +138,14 @@ def _geom(X, xc, box):
 
 
 def density(X=None, mass=None, h_init=None, box=1.0, n_target=64.0, tol=1e-10, max_iter=200,
-            active=None, brute=False, fixed_h=False, xc=None):
+            active=None, brute=False, fixed_h=False, xc=None, hash_offset=0):
     """Density pass (and smoothing-length solve unless ``fixed_h``).
 
     Pass integer positions ``X`` (quantised geometry, exact predicate) or
     continuous FP64 positions ``xc``. Returns a dict of per-particle arrays
-    (entries of inactive particles are NaN / -1).
+    (entries of inactive particles are NaN / -1). ``hash_offset`` is added to
+    every index the neighbour-set checksums hash (a box that sits at an
+    offset in a batch).
     """
     mode, Xc, xcc = _geom(X, xc, box)
     n = Xc.shape[0]
@@ -152,11 +156,13 @@ def density(X=None, mass=None, h_init=None, box=1.0, n_target=64.0, tol=1e-10, m
     out["n_ngb"] = np.full(n, -1, dtype=np.int64)
     out["hash"] = np.zeros(n, dtype=np.uint64)
     out["status"] = np.zeros(n, dtype=np.int32)
+    lib().orc_set_hash_offset(int(hash_offset))
     st = lib().orc_density(mode, _p(Xc), _p(xcc), n, float(box), _p(m), _p(hi), float(n_target),
                            float(tol), int(max_iter), _p(act), 0 if act is None else act.size,
                            int(bool(brute)), int(bool(fixed_h)), _p(out["h"]), _p(out["rho"]),
                            _p(out["drho_dh"]), _p(out["omega"]), _p(out["neff"]),
                            _p(out["n_ngb"]), _p(out["hash"]), _p(out["status"]))
+    lib().orc_set_hash_offset(0)
     out["any_status"] = int(st)
     return out
 
@@ -195,7 +201,7 @@ def conduction(X=None, mass=None, u=None, h=None, rho=None, kappa=None, box=1.0,
 
 
 def force(X=None, vel=None, mass=None, u=None, h=None, rho=None, omega=None, box=1.0,
-          alpha=1.0, gamma=5.0 / 3.0, active=None, brute=False, xc=None, divv=None, curlv=None):
+          alpha=1.0, gamma=5.0 / 3.0, active=None, brute=False, xc=None, divv=None, curlv=None, hash_offset=0):
     """Hydro-force pass. Returns acc (N,3), dudt, vsig, scale_a, scale_u,
     n_pairs, hash (entries of inactive particles NaN / -1). With divv and
     curlv, Balsara's switch limits the viscosity. alpha: a number, or one
@@ -213,10 +219,12 @@ def force(X=None, vel=None, mass=None, u=None, h=None, rho=None, omega=None, box
         out[k] = np.full(n, np.nan)
     out["n_pairs"] = np.full(n, -1, dtype=np.int64)
     out["hash"] = np.zeros(n, dtype=np.uint64)
+    lib().orc_set_hash_offset(int(hash_offset))
     lib().orc_force(mode, _p(Xc), _p(xcc), n, float(box), *[_p(a) for a in args], float(alpha), _p(alpha_p),
                     float(gamma), _p(sw[0]), _p(sw[1]), _p(act), 0 if act is None else act.size, int(bool(brute)),
                     _p(out["acc"]), _p(out["dudt"]), _p(out["vsig"]), _p(out["scale_a"]),
                     _p(out["scale_u"]), _p(out["n_pairs"]), _p(out["hash"]))
+    lib().orc_set_hash_offset(0)
     return out
 
 

@@ -288,6 +288,11 @@ static void orc_cands_for(const orc_pos *P, const orc_index *I, int64_t i, doubl
     orc_candidates(I, P->X + 3 * i, H, out);
 }
 
+/* Index offset of the neighbour-set checksums (test instrumentation: a box
+ * checked on its own whose particles sit at an offset in a batch). */
+static int64_t orc_hash_off = 0;
+void orc_set_hash_offset(int64_t off) { orc_hash_off = off; }
+
 /* splitmix64 finaliser (Steele, Lea, Flood 2014): order-independent
  * neighbour-set checksum = sum over the set of splitmix64(index). */
 uint64_t orc_splitmix64(uint64_t x)
@@ -326,7 +331,7 @@ static void orc_density_at(const orc_pos *P, const orc_index *I, const double *m
         sdw += orc_dWdh(r, h);
         rho += m[j] * W;
         drho += m[j] * orc_dWdh(r, h);
-        if (j != i) { ++nn; hs += orc_splitmix64((uint64_t)j); }
+        if (j != i) { ++nn; hs += orc_splitmix64((uint64_t)(j + orc_hash_off)); }
     }
     double f = 4.0 * ORC_PI / 3.0 * h * h * h;
     o->neff = f * sw;
@@ -587,7 +592,7 @@ void orc_force(int mode, const uint32_t *X, const double *xc, int64_t n, double 
                 else take = !in_i && in_j;             /* j's sphere only */
                 if (!take) continue;
                 ++np;
-                hs += orc_splitmix64((uint64_t)j);
+                hs += orc_splitmix64((uint64_t)(j + orc_hash_off));
                 double Pj = (gamma - 1.0) * rho[j] * u[j];
                 double cj = sqrt(gamma * Pj / rho[j]);
                 double Aj = omega[j] * Pj / (rho[j] * rho[j]);

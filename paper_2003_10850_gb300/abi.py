@@ -53,7 +53,8 @@ SPH_SORT_STATIC_MAX_KEYS = 1 << 20
 class sph_params(ctypes.Structure):
     _fields_ = [("box", ctypes.c_double), ("n_target", ctypes.c_double), ("n_tol", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("alpha_visc", ctypes.c_double), ("gamma", ctypes.c_double),
-                ("flags", ctypes.c_int), ("group_size", ctypes.c_int), ("blocks_per_sm", ctypes.c_int)]
+                ("flags", ctypes.c_int), ("group_size", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
+                ("walk_radius", ctypes.c_double)]
 
 
 class sph_stats(ctypes.Structure):

@@ -4,8 +4,10 @@ Times a small set of configurations of each pass on the caller's own grid and
 state (CUDA events on the current stream, best of `reps`), picks the fastest
 per pass, and caches the choice per (GPU name, particle count, workload tag)
 in paper_2003_10850_gb300/_build/autotune.json. The knobs are those of
-sph_params: persistent blocks per SM and the kernel family (warp per
-particle, warp-cooperative, per-thread walks, and the warp-group path).
+sph_params: persistent blocks per SM (a register budget) and the walk radius
+of the density pass (the radius of its near lists, as a multiple of h: larger
+radii mean longer lists but fewer walks again when h grows), against the
+per-thread walks as the other kernel family.
 """
 from __future__ import annotations
 
@@ -14,21 +16,16 @@ import os
 
 import torch
 
-from . import (SPH_COOP_WALK, SPH_PER_THREAD_WALK, SPH_WARP_GROUP, default_params, sph_density,
-               sph_hydro_force, sph_sync_status)
+from . import SPH_PER_THREAD_WALK, default_params, sph_density, sph_hydro_force, sph_sync_status
 
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
 
-# warp-per-particle walks (the default path, flags 0) at several register
-# budgets (density: 128 or 96 registers), the warp-cooperative walks and
-# the per-thread walks
-DENSITY_CANDIDATES = ([dict(flags=0, blocks_per_sm=b) for b in (4, 5)] +
-                      [dict(flags=SPH_COOP_WALK, blocks_per_sm=10),
-                       dict(flags=SPH_PER_THREAD_WALK, blocks_per_sm=16)])
+# default path (flags 0) at two register budgets and three walk radii, and the
+# per-thread walks
+DENSITY_CANDIDATES = ([dict(flags=0, blocks_per_sm=b, walk_radius=r) for b in (4, 5) for r in (1.03, 1.04, 1.06)] +
+                      [dict(flags=SPH_PER_THREAD_WALK, blocks_per_sm=16)])
 FORCE_CANDIDATES = ([dict(flags=0, blocks_per_sm=b) for b in (6, 8)] +
-                    [dict(flags=SPH_COOP_WALK, blocks_per_sm=8),
-                     dict(flags=SPH_PER_THREAD_WALK, blocks_per_sm=16)])
-WARP_CANDIDATE = dict(flags=SPH_WARP_GROUP, blocks_per_sm=4, group_size=32)
+                    [dict(flags=SPH_PER_THREAD_WALK, blocks_per_sm=16)])
 
 
 def _load():
@@ -59,8 +56,7 @@ def _time(fn, reps):
     return best
 
 
-def tune(ctx, grid, st, vel, u, h, h_guess, active=None, tag="default", reps=2, use_cache=True,
-         include_warp=False):
+def tune(ctx, grid, st, vel, u, h, h_guess, active=None, tag="default", reps=2, use_cache=True):
     """Returns (density_params, force_params, report). `st` holds the output
     buffers rho, omega, n_ngb, flags, acc, dudt, vsig; h is overwritten with
     h_guess before every density trial."""
@@ -69,7 +65,7 @@ def tune(ctx, grid, st, vel, u, h, h_guess, active=None, tag="default", reps=2, 
     if key in cache:
         e = cache[key]
         return default_params(**e["density"]), default_params(**e["force"]), e
-    dens = list(DENSITY_CANDIDATES) + ([WARP_CANDIDATE] if include_warp else [])
+    dens = list(DENSITY_CANDIDATES)
     rep = {"density": {}, "force": {}}
 
     def run_d(kw):
@@ -91,7 +87,7 @@ def tune(ctx, grid, st, vel, u, h, h_guess, active=None, tag="default", reps=2, 
                         None, default_params(**kw))
 
     best_f, best_ft = None, float("inf")
-    for kw in FORCE_CANDIDATES + ([WARP_CANDIDATE] if include_warp else []):
+    for kw in FORCE_CANDIDATES:
         t = _time(lambda: run_f(kw), reps)
         rep["force"][json.dumps(kw, sort_keys=True)] = t
         if t < best_ft:

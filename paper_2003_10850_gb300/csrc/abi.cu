@@ -35,33 +35,27 @@ sph_status check_params(sph_ctx* ctx, const sph_params* p) {
     if (p->group_size != 0 && p->group_size != 16 && p->group_size != 32)
         return fail(ctx, SPH_ERR_INVALID, "params.group_size must be 0, 16 or 32");
     if (p->blocks_per_sm < 0 || p->blocks_per_sm > 32) return fail(ctx, SPH_ERR_INVALID, "params.blocks_per_sm out of range");
+    if (!(p->walk_radius == 0.0 || (p->walk_radius >= 1.0 && p->walk_radius <= 2.0)))
+        return fail(ctx, SPH_ERR_INVALID, "params.walk_radius must be 0 (default) or in [1, 2]");
     if ((p->flags & SPH_FP64) && (p->flags & SPH_PLAIN_FP32))
         return fail(ctx, SPH_ERR_INVALID, "SPH_FP64 and SPH_PLAIN_FP32 are exclusive");
-    if ((p->flags & SPH_WARP_GROUP) && (p->flags & SPH_PLAIN_FP32))
-        return fail(ctx, SPH_ERR_INVALID, "SPH_WARP_GROUP and SPH_PLAIN_FP32 are exclusive");
-    if ((p->flags & SPH_WARP_GROUP) && (p->flags & SPH_PER_THREAD_WALK))
-        return fail(ctx, SPH_ERR_INVALID, "SPH_WARP_GROUP and SPH_PER_THREAD_WALK are exclusive");
-    if ((p->flags & SPH_COOP_WALK) && (p->flags & (SPH_PER_THREAD_WALK | SPH_WARP_GROUP)))
-        return fail(ctx, SPH_ERR_INVALID, "SPH_COOP_WALK excludes SPH_PER_THREAD_WALK and SPH_WARP_GROUP");
+    if (p->flags & (SPH_WARP_GROUP | SPH_COOP_WALK))
+        return fail(ctx, SPH_ERR_INVALID, "SPH_WARP_GROUP and SPH_COOP_WALK name paths that are no longer built");
     if ((p->flags & SPH_WARP_WALK) &&
-        (p->flags & (SPH_PER_THREAD_WALK | SPH_WARP_GROUP | SPH_COOP_WALK | SPH_PLAIN_FP32 | SPH_FP64 | SPH_DENSITY_BUFFERED)))
+        (p->flags & (SPH_PER_THREAD_WALK | SPH_PLAIN_FP32 | SPH_FP64 | SPH_DENSITY_BUFFERED)))
         return fail(ctx, SPH_ERR_INVALID, "SPH_WARP_WALK excludes the other path flags and SPH_FP64");
     return SPH_OK;
 }
 
-int group_size(const sph_params* p) { return p->group_size ? p->group_size : 32; }
-
 // Which kernel family runs a density or force call. With no path flag the
-// warp-per-particle kernels run: on the 10M clustered time bins they are the
-// fastest at every active fraction measured (100, 10, 1 and 0.1 %). SPH_FP64
-// selects the per-thread walks in double (or the warp-group path in double
-// with SPH_WARP_GROUP).
-enum class Path { Plain, WarpGroup, Wpp, Coop, Thread };
+// warp-per-particle kernels run (member-parallel for groups, one particle per
+// warp for the rest): on the 10M clustered time bins they are the fastest at
+// every active fraction measured (100, 10, 1 and 0.1 %). SPH_FP64 selects the
+// per-thread walks in double.
+enum class Path { Plain, Wpp, Thread };
 Path pick_path(int flags) {
     if (flags & SPH_PLAIN_FP32) return Path::Plain;
-    if (flags & SPH_WARP_GROUP) return Path::WarpGroup;
     if (flags & (SPH_PER_THREAD_WALK | SPH_DENSITY_BUFFERED | SPH_FP64)) return Path::Thread;
-    if (flags & SPH_COOP_WALK) return Path::Coop;
     return Path::Wpp;
 }
 
@@ -216,8 +210,7 @@ static sph_status density_call(sph_ctx* ctx, const sph_grid* grid, float* h, con
     cudaStream_t s = (cudaStream_t)stream;
     sph_grid* g = const_cast<sph_grid*>(grid);  // per-call scratch lives in the grid
     const Path path = pick_path(params->flags);
-    const bool coop = path == Path::Coop, warp_group = path == Path::WarpGroup;
-    grid_active(g, active, n_active, coop ? 32 : group_size(params), warp_group || coop, s);
+    grid_active(g, active, n_active, s);
     DensityLaunch a;
     a.g = g;
     a.h = h;
@@ -233,16 +226,15 @@ static sph_status density_call(sph_ctx* ctx, const sph_grid* grid, float* h, con
     a.guess_h = (params->flags & SPH_H_GUESS) ? 1 : 0;
     a.fp64 = (params->flags & SPH_FP64) ? 1 : 0;
     a.blocks_per_sm = params->blocks_per_sm;
+    a.walk_radius = params->walk_radius;
     a.time_kernels = (params->flags & SPH_TIME_KERNELS) ? 1 : 0;
     a.buffered = (params->flags & SPH_DENSITY_BUFFERED) ? 1 : 0;
     a.vel = vel;
     a.divv = divv;
     a.curlv = curlv;
-    cudaError_t e = path == Path::Plain       ? run_density_plain(ctx, a, na, s)
-                    : path == Path::WarpGroup ? launch_density(ctx, a, s)
-                    : path == Path::Wpp       ? launch_density_wpp(ctx, a, na, s)
-                    : path == Path::Coop      ? launch_density_coop(ctx, a, s)
-                                              : launch_density_tpp(ctx, a, na, s);
+    cudaError_t e = path == Path::Plain ? run_density_plain(ctx, a, na, s)
+                    : path == Path::Wpp ? launch_density_wpp(ctx, a, na, s)
+                                        : launch_density_tpp(ctx, a, na, s);
     if (!e) e = cudaGetLastError();
     if (e) return cuda_fail(ctx, e, "sph_density");
     return SPH_OK;
@@ -285,9 +277,8 @@ static sph_status force_call(sph_ctx* ctx, const sph_grid* grid, const float* ve
     cudaStream_t s = (cudaStream_t)stream;
     sph_grid* g = const_cast<sph_grid*>(grid);
     const Path path = pick_path(params->flags & ~SPH_DENSITY_BUFFERED);
-    const bool coop = path == Path::Coop, warp_group = path == Path::WarpGroup;
     grid_refresh_hmax(g, h, s);
-    grid_active(g, active, n_active, coop ? 32 : group_size(params), warp_group || coop, s);
+    grid_active(g, active, n_active, s);
     ForceLaunch a;
     a.g = g;
     a.vel = vel;
@@ -309,11 +300,9 @@ static sph_status force_call(sph_ctx* ctx, const sph_grid* grid, const float* ve
     a.kappa = kappa;
     a.dudt_cond = dudt_cond;
     a.alpha_v = alpha_v;
-    cudaError_t e = path == Path::Plain       ? launch_force_plain(ctx, a, na, s)
-                    : path == Path::WarpGroup ? launch_force(ctx, a, s)
-                    : path == Path::Wpp       ? launch_force_wpp(ctx, a, na, s)
-                    : path == Path::Coop      ? launch_force_coop(ctx, a, s)
-                                              : launch_force_tpp(ctx, a, na, s);
+    cudaError_t e = path == Path::Plain ? launch_force_plain(ctx, a, na, s)
+                    : path == Path::Wpp ? launch_force_wpp(ctx, a, na, s)
+                                        : launch_force_tpp(ctx, a, na, s);
     if (!e) e = cudaGetLastError();
     if (e) return cuda_fail(ctx, e, "sph_hydro_force");
     return SPH_OK;
@@ -384,7 +373,7 @@ sph_status sph_gravity(sph_ctx* ctx, const sph_grid* grid, const int32_t* active
     if (cudaSetDevice(ctx->device)) return fail(ctx, SPH_ERR_CUDA, "cudaSetDevice failed");
     cudaStream_t s = (cudaStream_t)stream;
     sph_grid* g = const_cast<sph_grid*>(grid);
-    grid_active(g, active, n_active, 32, false, s);
+    grid_active(g, active, n_active, s);
     GravityLaunch L;
     L.g = g;
     L.G = gp->G;

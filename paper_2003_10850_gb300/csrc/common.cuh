@@ -45,15 +45,6 @@ struct BoxDesc {
     double S;               // 2^32 / L in FP64 (correctly rounded; exact when pow2)
 };
 
-// Active groups of one call: group g covers active-list entries
-// [first, first + count) of box `box`.
-struct Group {
-    int box;
-    int first;
-    int count;
-    int pad;
-};
-
 // Device counters and status of a context (cleared by sph_sync_status).
 struct Counters {
     unsigned int status;

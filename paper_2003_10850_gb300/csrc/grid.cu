@@ -374,7 +374,7 @@ __global__ void k_node_hmax(int lev, const BoxDesc* __restrict__ boxes, float* _
 }
 
 // ---------------------------------------------------------------------------
-// a6: active list and groups
+// a6: active list
 // ---------------------------------------------------------------------------
 
 __global__ void k_iota(int32_t* a, int n) {
@@ -406,38 +406,6 @@ __global__ void k_compact(const uint8_t* __restrict__ flag, const uint32_t* __re
     if (k < n && flag[k]) act[scan[k]] = k;
 }
 
-// One thread: per-box active ranges and group counts, then the group prefix.
-__global__ void k_box_groups(const BoxDesc* __restrict__ boxes, int nb, const uint32_t* __restrict__ scan,
-                             int gs, int* __restrict__ box_act, int* __restrict__ n_groups) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    int goff = 0;
-    for (int b = 0; b < nb; ++b) {
-        const BoxDesc& B = boxes[b];
-        int a0 = scan ? (int)scan[B.off] : (int)B.off;
-        int a1 = scan ? (int)scan[B.off + B.n] : (int)(B.off + B.n);
-        int ng = (a1 - a0 + gs - 1) / gs;
-        box_act[4 * b + 0] = a0;
-        box_act[4 * b + 1] = a1 - a0;
-        box_act[4 * b + 2] = goff;
-        box_act[4 * b + 3] = ng;
-        goff += ng;
-    }
-    *n_groups = goff;
-}
-
-__global__ void k_fill_groups(int nb, const int* __restrict__ box_act, int gs, Group* __restrict__ groups) {
-    int b = blockIdx.y;
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    int a0 = box_act[4 * b], an = box_act[4 * b + 1], g0 = box_act[4 * b + 2], ng = box_act[4 * b + 3];
-    if (t >= ng) return;
-    Group g;
-    g.box = b;
-    g.first = a0 + t * gs;
-    g.count = min(gs, an - t * gs);
-    g.pad = 0;
-    groups[g0 + t] = g;
-}
-
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
@@ -455,10 +423,9 @@ __global__ void k_fill_groups(int nb, const int* __restrict__ box_act, int gs, G
 void grid_free(sph_grid* g) {
     if (!g) return;
     void* ptrs[] = {g->boxes, g->posm, g->xq, g->perm, g->rank, g->keys, g->node_lo, g->node_hi,
-                    g->node_hmax, g->act, g->flag, g->scan, g->scan_tmp, g->box_act, g->n_groups,
-                    g->groups, g->list_a, g->list_b, g->st_lo, g->st_hi, g->list_n, g->d_off, g->d_L,
+                    g->node_hmax, g->act, g->flag, g->scan, g->scan_tmp, g->list_a, g->list_b, g->st_lo, g->st_hi, g->list_n, g->d_off, g->d_L,
                     g->k2, g->v1, g->v2, g->counts, g->cscan, g->node_c, g->node_e, g->posf,
-                    g->fvel, g->fthermo, g->fposh, g->fvm, g->fbal, g->fcond, g->fvisc, g->node_m, g->box_rci, g->nbr, g->nbr_off, g->nbr_n, g->ext_n, g->ext, g->list_h, g->list_st, g->fb_list, g->bw_ga, g->bw_xbar, g->bw_rd, g->bw_f, g->lcache, g->mp_j, g->den_left};
+                    g->fvel, g->fthermo, g->fposh, g->fvm, g->fbal, g->fcond, g->fvisc, g->node_m, g->box_rci, g->nbr, g->nbr_off, g->nbr_n, g->ext_n, g->ext, g->list_h, g->list_st, g->fb_list, g->bw_ga, g->bw_xbar, g->bw_rd, g->bw_f, g->mp_j, g->den_left};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete g;
@@ -500,7 +467,7 @@ sph_status grid_build(sph_ctx* ctx, const void* pos, int f64, const float* mass,
     g->box_bits = bb;
     // implicit hierarchy layout, box-major, level-minor
     g->boxes_h.resize(nb);
-    int node = 0, maxleaf = 0, maxgroups = 0, maxlev = 0;
+    int node = 0, maxleaf = 0, maxlev = 0;
     for (int b = 0; b < nb; ++b) {
         BoxDesc& B = g->boxes_h[b];
         B = BoxDesc();
@@ -531,11 +498,9 @@ sph_status grid_build(sph_ctx* ctx, const void* pos, int f64, const float* mass,
         if ((double)B.capu < cap) B.capu = std::nextafter(B.capu, INFINITY);
         maxlev = std::max(maxlev, lev);
         maxleaf = std::max(maxleaf, B.lvl_n[0]);
-        maxgroups += (int)((B.n + 15) / 16);
     }
     g->n_nodes = node;
     g->max_leaves = maxleaf;
-    g->max_groups = maxgroups;
     g->max_lev = maxlev;
 
     const int nblk = (n + kRsTile - 1) / kRsTile;
@@ -572,9 +537,6 @@ sph_status grid_build(sph_ctx* ctx, const void* pos, int f64, const float* mass,
     GRID_CHECK(cudaMalloc(&g->fvisc, sizeof(float2) * n));
     GRID_CHECK(cudaMalloc(&g->node_m, sizeof(float4) * node));
     GRID_CHECK(cudaMalloc(&g->box_rci, sizeof(unsigned long long) * nb));
-    // a 64 x 32 leaf list per persistent warp of the cooperative density
-    // kernel (<= 16 blocks of 3 warps per SM)
-    GRID_CHECK(cudaMalloc(&g->lcache, sizeof(int) * (size_t)ctx->sm_count * 16 * 3 * 64 * 32));
     // the near-list indices of the density pass's member-parallel path, one
     // block of kMpMembers x kMpCap per persistent warp
     GRID_CHECK(cudaMalloc(&g->mp_j, sizeof(int32_t) * (size_t)ctx->sm_count * kMpWarpsPerSm * kMpMembers * kMpCap));
@@ -605,9 +567,6 @@ sph_status grid_build(sph_ctx* ctx, const void* pos, int f64, const float* mass,
     GRID_CHECK(cudaMalloc(&g->flag, n));
     GRID_CHECK(cudaMalloc(&g->scan, sizeof(uint32_t) * (n + 1)));
     GRID_CHECK(cudaMalloc(&g->scan_tmp, sizeof(uint32_t) * tmp_words));
-    GRID_CHECK(cudaMalloc(&g->box_act, sizeof(int) * 4 * nb));
-    GRID_CHECK(cudaMalloc(&g->n_groups, sizeof(int)));
-    GRID_CHECK(cudaMalloc(&g->groups, sizeof(Group) * maxgroups));
     GRID_CHECK(cudaMalloc(&g->list_a, sizeof(int32_t) * n));
     GRID_CHECK(cudaMalloc(&g->list_b, sizeof(int32_t) * n));
     GRID_CHECK(cudaMalloc(&g->st_lo, sizeof(float) * n));
@@ -648,9 +607,8 @@ void grid_refresh_hmax(sph_grid* g, const float* h, cudaStream_t s) {
     }
 }
 
-void grid_active(sph_grid* g, const int32_t* active, int64_t n_active, int gs, bool groups, cudaStream_t s) {
-    int n = (int)g->n, nb = g->n_boxes;
-    const uint32_t* sc = nullptr;
+void grid_active(sph_grid* g, const int32_t* active, int64_t n_active, cudaStream_t s) {
+    int n = (int)g->n;
     unsigned& nl = g->ctx->launches;
     if (!active) {
         k_iota_count<<<(n + 255) / 256, 256, 0, s>>>(g->act, n, g->scan + n);
@@ -665,15 +623,7 @@ void grid_active(sph_grid* g, const int32_t* active, int64_t n_active, int gs, b
         scan_exclusive<uint8_t>(g->flag, n, g->scan, g->scan_tmp, s, &nl);
         k_compact<<<(n + 255) / 256, 256, 0, s>>>(g->flag, g->scan, n, g->act);
         ++nl;
-        sc = g->scan;
     }
-    if (!groups) return;
-    k_box_groups<<<1, 32, 0, s>>>(g->boxes, nb, sc, gs, g->box_act, g->n_groups);
-    nl += 2;
-    long long mx = 0;
-    for (auto& B : g->boxes_h) mx = std::max(mx, (B.n + gs - 1) / gs);
-    dim3 fg((unsigned)((mx + 127) / 128), nb);
-    k_fill_groups<<<fg, 128, 0, s>>>(nb, g->box_act, gs, g->groups);
 }
 
 }  // namespace sph

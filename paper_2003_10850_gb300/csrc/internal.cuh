@@ -60,10 +60,6 @@ struct sph_grid {
     uint8_t* flag = nullptr;               // n
     uint32_t* scan = nullptr;              // n + 1
     uint32_t* scan_tmp = nullptr;          // block sums
-    int* box_act = nullptr;                // per box: act_off, act_n, grp_off, grp_n
-    int* n_groups = nullptr;               // device scalar
-    sph::Group* groups = nullptr;          // capacity max_groups
-    int max_groups = 0;
     // plain-path scratch
     int32_t* list_a = nullptr;
     int32_t* list_b = nullptr;
@@ -78,7 +74,6 @@ struct sph_grid {
     unsigned* v2 = nullptr;
     unsigned* counts = nullptr;
     unsigned* cscan = nullptr;
-    int* lcache = nullptr;                 // cooperative density: leaf lists reused across iterations
     int32_t* mp_j = nullptr;               // density, member-parallel path: near-list indices per persistent warp
     int32_t* den_left = nullptr;           // density: particles left to the one-particle kernel (n)
     // neighbour lists recorded by an all-active density call on the default path and
@@ -128,16 +123,15 @@ void grid_free(sph_grid* g);
 sph_status grid_update(sph_grid* g, const void* pos, int f64, const float* mass, cudaStream_t s);
 // hmax of every node from the caller-order h
 void grid_refresh_hmax(sph_grid* g, const float* h, cudaStream_t s);
-// active list (sorted indices in g->act, count in g->scan[n]) and, if asked,
-// groups of at most gs particles per box
-void grid_active(sph_grid* g, const int32_t* active, int64_t n_active, int gs, bool groups, cudaStream_t s);
+// active list: sorted indices in g->act, count in g->scan[n]
+void grid_active(sph_grid* g, const int32_t* active, int64_t n_active, cudaStream_t s);
 // exclusive scan of n values into out[0..n] (out[n] = total); tmp >= n/4096+2 words
 template <typename In>
 void scan_exclusive(const In* in, int n, uint32_t* out, uint32_t* tmp, cudaStream_t s, unsigned* launches);
 // SPH_TIME_KERNELS support: event pair around one kernel launch
 cudaEvent_t timing_event(sph_ctx* ctx);
 
-// density.cu
+// the density pass (launch descriptions shared by the paths)
 struct DensityLaunch {
     const sph_grid* g;
     float* h;
@@ -151,6 +145,7 @@ struct DensityLaunch {
     int fixed_h, guess_h;
     int fp64;
     int blocks_per_sm;
+    double walk_radius;   // 0: default
     int time_kernels;
     int buffered;
     // velocity divergence and curl at the final h (default path only; NULL: not asked)
@@ -158,11 +153,11 @@ struct DensityLaunch {
     float* divv = nullptr;
     float* curlv = nullptr;
 };
-cudaError_t launch_density(sph_ctx* ctx, const DensityLaunch& a, cudaStream_t s);
+// plain.cu
 cudaError_t run_density_plain(sph_ctx* ctx, const DensityLaunch& a, int64_t n_active,
                               cudaStream_t s);
 
-// force.cu
+// the force pass
 struct ForceLaunch {
     const sph_grid* g;
     const float* vel;
@@ -187,7 +182,6 @@ struct ForceLaunch {
     // per-particle viscosity parameter (default path only; NULL: alpha for every pair)
     const float* alpha_v = nullptr;
 };
-cudaError_t launch_force(sph_ctx* ctx, const ForceLaunch& a, cudaStream_t s);
 cudaError_t launch_force_plain(sph_ctx* ctx, const ForceLaunch& a, int64_t n_active,
                                cudaStream_t s);
 
@@ -207,9 +201,6 @@ struct BackwardLaunch {
 };
 cudaError_t run_backward(sph_ctx* ctx, sph_grid* g, const BackwardLaunch& b, cudaStream_t s);
 
-// coop.cu (default path)
-cudaError_t launch_density_coop(sph_ctx* ctx, const DensityLaunch& a, cudaStream_t s);
-cudaError_t launch_force_coop(sph_ctx* ctx, const ForceLaunch& a, cudaStream_t s);
 
 // gravity.cu
 struct GravityLaunch {

@@ -41,21 +41,24 @@ constexpr int kWppThreads = kWppWarps * 32;
 constexpr int kWppDensityBps = 5;
 constexpr int kWppDensityMaxBps = 5;
 constexpr int kWppLeftBps = 6;   // the one-particle density kernel over the leftovers: 80 registers
+constexpr int kWppFmBps = 6;     // the member-parallel force walk: 80 registers
 constexpr int kWppForceBps = 8;
 constexpr int kWppMaxBps = 16;
 constexpr int kWppStack = 256;       // see the bound below
 constexpr int kWppPop4 = 96;         // pop four nodes per step only while sp <= this
+constexpr int kWppPop8 = 96;         // group walk: pop eight nodes per step only while sp <= this
 constexpr int kWppLeaves = 128;      // leaf list per warp; a step adds <= 32
 constexpr int kWppHits = 64;         // hit buffer per warp; drained at >= 32
 constexpr int kWppNear = 128;        // density: pairs within the walk radius, kept across h iterations
-constexpr int kWppGrpLeaves = 384;   // leaf list of a group walk, shared by the group's particles
+constexpr int kWppGrpLeaves = 448;   // leaf list of a group walk, shared by the group's particles
 constexpr int kWppGrpSpan = 64;      // a group never leaves one leaf-parent node (kLeaf * kFan particles)
-constexpr float kWppWalkR = 1.04f;   // density walks at 1.04 h so that later iterations reuse the list
+constexpr float kWppWalkR = 1.04f;   // default walk radius of the density pass (times the starting h)
 
 // Stack bound: a pop-4 step starts from sp <= 96 and ends at sp <= 92 + 32 =
-// 124. Above that, in the pop-1 regime, the entries above the base form a
-// depth-first stack with at most 7 pending siblings per level, so sp stays
-// below 124 + 8 * kMaxLev = 220 < kWppStack.
+// 124; a pop-8 step of the group walk ends at sp <= 88 + 64 = 152. Above that,
+// in the pop-1 regime, the entries above the base form a depth-first stack
+// with at most 7 pending siblings per level, so sp stays below
+// 152 + 8 * kMaxLev = 248 < kWppStack.
 
 struct WppSmem {
     int glf[kWppGrpLeaves];  // group walk: leaves within reach of at least one particle of the group
@@ -95,6 +98,7 @@ struct WppArgs {
     double n_target, n_tol;
     int max_iter;
     int guess_h, fixed_h;
+    float walk_r;                // density: near-list radius / h (see kWppWalkR)
     // force
     const float4* fvel;
     const float4* fthermo;
@@ -346,7 +350,8 @@ __device__ __forceinline__ WppGroup wpp_group(const BoxDesc* boxes, int nb, cons
     return g;
 }
 
-// One walk of the hierarchy for a whole group, whose members' integer
+// One walk of the hierarchy for a whole group (sm: any shared-memory block
+// with a leaf list glf[kWppGrpLeaves] and a stack stk[kWppStack]), whose members' integer
 // positions lie within hx[a] (integer units, per axis) of the integer centre
 // Gc; eg = hx * (L/2^32), rounded up. A node passes when its box comes within
 // radius(E) of the group's box. This holds whenever the node passes the test
@@ -368,8 +373,8 @@ struct WppGroupGeom {
     float eb;
 };
 
-template <class Radius>
-__device__ __forceinline__ int wpp_group_walk(WppSmem& sm, const BoxDesc& B, const uint4* __restrict__ node_c,
+template <class SM, class Radius>
+__device__ __forceinline__ int wpp_group_walk(SM& sm, const BoxDesc& B, const uint4* __restrict__ node_c,
                                               const float4* __restrict__ node_e, WppGroupGeom& gg, float sf,
                                               Radius&& radius) {
     const unsigned lane = lane_id();
@@ -383,17 +388,12 @@ __device__ __forceinline__ int wpp_group_walk(WppSmem& sm, const BoxDesc& B, con
     if (lane == 0) sm.stk[0] = (B.nlev - 1) << 27;
     int sp = 1;
     __syncwarp();
-    while (sp > 0) {
-        if (ngl > kWppGrpLeaves - 32) return -1;
-        const int npop = sp <= kWppPop4 ? min(sp, 4) : 1;
-        const int slot = (int)(lane >> 3), c = (int)(lane & 7u);
-        const int enc = slot < npop ? sm.stk[sp - 1 - slot] : 0;
-        __syncwarp();
-        sp -= npop;
+    // One child test of the walk: pass/leaf/internal for child c of node enc.
+    auto test = [&](int enc, int c, bool live, int& ct, bool& isleaf, bool& isint) {
         const int lev = enc >> 27, t = enc & ((1 << 27) - 1);
         const int cl = lev - 1;
-        int ct = t * kFan + c;
-        const bool ok = slot < npop && ct < B.lvl_n[max(cl, 0)];
+        ct = t * kFan + c;
+        const bool ok = live && ct < B.lvl_n[max(cl, 0)];
         bool pass = false;
         if (ok) {
             const int nd = B.lvl_off[cl] + ct;
@@ -413,13 +413,34 @@ __device__ __forceinline__ int wpp_group_walk(WppSmem& sm, const BoxDesc& B, con
                     eb = fmaxf(eb, rel * (4.f * (E.x + E.y + E.z) + 2.f * (fabsf(dx) + fabsf(dy) + fabsf(dz))));
             }
         }
-        const bool isleaf = pass && cl == 0, isint = pass && cl > 0;
-        const unsigned ml = __ballot_sync(0xffffffffu, isleaf);
-        const unsigned mi = __ballot_sync(0xffffffffu, isint);
-        if (isleaf) sm.glf[ngl + __popc(ml & lt)] = ct;
-        if (isint) sm.stk[sp + __popc(mi & lt)] = (cl << 27) | ct;
-        ngl += __popc(ml);
-        sp += __popc(mi);
+        isleaf = pass && cl == 0;
+        isint = pass && cl > 0;
+    };
+    // Up to eight nodes per step while the stack is shallow (two children per
+    // lane, their loads in flight together), one node per step beyond.
+    while (sp > 0) {
+        if (ngl > kWppGrpLeaves - 64) return -1;
+        const int npop = sp <= kWppPop8 ? min(sp, 8) : 1;
+        const int slot = (int)(lane >> 3), c = (int)(lane & 7u);
+        const int encA = slot < npop ? sm.stk[sp - 1 - slot] : 0;
+        const int encB = slot + 4 < npop ? sm.stk[sp - 5 - slot] : 0;
+        __syncwarp();
+        sp -= npop;
+        int ctA, ctB;
+        bool leafA, intA, leafB, intB;
+        test(encA, c, slot < npop, ctA, leafA, intA);
+        test(encB, c, slot + 4 < npop, ctB, leafB, intB);
+        const int clA = (encA >> 27) - 1, clB = (encB >> 27) - 1;
+        const unsigned mlA = __ballot_sync(0xffffffffu, leafA), miA = __ballot_sync(0xffffffffu, intA);
+        const unsigned mlB = __ballot_sync(0xffffffffu, leafB), miB = __ballot_sync(0xffffffffu, intB);
+        if (leafA) sm.glf[ngl + __popc(mlA & lt)] = ctA;
+        if (intA) sm.stk[sp + __popc(miA & lt)] = (clA << 27) | ctA;
+        ngl += __popc(mlA);
+        sp += __popc(miA);
+        if (leafB) sm.glf[ngl + __popc(mlB & lt)] = ctB;
+        if (intB) sm.stk[sp + __popc(miB & lt)] = (clB << 27) | ctB;
+        ngl += __popc(mlB);
+        sp += __popc(miB);
         __syncwarp();
     }
     gg.eb = warp_max(eb) + rel * 2.f * egs;
@@ -429,8 +450,8 @@ __device__ __forceinline__ int wpp_group_walk(WppSmem& sm, const BoxDesc& B, con
 // Group geometry from the members' integer positions (lanes with `valid`),
 // then the group walk. Returns -1 (no shared list) when the group spans a
 // quarter of the box or more on some axis.
-template <class Radius>
-__device__ __forceinline__ int wpp_group_leaves(WppSmem& sm, const BoxDesc& B, const uint4* __restrict__ node_c,
+template <class SM, class Radius>
+__device__ __forceinline__ int wpp_group_leaves(SM& sm, const BoxDesc& B, const uint4* __restrict__ node_c,
                                                 const float4* __restrict__ node_e, uint4 Xl, bool valid, float sf,
                                                 Radius&& radius, WppGroupGeom& gg) {
     const unsigned X0x = __shfl_sync(0xffffffffu, Xl.x, 0), X0y = __shfl_sync(0xffffffffu, Xl.y, 0),
@@ -671,6 +692,10 @@ static inline WppArgs wpp_common(sph_ctx* ctx, const sph_grid* g, unsigned* queu
     return c;
 }
 
+
+// The member-parallel kernels pay only when active particles share leaves:
+// below 1 in 16 active, groups are mostly single particles.
+static inline bool wpp_groups_pay(int64_t n_active, int64_t n) { return n_active * 16 >= n; }
 
 // Grid of a warp-per-particle helper kernel over n particles (256 threads).
 static inline int helper_blocks(sph_ctx* ctx, int64_t n) {

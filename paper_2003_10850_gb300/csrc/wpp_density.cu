@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_density_mp(WppArgs a) {
             float Rg = 0.f;
             WppGroupGeom gg;
             if (G.n >= 2 && B.nlev > 1) {
-                Rg = warp_max(a.fixed_h ? hl : hl * kWppWalkR);
+                Rg = warp_max(a.fixed_h ? hl : hl * a.walk_r);
                 ngl = wpp_group_leaves(sm, B, a.node_c, a.node_e, Xl, G.p >= 0, sf, [&](float4) { return Rg; }, gg);
             }
             unsigned todo = (1u << G.n) - 1u;   // members left for the one-particle path
@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_density_mp(WppArgs a) {
                 if ((int)lane < kMpMembers) {
                     float4 mem = make_float4(0.f, 0.f, 0.f, -1.f);
                     if ((int)lane < G.n) {
-                        const float Rw = a.fixed_h ? hl : hl * kWppWalkR;
+                        const float Rw = a.fixed_h ? hl : hl * a.walk_r;
                         const float tR = Rw + eT + 2.f * rel * Rw;
                         mem = make_float4((float)(int)(Xl.x - gg.Gc.x) * sf, (float)(int)(Xl.y - gg.Gc.y) * sf,
                                           (float)(int)(Xl.z - gg.Gc.z) * sf, tR * tR * (1.f + 4.f * rel));
@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_density_mp(WppArgs a) {
                 const int oim = __shfl_sync(0xffffffffu, ol, mm);
                 const uint4 Xm = mp.X[mm];
                 const int32_t* jm = mpj + mm * kMpCap;
-                const float Rwm = a.fixed_h ? h : h * kWppWalkR;
+                const float Rwm = a.fixed_h ? h : h * a.walk_r;
                 bool run = mval && cm <= kMpCap;
                 bool rew = mval && cm > kMpCap;   // near list overflowed: one-particle path
                 float blo = 0.f, bhi = INFINITY, dold = INFINITY;
@@ -488,7 +488,7 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_density_wpp(WppArgs a) {
             }
             int ngl = -1;
             if (G.n >= 2 && B.nlev > 1) {
-                const float Rg = warp_max(a.fixed_h ? hl : hl * kWppWalkR);
+                const float Rg = warp_max(a.fixed_h ? hl : hl * a.walk_r);
                 ngl = wpp_group_leaves(sm, B, a.node_c, a.node_e, Xl, G.p >= 0, sf, [&](float4) { return Rg; });
             }
             for (int m = 0; m < G.n; ++m) {
@@ -606,7 +606,7 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_density_wpp(WppArgs a) {
                     };
                     const bool rewalk = !complete || !(h <= Rw * 0.99999f);
                     if (rewalk) {
-                        Rw = a.fixed_h ? h : h * kWppWalkR;
+                        Rw = a.fixed_h ? h : h * a.walk_r;
                         nlf = 0;
                         nnear = 0;
                         complete = true;
@@ -1014,6 +1014,7 @@ cudaError_t launch_density_wpp(sph_ctx* ctx, const DensityLaunch& a, int64_t n_a
     c.max_iter = a.max_iter;
     c.guess_h = a.guess_h;
     c.fixed_h = a.fixed_h;
+    c.walk_r = a.walk_radius > 0.0 ? (float)a.walk_radius : kWppWalkR;
     // the scratch holds kMpWarpsPerSm warps per SM of the device the grid was built on
     c.mp_j = g->ctx->sm_count >= ctx->sm_count ? g->mp_j : nullptr;
     if (a.divv) {
@@ -1040,35 +1041,45 @@ cudaError_t launch_density_wpp(sph_ctx* ctx, const DensityLaunch& a, int64_t n_a
         c.list_chunk = (int)std::max<long long>(32, std::min<long long>(kListChunk, g->list_pool / (4 * warps)));
         if ((e = cudaMemsetAsync(g->list_st, 0, sizeof(unsigned) * kListSt, s))) return e;
     }
-    // leftovers of the member-parallel kernel: list g->den_left, count queue[6],
-    // work queue queue[5]
-    if ((e = cudaMemsetAsync(ctx->queue + 5, 0, 2 * sizeof(unsigned), s))) return e;
-    c.left = g->den_left;
-    c.left_n = ctx->queue + 6;
     WppSpan sp;
     if ((e = span_begin(ctx, a.time_kernels, 0, s, sp))) return e;
     const bool dc = a.divv != nullptr;
-    // 4 or 5 resident blocks (the shared memory of a block holds the member
-    // near lists: 5 blocks fill an SM), 128 or 96 registers
-    auto kd = bps <= 4 ? (a.hash ? (dc ? k_density_mp<true, 4, true> : k_density_mp<true, 4, false>)
-                                 : (dc ? k_density_mp<false, 4, true> : k_density_mp<false, 4, false>))
-                       : (a.hash ? (dc ? k_density_mp<true, 5, true> : k_density_mp<true, 5, false>)
-                                 : (dc ? k_density_mp<false, 5, true> : k_density_mp<false, 5, false>));
-    kd<<<blocks, kWppThreads, 0, s>>>(c);
-    // the leftovers, one particle per warp (count on the device), from the h the
-    // member-parallel kernel left for them
-    WppArgs cl = c;
-    cl.act = g->den_left;
-    cl.count_ptr = ctx->queue + 6;
-    cl.queue = ctx->queue + 5;
-    cl.chunk = 1;
-    cl.guess_h = 0;
-    int lblocks = 0, lchunk = 0;
-    wpp_shape(ctx, kWppLeftBps, n_active, lblocks, lchunk);
-    auto kl = a.hash ? (dc ? k_density_wpp<true, kWppLeftBps, true> : k_density_wpp<true, kWppLeftBps, false>)
-                     : (dc ? k_density_wpp<false, kWppLeftBps, true> : k_density_wpp<false, kWppLeftBps, false>);
-    kl<<<lblocks, kWppThreads, 0, s>>>(cl);
-    ctx->launches += 2;
+    if (!wpp_groups_pay(n_active, g->n) || !c.mp_j) {
+        // sparse active sets form groups of one: the one-particle kernel alone
+        auto k1 = a.hash ? (dc ? k_density_wpp<true, kWppLeftBps, true> : k_density_wpp<true, kWppLeftBps, false>)
+                         : (dc ? k_density_wpp<false, kWppLeftBps, true> : k_density_wpp<false, kWppLeftBps, false>);
+        int b1 = 0;
+        wpp_shape(ctx, kWppLeftBps, n_active, b1, c.chunk);
+        k1<<<b1, kWppThreads, 0, s>>>(c);
+        ++ctx->launches;
+    } else {
+        // leftovers of the member-parallel kernel: list g->den_left, count queue[6],
+        // work queue queue[5]
+        if ((e = cudaMemsetAsync(ctx->queue + 5, 0, 2 * sizeof(unsigned), s))) return e;
+        c.left = g->den_left;
+        c.left_n = ctx->queue + 6;
+        // 4 or 5 resident blocks (the shared memory of a block holds the member
+        // near lists: 5 blocks fill an SM), 128 or 96 registers
+        auto kd = bps <= 4 ? (a.hash ? (dc ? k_density_mp<true, 4, true> : k_density_mp<true, 4, false>)
+                                     : (dc ? k_density_mp<false, 4, true> : k_density_mp<false, 4, false>))
+                           : (a.hash ? (dc ? k_density_mp<true, 5, true> : k_density_mp<true, 5, false>)
+                                     : (dc ? k_density_mp<false, 5, true> : k_density_mp<false, 5, false>));
+        kd<<<blocks, kWppThreads, 0, s>>>(c);
+        // the leftovers, one particle per warp (count on the device), from the h the
+        // member-parallel kernel left for them
+        WppArgs cl = c;
+        cl.act = g->den_left;
+        cl.count_ptr = ctx->queue + 6;
+        cl.queue = ctx->queue + 5;
+        cl.chunk = 1;
+        cl.guess_h = 0;
+        int lblocks = 0, lchunk = 0;
+        wpp_shape(ctx, kWppLeftBps, n_active, lblocks, lchunk);
+        auto kl = a.hash ? (dc ? k_density_wpp<true, kWppLeftBps, true> : k_density_wpp<true, kWppLeftBps, false>)
+                         : (dc ? k_density_wpp<false, kWppLeftBps, true> : k_density_wpp<false, kWppLeftBps, false>);
+        kl<<<lblocks, kWppThreads, 0, s>>>(cl);
+        ctx->launches += 2;
+    }
     // SPH_TIME_KERNELS times the density kernel alone; the list build follows
     if ((e = span_end(ctx, sp, s))) return e;
     if (full) {

@@ -37,6 +37,10 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_force_wpp(WppArgs a) {
         act = a.fb_act;
         cnt = (int)*a.fb_count;
         chunk = 1;
+    } else if (a.left) {   // after the member-parallel walk: the particles it left
+        act = a.left;
+        cnt = (int)*a.left_n;
+        chunk = 1;
     }
     unsigned long long c_pairs = 0, c_tests = 0;   // lane 0's per-warp totals
     for (;;) {
@@ -278,6 +282,266 @@ __global__ void __launch_bounds__(128, 8) k_force_list(WppArgs a) {
 }
 
 
+// ---------------------------------------------------------------------------
+// Member-parallel force walk (active sets the neighbour lists cannot serve)
+// ---------------------------------------------------------------------------
+//
+// For a group of up to 8 active particles of one leaf-parent node: one walk
+// of the hierarchy at radius max(h_max of the group, h_max of the node), then
+// one sweep of the group's leaves with one candidate j per lane, decided for
+// every member i at once: j is a partner when r_ij < h_i or r_ij < h_j, in
+// FP32 outside a thin band around either radius and by the exact predicate
+// inside it. Each member's partners go to its pair list in the warp's global
+// scratch (kFmCap entries); the pair terms are then summed from the lists, a
+// member at a time, as the list-based force pass does. Singletons, groups
+// whose leaf list overflows and members whose pair list overflows are left
+// to the one-particle walk (k_force_wpp).
+constexpr int kFmCap = 256;   // pairs per member in the scratch list
+static_assert(kMpMembers * kFmCap <= 2 * kMpMembers * kMpCap, "scratch of a force warp");
+
+struct WppFmSmem {
+    int glf[kWppGrpLeaves];
+    int stk[kWppStack];
+    float4 mem[kMpMembers];   // member offset from the group centre, (h_i (1 + 2^-19) + eb)^2 (1 + 2^-18)
+    float lo[kMpMembers];     // (h_i (1 - 2^-19) - eb)^2 (1 - 2^-18): surely inside below this
+    float hm[kMpMembers];     // h_i
+    uint4 X[kMpMembers];      // integer positions
+    int cnt[kMpMembers];      // pairs found per member
+};
+
+template <bool HASH, int MINB, int VISC, bool COND>
+__global__ void __launch_bounds__(kWppThreads, MINB) k_force_mp(WppArgs a) {
+    // the recorded lists served this call: the walk takes only their fallbacks
+    if (a.fb_act && wpp_lists_valid(a.list_st, a.n_total)) return;
+    __shared__ WppFmSmem smem[kWppWarps];
+    const int wib = (int)(threadIdx.x >> 5);
+    WppFmSmem& sm = smem[wib];
+    // this warp's pair lists: kMpMembers x kFmCap entries
+    int32_t* pj = a.mp_j + ((size_t)blockIdx.x * kWppWarps + wib) * (kMpMembers * kFmCap);
+    const unsigned lane = lane_id();
+    const unsigned lt = (1u << lane) - 1u;
+    const float rel = 9.5367431640625e-07f;  // 2^-20
+    const float elo = 1.f - 4.f * rel, ehi = 1.f + 4.f * rel;
+    const float kNorm = (float)(8.0 / 3.141592653589793);
+    const int cnt = (int)*a.count_ptr;
+    unsigned long long c_pairs = 0, c_tests = 0;   // lane 0
+    for (;;) {
+        int t0 = 0;
+        if (lane == 0) t0 = (int)atomicAdd(a.queue, (unsigned)a.chunk);
+        t0 = __shfl_sync(0xffffffffu, t0, 0);
+        if (t0 >= cnt) break;
+        const int t1 = min(t0 + a.chunk, cnt);
+        for (int t = t0; t < t1;) {
+            const WppGroup G = wpp_group(a.boxes, a.n_boxes, a.act, t, t1);
+            t += G.n;
+            const BoxDesc& B = a.boxes[G.box];
+            const float sf = B.sf;
+            const int off = (int)B.off, pend = (int)(B.off + B.n);
+            uint4 Xl = make_uint4(0u, 0u, 0u, 0u);
+            float hl = 0.f;
+            if (G.p >= 0) {
+                Xl = a.posm[G.p];
+                hl = a.fvel[G.p].w;
+            }
+            int ngl = -1;
+            WppGroupGeom gg;
+            if (G.n >= 2 && B.nlev > 1) {
+                const float hg = warp_max(hl);
+                ngl = wpp_group_leaves(sm, B, a.node_c, a.node_e, Xl, G.p >= 0, sf,
+                                       [&](float4 e) { return fmaxf(hg, e.w); }, gg);
+            }
+            unsigned todo = (1u << G.n) - 1u;   // members left to the one-particle walk
+            if (ngl >= 0) {
+                const float eT = gg.eb;
+                if ((int)lane < kMpMembers) {
+                    float4 mem = make_float4(0.f, 0.f, 0.f, -1.f);
+                    float lo = -1.f;
+                    if ((int)lane < G.n) {
+                        const float ti = hl * (1.f + 2.f * rel) + eT, si = fmaxf(hl * (1.f - 2.f * rel) - eT, 0.f);
+                        mem = make_float4((float)(int)(Xl.x - gg.Gc.x) * sf, (float)(int)(Xl.y - gg.Gc.y) * sf,
+                                          (float)(int)(Xl.z - gg.Gc.z) * sf, ti * ti * ehi);
+                        lo = si * si * elo;
+                    }
+                    sm.mem[lane] = mem;
+                    sm.lo[lane] = lo;
+                    sm.hm[lane] = hl;
+                    sm.X[lane] = Xl;
+                }
+                __syncwarp();
+                int cntm[kMpMembers], pmv[kMpMembers];
+#pragma unroll
+                for (int k = 0; k < kMpMembers; ++k) {
+                    cntm[k] = 0;
+                    pmv[k] = __shfl_sync(0xffffffffu, G.p, k);   // -1 past G.n
+                }
+                unsigned ctest = 0;
+                const int lvl0 = B.lvl_off[0];
+                auto fetch = [&](int base, int& e, int& q, bool& cand, uint4& C, float4& f) {
+                    const int li = base + (int)(lane >> 3);
+                    e = li < ngl ? sm.glf[li] : 0;
+                    const int qq = off + (e & 0x7fffffff) * kLeaf + (int)(lane & 7u);
+                    cand = li < ngl && qq < pend;
+                    q = cand ? qq : off;
+                    C = a.node_c[lvl0 + (e & 0x7fffffff)];
+                    f = __ldg(a.fposh + q);
+                };
+                int e_n, q_n;
+                bool cand_n;
+                uint4 C_n;
+                float4 f_n;
+                fetch(0, e_n, q_n, cand_n, C_n, f_n);
+                for (int base = 0; base < ngl; base += 4) {
+                    const int e = e_n, q = q_n;
+                    const bool cand = cand_n;
+                    const uint4 C = C_n;
+                    const float4 f = f_n;
+                    if (base + 4 < ngl) fetch(base + 4, e_n, q_n, cand_n, C_n, f_n);
+                    const float px = (float)(int)(C.x - gg.Gc.x) * sf + f.x, py = (float)(int)(C.y - gg.Gc.y) * sf + f.y,
+                                pz = (float)(int)(C.z - gg.Gc.z) * sf + f.z;
+                    // j side of the band: h_j (1 +- 2^-19) widened/narrowed by the rounding bound
+                    const float hj = f.w;
+                    const float tj = hj * (1.f + 2.f * rel) + eT, sj = fmaxf(hj * (1.f - 2.f * rel) - eT, 0.f);
+                    const float hij = tj * tj * ehi, loj = sj * sj * elo;
+                    const bool wide = cand && e < 0;
+                    const bool anyw = __any_sync(0xffffffffu, wide);
+                    uint4 Xq = make_uint4(0u, 0u, 0u, 0u);
+                    if (anyw && wide) Xq = a.posm[q];
+                    ctest += __popc(__ballot_sync(0xffffffffu, cand));
+                    unsigned bandm = 0;   // members for which this lane's pair lies in the band
+#pragma unroll
+                    for (int m = 0; m < kMpMembers; ++m) {
+                        const float4 g = sm.mem[m];
+                        float dx = px - g.x, dy = py - g.y, dz = pz - g.z;
+                        if (anyw) {
+                            if (wide) {   // exact integer separations from the member
+                                const uint4 Xm = sm.X[m];
+                                dx = (float)(int)(Xq.x - Xm.x) * sf;
+                                dy = (float)(int)(Xq.y - Xm.y) * sf;
+                                dz = (float)(int)(Xq.z - Xm.z) * sf;
+                            }
+                        }
+                        const float r2 = dx * dx + dy * dy + dz * dz;
+                        const bool ok = cand && q != pmv[m];
+                        const bool in = ok && (r2 < sm.lo[m] || r2 < loj);
+                        const bool band = ok && !in && (r2 < g.w || r2 < hij);
+                        bandm |= band ? 1u << m : 0u;
+                        const unsigned msk = __ballot_sync(0xffffffffu, in);
+                        const int k = cntm[m] + __popc(msk & lt);
+                        if (in && k < kFmCap) pj[m * kFmCap + k] = q;
+                        cntm[m] += __popc(msk);
+                    }
+                    // the rare pairs within the band of either radius: the exact predicate
+                    const unsigned anyb = __reduce_or_sync(0xffffffffu, bandm);
+                    if (anyb) {
+                        const uint4 Xj = (bandm != 0u) ? a.posm[q] : make_uint4(0u, 0u, 0u, 0u);
+                        double HHj = -1.0;
+#pragma unroll 1
+                        for (int m = 0; m < kMpMembers; ++m) {
+                            if (!((anyb >> m) & 1u)) continue;
+                            bool in = false;
+                            if ((bandm >> m) & 1u) {   // r < h_i or r < h_j, exactly
+                                const unsigned long long D2 = exact_d2(sm.X[m], Xj);
+                                in = exact_pred(D2, wpp_hh(sm.hm[m], B));
+                                if (!in) {
+                                    if (HHj < 0.0) HHj = wpp_hh(hj, B);
+                                    in = exact_pred(D2, HHj);
+                                }
+                            }
+                            const unsigned msk = __ballot_sync(0xffffffffu, in);
+                            int c = 0;
+#pragma unroll
+                            for (int k2 = 0; k2 < kMpMembers; ++k2) c = m == k2 ? cntm[k2] : c;
+                            const int k = c + __popc(msk & lt);
+                            if (in && k < kFmCap) pj[m * kFmCap + k] = q;
+#pragma unroll
+                            for (int k2 = 0; k2 < kMpMembers; ++k2) cntm[k2] += m == k2 ? __popc(msk) : 0;
+                        }
+                    }
+                }
+                if (lane == 0) c_tests += (unsigned long long)ctest * (unsigned)G.n;
+                // members whose list overflowed go to the one-particle walk
+                todo = 0;
+                int cmine = 0;
+#pragma unroll
+                for (int k = 0; k < kMpMembers; ++k) {
+                    todo |= (k < G.n && cntm[k] > kFmCap) ? 1u << k : 0u;
+                    cmine = (int)lane == k ? cntm[k] : cmine;
+                }
+                if ((int)lane < kMpMembers) sm.cnt[lane] = cmine;
+                __syncwarp();
+                // pair terms from each member's list (as k_force_list)
+                for (int m = 0; m < G.n; ++m) {
+                    const int tot = sm.cnt[m];
+                    if (tot > kFmCap) continue;
+                    const int p = __shfl_sync(0xffffffffu, G.p, m);
+                    const uint4 Xi = sm.X[m];
+                    const int oi = a.perm[p];
+                    const float4 vi = a.fvm[p];
+                    const float4 thi = a.fthermo[p];
+                    const float2 ci = COND ? a.fcond[p] : make_float2(0.f, 0.f);
+                    const float2 bi = wpp_visc_i<VISC>(a, p);
+                    const WppForceI I = {vi.x, vi.y, vi.z, thi.w, thi.x, thi.y, thi.z,
+                                         kNorm * thi.w * thi.w * thi.w * thi.w, bi.x, ci.x, ci.y, bi.y};
+                    float Sx = 0.f, Sy = 0.f, Sz = 0.f, Su = 0.f, Sc = 0.f, vsmax = 0.f;
+                    unsigned long long hs = 0;
+                    const int32_t* lst = pj + m * kFmCap;
+                    for (int k = (int)lane; k < tot; k += 64) {
+                        const int k1 = k + 32;
+                        const bool two = k1 < tot;
+                        const int q0 = lst[k], q1 = two ? lst[k1] : q0;
+                        const uint4 X0 = a.posm[q0], X1 = a.posm[q1];
+                        const float4 v0 = __ldg(a.fvm + q0), v1 = __ldg(a.fvm + q1);
+                        const float4 th0 = __ldg(a.fthermo + q0), th1 = __ldg(a.fthermo + q1);
+                        const float2 b0 = wpp_visc_j<VISC>(a, q0), b1 = wpp_visc_j<VISC>(a, q1);
+                        const float2 c0 = COND ? __ldg(a.fcond + q0) : make_float2(0.f, 0.f);
+                        const float2 c1 = COND ? __ldg(a.fcond + q1) : make_float2(0.f, 0.f);
+                        wpp_force_pair<VISC, COND>(I, (float)(int)(X0.x - Xi.x) * sf, (float)(int)(X0.y - Xi.y) * sf,
+                                                   (float)(int)(X0.z - Xi.z) * sf, v0, th0, b0, c0, a.alpha, Sx, Sy, Sz,
+                                                   Su, Sc, vsmax);
+                        if (HASH) hs += splitmix64((unsigned long long)a.perm[q0]);
+                        if (two) {
+                            wpp_force_pair<VISC, COND>(I, (float)(int)(X1.x - Xi.x) * sf, (float)(int)(X1.y - Xi.y) * sf,
+                                                       (float)(int)(X1.z - Xi.z) * sf, v1, th1, b1, c1, a.alpha, Sx, Sy,
+                                                       Sz, Su, Sc, vsmax);
+                            if (HASH) hs += splitmix64((unsigned long long)a.perm[q1]);
+                        }
+                    }
+                    const float fs = wpp_fold4(Sx, Sy, Sz, Su);
+                    vsmax = warp_max(vsmax);
+                    if (HASH) hs = warp_sum(hs);
+                    if ((lane & 7u) == 0u) {
+                        const int comp = (int)(lane >> 3);
+                        if (comp < 3) a.acc[3 * (size_t)oi + comp] = fs;
+                        else a.dudt[oi] = fs;
+                    }
+                    if (COND) {
+                        float cs, cc, z0, z1;
+                        wpp_fold2(Sc, 0.f, cs, cc, z0, z1);
+                        if (lane == 0) a.dudt_cond[oi] = __fsub_rn(cs, cc);
+                    }
+                    if (lane == 0) {
+                        a.vsig[oi] = vsmax;
+                        if (HASH) a.hash[oi] = hs;
+                        c_pairs += (unsigned long long)tot;
+                    }
+                }
+                __syncwarp();
+            }
+            // the members left over go to the one-particle walk
+            if (todo) {
+                unsigned o = 0;
+                if (lane == 0) o = atomicAdd(a.left_n, (unsigned)__popc(todo));
+                o = __shfl_sync(0xffffffffu, o, 0);
+                if ((int)lane < G.n && ((todo >> lane) & 1u)) a.left[o + __popc(todo & lt)] = G.p;
+            }
+        }
+    }
+    if (lane == 0) {
+        atomicAdd(&a.ctr->force_pairs, c_pairs);
+        atomicAdd(&a.ctr->pair_tests, c_tests);
+    }
+}
+
 // Kernel variants of the force pass: hash output, register budget,
 // viscosity (kViscScalar ...), conduction. Per-particle viscosity comes
 // without conduction (no entry point asks for both).
@@ -304,6 +568,18 @@ static void launch_fw(int visc, bool cond, int blocks, cudaStream_t s, const Wpp
     } else {
         if (cond) k_force_wpp<H, M, kViscScalar, true><<<blocks, kWppThreads, 0, s>>>(c);
         else k_force_wpp<H, M, kViscScalar, false><<<blocks, kWppThreads, 0, s>>>(c);
+    }
+}
+template <bool H>
+static void launch_fm(int visc, bool cond, int blocks, cudaStream_t s, const WppArgs& c) {
+    constexpr int M = kWppFmBps;
+    if (visc == kViscPerParticle) k_force_mp<H, M, kViscPerParticle, false><<<blocks, kWppThreads, 0, s>>>(c);
+    else if (visc == kViscBalsara) {
+        if (cond) k_force_mp<H, M, kViscBalsara, true><<<blocks, kWppThreads, 0, s>>>(c);
+        else k_force_mp<H, M, kViscBalsara, false><<<blocks, kWppThreads, 0, s>>>(c);
+    } else {
+        if (cond) k_force_mp<H, M, kViscScalar, true><<<blocks, kWppThreads, 0, s>>>(c);
+        else k_force_mp<H, M, kViscScalar, false><<<blocks, kWppThreads, 0, s>>>(c);
     }
 }
 static void launch_force_walk(bool hash, bool six, int visc, bool cond, int blocks, cudaStream_t s,
@@ -358,6 +634,24 @@ cudaError_t launch_force_wpp(sph_ctx* ctx, const ForceLaunch& a, int64_t n_activ
         ++ctx->launches;
         c.fb_act = g->fb_list;
         c.fb_count = g->list_st + 3;
+    }
+    // the walk: member-parallel for groups (nothing to do when the lists served
+    // the call), then one particle per warp for what it leaves and for the
+    // particles the lists could not serve
+    if (g->ctx->sm_count >= ctx->sm_count && wpp_groups_pay(n_active, g->n)) {
+        if ((e = cudaMemsetAsync(ctx->queue + 6, 0, 2 * sizeof(unsigned), s))) return e;
+        WppArgs cm = c;
+        cm.mp_j = g->mp_j;
+        cm.left = g->den_left;
+        cm.left_n = ctx->queue + 6;
+        // a force warp uses the scratch of two density warps: at most half as many warps
+        const int fb = std::min(blocks, ctx->sm_count * (kMpWarpsPerSm / (2 * kWppWarps)));
+        a.hash ? launch_fm<true>(visc, c.fcond != nullptr, fb, s, cm)
+               : launch_fm<false>(visc, c.fcond != nullptr, fb, s, cm);
+        ++ctx->launches;
+        c.left = g->den_left;
+        c.left_n = ctx->queue + 6;
+        c.queue = ctx->queue + 7;
     }
     launch_force_walk(a.hash != nullptr, bps <= 6, visc, c.fcond != nullptr, blocks, s, c);
     ++ctx->launches;

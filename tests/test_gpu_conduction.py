@@ -82,4 +82,4 @@ def test_conduction_requires_kappa_and_default_path(S, ctx):
     with pytest.raises(S.SPHError):
         S.sph_hydro_force_conduction(ctx, grid, dev(p.vel), dev(p.u), z(n) + 0.1, z(n) + 1, z(n) + 1, None, None,
                                      dev(kappa), None, z(n, 3), z(n), z(n), z(n), None,
-                                     S.default_params(box=p.box, flags=S.SPH_COOP_WALK))
+                                     S.default_params(box=p.box, flags=S.SPH_PER_THREAD_WALK))

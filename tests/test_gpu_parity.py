@@ -78,14 +78,13 @@ def test_batched_keys_and_sort_exact(S, ctx):
 
 # ---- a4: density ------------------------------------------------------------
 
-PATHS = ["wpp", "coop", "thread", "warp"]
+PATHS = ["wpp", "thread"]
 
 
 def _flags(S, path, fp64):
     if path == "wpp" and fp64:
         pytest.skip("the warp-per-particle path is FP32 only (FP64 runs the per-thread walks)")
-    extra = {"wpp": S.SPH_WARP_WALK, "coop": S.SPH_COOP_WALK, "thread": S.SPH_PER_THREAD_WALK,
-             "warp": S.SPH_WARP_GROUP}[path]
+    extra = {"wpp": S.SPH_WARP_WALK, "thread": S.SPH_PER_THREAD_WALK}[path]
     return (S.SPH_FP64 if fp64 else 0) | extra
 
 
@@ -413,6 +412,11 @@ def test_error_statuses(S, ctx):
         S.sph_build_grid(ctx, dev(q.pos), dev(q.mass), S.default_params(box=-1.0))
     with pytest.raises(TypeError):
         S.sph_build_grid(ctx, dev(q.pos).double().cpu(), dev(q.mass), params)
+    # the warp-group and cooperative paths are no longer built: their flags are rejected
+    for fl in (S.SPH_WARP_GROUP, S.SPH_COOP_WALK):
+        with pytest.raises(S.SPHError) as e:
+            gpu_grid(S, ctx, q, S.default_params(flags=fl))
+        assert e.value.status == abi.SPH_ERR_INVALID
 
 
 def test_single_particle_and_tiny(S, ctx):
