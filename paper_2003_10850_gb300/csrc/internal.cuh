@@ -84,7 +84,8 @@ struct sph_grid {
     uint32_t* ext_n = nullptr;             // n: extra partners of i (j with h_i <= r_ij < h_j); after
                                            // the sort, kExtUnusable if they overflowed their segment
     int32_t* ext = nullptr;                // n segments of kExtCap: i's extra partners, ascending
-    float* list_h = nullptr;               // n: the h the lists were made with (sorted order)
+    uint4* list_xh = nullptr;              // n: integer position and the bits of the h the lists were
+                                           // made with (sorted order): one gather for the transpose
     unsigned* list_st = nullptr;           // device, kListSt words (see kListSt)
     int32_t* fb_list = nullptr;            // n: active particles the list force pass hands to the walk
     bool lists_full = false;               // host: the last density call recorded every particle's list
@@ -217,12 +218,12 @@ cudaError_t launch_density_wpp(sph_ctx* ctx, const DensityLaunch& a, int64_t n_a
 cudaError_t launch_force_wpp(sph_ctx* ctx, const ForceLaunch& a, int64_t n_active, cudaStream_t s);
 
 // tpp.cu (per-thread walks)
-// list_h / h_changed (optional): set *h_changed if some h differs from list_h;
+// list_xh / h_changed (optional): set *h_changed if some h differs from the h in list_xh;
 // divv / curlv (optional, caller order): Balsara factors into g->fbal;
 // kappa (optional, caller order): (u, kappa) into g->fcond;
 // alpha_v (optional, caller order): (Balsara factor or 1, alpha) into g->fvisc
 void force_pack(const sph_grid* g, const float* vel, const float* u, const float* h, const float* rho,
-                const float* omega, float gamma, cudaStream_t s, const float* list_h = nullptr,
+                const float* omega, float gamma, cudaStream_t s, const uint4* list_xh = nullptr,
                 unsigned* h_changed = nullptr, const float* divv = nullptr, const float* curlv = nullptr,
                 const float* kappa = nullptr, const float* alpha_v = nullptr);
 cudaError_t launch_density_tpp(sph_ctx* ctx, const DensityLaunch& a, int64_t n_active, cudaStream_t s);

@@ -521,7 +521,7 @@ __global__ void k_force_pack(int n, const int32_t* __restrict__ perm, const floa
                              const float* __restrict__ u, const float* __restrict__ h, const float* __restrict__ rho,
                              const float* __restrict__ omega, float gam, const float4* __restrict__ posf,
                              float4* __restrict__ fvel, float4* __restrict__ fthermo, float4* __restrict__ fposh,
-                             float4* __restrict__ fvm, const float* __restrict__ list_h, unsigned* h_changed,
+                             float4* __restrict__ fvm, const uint4* __restrict__ list_xh, unsigned* h_changed,
                              const float* __restrict__ divv, const float* __restrict__ curlv,
                              float* __restrict__ fbal, const float* __restrict__ kappa, float2* __restrict__ fcond,
                              const float* __restrict__ alpha_v, float2* __restrict__ fvisc) {
@@ -547,7 +547,7 @@ __global__ void k_force_pack(int n, const int32_t* __restrict__ perm, const floa
     if (fcond) fcond[p] = make_float2(u[o], kappa[o]);
     fposh[p] = make_float4(f.x, f.y, f.z, hh);
     // recorded neighbour lists are usable only if every h equals the one they were made with
-    if (list_h && !(hh == list_h[p])) atomicOr(h_changed, 1u);
+    if (list_xh && !(hh == __uint_as_float(list_xh[p].w))) atomicOr(h_changed, 1u);
 }
 
 struct TppForceArgs {
@@ -925,11 +925,11 @@ cudaError_t launch_density_tpp(sph_ctx* ctx, const DensityLaunch& a, int64_t n_a
 }
 
 void force_pack(const sph_grid* g, const float* vel, const float* u, const float* h, const float* rho,
-                const float* omega, float gamma, cudaStream_t s, const float* list_h, unsigned* h_changed,
+                const float* omega, float gamma, cudaStream_t s, const uint4* list_xh, unsigned* h_changed,
                 const float* divv, const float* curlv, const float* kappa, const float* alpha_v) {
     const int n = (int)g->n;
     k_force_pack<<<(n + 255) / 256, 256, 0, s>>>(n, g->perm, vel, u, h, rho, omega, gamma, g->posf, g->fvel, g->fthermo,
-                                                 g->fposh, g->fvm, list_h, h_changed, divv, curlv,
+                                                 g->fposh, g->fvm, list_xh, h_changed, divv, curlv,
                                                  divv && !alpha_v ? g->fbal : nullptr, kappa,
                                                  kappa ? g->fcond : nullptr, alpha_v,
                                                  alpha_v ? g->fvisc : nullptr);

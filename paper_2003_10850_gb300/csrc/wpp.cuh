@@ -116,7 +116,7 @@ struct WppArgs {
     int32_t* nbr_n;
     const int32_t* ext;          // n segments of kExtCap entries, ascending per particle
     const uint32_t* ext_n;       // extra partners per particle; kExtUnusable: not usable
-    float* list_h;
+    uint4* list_xh;              // the lists' particle data: integer position, bits of the h they were made with
     unsigned* list_st;           // see kListSt
     // density: velocity divergence and curl (NULL: not asked)
     const float4* vpack;         // sorted (v, m)

@@ -400,7 +400,7 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_density_mp(WppArgs a) {
                     if (a.nbr) {
                         a.nbr_off[pm] = loff >= 0 ? (int)loff : 0;
                         a.nbr_n[pm] = loff >= 0 ? nnm : -1;
-                        a.list_h[pm] = h;
+                        a.list_xh[pm] = make_uint4(Xm.x, Xm.y, Xm.z, __float_as_uint(h));
                         ++c_lists;
                     }
                     if (DIVCURL) {
@@ -805,7 +805,7 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_density_wpp(WppArgs a) {
                         if (lane == 0) {
                             a.nbr_off[p] = loff >= 0 ? loff : 0;
                             a.nbr_n[p] = loff >= 0 ? nn : -1;
-                            a.list_h[p] = h;
+                            a.list_xh[p] = make_uint4(Xi.x, Xi.y, Xi.z, __float_as_uint(h));
                         }
                         ++c_lists;
                     }
@@ -871,7 +871,7 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_density_wpp(WppArgs a) {
 __global__ void __launch_bounds__(256) k_list_ext(const BoxDesc* __restrict__ boxes, int nb, int n,
                                                   const uint4* __restrict__ posm, const int32_t* __restrict__ nbr,
                                                   const int32_t* __restrict__ nbr_off,
-                                                  const int32_t* __restrict__ nbr_n, const float* __restrict__ list_h,
+                                                  const int32_t* __restrict__ nbr_n, const uint4* __restrict__ list_xh,
                                                   uint32_t* __restrict__ ext_n, int32_t* __restrict__ ext,
                                                   unsigned* list_st) {
     // the lists serve a force call only if every particle's was written: when
@@ -889,8 +889,8 @@ __global__ void __launch_bounds__(256) k_list_ext(const BoxDesc* __restrict__ bo
         const int32_t* lj = nbr + nbr_off[j];
         const BoxDesc& B = boxes[nb == 1 ? 0 : wpp_box(boxes, nb, j)];
         const float Hs = B.Hs;   // integer units per box unit
-        const uint4 Xj = posm[j];
-        const float hj = list_h[j];
+        const uint4 Xj = list_xh[j];   // integer position, h bits
+        const float hj = __uint_as_float(Xj.w);
         auto decide = [&](float hi, uint4 Xi) {
             bool x = false;
             if (hi < hj) {
@@ -910,10 +910,10 @@ __global__ void __launch_bounds__(256) k_list_ext(const BoxDesc* __restrict__ bo
             const int k1 = k + 32;
             const bool two = k1 < cnt;
             const int i0 = lj[k], i1 = two ? lj[k1] : i0;
-            const float h0 = list_h[i0], h1 = list_h[i1];
-            const uint4 X0 = h0 < hj ? posm[i0] : Xj, X1 = (two && h1 < hj) ? posm[i1] : Xj;
-            if (decide(h0, X0)) place(i0);
-            if (two && decide(h1, X1)) place(i1);
+            // one 16-byte gather gives both h_i and X_i
+            const uint4 X0 = list_xh[i0], X1 = list_xh[i1];
+            if (decide(__uint_as_float(X0.w), X0)) place(i0);
+            if (two && decide(__uint_as_float(X1.w), X1)) place(i1);
         }
     }
 }
@@ -1033,7 +1033,7 @@ cudaError_t launch_density_wpp(sph_ctx* ctx, const DensityLaunch& a, int64_t n_a
         c.nbr = g->nbr;
         c.nbr_off = g->nbr_off;
         c.nbr_n = g->nbr_n;
-        c.list_h = g->list_h;
+        c.list_xh = g->list_xh;
         c.list_st = g->list_st;
         c.list_pool = g->list_pool;
         // chunks small enough that every warp's first reservations fit in a quarter of the pool
@@ -1085,7 +1085,7 @@ cudaError_t launch_density_wpp(sph_ctx* ctx, const DensityLaunch& a, int64_t n_a
     if (full) {
         const int n = (int)g->n, hb = helper_blocks(ctx, n);
         if ((e = cudaMemsetAsync(g->ext_n, 0, sizeof(uint32_t) * n, s))) return e;
-        k_list_ext<<<hb, 256, 0, s>>>(g->boxes, g->n_boxes, n, g->posm, g->nbr, g->nbr_off, g->nbr_n, g->list_h,
+        k_list_ext<<<hb, 256, 0, s>>>(g->boxes, g->n_boxes, n, g->posm, g->nbr, g->nbr_off, g->nbr_n, g->list_xh,
                                       g->ext_n, g->ext, g->list_st);
         k_list_sort<<<hb, 256, 0, s>>>(n, g->ext, g->ext_n, g->list_st);
         ctx->launches += 2;

@@ -593,7 +593,7 @@ cudaError_t launch_force_wpp(sph_ctx* ctx, const ForceLaunch& a, int64_t n_activ
     cudaError_t e;
     const bool lists = g->nbr != nullptr && g->lists_full;
     if (lists && (e = cudaMemsetAsync(g->list_st + 2, 0, 2 * sizeof(unsigned), s))) return e;
-    force_pack(g, a.vel, a.u, a.h, a.rho, a.omega, (float)a.gamma, s, lists ? g->list_h : nullptr,
+    force_pack(g, a.vel, a.u, a.h, a.rho, a.omega, (float)a.gamma, s, lists ? g->list_xh : nullptr,
                lists ? g->list_st + 2 : nullptr, a.divv, a.curlv, a.kappa, a.alpha_v);
     ++ctx->launches;
     if ((e = cudaMemsetAsync(ctx->queue + 3, 0, sizeof(unsigned), s))) return e;
