@@ -65,6 +65,14 @@ typedef enum {
 #define SPH_NO_LISTS 0x400        /* sph_build_grid: do not allocate the neighbour lists that the
                                      default path records in an all-active density pass and reuses
                                      in the force pass (saves ~1,040 bytes per particle) */
+#define SPH_PARTIAL_LISTS 0x800   /* sph_density on the default path with an active list (when the
+                                     member-parallel kernel runs): record the active particles' lists
+                                     and their extra partners (j with h_i <= r_ij < h_j), those
+                                     among the inactive particles found by a wider sweep of the
+                                     density pass, so that a force call on that set reads them.
+                                     The wider sweep costs the density pass about what the lists
+                                     save the force pass; without the flag such a call records
+                                     nothing and the force pass walks. */
 
 /* Device status bits returned in sph_stats.status */
 #define SPH_ST_NOT_CONVERGED 0x01
@@ -106,6 +114,8 @@ typedef struct {
     uint32_t force_launches;   /* SPH_TIME_KERNELS: timed force kernel launches */
     uint64_t grav_nodes;      /* sph_gravity: node (monopole) interactions */
     uint64_t grav_pairs;      /* sph_gravity: particle interactions inside the cutoff */
+    uint64_t list_force;      /* force: active particles served from the neighbour lists that
+                                 the last density call recorded (the others walk) */
 } sph_stats;
 
 /* Fills *p with the library defaults: L = 1, N_t = 64, n_tol = 1e-6 N_t,

@@ -12,7 +12,7 @@ import ctypes
 import torch
 
 from . import abi
-from .abi import (SPH_FIXED_H, SPH_FP64, SPH_H_GUESS, SPH_PLAIN_FP32, SPH_TIME_KERNELS, SPH_WARP_GROUP, SPH_DENSITY_BUFFERED, SPH_PER_THREAD_WALK, SPH_COOP_WALK, SPH_WARP_WALK, SPH_NO_LISTS, SPHError,
+from .abi import (SPH_FIXED_H, SPH_FP64, SPH_H_GUESS, SPH_PLAIN_FP32, SPH_TIME_KERNELS, SPH_WARP_GROUP, SPH_DENSITY_BUFFERED, SPH_PER_THREAD_WALK, SPH_COOP_WALK, SPH_WARP_WALK, SPH_NO_LISTS, SPH_PARTIAL_LISTS, SPHError,
                   default_params, sph_gravity_params, sph_params, sph_stats)
 
 __all__ = ["Context", "Grid", "sph_create", "sph_build_grid", "sph_build_grid_batched", "sph_grid_update",
@@ -21,7 +21,7 @@ __all__ = ["Context", "Grid", "sph_create", "sph_build_grid", "sph_build_grid_ba
            "sph_predict_scalar", "sph_gravity", "gravity_params", "sph_gravity_params", "sph_timebins", "sph_active_from_bins", "sph_kick", "sph_drift",
            "sph_backward", "sph_sync_status", "sph_grid_export", "sph_sort_keys_static", "density",
            "hydro_force", "default_params", "sph_params", "sph_stats", "SPHError", "SPH_FP64",
-           "SPH_PLAIN_FP32", "SPH_FIXED_H", "SPH_H_GUESS", "SPH_TIME_KERNELS", "SPH_WARP_GROUP", "SPH_DENSITY_BUFFERED", "SPH_PER_THREAD_WALK", "SPH_COOP_WALK", "SPH_WARP_WALK", "SPH_NO_LISTS"]
+           "SPH_PLAIN_FP32", "SPH_FIXED_H", "SPH_H_GUESS", "SPH_TIME_KERNELS", "SPH_WARP_GROUP", "SPH_DENSITY_BUFFERED", "SPH_PER_THREAD_WALK", "SPH_COOP_WALK", "SPH_WARP_WALK", "SPH_NO_LISTS", "SPH_PARTIAL_LISTS"]
 
 
 def _ptr(t, dtype=None, name="tensor"):

@@ -35,6 +35,7 @@ SPH_PER_THREAD_WALK = 0x80
 SPH_COOP_WALK = 0x100
 SPH_WARP_WALK = 0x200
 SPH_NO_LISTS = 0x400
+SPH_PARTIAL_LISTS = 0x800
 
 SPH_ST_NOT_CONVERGED = 0x01
 SPH_ST_H_TOO_LARGE = 0x02
@@ -64,7 +65,7 @@ class sph_stats(ctypes.Structure):
                 ("groups", ctypes.c_uint64), ("density_kernel_ms", ctypes.c_double),
                 ("force_kernel_ms", ctypes.c_double), ("density_launches", ctypes.c_uint32),
                 ("force_launches", ctypes.c_uint32), ("grav_nodes", ctypes.c_uint64),
-                ("grav_pairs", ctypes.c_uint64)]
+                ("grav_pairs", ctypes.c_uint64), ("list_force", ctypes.c_uint64)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

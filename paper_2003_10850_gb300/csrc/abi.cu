@@ -229,9 +229,12 @@ static sph_status density_call(sph_ctx* ctx, const sph_grid* grid, float* h, con
     a.walk_radius = params->walk_radius;
     a.time_kernels = (params->flags & SPH_TIME_KERNELS) ? 1 : 0;
     a.buffered = (params->flags & SPH_DENSITY_BUFFERED) ? 1 : 0;
+    a.active_list = active ? 1 : 0;
+    a.partial_lists = (params->flags & SPH_PARTIAL_LISTS) ? 1 : 0;
     a.vel = vel;
     a.divv = divv;
     a.curlv = curlv;
+    g->lists_rec = false;   // set again by a call that records neighbour lists
     cudaError_t e = path == Path::Plain ? run_density_plain(ctx, a, na, s)
                     : path == Path::Wpp ? launch_density_wpp(ctx, a, na, s)
                                         : launch_density_tpp(ctx, a, na, s);
@@ -454,6 +457,7 @@ sph_status sph_sync_status(sph_ctx* ctx, void* stream, sph_stats* stats) {
         stats->density_evals = c.density_evals;
         stats->pair_tests = c.pair_tests;
         stats->groups = c.groups;
+        stats->list_force = c.list_force;
         stats->grav_nodes = c.grav_nodes;
         stats->grav_pairs = c.grav_pairs;
     }

@@ -56,6 +56,7 @@ struct Counters {
     unsigned long long groups;
     unsigned long long grav_nodes;
     unsigned long long grav_pairs;
+    unsigned long long list_force;
 };
 
 // -------------------------------------------------------------------------

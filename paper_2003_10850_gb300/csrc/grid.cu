@@ -425,7 +425,7 @@ void grid_free(sph_grid* g) {
     void* ptrs[] = {g->boxes, g->posm, g->xq, g->perm, g->rank, g->keys, g->node_lo, g->node_hi,
                     g->node_hmax, g->act, g->flag, g->scan, g->scan_tmp, g->list_a, g->list_b, g->st_lo, g->st_hi, g->list_n, g->d_off, g->d_L,
                     g->k2, g->v1, g->v2, g->counts, g->cscan, g->node_c, g->node_e, g->posf,
-                    g->fvel, g->fthermo, g->fposh, g->fvm, g->fbal, g->fcond, g->fvisc, g->node_m, g->box_rci, g->nbr, g->nbr_off, g->nbr_n, g->ext_n, g->ext, g->list_xh, g->list_st, g->fb_list, g->bw_ga, g->bw_xbar, g->bw_rd, g->bw_f, g->mp_j, g->den_left};
+                    g->fvel, g->fthermo, g->fposh, g->fvm, g->fbal, g->fcond, g->fvisc, g->node_m, g->box_rci, g->nbr, g->nbr_off, g->nbr_n, g->ext_n, g->ext, g->list_xh, g->list_st, g->fb_list, g->list_ep, g->mp_x, g->bw_ga, g->bw_xbar, g->bw_rd, g->bw_f, g->mp_j, g->den_left};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete g;
@@ -548,13 +548,16 @@ sph_status grid_build(sph_ctx* ctx, const void* pos, int f64, const float* mass,
         const long long lim = (1ll << 31) - (1ll << 12);
         g->list_pool = (int64_t)std::min<long long>((long long)n * kListPool, lim);
         void** lp[] = {(void**)&g->nbr, (void**)&g->nbr_off, (void**)&g->nbr_n, (void**)&g->ext_n,
-                       (void**)&g->ext, (void**)&g->list_xh, (void**)&g->list_st, (void**)&g->fb_list};
+                       (void**)&g->ext, (void**)&g->list_xh, (void**)&g->list_st, (void**)&g->fb_list,
+                       (void**)&g->list_ep, (void**)&g->mp_x};
         const size_t sz[] = {sizeof(int32_t) * (size_t)g->list_pool, sizeof(int32_t) * n, sizeof(int32_t) * n,
                              sizeof(uint32_t) * n, sizeof(int32_t) * (size_t)n * kExtCap, sizeof(uint4) * n,
-                             sizeof(unsigned) * kListSt, sizeof(int32_t) * n};
+                             sizeof(unsigned) * kListSt, sizeof(int32_t) * n, sizeof(uint32_t) * n,
+                             sizeof(int32_t) * (size_t)ctx->sm_count * kMpWarpsPerSm * kMpMembers * kMpFar};
         bool ok = true;
-        for (int k = 0; k < 8 && ok; ++k) ok = cudaMalloc(lp[k], sz[k]) == cudaSuccess;
+        for (int k = 0; k < 10 && ok; ++k) ok = cudaMalloc(lp[k], sz[k]) == cudaSuccess;
         if (ok) ok = cudaMemset(g->list_st, 0, sizeof(unsigned) * kListSt) == cudaSuccess;
+        if (ok) ok = cudaMemset(g->list_ep, 0, sizeof(uint32_t) * n) == cudaSuccess;
         if (!ok) {
             (void)cudaGetLastError();
             for (void** q : lp) {
@@ -585,7 +588,7 @@ sph_status grid_build(sph_ctx* ctx, const void* pos, int f64, const float* mass,
 }
 
 sph_status grid_update(sph_grid* g, const void* pos, int f64, const float* mass, cudaStream_t s) {
-    g->lists_full = false;   // the particles may have moved: recorded neighbour lists are stale
+    g->lists_rec = false;   // the particles may have moved: recorded neighbour lists are stale
     grid_fill(g, pos, f64, mass, s);
     cudaError_t e = cudaGetLastError();
     if (e) {

@@ -88,7 +88,11 @@ struct sph_grid {
                                            // made with (sorted order): one gather for the transpose
     unsigned* list_st = nullptr;           // device, kListSt words (see kListSt)
     int32_t* fb_list = nullptr;            // n: active particles the list force pass hands to the walk
-    bool lists_full = false;               // host: the last density call recorded every particle's list
+    bool lists_rec = false;                // host: the last density call recorded lists (all or some particles)
+    uint32_t* list_ep = nullptr;           // n: generation (list_st word kListGen) of the call that recorded
+                                           // the particle's list and extra partners
+    int32_t* mp_x = nullptr;               // density, member-parallel path of a partial call: per warp,
+                                           // kMpMembers x kMpFar inactive partners beyond the near radius
     int64_t list_pool = 0;                 // entries of the nbr pool
     // adjoint scratch (allocated by the first sph_backward on the grid)
     float4* bw_ga = nullptr;
@@ -110,10 +114,13 @@ constexpr int kListChunk = 2048; // pool entries a warp reserves at a time for i
 constexpr int kMpMembers = 8;
 constexpr int kMpCap = 128;
 constexpr int kMpWarpsPerSm = 64;
-// list_st words: [0] lists written, [1] a list missing (pool full), [2] h
-// changed since the lists were made, [3] fallback count, [4..5] pool entries
-// reserved (64-bit)
-constexpr int kListSt = 6;
+// list_st words: [0] lists written, [1] a list missing (pool full) or the
+// extra partners incomplete, [2] h changed since the lists were made, [3]
+// fallback count, [4..5] pool entries reserved (64-bit), [6] generation: one
+// more for every density call (never cleared), [7] unused
+constexpr int kListSt = 8;
+constexpr int kListGen = 6;
+constexpr int kMpFar = 128;     // inactive partners beyond the near radius per member (partial calls)
 
 // grid.cu
 sph_status grid_build(sph_ctx* ctx, const void* pos, int f64, const float* mass, bool lists,
@@ -149,6 +156,8 @@ struct DensityLaunch {
     double walk_radius;   // 0: default
     int time_kernels;
     int buffered;
+    int active_list = 0;  // the caller gave an active list (the device count may be below n_active)
+    int partial_lists = 0; // SPH_PARTIAL_LISTS
     // velocity divergence and curl at the final h (default path only; NULL: not asked)
     const float* vel = nullptr;
     float* divv = nullptr;

@@ -114,8 +114,8 @@ struct WppArgs {
     int32_t* nbr;                // pool of list_pool entries
     int32_t* nbr_off;
     int32_t* nbr_n;
-    const int32_t* ext;          // n segments of kExtCap entries, ascending per particle
-    const uint32_t* ext_n;       // extra partners per particle; kExtUnusable: not usable
+    int32_t* ext;                // n segments of kExtCap entries, ascending per particle
+    uint32_t* ext_n;             // extra partners per particle; kExtUnusable: not usable
     uint4* list_xh;              // the lists' particle data: integer position, bits of the h they were made with
     unsigned* list_st;           // see kListSt
     // density: velocity divergence and curl (NULL: not asked)
@@ -142,12 +142,19 @@ struct WppArgs {
     // density: the particles the member-parallel kernel leaves to the one-particle kernel
     int32_t* left;
     unsigned* left_n;
+    // lists of a partial active set: the active flag per sorted particle, the
+    // far-partner scratch (kMpMembers x kMpFar per warp), and the generation
+    // stamp per particle (a list serves only if its stamp is the current one)
+    const uint8_t* flagp;
+    int32_t* mp_x;
+    uint32_t* list_ep;
 };
 
-// The recorded lists can serve this force call: every particle's list was
-// written by the last density call, none is missing, and h is unchanged.
-__device__ __forceinline__ bool wpp_lists_valid(const unsigned* st, int n) {
-    return st[0] == (unsigned)n && st[1] == 0u && st[2] == 0u;
+// The recorded lists can serve this force call: none of the recorded lists
+// is missing or has incomplete extra partners, and h is unchanged. (Whether a
+// particle's own list is from the last density call is its list_ep stamp.)
+__device__ __forceinline__ bool wpp_lists_valid(const unsigned* st) {
+    return st[1] == 0u && st[2] == 0u;
 }
 
 __device__ __forceinline__ int wpp_box(const BoxDesc* boxes, int nb, long long p) {

@@ -53,13 +53,21 @@ __device__ __forceinline__ void wpp_fold_quad2(float& s1, float& c1, float& s2, 
     }
 }
 
-template <bool HASH, int MINB, bool DIVCURL>
+// PART: a call on part of the particles that records lists; each member also
+// collects its extra partners among the inactive particles (j with
+// h_i <= r_ij < h_j), whose h is fixed: the walk reaches the inactive
+// particles' h_max (node_e.w, refreshed for this call), and the sweep keeps
+// inactive candidates within h_j beyond the member's near radius in a "far"
+// list in the warp's scratch.
+template <bool HASH, int MINB, bool DIVCURL, bool PART>
 __global__ void __launch_bounds__(kWppThreads, MINB) k_density_mp(WppArgs a) {
     __shared__ __align__(16) unsigned char sraw[kWppWarps][kDenSmemWarp];
     const int wib = (int)(threadIdx.x >> 5);
     WppSmem& sm = *reinterpret_cast<WppSmem*>(sraw[wib]);
     WppMpSmem& mp = *reinterpret_cast<WppMpSmem*>(sraw[wib] + kGlfBytes);
     int32_t* mpj = a.mp_j ? a.mp_j + ((size_t)blockIdx.x * kWppWarps + wib) * (kMpMembers * kMpCap) : nullptr;
+    int32_t* mpx = PART ? a.mp_x + ((size_t)blockIdx.x * kWppWarps + wib) * (kMpMembers * kMpFar) : nullptr;
+    const unsigned gen = a.list_st ? a.list_st[kListGen] : 0u;   // this call's generation
     const unsigned lane = lane_id();
     const unsigned lt = (1u << lane) - 1u;
     const float rel = 9.5367431640625e-07f;  // 2^-20
@@ -119,7 +127,8 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_density_mp(WppArgs a) {
             WppGroupGeom gg;
             if (G.n >= 2 && B.nlev > 1) {
                 Rg = warp_max(a.fixed_h ? hl : hl * a.walk_r);
-                ngl = wpp_group_leaves(sm, B, a.node_c, a.node_e, Xl, G.p >= 0, sf, [&](float4) { return Rg; }, gg);
+                ngl = wpp_group_leaves(sm, B, a.node_c, a.node_e, Xl, G.p >= 0, sf,
+                                       [&](float4 e) { return PART ? fmaxf(Rg, e.w) : Rg; }, gg);
             }
             unsigned todo = (1u << G.n) - 1u;   // members left for the one-particle path
             if (ngl >= 0 && mpj && G.n >= 2) {
@@ -170,6 +179,18 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_density_mp(WppArgs a) {
                     const uint4 C = C_n;
                     const float4 f = f_n;
                     if (base + 4 < ngl) fetch(base + 4, e_n, q_n, cand_n, C_n, f_n);
+                    // PART: candidate j inactive, and the square of its h widened by the
+                    // rounding bound (the far test is inclusive; the last sweep decides)
+                    bool ina = false;
+                    float Tj = -1.f;
+                    if (PART && cand) {
+                        ina = a.flagp[q] == 0;
+                        if (ina) {
+                            const float tj = __uint_as_float(a.list_xh[q].w) * (1.f + 2.f * rel) + eT;
+                            Tj = tj * tj * (1.f + 4.f * rel);
+                        }
+                    }
+                    const bool anyina = PART && __any_sync(0xffffffffu, ina);
                     const float px = (float)(int)(C.x - gg.Gc.x) * sf + f.x, py = (float)(int)(C.y - gg.Gc.y) * sf + f.y,
                                 pz = (float)(int)(C.z - gg.Gc.z) * sf + f.z;
                     const bool wide = cand && e < 0;
@@ -182,12 +203,19 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_density_mp(WppArgs a) {
                             const float r2 = dx * dx + dy * dy + dz * dz;
                             const bool in = cand && q != pmv[m] && r2 < g.w;
                             const unsigned msk = __ballot_sync(0xffffffffu, in);
-                            const int k = cntm[m] + __popc(msk & lt);
+                            const int k = (cntm[m] & 0xffff) + __popc(msk & lt);
                             if (in && k < kMpCap) {
                                 mp.d[m][k] = make_float2(r2, f.w);
                                 mpj[m * kMpCap + k] = q;
                             }
                             cntm[m] += __popc(msk);
+                            if (anyina) {
+                                const bool far = ina && m < G.n && !(r2 < g.w) && r2 < Tj;
+                                const unsigned fm = __ballot_sync(0xffffffffu, far);
+                                const int kf = (cntm[m] >> 16) + __popc(fm & lt);
+                                if (far && kf < kMpFar) mpx[m * kMpFar + kf] = q;
+                                cntm[m] += __popc(fm) << 16;
+                            }
                         }
                     } else {
                         // a wide leaf in the step: exact integer separations from each member there
@@ -205,12 +233,19 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_density_mp(WppArgs a) {
                             const float r2 = dx * dx + dy * dy + dz * dz;
                             const bool in = cand && q != pmv[m] && r2 < g.w;
                             const unsigned msk = __ballot_sync(0xffffffffu, in);
-                            const int k = cntm[m] + __popc(msk & lt);
+                            const int k = (cntm[m] & 0xffff) + __popc(msk & lt);
                             if (in && k < kMpCap) {
                                 mp.d[m][k] = make_float2(r2, f.w);
                                 mpj[m * kMpCap + k] = q;
                             }
                             cntm[m] += __popc(msk);
+                            if (anyina) {
+                                const bool far = ina && m < G.n && !(r2 < g.w) && r2 < Tj;
+                                const unsigned fm = __ballot_sync(0xffffffffu, far);
+                                const int kf = (cntm[m] >> 16) + __popc(fm & lt);
+                                if (far && kf < kMpFar) mpx[m * kMpFar + kf] = q;
+                                cntm[m] += __popc(fm) << 16;
+                            }
                         }
                     }
                 }
@@ -221,6 +256,8 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_density_mp(WppArgs a) {
                 int cm = 0;
 #pragma unroll
                 for (int k = 0; k < kMpMembers; ++k) cm = mm == k ? cntm[k] : cm;
+                const int cf = PART ? (cm >> 16) : 0;   // far entries (inactive, beyond the near radius)
+                cm &= 0xffff;
                 const bool mval = mm < G.n;
                 float h = __shfl_sync(0xffffffffu, hl, mm);
                 const int pm = __shfl_sync(0xffffffffu, G.p, mm);
@@ -317,10 +354,30 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_density_mp(WppArgs a) {
                         pre += k < mm ? v : 0;
                         tot += v;
                     }
-                    const long long gb = tot > 0 ? reserve(tot) : -1;
+                    const long long gb = tot > 0 ? reserve(tot) : 0;   // (empty lists need no space)
                     loff = gb >= 0 ? gb + pre : -1;
                 }
                 const bool rec = loff >= 0 && nnm > 0;
+                // PART: member mm's extra partners among the inactive particles go
+                // straight into its segment (the transpose adds the active ones after)
+                int nex = 0;
+                int32_t* seg = PART && pm >= 0 ? a.ext + (size_t)pm * kExtCap : nullptr;
+                auto add_extra = [&](bool xt, int q) {
+                    const unsigned xb = (__ballot_sync(0xffffffffu, xt) >> (4 * mm)) & 0xfu;
+                    const int sl = nex + __popc(xb & ((1u << sub) - 1u));
+                    if (xt && sl < kExtCap) seg[sl] = q;
+                    nex += __popc(xb);
+                };
+                // r_ij < h_j for a partner with position and h bits Xq: FP32 outside a
+                // band of 2^-20 around h_j^2 (integer units), the exact predicate inside
+                auto within_hj = [&](uint4 Xq) {
+                    const float hj = __uint_as_float(Xq.w);
+                    const unsigned long long D2 = exact_d2(Xm, Xq);
+                    const float d2 = __ull2float_rn(D2), Hj = hj * B.Hs, H2 = Hj * Hj;
+                    if (d2 < H2 * (1.f - rel)) return true;
+                    if (d2 > H2 * (1.f + rel)) return false;
+                    return exact_pred(D2, wpp_hh(hj, B));
+                };
                 unsigned long long hs = 0;
                 float Dd = 0.f, Dx = 0.f, Dy = 0.f, Dz = 0.f;   // per-lane div/curl sums
                 if (a.nbr || DIVCURL || HASH) {
@@ -333,10 +390,11 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_density_mp(WppArgs a) {
                     const int kend = okm ? cm : 0;
                     int pos = 0;
                     for (int k = sub; __any_sync(0xffffffffu, k < kend); k += 4) {
-                        bool in = false;
+                        bool in = false, xt = false;
                         int q = 0;
                         if (k < kend) {
                             const float x2 = mp.d[mm][k].x;
+                            if (PART) q = jm[k];
                             if (x2 < hi2) {
                                 q = jm[k];
                                 in = x2 < lo2;
@@ -345,7 +403,10 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_density_mp(WppArgs a) {
                                     in = exact_pred(exact_d2(Xm, a.posm[q]), HH);
                                 }
                             }
+                            // an inactive near entry outside h_i with r_ij < h_j: an extra partner
+                            if (PART && !in && a.flagp[q] == 0) xt = within_hj(a.list_xh[q]);
                         }
+                        if (PART) add_extra(xt, q);
                         const unsigned nib = (__ballot_sync(0xffffffffu, in) >> (4 * mm)) & 0xfu;
                         if (in) {
                             const int kk = pos + __popc(nib & ((1u << sub) - 1u));
@@ -374,6 +435,20 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_density_mp(WppArgs a) {
                         pos += __popc(nib);
                     }
                     if (rec && pos != nnm) loff = -1;   // cannot happen: the same predicate counted nnm
+                    if (PART) {
+                        // the far entries: r_ij > h_i surely, partners when r_ij < h_j
+                        const int kf = okm ? min(cf, kMpFar) : 0;
+                        const int32_t* xm = mpx + mm * kMpFar;
+                        for (int k = sub; __any_sync(0xffffffffu, k < kf); k += 4) {
+                            bool xt = false;
+                            int q = 0;
+                            if (k < kf) {
+                                q = xm[k];
+                                xt = within_hj(a.list_xh[q]);
+                            }
+                            add_extra(xt, q);
+                        }
+                    }
                     if (HASH) {
                         hs += __shfl_xor_sync(0xffffffffu, hs, 1);
                         hs += __shfl_xor_sync(0xffffffffu, hs, 2);
@@ -401,6 +476,8 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_density_mp(WppArgs a) {
                         a.nbr_off[pm] = loff >= 0 ? (int)loff : 0;
                         a.nbr_n[pm] = loff >= 0 ? nnm : -1;
                         a.list_xh[pm] = make_uint4(Xm.x, Xm.y, Xm.z, __float_as_uint(h));
+                        a.list_ep[pm] = gen;
+                        if (PART) a.ext_n[pm] = cf > kMpFar || nex > kExtCap ? (unsigned)kExtCap + 1u : (unsigned)nex;
                         ++c_lists;
                     }
                     if (DIVCURL) {
@@ -432,6 +509,8 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_density_mp(WppArgs a) {
                 if ((int)lane < G.n && ((todo >> lane) & 1u)) {
                     a.left[o + __popc(todo & lt)] = G.p;
                     a.h[ol] = hl;
+                    // PART: the one-particle kernel finds no far partners; the force pass walks for it
+                    if (PART) a.ext_n[G.p] = (unsigned)kExtCap + 1u;
                 }
             }
         }
@@ -806,6 +885,7 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_density_wpp(WppArgs a) {
                             a.nbr_off[p] = loff >= 0 ? loff : 0;
                             a.nbr_n[p] = loff >= 0 ? nn : -1;
                             a.list_xh[p] = make_uint4(Xi.x, Xi.y, Xi.z, __float_as_uint(h));
+                            a.list_ep[p] = a.list_st[kListGen];
                         }
                         ++c_lists;
                     }
@@ -873,14 +953,28 @@ __global__ void __launch_bounds__(256) k_list_ext(const BoxDesc* __restrict__ bo
                                                   const int32_t* __restrict__ nbr_off,
                                                   const int32_t* __restrict__ nbr_n, const uint4* __restrict__ list_xh,
                                                   uint32_t* __restrict__ ext_n, int32_t* __restrict__ ext,
-                                                  unsigned* list_st) {
-    // the lists serve a force call only if every particle's was written: when
-    // the density call had a smaller active set there is nothing to complete
-    if (list_st[0] != (unsigned)n) return;
+                                                  unsigned* list_st, const int32_t* __restrict__ act,
+                                                  const uint32_t* __restrict__ count, const uint8_t* __restrict__ flag,
+                                                  const uint32_t* __restrict__ list_ep) {
+    // Every particle of the call must have had its list written, else the
+    // extra lists cannot be completed: the active list (act given), or else
+    // all n particles (the device count must then be n as well).
+    const int na = (int)*count;
+    const int nj = act ? na : n;
+    if (list_st[0] != (unsigned)nj || (!act && na != n)) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&list_st[1], 2u);
+        return;
+    }
+    const unsigned gen = list_st[kListGen];
     const unsigned lane = lane_id();
     const int warps = gridDim.x * (blockDim.x >> 5);
     const float band = 9.5367431640625e-07f;  // 2^-20
-    for (int j = blockIdx.x * (blockDim.x >> 5) + (int)(threadIdx.x >> 5); j < n; j += warps) {
+    for (int t = blockIdx.x * (blockDim.x >> 5) + (int)(threadIdx.x >> 5); t < nj; t += warps) {
+        const int j = act ? act[t] : t;
+        if (act && list_ep[j] != gen) {   // not recorded by this call
+            if (lane == 0) atomicOr(&list_st[1], 1u);
+            continue;
+        }
         const int cnt = nbr_n[j];
         if (cnt < 0) {   // j's list is missing: the extra lists cannot be completed
             if (lane == 0) atomicOr(&list_st[1], 1u);
@@ -902,6 +996,7 @@ __global__ void __launch_bounds__(256) k_list_ext(const BoxDesc* __restrict__ bo
             return x;
         };
         auto place = [&](int i) {
+            if (act && !flag[i]) return;   // an inactive i: its extra partners are not needed
             const unsigned slot = atomicAdd(&ext_n[i], 1u);
             if (slot < (unsigned)kExtCap) ext[(size_t)i * kExtCap + slot] = j;
         };
@@ -923,13 +1018,16 @@ __global__ void __launch_bounds__(256) k_list_ext(const BoxDesc* __restrict__ bo
 // up to kExtCap through a bitonic sort in shared memory. A segment that
 // overflowed is marked kExtUnusable, and the force pass walks for that particle.
 __global__ void __launch_bounds__(256) k_list_sort(int n, int32_t* __restrict__ ext, uint32_t* __restrict__ ext_n,
-                                                   const unsigned* __restrict__ list_st) {
-    if (list_st[0] != (unsigned)n) return;   // as k_list_ext
+                                                   const unsigned* __restrict__ list_st,
+                                                   const int32_t* __restrict__ act, const uint32_t* __restrict__ count) {
+    if (list_st[1] != 0u) return;   // the lists cannot serve a force call
     __shared__ int buf[8][kExtCap];
     int* sb = buf[threadIdx.x >> 5];
     const unsigned lane = lane_id();
     const int warps = gridDim.x * (blockDim.x >> 5);
-    for (int i = blockIdx.x * (blockDim.x >> 5) + (int)(threadIdx.x >> 5); i < n; i += warps) {
+    const int ni = act ? (int)*count : n;
+    for (int t = blockIdx.x * (blockDim.x >> 5) + (int)(threadIdx.x >> 5); t < ni; t += warps) {
+        const int i = act ? act[t] : t;
         const unsigned cu = ext_n[i];
         if (cu > (unsigned)kExtCap) {
             if (lane == 0) ext_n[i] = kExtUnusable;
@@ -986,6 +1084,30 @@ __global__ void __launch_bounds__(256) k_list_sort(int n, int32_t* __restrict__ 
     }
 }
 
+// Start of a density call that records lists: clear the status words, one
+// more generation (the stamp of the lists this call writes).
+__global__ void k_list_begin(unsigned* list_st) {
+    const int t = (int)threadIdx.x;
+    if (t < kListGen) list_st[t] = 0u;
+    else if (t == kListGen) list_st[kListGen] += 1u;
+}
+
+// A call on part of the particles: the h every inactive particle keeps (with
+// its position, in sorted order) for the extra-partner tests, and the h of
+// the inactive particles alone in caller order (0 for the active ones) for the
+// node h_max that bounds where such partners can be.
+__global__ void k_list_snap(int n, const int32_t* __restrict__ perm, const float* __restrict__ h,
+                            const uint4* __restrict__ posm, const uint8_t* __restrict__ flag,
+                            uint4* __restrict__ list_xh, float* __restrict__ h_inactive) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const int o = perm[p];
+    const float hp = h[o];
+    const uint4 X = posm[p];
+    list_xh[p] = make_uint4(X.x, X.y, X.z, __float_as_uint(hp));
+    h_inactive[o] = flag[p] ? 0.f : hp;
+}
+
 // Sorted (v, m) for the density pass's velocity divergence and curl.
 __global__ void k_vel_pack(int n, const int32_t* __restrict__ perm, const float* __restrict__ vel,
                            const float4* __restrict__ posf, float4* __restrict__ vm) {
@@ -1024,27 +1146,46 @@ cudaError_t launch_density_wpp(sph_ctx* ctx, const DensityLaunch& a, int64_t n_a
         c.divv = a.divv;
         c.curlv = a.curlv;
     }
-    // Neighbour lists: recorded when the active count can cover all particles.
-    // They serve a force call only if every particle was in fact active
-    // (checked on the device: lists written == n); a call on a smaller active
-    // set leaves them unusable.
-    const bool full = g->nbr != nullptr && n_active == g->n;
-    if (full) {
+    // Neighbour lists for the force pass, each stamped with this call's
+    // generation. A call whose active set can cover every particle (no list,
+    // or a list of n entries) records them whatever the kernel; they serve a
+    // force call only if every particle was in fact active (checked on the
+    // device: the list count and the lists written both equal n). With
+    // SPH_PARTIAL_LISTS, a call on an active list (padded or not) that runs the
+    // member-parallel kernel records the active particles' lists and also
+    // finds their extra partners among the inactive ones.
+    const bool mp_path = wpp_groups_pay(n_active, g->n) && c.mp_j != nullptr;
+    const bool part = g->nbr != nullptr && a.active_list && a.partial_lists && mp_path;
+    const bool rec = part || (g->nbr != nullptr && n_active == g->n);
+    if (rec) {
         c.nbr = g->nbr;
         c.nbr_off = g->nbr_off;
         c.nbr_n = g->nbr_n;
         c.list_xh = g->list_xh;
         c.list_st = g->list_st;
+        c.list_ep = g->list_ep;
+        c.ext = g->ext;
+        c.ext_n = g->ext_n;
         c.list_pool = g->list_pool;
         // chunks small enough that every warp's first reservations fit in a quarter of the pool
         const long long warps = (long long)blocks * kWppWarps;
         c.list_chunk = (int)std::max<long long>(32, std::min<long long>(kListChunk, g->list_pool / (4 * warps)));
-        if ((e = cudaMemsetAsync(g->list_st, 0, sizeof(unsigned) * kListSt, s))) return e;
+        k_list_begin<<<1, 32, 0, s>>>(g->list_st);
+        ++ctx->launches;
+        if ((e = cudaMemsetAsync(g->ext_n, 0, sizeof(uint32_t) * g->n, s))) return e;
+        if (part) {
+            const int n = (int)g->n;
+            k_list_snap<<<(n + 255) / 256, 256, 0, s>>>(n, g->perm, a.h, g->posm, g->flag, g->list_xh, g->st_lo);
+            ++ctx->launches;
+            grid_refresh_hmax(g, g->st_lo, s);
+            c.flagp = g->flag;
+            c.mp_x = g->mp_x;
+        }
     }
     WppSpan sp;
     if ((e = span_begin(ctx, a.time_kernels, 0, s, sp))) return e;
     const bool dc = a.divv != nullptr;
-    if (!wpp_groups_pay(n_active, g->n) || !c.mp_j) {
+    if (!mp_path) {
         // sparse active sets form groups of one: the one-particle kernel alone
         auto k1 = a.hash ? (dc ? k_density_wpp<true, kWppLeftBps, true> : k_density_wpp<true, kWppLeftBps, false>)
                          : (dc ? k_density_wpp<false, kWppLeftBps, true> : k_density_wpp<false, kWppLeftBps, false>);
@@ -1058,12 +1199,20 @@ cudaError_t launch_density_wpp(sph_ctx* ctx, const DensityLaunch& a, int64_t n_a
         if ((e = cudaMemsetAsync(ctx->queue + 5, 0, 2 * sizeof(unsigned), s))) return e;
         c.left = g->den_left;
         c.left_n = ctx->queue + 6;
+        // whole groups per queue grab, whatever the active count: a warp's
+        // group costs little more than one particle (the leftover kernel below
+        // takes one particle at a time)
+        c.chunk = kMpMembers;
         // 4 or 5 resident blocks (the shared memory of a block holds the member
         // near lists: 5 blocks fill an SM), 128 or 96 registers
-        auto kd = bps <= 4 ? (a.hash ? (dc ? k_density_mp<true, 4, true> : k_density_mp<true, 4, false>)
-                                     : (dc ? k_density_mp<false, 4, true> : k_density_mp<false, 4, false>))
-                           : (a.hash ? (dc ? k_density_mp<true, 5, true> : k_density_mp<true, 5, false>)
-                                     : (dc ? k_density_mp<false, 5, true> : k_density_mp<false, 5, false>));
+        auto kd = part ? (bps <= 4 ? (a.hash ? (dc ? k_density_mp<true, 4, true, true> : k_density_mp<true, 4, false, true>)
+                                            : (dc ? k_density_mp<false, 4, true, true> : k_density_mp<false, 4, false, true>))
+                                  : (a.hash ? (dc ? k_density_mp<true, 5, true, true> : k_density_mp<true, 5, false, true>)
+                                            : (dc ? k_density_mp<false, 5, true, true> : k_density_mp<false, 5, false, true>)))
+                       : (bps <= 4 ? (a.hash ? (dc ? k_density_mp<true, 4, true, false> : k_density_mp<true, 4, false, false>)
+                                            : (dc ? k_density_mp<false, 4, true, false> : k_density_mp<false, 4, false, false>))
+                                  : (a.hash ? (dc ? k_density_mp<true, 5, true, false> : k_density_mp<true, 5, false, false>)
+                                            : (dc ? k_density_mp<false, 5, true, false> : k_density_mp<false, 5, false, false>)));
         kd<<<blocks, kWppThreads, 0, s>>>(c);
         // the leftovers, one particle per warp (count on the device), from the h the
         // member-parallel kernel left for them
@@ -1073,6 +1222,9 @@ cudaError_t launch_density_wpp(sph_ctx* ctx, const DensityLaunch& a, int64_t n_a
         cl.queue = ctx->queue + 5;
         cl.chunk = 1;
         cl.guess_h = 0;
+        // each list reserved alone: the leftovers are few and scattered over
+        // the warps, and a pool chunk per warp would be mostly unused
+        cl.list_chunk = 0;
         int lblocks = 0, lchunk = 0;
         wpp_shape(ctx, kWppLeftBps, n_active, lblocks, lchunk);
         auto kl = a.hash ? (dc ? k_density_wpp<true, kWppLeftBps, true> : k_density_wpp<true, kWppLeftBps, false>)
@@ -1082,15 +1234,16 @@ cudaError_t launch_density_wpp(sph_ctx* ctx, const DensityLaunch& a, int64_t n_a
     }
     // SPH_TIME_KERNELS times the density kernel alone; the list build follows
     if ((e = span_end(ctx, sp, s))) return e;
-    if (full) {
+    if (rec) {
         const int n = (int)g->n, hb = helper_blocks(ctx, n);
-        if ((e = cudaMemsetAsync(g->ext_n, 0, sizeof(uint32_t) * n, s))) return e;
+        const int32_t* act = part ? g->act : nullptr;
+        const uint32_t* count = g->scan + n;
         k_list_ext<<<hb, 256, 0, s>>>(g->boxes, g->n_boxes, n, g->posm, g->nbr, g->nbr_off, g->nbr_n, g->list_xh,
-                                      g->ext_n, g->ext, g->list_st);
-        k_list_sort<<<hb, 256, 0, s>>>(n, g->ext, g->ext_n, g->list_st);
+                                      g->ext_n, g->ext, g->list_st, act, count, g->flag, g->list_ep);
+        k_list_sort<<<hb, 256, 0, s>>>(n, g->ext, g->ext_n, g->list_st, act, count);
         ctx->launches += 2;
     }
-    g->lists_full = full;
+    g->lists_rec = rec;
     return cudaGetLastError();
 }
 

@@ -33,7 +33,7 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_force_wpp(WppArgs a) {
     // queue grab (walked alone), unless the lists could not serve the call
     const int32_t* act = a.act;
     int cnt = (int)*a.count_ptr, chunk = a.chunk;
-    if (a.fb_act && wpp_lists_valid(a.list_st, a.n_total)) {
+    if (a.fb_act && wpp_lists_valid(a.list_st)) {
         act = a.fb_act;
         cnt = (int)*a.fb_count;
         chunk = 1;
@@ -206,17 +206,19 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_force_wpp(WppArgs a) {
 // particles whose own lists did not fit go to fb_list for that walk.
 template <bool HASH, int VISC, bool COND>
 __global__ void __launch_bounds__(128, 8) k_force_list(WppArgs a) {
-    if (!wpp_lists_valid(a.list_st, a.n_total)) return;
+    if (!wpp_lists_valid(a.list_st)) return;
+    const unsigned gen = a.list_st[kListGen];
     const unsigned lane = lane_id();
     const int warps = gridDim.x * (blockDim.x >> 5);
     const int cnt = (int)*a.count_ptr;
     const float kNorm = (float)(8.0 / 3.141592653589793);
-    unsigned long long c_pairs = 0;   // per warp, lane-uniform
+    unsigned long long c_pairs = 0, c_served = 0;   // per warp, lane-uniform
     for (int t = blockIdx.x * (blockDim.x >> 5) + (int)(threadIdx.x >> 5); t < cnt; t += warps) {
         const int p = a.act[t];
         const int cn = a.nbr_n[p];
         const unsigned ec = a.ext_n[p];
-        if (cn < 0 || ec > (unsigned)kExtCap) {   // (kExtUnusable included)
+        // (kExtUnusable included; a stale stamp: p was not active in the call that recorded)
+        if (cn < 0 || ec > (unsigned)kExtCap || a.list_ep[p] != gen) {
             if (lane == 0) a.fb_list[atomicAdd(&a.list_st[3], 1u)] = p;
             continue;
         }
@@ -277,8 +279,10 @@ __global__ void __launch_bounds__(128, 8) k_force_list(WppArgs a) {
             if (HASH) a.hash[oi] = hs;
         }
         c_pairs += (unsigned long long)tot;
+        ++c_served;
     }
     if (lane == 0 && c_pairs) atomicAdd(&a.ctr->force_pairs, c_pairs);
+    if (lane == 0 && c_served) atomicAdd(&a.ctr->list_force, c_served);
 }
 
 
@@ -312,7 +316,7 @@ struct WppFmSmem {
 template <bool HASH, int MINB, int VISC, bool COND>
 __global__ void __launch_bounds__(kWppThreads, MINB) k_force_mp(WppArgs a) {
     // the recorded lists served this call: the walk takes only their fallbacks
-    if (a.fb_act && wpp_lists_valid(a.list_st, a.n_total)) return;
+    if (a.fb_act && wpp_lists_valid(a.list_st)) return;
     __shared__ WppFmSmem smem[kWppWarps];
     const int wib = (int)(threadIdx.x >> 5);
     WppFmSmem& sm = smem[wib];
@@ -591,7 +595,7 @@ static void launch_force_walk(bool hash, bool six, int visc, bool cond, int bloc
 cudaError_t launch_force_wpp(sph_ctx* ctx, const ForceLaunch& a, int64_t n_active, cudaStream_t s) {
     sph_grid* g = const_cast<sph_grid*>(a.g);
     cudaError_t e;
-    const bool lists = g->nbr != nullptr && g->lists_full;
+    const bool lists = g->nbr != nullptr && g->lists_rec;
     if (lists && (e = cudaMemsetAsync(g->list_st + 2, 0, 2 * sizeof(unsigned), s))) return e;
     force_pack(g, a.vel, a.u, a.h, a.rho, a.omega, (float)a.gamma, s, lists ? g->list_xh : nullptr,
                lists ? g->list_st + 2 : nullptr, a.divv, a.curlv, a.kappa, a.alpha_v);
@@ -627,6 +631,7 @@ cudaError_t launch_force_wpp(sph_ctx* ctx, const ForceLaunch& a, int64_t n_activ
         c.ext = g->ext;
         c.ext_n = g->ext_n;
         c.list_st = g->list_st;
+        c.list_ep = g->list_ep;
         c.fb_list = g->fb_list;
         const int lb = (int)std::max<long long>(
             1, std::min<long long>((long long)ctx->sm_count * 16, (n_active + 3) / 4));
@@ -644,6 +649,7 @@ cudaError_t launch_force_wpp(sph_ctx* ctx, const ForceLaunch& a, int64_t n_activ
         cm.mp_j = g->mp_j;
         cm.left = g->den_left;
         cm.left_n = ctx->queue + 6;
+        cm.chunk = kMpMembers;   // whole groups per queue grab
         // a force warp uses the scratch of two density warps: at most half as many warps
         const int fb = std::min(blocks, ctx->sm_count * (kMpWarpsPerSm / (2 * kWppWarps)));
         a.hash ? launch_fm<true>(visc, c.fcond != nullptr, fb, s, cm)

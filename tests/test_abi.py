@@ -45,7 +45,7 @@ def test_default_params_and_struct_layout(lib):
     assert abs(p.n_tol - 64e-6) < 1e-18 and abs(p.gamma - 5.0 / 3.0) < 1e-15
     assert p.walk_radius == 0.0 and p.blocks_per_sm == 0
     assert ctypes.sizeof(abi.sph_params) == 72
-    assert ctypes.sizeof(abi.sph_stats) == 88
+    assert ctypes.sizeof(abi.sph_stats) == 96
     assert ctypes.sizeof(abi.sph_gravity_params) == 40
 
 

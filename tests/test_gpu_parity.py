@@ -135,14 +135,18 @@ def test_density_converged(S, ctx, kind, fp64, path, lattice32, clustered50k):
 @pytest.mark.parametrize("bps", [4, 5, 6, 8])
 def test_register_budgets_agree(S, ctx, bps, clustered50k):
     """The default path's kernels at each register budget the autotuner can
-    pick (blocks per SM: density 4 or 5, force 6 or 8): converged density and
-    the force from the recorded lists against the oracle, pair sets exact."""
+    pick (blocks per SM: density 4 or 5, force 6 or 8): converged density
+    against the oracle; then, at the oracle's h (a fixed-h density call that
+    records the lists), the force from the recorded lists against the oracle,
+    pair sets exact."""
     p, (X, d, _) = clustered50k
     params = S.default_params(box=p.box, blocks_per_sm=bps)
     grid = gpu_grid(S, ctx, p, params)
     g = gpu_density(S, ctx, grid, W.perturb(d["h"], 0.02, seed=4).astype(np.float32), params)
     _density_converged_checks(g, p, X, d, False)
-    h, rho, om = (g[k].astype(np.float32) for k in ("h", "rho", "omega"))
+    h, rho, om = _oracle_inputs32(d)
+    gd = gpu_density(S, ctx, grid, h, S.default_params(box=p.box, blocks_per_sm=bps, flags=S.SPH_FIXED_H))
+    assert gd["rc"] == 0
     f = oracle.force(X, p.vel, p.mass, p.u, h, rho, om, box=p.box)
     gf = gpu_force(S, ctx, grid, p, h, rho, om, params)
     assert gf["rc"] == 0 and gf["stats"]["pair_tests"] == 0
@@ -211,6 +215,102 @@ def test_force_reuses_density_lists(S, ctx, kind, lattice32, clustered50k):
     g3 = gpu_force(S, ctx, grid, p, h, rho, om, params, active=act)
     assert g3["stats"]["pair_tests"] == 0
     check_force(g3, f, act, 1e-4)
+
+
+def _partial_selection(p, d, sel):
+    """Active sets of the shapes a time-bin hierarchy gives: the densest 20%
+    (small h: short time steps, spatially clumped), a ball around the densest
+    particle, and a scattered 15% (mostly lone members of their leaves)."""
+    if sel == "dense":
+        return np.nonzero(d["h"] <= np.quantile(d["h"], 0.2))[0].astype(np.int32)
+    if sel == "ball":
+        c = p.pos[int(np.argmin(d["h"]))]
+        r = np.linalg.norm((p.pos - c + 0.5 * p.box) % p.box - 0.5 * p.box, axis=1)
+        return np.nonzero(r <= np.quantile(r, 0.1))[0].astype(np.int32)
+    return W.sample_indices(p.n, int(0.15 * p.n), seed=33).astype(np.int32)
+
+
+@pytest.mark.parametrize("sel", ["dense", "ball", "scattered"])
+def test_force_reuses_partial_density_lists(S, ctx, sel, clustered50k):
+    """With SPH_PARTIAL_LISTS a density call on an active list records the
+    active particles' lists and their extra partners: the active ones through
+    the transpose, the
+    inactive ones (fixed h) found by the member-parallel sweep. The force pass
+    on that list reads them (members the sweep left to the one-particle kernel
+    walk), with the oracle's results and pair sets. Also: the list padded with
+    -1 up to n (its count on the device), and a force set larger than the
+    density set (the particles without a list of this call walk)."""
+    p, (X, d, _) = clustered50k
+    h, rho, om = _oracle_inputs32(d)
+    act = _partial_selection(p, d, sel)
+    params = S.default_params(box=p.box)
+    pf = S.default_params(box=p.box, flags=S.SPH_FIXED_H | S.SPH_PARTIAL_LISTS)
+    grid = gpu_grid(S, ctx, p, params)
+    f = oracle.force(X, p.vel, p.mass, p.u, h, rho, om, box=p.box)
+    # walked: without SPH_PARTIAL_LISTS a density call on an active list records no lists
+    gd = gpu_density(S, ctx, grid, h, S.default_params(box=p.box, flags=S.SPH_FIXED_H), active=act)
+    assert gd["rc"] == 0
+    g0 = gpu_force(S, ctx, grid, p, h, rho, om, params, active=act)
+    assert g0["rc"] == 0 and g0["stats"]["list_force"] == 0
+    check_force(g0, f, act, 1e-4)
+    # walked: a density call on the per-thread path records no lists
+    gd = gpu_density(S, ctx, grid, h, S.default_params(box=p.box, flags=S.SPH_FIXED_H | S.SPH_PER_THREAD_WALK),
+                     active=act)
+    assert gd["rc"] == 0
+    gw = gpu_force(S, ctx, grid, p, h, rho, om, params, active=act)
+    assert gw["rc"] == 0
+    check_force(gw, f, act, 1e-4)
+    walked = gw["stats"]["pair_tests"]
+    assert walked > 0
+    # recorded by the partial density call
+    gd = gpu_density(S, ctx, grid, h, pf, active=act)
+    assert gd["rc"] == 0
+    g = gpu_force(S, ctx, grid, p, h, rho, om, params, active=act)
+    assert g["rc"] == 0
+    check_force(g, f, act, 1e-4)
+    assert g["stats"]["force_pairs"] == int(f["n_pairs"][act].sum())
+    if sel != "scattered":   # clumped sets: nearly every active particle reads its lists
+        assert g["stats"]["pair_tests"] < walked / 4, (g["stats"]["pair_tests"], walked)
+        assert g["stats"]["list_force"] >= 0.9 * act.size
+    # padded to n, count on the device
+    pad = np.concatenate([act, np.full(p.n - act.size, -1, np.int32)])
+    gd = gpu_density(S, ctx, grid, h, pf, active=pad)
+    assert gd["rc"] == 0
+    g2 = gpu_force(S, ctx, grid, p, h, rho, om, params, active=pad)
+    assert g2["rc"] == 0
+    check_force(g2, f, act, 1e-4)
+    if sel != "scattered":
+        assert g2["stats"]["pair_tests"] < walked / 4
+    # a larger force set: the particles outside the density set walk
+    more = np.union1d(act, W.sample_indices(p.n, p.n // 20, seed=34)).astype(np.int32)
+    g3 = gpu_force(S, ctx, grid, p, h, rho, om, params, active=more)
+    assert g3["rc"] == 0
+    check_force(g3, f, more, 1e-4)
+
+
+def test_lists_from_an_explicit_list_of_all_particles(S, ctx, clustered50k):
+    """An active list that names every particle (shuffled) records the full
+    lists like a call without a list; the same list padded with -1 in place of
+    a tenth of its entries (count below n on the device) records lists that
+    cannot serve, and the force pass walks, with the oracle's results."""
+    p, (X, d, _) = clustered50k
+    h, rho, om = _oracle_inputs32(d)
+    params = S.default_params(box=p.box)
+    pf = S.default_params(box=p.box, flags=S.SPH_FIXED_H)
+    grid = gpu_grid(S, ctx, p, params)
+    f = oracle.force(X, p.vel, p.mass, p.u, h, rho, om, box=p.box)
+    every = np.random.default_rng(35).permutation(p.n).astype(np.int32)
+    assert gpu_density(S, ctx, grid, h, pf, active=every)["rc"] == 0
+    g = gpu_force(S, ctx, grid, p, h, rho, om, params, active=every)
+    assert g["rc"] == 0 and g["stats"]["list_force"] == p.n and g["stats"]["pair_tests"] == 0
+    check_force(g, f, np.arange(p.n), 1e-4)
+    pad = every.copy()
+    pad[: p.n // 10] = -1
+    act = np.sort(pad[pad >= 0])
+    assert gpu_density(S, ctx, grid, h, pf, active=pad)["rc"] == 0
+    g2 = gpu_force(S, ctx, grid, p, h, rho, om, params, active=pad)
+    assert g2["rc"] == 0 and g2["stats"]["list_force"] == 0 and g2["stats"]["pair_tests"] > 0
+    check_force(g2, f, act, 1e-4)
 
 
 def test_force_lists_that_do_not_fit(S, ctx):
