@@ -26,11 +26,21 @@ struct WppMpSmem {
     float2 d[kMpMembers][kMpStride];    // (r^2, m_j) of each member's near list
     float4 mem[kMpMembers];             // member offset from the group centre (box units), inclusive threshold
     uint4 X[kMpMembers];                // member integer positions (and mass bits)
+    int pm[kMpMembers];                 // member sorted indices (-1: no member)
+    // candidates that passed the box prefilter, waiting for the member tests:
+    // offset from the group centre and mass (sign bit: a wide leaf's), index,
+    // and (partial calls) the inactive candidate's squared reach (-1: active)
+    float4 bp[32];
+    int bq[32];
+    float bt[32];
 };
 constexpr int kGlfBytes = (int)sizeof(int) * kWppGrpLeaves;   // WppSmem starts with glf
 constexpr int kDenSmemWarp = (int)(sizeof(WppSmem) > kGlfBytes + sizeof(WppMpSmem) ? sizeof(WppSmem)
                                                                                       : kGlfBytes + sizeof(WppMpSmem));
 static_assert(kWppWarps * kDenSmemWarp <= 48 * 1024, "static shared memory of the density block");
+// five resident blocks per SM (the 96-register budget) must fit the SM's 228 KB,
+// with the 1 KB the hardware reserves per block
+static_assert(5 * (kWppWarps * kDenSmemWarp + 1024) <= 228 * 1024, "five density blocks per SM");
 
 // Error-free (TwoSum) fold of two per-lane sums over aligned quads of lanes:
 // every lane of the quad ends with both totals as (s, c), value s - c.
@@ -133,10 +143,9 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_density_mp(WppArgs a) {
             unsigned todo = (1u << G.n) - 1u;   // members left for the one-particle path
             if (ngl >= 0 && mpj && G.n >= 2) {
                 // ---------------- candidates: one sweep of the group's leaves ----------------
-                // Every member tests every candidate of a step without a branch (a
-                // member slot past G.n has a negative threshold), so the eight
-                // members' dependent chains interleave; the next step's candidates
-                // are loaded while this step's are tested.
+                // 32 candidates per step (the next step's loaded while this one's are
+                // tested); those within reach of the group's box wait in a buffer,
+                // and every 32 of them go through the member tests.
                 const float eT = gg.eb;   // rounding bound of a computed separation (non-wide leaves)
                 if ((int)lane < kMpMembers) {
                     float4 mem = make_float4(0.f, 0.f, 0.f, -1.f);
@@ -148,14 +157,19 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_density_mp(WppArgs a) {
                     }
                     mp.mem[lane] = mem;
                     mp.X[lane] = Xl;
+                    mp.pm[lane] = G.p;   // -1 past G.n
                 }
                 __syncwarp();
-                int cntm[kMpMembers], pmv[kMpMembers];
+                int cntm[kMpMembers];
 #pragma unroll
-                for (int k = 0; k < kMpMembers; ++k) {
-                    cntm[k] = 0;
-                    pmv[k] = __shfl_sync(0xffffffffu, G.p, k);   // -1 past G.n
-                }
+                for (int k = 0; k < kMpMembers; ++k) cntm[k] = 0;
+                // Box prefilter: a candidate goes on to the member tests only if it
+                // comes within the largest member threshold of the group's box (or,
+                // PART, within its own h of it). Both tests run on the same computed
+                // offsets; the margin of 2^-12 of the squared radius covers their
+                // rounding, so a candidate that some member takes always passes.
+                const float Tmax = warp_max((int)lane < kMpMembers ? mp.mem[lane].w : -1.f) * (1.f + 2.44140625e-4f);
+                const float egx = gg.egx, egy = gg.egy, egz = gg.egz;
                 unsigned ctest = 0;
                 const int lvl0 = B.lvl_off[0];
                 // the candidate of this lane in step `base`: leaf entry, index, centre, (offset, mass)
@@ -168,6 +182,75 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_density_mp(WppArgs a) {
                     C = a.node_c[lvl0 + (e & 0x7fffffff)];
                     f = __ldg(a.posf + q);
                 };
+                // Every member tests the buffer's first kb candidates (one per lane)
+                // without a branch (a member slot past G.n has a negative
+                // threshold), so the eight members' dependent chains interleave.
+                auto members = [&](int kb) {
+                    __syncwarp();
+                    const bool cand = (int)lane < kb;
+                    const float4 f0 = mp.bp[lane];
+                    const int q = mp.bq[lane];
+                    const float Tj = PART ? mp.bt[lane] : -1.f;
+                    __syncwarp();   // read before the next candidates overwrite the entry
+                    const bool wide = cand && (__float_as_uint(f0.w) >> 31) != 0u;
+                    const float mj = __uint_as_float(__float_as_uint(f0.w) & 0x7fffffffu);
+                    const bool ina = PART && cand && Tj >= 0.f;
+                    const bool anyina = PART && __any_sync(0xffffffffu, ina);
+                    if (!__any_sync(0xffffffffu, wide)) {
+#pragma unroll
+                        for (int m = 0; m < kMpMembers; ++m) {
+                            const float4 g = mp.mem[m];
+                            const float dx = f0.x - g.x, dy = f0.y - g.y, dz = f0.z - g.z;
+                            const float r2 = dx * dx + dy * dy + dz * dz;
+                            const bool in = cand && q != mp.pm[m] && r2 < g.w;
+                            const unsigned msk = __ballot_sync(0xffffffffu, in);
+                            const int k = (cntm[m] & 0xffff) + __popc(msk & lt);
+                            if (in && k < kMpCap) {
+                                mp.d[m][k] = make_float2(r2, mj);
+                                mpj[m * kMpCap + k] = q;
+                            }
+                            cntm[m] += __popc(msk);
+                            if (anyina) {
+                                const bool far = ina && m < G.n && !(r2 < g.w) && r2 < Tj;
+                                const unsigned fm = __ballot_sync(0xffffffffu, far);
+                                const int kf = (cntm[m] >> 16) + __popc(fm & lt);
+                                if (far && kf < kMpFar) mpx[m * kMpFar + kf] = q;
+                                cntm[m] += __popc(fm) << 16;
+                            }
+                        }
+                    } else {
+                        // a wide leaf among them: exact integer separations from each member there
+                        const uint4 Xq = wide ? a.posm[q] : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+                        for (int m = 0; m < kMpMembers; ++m) {
+                            const float4 g = mp.mem[m];
+                            float dx = f0.x - g.x, dy = f0.y - g.y, dz = f0.z - g.z;
+                            if (wide) {
+                                const uint4 Xm = mp.X[m];
+                                dx = (float)(int)(Xq.x - Xm.x) * sf;
+                                dy = (float)(int)(Xq.y - Xm.y) * sf;
+                                dz = (float)(int)(Xq.z - Xm.z) * sf;
+                            }
+                            const float r2 = dx * dx + dy * dy + dz * dz;
+                            const bool in = cand && q != mp.pm[m] && r2 < g.w;
+                            const unsigned msk = __ballot_sync(0xffffffffu, in);
+                            const int k = (cntm[m] & 0xffff) + __popc(msk & lt);
+                            if (in && k < kMpCap) {
+                                mp.d[m][k] = make_float2(r2, mj);
+                                mpj[m * kMpCap + k] = q;
+                            }
+                            cntm[m] += __popc(msk);
+                            if (anyina) {
+                                const bool far = ina && m < G.n && !(r2 < g.w) && r2 < Tj;
+                                const unsigned fm = __ballot_sync(0xffffffffu, far);
+                                const int kf = (cntm[m] >> 16) + __popc(fm & lt);
+                                if (far && kf < kMpFar) mpx[m * kMpFar + kf] = q;
+                                cntm[m] += __popc(fm) << 16;
+                            }
+                        }
+                    }
+                };
+                int nb = 0;   // candidates waiting in the buffer (warp-uniform)
                 int e_n, q_n;
                 bool cand_n;
                 uint4 C_n;
@@ -181,74 +264,44 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_density_mp(WppArgs a) {
                     if (base + 4 < ngl) fetch(base + 4, e_n, q_n, cand_n, C_n, f_n);
                     // PART: candidate j inactive, and the square of its h widened by the
                     // rounding bound (the far test is inclusive; the last sweep decides)
-                    bool ina = false;
                     float Tj = -1.f;
-                    if (PART && cand) {
-                        ina = a.flagp[q] == 0;
-                        if (ina) {
-                            const float tj = __uint_as_float(a.list_xh[q].w) * (1.f + 2.f * rel) + eT;
-                            Tj = tj * tj * (1.f + 4.f * rel);
-                        }
+                    if (PART && cand && a.flagp[q] == 0) {
+                        const float tj = __uint_as_float(a.list_xh[q].w) * (1.f + 2.f * rel) + eT;
+                        Tj = tj * tj * (1.f + 4.f * rel);
                     }
-                    const bool anyina = PART && __any_sync(0xffffffffu, ina);
                     const float px = (float)(int)(C.x - gg.Gc.x) * sf + f.x, py = (float)(int)(C.y - gg.Gc.y) * sf + f.y,
                                 pz = (float)(int)(C.z - gg.Gc.z) * sf + f.z;
                     const bool wide = cand && e < 0;
                     ctest += __popc(__ballot_sync(0xffffffffu, cand));
-                    if (!__any_sync(0xffffffffu, wide)) {
-#pragma unroll
-                        for (int m = 0; m < kMpMembers; ++m) {
-                            const float4 g = mp.mem[m];
-                            const float dx = px - g.x, dy = py - g.y, dz = pz - g.z;
-                            const float r2 = dx * dx + dy * dy + dz * dz;
-                            const bool in = cand && q != pmv[m] && r2 < g.w;
-                            const unsigned msk = __ballot_sync(0xffffffffu, in);
-                            const int k = (cntm[m] & 0xffff) + __popc(msk & lt);
-                            if (in && k < kMpCap) {
-                                mp.d[m][k] = make_float2(r2, f.w);
-                                mpj[m * kMpCap + k] = q;
-                            }
-                            cntm[m] += __popc(msk);
-                            if (anyina) {
-                                const bool far = ina && m < G.n && !(r2 < g.w) && r2 < Tj;
-                                const unsigned fm = __ballot_sync(0xffffffffu, far);
-                                const int kf = (cntm[m] >> 16) + __popc(fm & lt);
-                                if (far && kf < kMpFar) mpx[m * kMpFar + kf] = q;
-                                cntm[m] += __popc(fm) << 16;
-                            }
+                    // a wide leaf's offsets are not accurate enough for the box test: it passes
+                    bool pass = cand;
+                    if (cand && !wide) {
+                        const float bx = fmaxf(fabsf(px) - egx, 0.f), by = fmaxf(fabsf(py) - egy, 0.f),
+                                    bz = fmaxf(fabsf(pz) - egz, 0.f);
+                        const float b2 = bx * bx + by * by + bz * bz;
+                        pass = b2 < Tmax || (PART && b2 < Tj * (1.f + 2.44140625e-4f));
+                    }
+                    const unsigned pb = __ballot_sync(0xffffffffu, pass);
+                    const int slot = nb + __popc(pb & lt);
+                    const float4 ent = make_float4(px, py, pz,
+                                                   __uint_as_float(__float_as_uint(f.w) | (wide ? 0x80000000u : 0u)));
+                    if (pass && slot < 32) {
+                        mp.bp[slot] = ent;
+                        mp.bq[slot] = q;
+                        if (PART) mp.bt[slot] = Tj;
+                    }
+                    nb += __popc(pb);
+                    if (nb >= 32) {
+                        members(32);
+                        if (pass && slot >= 32) {
+                            mp.bp[slot - 32] = ent;
+                            mp.bq[slot - 32] = q;
+                            if (PART) mp.bt[slot - 32] = Tj;
                         }
-                    } else {
-                        // a wide leaf in the step: exact integer separations from each member there
-                        const uint4 Xq = wide ? a.posm[q] : make_uint4(0u, 0u, 0u, 0u);
-#pragma unroll
-                        for (int m = 0; m < kMpMembers; ++m) {
-                            const float4 g = mp.mem[m];
-                            float dx = px - g.x, dy = py - g.y, dz = pz - g.z;
-                            if (wide) {
-                                const uint4 Xm = mp.X[m];
-                                dx = (float)(int)(Xq.x - Xm.x) * sf;
-                                dy = (float)(int)(Xq.y - Xm.y) * sf;
-                                dz = (float)(int)(Xq.z - Xm.z) * sf;
-                            }
-                            const float r2 = dx * dx + dy * dy + dz * dz;
-                            const bool in = cand && q != pmv[m] && r2 < g.w;
-                            const unsigned msk = __ballot_sync(0xffffffffu, in);
-                            const int k = (cntm[m] & 0xffff) + __popc(msk & lt);
-                            if (in && k < kMpCap) {
-                                mp.d[m][k] = make_float2(r2, f.w);
-                                mpj[m * kMpCap + k] = q;
-                            }
-                            cntm[m] += __popc(msk);
-                            if (anyina) {
-                                const bool far = ina && m < G.n && !(r2 < g.w) && r2 < Tj;
-                                const unsigned fm = __ballot_sync(0xffffffffu, far);
-                                const int kf = (cntm[m] >> 16) + __popc(fm & lt);
-                                if (far && kf < kMpFar) mpx[m * kMpFar + kf] = q;
-                                cntm[m] += __popc(fm) << 16;
-                            }
-                        }
+                        nb -= 32;
                     }
                 }
+                if (nb > 0) members(nb);
                 if (lane == 0) c_tests += (unsigned long long)ctest * (unsigned)G.n;
                 __syncwarp();
                 // ---------------- h iteration: lanes 4m..4m+3 serve member m ----------------
