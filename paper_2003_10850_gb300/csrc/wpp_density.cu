@@ -1001,6 +1001,10 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_density_wpp(WppArgs a) {
 // h_i^2 and in FP64 inside it. The pair goes straight into i's fixed segment
 // of kExtCap entries at the slot its counter hands out (scatter order); a
 // count beyond kExtCap leaves the segment incomplete, which the sort marks.
+// The pass is bound by the latency of its dependent loads (list head, list
+// entries, then each entry's (X_i, h_i)), so a warp keeps three particles in
+// flight: the head of the one after next, the first 64 entries of the next,
+// and the gathers of the current one.
 __global__ void __launch_bounds__(256) k_list_ext(const BoxDesc* __restrict__ boxes, int nb, int n,
                                                   const uint4* __restrict__ posm, const int32_t* __restrict__ nbr,
                                                   const int32_t* __restrict__ nbr_off,
@@ -1022,54 +1026,84 @@ __global__ void __launch_bounds__(256) k_list_ext(const BoxDesc* __restrict__ bo
     const unsigned lane = lane_id();
     const int warps = gridDim.x * (blockDim.x >> 5);
     const float band = 9.5367431640625e-07f;  // 2^-20
-    for (int t = blockIdx.x * (blockDim.x >> 5) + (int)(threadIdx.x >> 5); t < nj; t += warps) {
-        const int j = act ? act[t] : t;
-        if (act && list_ep[j] != gen) {   // not recorded by this call
-            if (lane == 0) atomicOr(&list_st[1], 1u);
-            continue;
+    // a list head: the particle (-1 past the end), its list (count -2: not
+    // recorded by this call, -1: missing) and its (X_j, h_j)
+    struct Head {
+        int j, cnt, off;
+        uint4 X;
+    };
+    auto head = [&](int t) {
+        Head hd = {-1, 0, 0, make_uint4(0u, 0u, 0u, 0u)};
+        if (t < nj) {
+            hd.j = act ? act[t] : t;
+            hd.cnt = nbr_n[hd.j];
+            hd.off = nbr_off[hd.j];
+            hd.X = list_xh[hd.j];
+            if (act && list_ep[hd.j] != gen) hd.cnt = -2;
         }
-        const int cnt = nbr_n[j];
-        if (cnt < 0) {   // j's list is missing: the extra lists cannot be completed
+        return hd;
+    };
+    // its first 64 entries, two per lane
+    auto first = [&](const Head& hd, int& i0, int& i1) {
+        i0 = hd.j >= 0 && (int)lane < hd.cnt ? nbr[hd.off + (int)lane] : -1;
+        i1 = hd.j >= 0 && (int)lane + 32 < hd.cnt ? nbr[hd.off + (int)lane + 32] : -1;
+    };
+    int t = blockIdx.x * (blockDim.x >> 5) + (int)(threadIdx.x >> 5);
+    Head cur = head(t), nxt = head(t + warps);
+    int i0, i1;
+    first(cur, i0, i1);
+    while (cur.j >= 0) {
+        const Head far = head(t + 2 * warps);
+        int n0, n1;
+        first(nxt, n0, n1);
+        const uint4 X0 = i0 >= 0 ? list_xh[i0] : make_uint4(0u, 0u, 0u, 0u);
+        const uint4 X1 = i1 >= 0 ? list_xh[i1] : make_uint4(0u, 0u, 0u, 0u);
+        if (cur.cnt < 0) {   // j's list is missing: the extra lists cannot be completed
             if (lane == 0) atomicOr(&list_st[1], 1u);
-            continue;
-        }
-        const int32_t* lj = nbr + nbr_off[j];
-        const BoxDesc& B = boxes[nb == 1 ? 0 : wpp_box(boxes, nb, j)];
-        const float Hs = B.Hs;   // integer units per box unit
-        const uint4 Xj = list_xh[j];   // integer position, h bits
-        const float hj = __uint_as_float(Xj.w);
-        auto decide = [&](float hi, uint4 Xi) {
-            bool x = false;
-            if (hi < hj) {
-                const unsigned long long D2 = exact_d2(Xi, Xj);
-                const float d2 = __ull2float_rn(D2), Hi = hi * Hs, H2 = Hi * Hi;
-                if (d2 > H2 * (1.f + band)) x = true;
-                else if (!(d2 < H2 * (1.f - band))) x = !exact_pred(D2, wpp_hh(hi, B));
+        } else {
+            const int j = cur.j;
+            const BoxDesc& B = boxes[nb == 1 ? 0 : wpp_box(boxes, nb, j)];
+            const float Hs = B.Hs;   // integer units per box unit
+            const uint4 Xj = cur.X;
+            const float hj = __uint_as_float(Xj.w);
+            auto decide = [&](uint4 Xi) {
+                const float hi = __uint_as_float(Xi.w);
+                bool x = false;
+                if (hi < hj) {
+                    const unsigned long long D2 = exact_d2(Xi, Xj);
+                    const float d2 = __ull2float_rn(D2), Hi = hi * Hs, H2 = Hi * Hi;
+                    if (d2 > H2 * (1.f + band)) x = true;
+                    else if (!(d2 < H2 * (1.f - band))) x = !exact_pred(D2, wpp_hh(hi, B));
+                }
+                return x;
+            };
+            auto place = [&](int i) {
+                if (act && !flag[i]) return;   // an inactive i: its extra partners are not needed
+                const unsigned slot = atomicAdd(&ext_n[i], 1u);
+                if (slot < (unsigned)kExtCap) ext[(size_t)i * kExtCap + slot] = j;
+            };
+            if (i0 >= 0 && decide(X0)) place(i0);
+            if (i1 >= 0 && decide(X1)) place(i1);
+            // entries past the first 64 (rare)
+            for (int k = 64 + (int)lane; k < cur.cnt; k += 32) {
+                const int i = nbr[cur.off + k];
+                if (decide(list_xh[i])) place(i);
             }
-            return x;
-        };
-        auto place = [&](int i) {
-            if (act && !flag[i]) return;   // an inactive i: its extra partners are not needed
-            const unsigned slot = atomicAdd(&ext_n[i], 1u);
-            if (slot < (unsigned)kExtCap) ext[(size_t)i * kExtCap + slot] = j;
-        };
-        // two entries per lane per step (k and k + 32), their gathers issued together
-        for (int k = (int)lane; k < cnt; k += 64) {
-            const int k1 = k + 32;
-            const bool two = k1 < cnt;
-            const int i0 = lj[k], i1 = two ? lj[k1] : i0;
-            // one 16-byte gather gives both h_i and X_i
-            const uint4 X0 = list_xh[i0], X1 = list_xh[i1];
-            if (decide(__uint_as_float(X0.w), X0)) place(i0);
-            if (two && decide(__uint_as_float(X1.w), X1)) place(i1);
         }
+        t += warps;
+        cur = nxt;
+        nxt = far;
+        i0 = n0;
+        i1 = n1;
     }
 }
 
-// Warp per particle: its extra partners (distinct indices) in ascending order,
-// in place in its segment: up to 64 entries each goes to its rank (registers),
-// up to kExtCap through a bitonic sort in shared memory. A segment that
-// overflowed is marked kExtUnusable, and the force pass walks for that particle.
+// Extra-partner segments in ascending order, in place (the order fixes the
+// force pass's sums): up to 64 entries each goes to its rank (registers), up
+// to kExtCap through a bitonic sort in shared memory. A segment that
+// overflowed is marked kExtUnusable, and the force pass walks for that
+// particle. A warp reads the counts of 32 particles at a time and sorts their
+// segments one after another.
 __global__ void __launch_bounds__(256) k_list_sort(int n, int32_t* __restrict__ ext, uint32_t* __restrict__ ext_n,
                                                    const unsigned* __restrict__ list_st,
                                                    const int32_t* __restrict__ act, const uint32_t* __restrict__ count) {
@@ -1079,61 +1113,64 @@ __global__ void __launch_bounds__(256) k_list_sort(int n, int32_t* __restrict__ 
     const unsigned lane = lane_id();
     const int warps = gridDim.x * (blockDim.x >> 5);
     const int ni = act ? (int)*count : n;
-    for (int t = blockIdx.x * (blockDim.x >> 5) + (int)(threadIdx.x >> 5); t < ni; t += warps) {
-        const int i = act ? act[t] : t;
-        const unsigned cu = ext_n[i];
-        if (cu > (unsigned)kExtCap) {
-            if (lane == 0) ext_n[i] = kExtUnusable;
-            continue;
-        }
-        const int c = (int)cu;
-        if (c < 2) continue;
-        int32_t* seg = ext + (size_t)i * kExtCap;
-        if (c <= 32) {   // one entry per lane: its rank among the c
-            const int v0 = (int)lane < c ? seg[lane] : 0x7fffffff;
-            int r0 = 0;
-            for (int k = 0; k < c; ++k) r0 += __shfl_sync(0xffffffffu, v0, k) < v0;
-            __syncwarp();   // every lane has read the segment before it is overwritten
-            if ((int)lane < c) seg[r0] = v0;
-        } else if (c <= 64) {
-            const int v0 = (int)lane < c ? seg[lane] : 0x7fffffff;
-            const int v1 = (int)lane + 32 < c ? seg[lane + 32] : 0x7fffffff;
-            int r0 = 0, r1 = 0;
-            const int c0 = min(c, 32);
-            for (int k = 0; k < c0; ++k) {
-                const int x = __shfl_sync(0xffffffffu, v0, k);
-                r0 += x < v0;
-                r1 += x < v1;
-            }
-            for (int k = 32; k < c; ++k) {
-                const int x = __shfl_sync(0xffffffffu, v1, k - 32);
-                r0 += x < v0;
-                r1 += x < v1;
-            }
-            __syncwarp();   // every lane has read the segment before it is overwritten
-            if ((int)lane < c) seg[r0] = v0;
-            if ((int)lane + 32 < c) seg[r1] = v1;
-        } else {
-            constexpr int P = kExtCap;   // a power of two
-            for (int k = (int)lane; k < P; k += 32) sb[k] = k < c ? seg[k] : 0x7fffffff;
-            __syncwarp();
-            for (int size = 2; size <= P; size <<= 1) {
-                for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                    for (int t = (int)lane; t < (P >> 1); t += 32) {
-                        const int lo = ((t & ~(stride - 1)) << 1) | (t & (stride - 1));
-                        const int hi = lo + stride;
-                        const int x = sb[lo], y = sb[hi];
-                        if ((x > y) == ((lo & size) == 0)) {
-                            sb[lo] = y;
-                            sb[hi] = x;
-                        }
-                    }
-                    __syncwarp();
+    for (int t0 = (blockIdx.x * (blockDim.x >> 5) + (int)(threadIdx.x >> 5)) * 32; t0 < ni; t0 += warps * 32) {
+        const int tl = t0 + (int)lane;
+        const int il = tl < ni ? (act ? act[tl] : tl) : -1;
+        const unsigned cl = il >= 0 ? ext_n[il] : 0u;
+        if (cl > (unsigned)kExtCap) ext_n[il] = kExtUnusable;
+        unsigned todo = __ballot_sync(0xffffffffu, cl >= 2u && cl <= (unsigned)kExtCap);
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1u;
+            const int i = __shfl_sync(0xffffffffu, il, src);
+            const int c = (int)__shfl_sync(0xffffffffu, cl, src);
+            int32_t* seg = ext + (size_t)i * kExtCap;
+            if (c <= 32) {   // one entry per lane: its rank among the c
+                const int v0 = (int)lane < c ? seg[lane] : 0x7fffffff;
+                int r0 = 0;
+                for (int k = 0; k < c; ++k) r0 += __shfl_sync(0xffffffffu, v0, k) < v0;
+                __syncwarp();   // every lane has read the segment before it is overwritten
+                if ((int)lane < c) seg[r0] = v0;
+            } else if (c <= 64) {
+                const int v0 = (int)lane < c ? seg[lane] : 0x7fffffff;
+                const int v1 = (int)lane + 32 < c ? seg[lane + 32] : 0x7fffffff;
+                int r0 = 0, r1 = 0;
+                const int c0 = min(c, 32);
+                for (int k = 0; k < c0; ++k) {
+                    const int x = __shfl_sync(0xffffffffu, v0, k);
+                    r0 += x < v0;
+                    r1 += x < v1;
                 }
+                for (int k = 32; k < c; ++k) {
+                    const int x = __shfl_sync(0xffffffffu, v1, k - 32);
+                    r0 += x < v0;
+                    r1 += x < v1;
+                }
+                __syncwarp();   // every lane has read the segment before it is overwritten
+                if ((int)lane < c) seg[r0] = v0;
+                if ((int)lane + 32 < c) seg[r1] = v1;
+            } else {
+                constexpr int P = kExtCap;   // a power of two
+                for (int k = (int)lane; k < P; k += 32) sb[k] = k < c ? seg[k] : 0x7fffffff;
+                __syncwarp();
+                for (int size = 2; size <= P; size <<= 1) {
+                    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                        for (int t = (int)lane; t < (P >> 1); t += 32) {
+                            const int lo = ((t & ~(stride - 1)) << 1) | (t & (stride - 1));
+                            const int hi = lo + stride;
+                            const int x = sb[lo], y = sb[hi];
+                            if ((x > y) == ((lo & size) == 0)) {
+                                sb[lo] = y;
+                                sb[hi] = x;
+                            }
+                        }
+                        __syncwarp();
+                    }
+                }
+                for (int k = (int)lane; k < c; k += 32) seg[k] = sb[k];
             }
-            for (int k = (int)lane; k < c; k += 32) seg[k] = sb[k];
+            __syncwarp();
         }
-        __syncwarp();
     }
 }
 
