@@ -311,6 +311,11 @@ struct WppFmSmem {
     float hm[kMpMembers];     // h_i
     uint4 X[kMpMembers];      // integer positions
     int cnt[kMpMembers];      // pairs found per member
+    int pm[kMpMembers];       // member sorted indices (-1: no member)
+    // candidates that passed the box prefilter, waiting for the member tests:
+    // offset from the group centre and h_j (sign bit: a wide leaf's), index
+    float4 bp[32];
+    int bq[32];
 };
 
 template <bool HASH, int MINB, int VISC, bool COND>
@@ -370,14 +375,19 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_force_mp(WppArgs a) {
                     sm.lo[lane] = lo;
                     sm.hm[lane] = hl;
                     sm.X[lane] = Xl;
+                    sm.pm[lane] = G.p;   // -1 past G.n
                 }
                 __syncwarp();
-                int cntm[kMpMembers], pmv[kMpMembers];
+                int cntm[kMpMembers];
 #pragma unroll
-                for (int k = 0; k < kMpMembers; ++k) {
-                    cntm[k] = 0;
-                    pmv[k] = __shfl_sync(0xffffffffu, G.p, k);   // -1 past G.n
-                }
+                for (int k = 0; k < kMpMembers; ++k) cntm[k] = 0;
+                // Box prefilter: a candidate goes on to the member tests only if it
+                // comes within the largest member threshold, or its own, of the
+                // group's box. Both tests run on the same computed offsets; the
+                // margin of 2^-12 of the squared radius covers their rounding, so
+                // a candidate that some member takes always passes.
+                const float Tmax = warp_max((int)lane < kMpMembers ? sm.mem[lane].w : -1.f);
+                const float egx = gg.egx, egy = gg.egy, egz = gg.egz;
                 unsigned ctest = 0;
                 const int lvl0 = B.lvl_off[0];
                 auto fetch = [&](int base, int& e, int& q, bool& cand, uint4& C, float4& f) {
@@ -389,33 +399,26 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_force_mp(WppArgs a) {
                     C = a.node_c[lvl0 + (e & 0x7fffffff)];
                     f = __ldg(a.fposh + q);
                 };
-                int e_n, q_n;
-                bool cand_n;
-                uint4 C_n;
-                float4 f_n;
-                fetch(0, e_n, q_n, cand_n, C_n, f_n);
-                for (int base = 0; base < ngl; base += 4) {
-                    const int e = e_n, q = q_n;
-                    const bool cand = cand_n;
-                    const uint4 C = C_n;
-                    const float4 f = f_n;
-                    if (base + 4 < ngl) fetch(base + 4, e_n, q_n, cand_n, C_n, f_n);
-                    const float px = (float)(int)(C.x - gg.Gc.x) * sf + f.x, py = (float)(int)(C.y - gg.Gc.y) * sf + f.y,
-                                pz = (float)(int)(C.z - gg.Gc.z) * sf + f.z;
+                // Every member tests the buffer's first kb candidates (one per lane).
+                auto members = [&](int kb) {
+                    __syncwarp();
+                    const bool cand = (int)lane < kb;
+                    const float4 f0 = sm.bp[lane];
+                    const int q = sm.bq[lane];
+                    __syncwarp();   // read before the next candidates overwrite the entry
+                    const bool wide = cand && (__float_as_uint(f0.w) >> 31) != 0u;
                     // j side of the band: h_j (1 +- 2^-19) widened/narrowed by the rounding bound
-                    const float hj = f.w;
+                    const float hj = __uint_as_float(__float_as_uint(f0.w) & 0x7fffffffu);
                     const float tj = hj * (1.f + 2.f * rel) + eT, sj = fmaxf(hj * (1.f - 2.f * rel) - eT, 0.f);
                     const float hij = tj * tj * ehi, loj = sj * sj * elo;
-                    const bool wide = cand && e < 0;
                     const bool anyw = __any_sync(0xffffffffu, wide);
                     uint4 Xq = make_uint4(0u, 0u, 0u, 0u);
                     if (anyw && wide) Xq = a.posm[q];
-                    ctest += __popc(__ballot_sync(0xffffffffu, cand));
                     unsigned bandm = 0;   // members for which this lane's pair lies in the band
 #pragma unroll
                     for (int m = 0; m < kMpMembers; ++m) {
                         const float4 g = sm.mem[m];
-                        float dx = px - g.x, dy = py - g.y, dz = pz - g.z;
+                        float dx = f0.x - g.x, dy = f0.y - g.y, dz = f0.z - g.z;
                         if (anyw) {
                             if (wide) {   // exact integer separations from the member
                                 const uint4 Xm = sm.X[m];
@@ -425,7 +428,7 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_force_mp(WppArgs a) {
                             }
                         }
                         const float r2 = dx * dx + dy * dy + dz * dz;
-                        const bool ok = cand && q != pmv[m];
+                        const bool ok = cand && q != sm.pm[m];
                         const bool in = ok && (r2 < sm.lo[m] || r2 < loj);
                         const bool band = ok && !in && (r2 < g.w || r2 < hij);
                         bandm |= band ? 1u << m : 0u;
@@ -461,7 +464,51 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_force_mp(WppArgs a) {
                             for (int k2 = 0; k2 < kMpMembers; ++k2) cntm[k2] += m == k2 ? __popc(msk) : 0;
                         }
                     }
+                };
+                int nb = 0;   // candidates waiting in the buffer (warp-uniform)
+                int e_n, q_n;
+                bool cand_n;
+                uint4 C_n;
+                float4 f_n;
+                fetch(0, e_n, q_n, cand_n, C_n, f_n);
+                for (int base = 0; base < ngl; base += 4) {
+                    const int e = e_n, q = q_n;
+                    const bool cand = cand_n;
+                    const uint4 C = C_n;
+                    const float4 f = f_n;
+                    if (base + 4 < ngl) fetch(base + 4, e_n, q_n, cand_n, C_n, f_n);
+                    const float px = (float)(int)(C.x - gg.Gc.x) * sf + f.x, py = (float)(int)(C.y - gg.Gc.y) * sf + f.y,
+                                pz = (float)(int)(C.z - gg.Gc.z) * sf + f.z;
+                    const bool wide = cand && e < 0;
+                    ctest += __popc(__ballot_sync(0xffffffffu, cand));
+                    // a wide leaf's offsets are not accurate enough for the box test: it passes
+                    bool pass = cand;
+                    if (cand && !wide) {
+                        const float bx = fmaxf(fabsf(px) - egx, 0.f), by = fmaxf(fabsf(py) - egy, 0.f),
+                                    bz = fmaxf(fabsf(pz) - egz, 0.f);
+                        const float tj = f.w * (1.f + 2.f * rel) + eT;
+                        const float T = fmaxf(Tmax, tj * tj * ehi) * (1.f + 2.44140625e-4f);
+                        pass = bx * bx + by * by + bz * bz < T;
+                    }
+                    const unsigned pb = __ballot_sync(0xffffffffu, pass);
+                    const int slot = nb + __popc(pb & lt);
+                    const float4 ent = make_float4(px, py, pz,
+                                                   __uint_as_float(__float_as_uint(f.w) | (wide ? 0x80000000u : 0u)));
+                    if (pass && slot < 32) {
+                        sm.bp[slot] = ent;
+                        sm.bq[slot] = q;
+                    }
+                    nb += __popc(pb);
+                    if (nb >= 32) {
+                        members(32);
+                        if (pass && slot >= 32) {
+                            sm.bp[slot - 32] = ent;
+                            sm.bq[slot - 32] = q;
+                        }
+                        nb -= 32;
+                    }
                 }
+                if (nb > 0) members(nb);
                 if (lane == 0) c_tests += (unsigned long long)ctest * (unsigned)G.n;
                 // members whose list overflowed go to the one-particle walk
                 todo = 0;
