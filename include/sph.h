@@ -65,8 +65,9 @@ typedef enum {
 #define SPH_NO_LISTS 0x400        /* sph_build_grid: do not allocate the neighbour lists that the
                                      default path records in an all-active density pass and reuses
                                      in the force pass (saves ~1,040 bytes per particle) */
-#define SPH_PARTIAL_LISTS 0x800   /* sph_density on the default path with an active list (when the
-                                     member-parallel kernel runs): record the active particles' lists
+#define SPH_PARTIAL_LISTS 0x800   /* sph_density on the default path with an active list of at least
+                                     n/256 entries (the member-parallel kernel then runs whatever the
+                                     count): record the active particles' lists
                                      and their extra partners (j with h_i <= r_ij < h_j), those
                                      among the inactive particles found by a wider sweep of the
                                      density pass, so that a force call on that set reads them.

@@ -1244,8 +1244,11 @@ cudaError_t launch_density_wpp(sph_ctx* ctx, const DensityLaunch& a, int64_t n_a
     // SPH_PARTIAL_LISTS, a call on an active list (padded or not) that runs the
     // member-parallel kernel records the active particles' lists and also
     // finds their extra partners among the inactive ones.
-    const bool mp_path = wpp_groups_pay(n_active, g->n) && c.mp_j != nullptr;
-    const bool part = g->nbr != nullptr && a.active_list && a.partial_lists && mp_path;
+    // (The partial lists need the member-parallel kernel: with the flag it runs
+    // for any active set that is not too sparse to form groups.)
+    const bool want_part = g->nbr != nullptr && a.active_list && a.partial_lists && n_active * 256 >= g->n;
+    const bool mp_path = (want_part || wpp_groups_pay(ctx, n_active, g->n)) && c.mp_j != nullptr;
+    const bool part = want_part && mp_path;
     const bool rec = part || (g->nbr != nullptr && n_active == g->n);
     if (rec) {
         c.nbr = g->nbr;

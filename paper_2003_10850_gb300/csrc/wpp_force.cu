@@ -690,7 +690,7 @@ cudaError_t launch_force_wpp(sph_ctx* ctx, const ForceLaunch& a, int64_t n_activ
     // the walk: member-parallel for groups (nothing to do when the lists served
     // the call), then one particle per warp for what it leaves and for the
     // particles the lists could not serve
-    if (g->ctx->sm_count >= ctx->sm_count && wpp_groups_pay(n_active, g->n)) {
+    if (g->ctx->sm_count >= ctx->sm_count && wpp_groups_pay(ctx, n_active, g->n)) {
         if ((e = cudaMemsetAsync(ctx->queue + 6, 0, 2 * sizeof(unsigned), s))) return e;
         WppArgs cm = c;
         cm.mp_j = g->mp_j;
