@@ -102,6 +102,17 @@ def oracle_step(s):
     return pairs, dt
 
 
+def host_cores():
+    """The host's logical CPUs and those this process may run on (a cgroup or
+    affinity mask can hold fewer than the machine has)."""
+    total = os.cpu_count() or 0
+    try:
+        usable = len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        usable = total
+    return {"host_cpus": total, "usable_cpus": usable}
+
+
 def run_reference(args, rank):
     if rank != 0:
         return
@@ -123,7 +134,7 @@ def run_reference(args, rank):
             "config": {"workload": f"10M clustered time-binned SPH step; CPU sample: same generator at "
                                    f"N={args.cpu_n}, all active, density (from perturbed h) + force"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-                             "sample": f"clustered N={args.cpu_n}, all active, density+force"},
+                             "sample": f"clustered N={args.cpu_n}, all active, density+force", **host_cores()},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -760,7 +771,7 @@ def main():
         oracle.build()
         s = oracle_sample(args.cpu_n)
         pr, dt = oracle_step(s)
-        cpu = {"value": pr / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+        cpu = {"value": pr / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle", **host_cores(),
                "sample": f"same generator at N={args.cpu_n} (blobs ~ sqrt N), all active, density from "
                          f"perturbed converged h + force, one step, {dt:.1f} s"}
         # the same step on one core, on a sixteenth of the sample

@@ -217,7 +217,10 @@ sph_status sph_grid_export(const sph_grid *grid, int32_t *perm, uint64_t *keys, 
  * h_i} at its final h in the grid, and, for each i, the partners j with
  * h_i <= r_ij < h_j (the transpose), so that a following sph_hydro_force can
  * take its pairs from these lists (see there). A call on a smaller active set
- * leaves the lists unusable.
+ * records nothing (the force pass then walks), unless SPH_PARTIAL_LISTS is
+ * given: then each active particle's list and extra partners are recorded
+ * and stamped with the call, and the lists of the particles that were not
+ * active in it stop serving the force pass.
  */
 sph_status sph_density(sph_ctx *ctx, const sph_grid *grid, float *h, const int32_t *active,
                        int64_t n_active, float *rho, float *omega, int32_t *n_ngb,
@@ -238,14 +241,15 @@ sph_status sph_density(sph_ctx *ctx, const sph_grid *grid, float *h, const int32
  * acc is n x 3. hash (optional) is the pair-set checksum as in sph_density.
  * Sums are folded error-free across the lanes that share a particle and
  * rounded once.
- * Pair source (default path): if the last sph_density call on this grid had
- * every particle active, the grid has not been updated since, and every h
- * equals the h that call ended with (checked on the device), the pairs come
- * from the neighbour lists that call recorded -- no hierarchy walk, no
- * candidate test. Otherwise, and for any particle whose lists did not fit
- * (the neighbour pool full, or more than 128 extra partners), the hierarchy is
- * walked.
- * Both give the same pair set.
+ * Pair source (default path): if the last sph_density call on this grid
+ * recorded lists (every particle active, or SPH_PARTIAL_LISTS), the grid has
+ * not been updated since, and every h equals the h that call ended with
+ * (checked on the device), the pairs of each active particle whose list that
+ * call recorded come from the lists -- no hierarchy walk, no candidate test.
+ * The other active particles (not active in that call, or whose lists did not
+ * fit: the neighbour pool full, or more than 128 extra partners) walk the
+ * hierarchy, and so does the whole active set when the lists cannot serve the
+ * call. Both give the same pair set.
  */
 sph_status sph_hydro_force(sph_ctx *ctx, const sph_grid *grid, const float *vel, const float *u,
                            const float *h, const float *rho, const float *omega,
