@@ -234,6 +234,57 @@ __device__ __forceinline__ float wpp_fold4(float x, float y, float z, float u) {
     return __fsub_rn(s, c);
 }
 
+// The same error-free fold of four per-lane sums within each aligned octet of
+// lanes (eight lanes per particle): lanes with bit 2 clear keep the first two
+// sums and the others the last two, then bit 1 picks one of the pair. Returns,
+// in lanes 2c and 2c + 1 of the octet, sum c as one correctly rounded s - c.
+__device__ __forceinline__ float wpp_fold4_oct(float x, float y, float z, float u) {
+    const unsigned lane = lane_id();
+    auto two_sum = [](float& s, float& c, float s2, float c2) {
+        const float t = __fadd_rn(s, s2);
+        const float bp = __fsub_rn(t, s);
+        const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(s2, bp));
+        s = t;
+        c = __fsub_rn(__fadd_rn(c, c2), e);
+    };
+    const bool lo4 = (lane & 4u) == 0u;
+    float s1 = lo4 ? x : z, s2 = lo4 ? y : u, c1 = 0.f, c2 = 0.f;
+    {
+        const float o1 = __shfl_xor_sync(0xffffffffu, lo4 ? z : x, 4);
+        const float o2 = __shfl_xor_sync(0xffffffffu, lo4 ? u : y, 4);
+        two_sum(s1, c1, o1, 0.f);
+        two_sum(s2, c2, o2, 0.f);
+    }
+    const bool lo2 = (lane & 2u) == 0u;
+    float s = lo2 ? s1 : s2, c = lo2 ? c1 : c2;
+    {
+        const float os = __shfl_xor_sync(0xffffffffu, lo2 ? s2 : s1, 2);
+        const float oc = __shfl_xor_sync(0xffffffffu, lo2 ? c2 : c1, 2);
+        two_sum(s, c, os, oc);
+    }
+    {
+        const float os = __shfl_xor_sync(0xffffffffu, s, 1), oc = __shfl_xor_sync(0xffffffffu, c, 1);
+        two_sum(s, c, os, oc);
+    }
+    return __fsub_rn(s, c);
+}
+
+// Error-free fold of one per-lane sum within each aligned octet of lanes;
+// every lane of the octet ends with the total rounded once.
+__device__ __forceinline__ float wpp_fold1_oct(float x) {
+    float s = x, c = 0.f;
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) {
+        const float s2 = __shfl_xor_sync(0xffffffffu, s, o), c2 = __shfl_xor_sync(0xffffffffu, c, o);
+        const float t = __fadd_rn(s, s2);
+        const float bp = __fsub_rn(t, s);
+        const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(s2, bp));
+        s = t;
+        c = __fsub_rn(__fadd_rn(c, c2), e);
+    }
+    return __fsub_rn(s, c);
+}
+
 // (h 2^32 / L)^2 in FP64, the right-hand side of the exact neighbour
 // predicate. Out of line so that the compiler cannot hoist the FP64 division
 // out of the rare band branches onto every evaluation: with one particle per

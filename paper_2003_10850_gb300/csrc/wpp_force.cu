@@ -199,88 +199,105 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_force_wpp(WppArgs a) {
     }
 }
 
-// Force pass from the recorded lists: warp per active particle, pairs 32 at a
-// time (the neighbour list, then the extra partners), the same pair terms and
-// fold as k_force_wpp. If the lists cannot serve the call at all the kernel
+// Force pass from the recorded lists: four active particles per warp, eight
+// lanes each, two pairs per lane per step (the neighbour list, then the extra
+// partners); the same pair terms as k_force_wpp, folded error-free within
+// each octet of lanes. If the lists cannot serve the call at all the kernel
 // does nothing and the walk that follows takes the whole active set;
 // particles whose own lists did not fit go to fb_list for that walk.
+constexpr int kFlPer = 4;   // particles per warp
 template <bool HASH, int VISC, bool COND>
 __global__ void __launch_bounds__(128, 8) k_force_list(WppArgs a) {
     if (!wpp_lists_valid(a.list_st)) return;
     const unsigned gen = a.list_st[kListGen];
     const unsigned lane = lane_id();
+    const int slot = (int)(lane >> 3), sub = (int)(lane & 7u);
     const int warps = gridDim.x * (blockDim.x >> 5);
     const int cnt = (int)*a.count_ptr;
     const float kNorm = (float)(8.0 / 3.141592653589793);
-    unsigned long long c_pairs = 0, c_served = 0;   // per warp, lane-uniform
-    for (int t = blockIdx.x * (blockDim.x >> 5) + (int)(threadIdx.x >> 5); t < cnt; t += warps) {
-        const int p = a.act[t];
-        const int cn = a.nbr_n[p];
-        const unsigned ec = a.ext_n[p];
-        // (kExtUnusable included; a stale stamp: p was not active in the call that recorded)
-        if (cn < 0 || ec > (unsigned)kExtCap || a.list_ep[p] != gen) {
-            if (lane == 0) a.fb_list[atomicAdd(&a.list_st[3], 1u)] = p;
-            continue;
+    unsigned long long c_pairs = 0, c_served = 0;   // per octet, lane-uniform within it
+    for (int t0 = (blockIdx.x * (blockDim.x >> 5) + (int)(threadIdx.x >> 5)) * kFlPer; t0 < cnt;
+         t0 += warps * kFlPer) {
+        const int t = t0 + slot;
+        int p = -1, cn = 0;
+        unsigned ec = 0;
+        if (t < cnt) {
+            p = a.act[t];
+            cn = a.nbr_n[p];
+            ec = a.ext_n[p];
+            // (kExtUnusable included; a stale stamp: p was not active in the call that recorded)
+            if (cn < 0 || ec > (unsigned)kExtCap || a.list_ep[p] != gen) {
+                if (sub == 0) a.fb_list[atomicAdd(&a.list_st[3], 1u)] = p;
+                p = -1;
+            }
         }
-        const BoxDesc& B = a.boxes[a.n_boxes == 1 ? 0 : wpp_box(a.boxes, a.n_boxes, p)];
+        const bool live = p >= 0;
+        const int pp = live ? p : 0;
+        const BoxDesc& B = a.boxes[a.n_boxes == 1 ? 0 : wpp_box(a.boxes, a.n_boxes, pp)];
         const float sf = B.sf;
-        const uint4 Xi = a.posm[p];
-        const int oi = a.perm[p];
-        const float4 vi = a.fvm[p];
-        const float4 thi = a.fthermo[p];
-        const float2 ci = COND ? a.fcond[p] : make_float2(0.f, 0.f);
-        const float2 bi = wpp_visc_i<VISC>(a, p);
+        const uint4 Xi = a.posm[pp];
+        const int oi = a.perm[pp];
+        const float4 vi = a.fvm[pp];
+        const float4 thi = a.fthermo[pp];
+        const float2 ci = COND ? a.fcond[pp] : make_float2(0.f, 0.f);
+        const float2 bi = wpp_visc_i<VISC>(a, pp);
         const WppForceI I = {vi.x, vi.y, vi.z, thi.w, thi.x, thi.y, thi.z, kNorm * thi.w * thi.w * thi.w * thi.w,
                              bi.x, ci.x, ci.y, bi.y};
         float Sx = 0.f, Sy = 0.f, Sz = 0.f, Su = 0.f, Sc = 0.f, vsmax = 0.f;
         unsigned long long hs = 0;
-        const int tot = cn + (int)ec;
-        const int32_t* ln = a.nbr + a.nbr_off[p];
-        const int32_t* le = a.ext + (size_t)p * kExtCap;
-        // two pairs per lane per step (k and k + 32), their loads issued together;
-        // each lane still sums its pairs in the order k, k + 32, k + 64, ...
-        for (int k = (int)lane; k < tot; k += 64) {
-            const int k1 = k + 32;
-            const bool two = k1 < tot;
-            const int q0 = k < cn ? ln[k] : le[k - cn];
-            const int q1 = two ? (k1 < cn ? ln[k1] : le[k1 - cn]) : q0;
-            const uint4 X0 = a.posm[q0], X1 = a.posm[q1];
-            const float4 v0 = __ldg(a.fvm + q0), v1 = __ldg(a.fvm + q1);
-            const float4 t0 = __ldg(a.fthermo + q0), t1 = __ldg(a.fthermo + q1);
-            const float2 b0 = wpp_visc_j<VISC>(a, q0), b1 = wpp_visc_j<VISC>(a, q1);
-            const float2 c0 = COND ? __ldg(a.fcond + q0) : make_float2(0.f, 0.f);
-            const float2 c1 = COND ? __ldg(a.fcond + q1) : make_float2(0.f, 0.f);
-            wpp_force_pair<VISC, COND>(I, (float)(int)(X0.x - Xi.x) * sf, (float)(int)(X0.y - Xi.y) * sf,
-                                      (float)(int)(X0.z - Xi.z) * sf, v0, t0, b0, c0, a.alpha, Sx, Sy, Sz, Su, Sc,
-                                      vsmax);
-            if (HASH) hs += splitmix64((unsigned long long)a.perm[q0]);
-            if (two) {
-                wpp_force_pair<VISC, COND>(I, (float)(int)(X1.x - Xi.x) * sf, (float)(int)(X1.y - Xi.y) * sf,
-                                          (float)(int)(X1.z - Xi.z) * sf, v1, t1, b1, c1, a.alpha, Sx, Sy, Sz, Su, Sc,
-                                          vsmax);
-                if (HASH) hs += splitmix64((unsigned long long)a.perm[q1]);
+        const int tot = live ? cn + (int)ec : 0;
+        const int32_t* ln = a.nbr + (live ? a.nbr_off[pp] : 0);
+        const int32_t* le = a.ext + (size_t)pp * kExtCap;
+        // two pairs per lane per step (k and k + 8), their loads issued together;
+        // each lane sums its pairs in the order k, k + 8, k + 16, ...
+        for (int k = sub; __any_sync(0xffffffffu, k < tot); k += 16) {
+            if (k < tot) {
+                const int k1 = k + 8;
+                const bool two = k1 < tot;
+                const int q0 = k < cn ? ln[k] : le[k - cn];
+                const int q1 = two ? (k1 < cn ? ln[k1] : le[k1 - cn]) : q0;
+                const uint4 X0 = a.posm[q0], X1 = a.posm[q1];
+                const float4 v0 = __ldg(a.fvm + q0), v1 = __ldg(a.fvm + q1);
+                const float4 t0v = __ldg(a.fthermo + q0), t1v = __ldg(a.fthermo + q1);
+                const float2 b0 = wpp_visc_j<VISC>(a, q0), b1 = wpp_visc_j<VISC>(a, q1);
+                const float2 c0 = COND ? __ldg(a.fcond + q0) : make_float2(0.f, 0.f);
+                const float2 c1 = COND ? __ldg(a.fcond + q1) : make_float2(0.f, 0.f);
+                wpp_force_pair<VISC, COND>(I, (float)(int)(X0.x - Xi.x) * sf, (float)(int)(X0.y - Xi.y) * sf,
+                                          (float)(int)(X0.z - Xi.z) * sf, v0, t0v, b0, c0, a.alpha, Sx, Sy, Sz, Su,
+                                          Sc, vsmax);
+                if (HASH) hs += splitmix64((unsigned long long)a.perm[q0]);
+                if (two) {
+                    wpp_force_pair<VISC, COND>(I, (float)(int)(X1.x - Xi.x) * sf, (float)(int)(X1.y - Xi.y) * sf,
+                                              (float)(int)(X1.z - Xi.z) * sf, v1, t1v, b1, c1, a.alpha, Sx, Sy, Sz,
+                                              Su, Sc, vsmax);
+                    if (HASH) hs += splitmix64((unsigned long long)a.perm[q1]);
+                }
             }
         }
-        const float fs = wpp_fold4(Sx, Sy, Sz, Su);
-        vsmax = warp_max(vsmax);
-        if (HASH) hs = warp_sum(hs);
-        if ((lane & 7u) == 0u) {
-            const int comp = (int)(lane >> 3);
-            if (comp < 3) a.acc[3 * (size_t)oi + comp] = fs;
-            else a.dudt[oi] = fs;
+        const float fs = wpp_fold4_oct(Sx, Sy, Sz, Su);
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) {
+            vsmax = fmaxf(vsmax, __shfl_xor_sync(0xffffffffu, vsmax, o));
+            if (HASH) hs += __shfl_xor_sync(0xffffffffu, hs, o);
         }
-        if (COND) {
-            float cs, cc, z0, z1;
-            wpp_fold2(Sc, 0.f, cs, cc, z0, z1);
-            if (lane == 0) a.dudt_cond[oi] = __fsub_rn(cs, cc);
+        const float cs = COND ? wpp_fold1_oct(Sc) : 0.f;
+        if (live) {
+            if ((sub & 1) == 0) {
+                const int comp = sub >> 1;
+                if (comp < 3) a.acc[3 * (size_t)oi + comp] = fs;
+                else a.dudt[oi] = fs;
+            }
+            if (sub == 0) {
+                if (COND) a.dudt_cond[oi] = cs;
+                a.vsig[oi] = vsmax;
+                if (HASH) a.hash[oi] = hs;
+                c_pairs += (unsigned long long)tot;
+                ++c_served;
+            }
         }
-        if (lane == 0) {
-            a.vsig[oi] = vsmax;
-            if (HASH) a.hash[oi] = hs;
-        }
-        c_pairs += (unsigned long long)tot;
-        ++c_served;
     }
+    c_pairs = warp_sum(c_pairs);
+    c_served = warp_sum(c_served);
     if (lane == 0 && c_pairs) atomicAdd(&a.ctr->force_pairs, c_pairs);
     if (lane == 0 && c_served) atomicAdd(&a.ctr->list_force, c_served);
 }
@@ -681,7 +698,7 @@ cudaError_t launch_force_wpp(sph_ctx* ctx, const ForceLaunch& a, int64_t n_activ
         c.list_ep = g->list_ep;
         c.fb_list = g->fb_list;
         const int lb = (int)std::max<long long>(
-            1, std::min<long long>((long long)ctx->sm_count * 16, (n_active + 3) / 4));
+            1, std::min<long long>((long long)ctx->sm_count * 16, (n_active + 4 * kFlPer - 1) / (4 * kFlPer)));
         launch_force_list(a.hash != nullptr, visc, c.fcond != nullptr, lb, s, c);
         ++ctx->launches;
         c.fb_act = g->fb_list;
