@@ -338,6 +338,397 @@ __global__ void __launch_bounds__(kWppThreads) k_gravity(GravArgs a) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Shared walk for a group of up to 8 active particles of one leaf-parent node
+// ---------------------------------------------------------------------------
+//
+// The members' integer positions lie in a box G (per axis an interval of
+// span < 2^30 starting at glo). For a node, bounds over G decide it for every
+// member at once, with the per-member rule's outcome:
+//   D2_G = sum_a (gap_a(G) >> 8)^2 <= every member's D2 (the gap from the
+//          interval to the node box: 0 if they overlap, else the smaller of
+//          the ends' gaps, since a point's gap has no interior minimum off the
+//          box);
+//   F2_G = sum_a ceil(far_a(G) / 256)^2 >= every member's F2 (a point's far
+//          distance max(x - lo, hi - x), continued by gap + side off the box,
+//          is convex on any interval that does not hold the point (lo + hi)/2
+//          + 2^31 where the nearest image switches, so its largest value is at
+//          an end; an interval that holds it gets no group decision).
+// D2_G >= RCi skips the node for all; the accept test on (D2_G, F2_G) accepts
+// it for all (D2 >= D2_G and F2 <= F2_G keep every inequality, and F2 < RCi
+// implies D2 < RCi). Other nodes are decided member by member with the exact
+// rule; the members that open a node carry on with it as a member mask. A
+// particle of an opened leaf is taken for every member of the leaf's mask
+// when its largest coarse distance to the interval is inside the cutoff,
+// dropped when the smallest is not, and tested member by member otherwise.
+// Interactions are buffered with their member masks and evaluated by lanes
+// 4m..4m+3 for member m, from exact integer separations (a node entry adds
+// its centre-of-mass offset), so every count and term is the one-particle
+// kernel's.
+constexpr int kGgMembers = 8;
+
+struct GravGroupSmem {
+    int stk[kGravStack];
+    unsigned char stm[kGravStack];   // member mask of each stacked node
+    int lf[kGravLeaves];
+    unsigned char lfm[kGravLeaves];  // member mask of each opened leaf
+    uint4 hA[kGravHits];    // integer anchor (particle position or node centre), mass bits
+    float4 hB[kGravHits];   // offset from the anchor (box units: a node's centre of mass)
+    int hq[kGravHits];      // particle index (-1: a node)
+    int hm[kGravHits];      // member mask
+    uint4 mX[kGgMembers];   // member integer positions
+};
+
+// One axis of a point's exact coarse geometry against [lo, hi]: raw gap and
+// far distance (the rule of grav_axis before the coarse shift).
+__device__ __forceinline__ void grav_axis_raw(unsigned x, unsigned lo, unsigned hi, unsigned& gap, unsigned& far) {
+    if (x < lo || x > hi) {
+        gap = min(lo - x, x - hi);
+        far = gap + (hi - lo);
+    } else {
+        gap = 0u;
+        far = max(x - lo, hi - x);
+    }
+}
+
+// The group bounds of one axis (interval [e1, e1 + span]): adds to D2_G and
+// F2_G; `ok` cleared when the interval holds the switching point of the
+// nearest image, where the far bound would not hold.
+__device__ __forceinline__ void grav_axis_group(unsigned e1, unsigned span, unsigned lo, unsigned hi,
+                                                unsigned long long& D2, unsigned long long& F2, unsigned& l,
+                                                bool& ok) {
+    unsigned g1, f1, g2, f2;
+    grav_axis_raw(e1, lo, hi, g1, f1);
+    grav_axis_raw(e1 + span, lo, hi, g2, f2);
+    const bool overlap = g1 == 0u || g2 == 0u || (lo - e1) <= span;
+    const unsigned gap = overlap ? 0u : min(g1, g2);
+    const unsigned sw = lo + ((hi - lo) >> 1) + 0x80000000u;
+    if ((sw - e1) <= span) ok = false;
+    const unsigned far = max(f1, f2);
+    const unsigned g = gap >> 8, f = (unsigned)(((unsigned long long)far + 255ull) >> 8);
+    D2 += (unsigned long long)g * g;
+    F2 += (unsigned long long)f * f;
+    l = max(l, (hi - lo) >> 8);
+}
+
+// The monopole rule of the walk (see the top of the file).
+__device__ __forceinline__ bool grav_accept(unsigned long long P, unsigned long long D2, unsigned long long F2,
+                                            unsigned long long L2, unsigned long long RCi) {
+    return P > 0ull && D2 > 0ull && F2 < RCi && L2 <= D2 && (L2 << 16) <= P * D2;
+}
+
+// Largest and smallest coarse distance (>> 8) on one axis from x to the
+// points of the interval [e1, e1 + span] (|x - y| is convex along the
+// interval: the largest is at an end, the smallest 0 inside, else at an end).
+__device__ __forceinline__ void grav_axis_pt(unsigned x, unsigned e1, unsigned span, unsigned& hi_, unsigned& lo_) {
+    const unsigned a1 = (unsigned)abs((int)(x - e1)), a2 = (unsigned)abs((int)(x - (e1 + span)));
+    hi_ = max(a1, a2) >> 8;
+    lo_ = (x - e1) <= span ? 0u : (min(a1, a2) >> 8);
+}
+
+// Error-free (TwoSum) fold of two per-lane sums over aligned quads of lanes;
+// every lane of the quad ends with both totals, rounded once.
+__device__ __forceinline__ void grav_fold_quad2(float& s1, float& s2) {
+    auto two_sum = [](float& s, float& c, float s2_, float c2_) {
+        const float t = __fadd_rn(s, s2_);
+        const float bp = __fsub_rn(t, s);
+        const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(s2_, bp));
+        s = t;
+        c = __fsub_rn(__fadd_rn(c, c2_), e);
+    };
+    float c1 = 0.f, c2 = 0.f;
+#pragma unroll
+    for (int o = 1; o <= 2; o <<= 1) {
+        const float a1 = __shfl_xor_sync(0xffffffffu, s1, o), b1 = __shfl_xor_sync(0xffffffffu, c1, o);
+        const float a2 = __shfl_xor_sync(0xffffffffu, s2, o), b2 = __shfl_xor_sync(0xffffffffu, c2, o);
+        two_sum(s1, c1, a1, b1);
+        two_sum(s2, c2, a2, b2);
+    }
+    s1 = __fsub_rn(s1, c1);
+    s2 = __fsub_rn(s2, c2);
+}
+
+__global__ void __launch_bounds__(kWppThreads) k_gravity_group(GravArgs a) {
+    __shared__ GravGroupSmem smem[kWppWarps];
+    GravGroupSmem& sm = smem[threadIdx.x >> 5];
+    const unsigned lane = lane_id();
+    const unsigned lt = (1u << lane) - 1u;
+    const int cnt = (int)*a.count_ptr;
+    const int mm = (int)(lane >> 2), sub = (int)(lane & 3u);   // evaluation: lane (member, quarter)
+    unsigned long long c_nodes = 0, c_pairs = 0;
+    for (;;) {
+        int t0 = 0;
+        if (lane == 0) t0 = (int)atomicAdd(a.queue, (unsigned)kGgMembers);
+        t0 = __shfl_sync(0xffffffffu, t0, 0);
+        if (t0 >= cnt) break;
+        const int t1 = min(t0 + kGgMembers, cnt);
+        for (int t = t0; t < t1;) {
+            const WppGroup G = wpp_group(a.boxes, a.n_boxes, a.act, t, t1);
+            t += G.n;
+            const BoxDesc& B = a.boxes[G.box];
+            const float sf = B.sf;
+            const unsigned long long RCi = a.box_rci[G.box];
+            const unsigned full = (1u << G.n) - 1u;
+            // members: lane l < G.n holds member l; the group's interval per axis
+            uint4 Xl = make_uint4(0u, 0u, 0u, 0u);
+            if (G.p >= 0) Xl = a.posm[G.p];
+            if ((int)lane < kGgMembers) sm.mX[lane] = Xl;
+            const unsigned X0x = __shfl_sync(0xffffffffu, Xl.x, 0), X0y = __shfl_sync(0xffffffffu, Xl.y, 0),
+                           X0z = __shfl_sync(0xffffffffu, Xl.z, 0);
+            const bool mv = G.p >= 0;
+            const int dx0 = mv ? (int)(Xl.x - X0x) : 0, dy0 = mv ? (int)(Xl.y - X0y) : 0,
+                      dz0 = mv ? (int)(Xl.z - X0z) : 0;
+            const int lox = warp_min(dx0), loy = warp_min(dy0), loz = warp_min(dz0);
+            const long long sxl = (long long)warp_max(dx0) - lox, syl = (long long)warp_max(dy0) - loy,
+                            szl = (long long)warp_max(dz0) - loz;
+            // a group spanning a quarter of the box or more takes no group decision
+            const bool gok = sxl < (1ll << 30) && syl < (1ll << 30) && szl < (1ll << 30);
+            const unsigned gex = X0x + (unsigned)lox, gey = X0y + (unsigned)loy, gez = X0z + (unsigned)loz;
+            const unsigned spx = (unsigned)sxl, spy = (unsigned)syl, spz = (unsigned)szl;
+            // the evaluation lanes' member
+            const uint4 Xm = make_uint4(__shfl_sync(0xffffffffu, Xl.x, mm), __shfl_sync(0xffffffffu, Xl.y, mm),
+                                        __shfl_sync(0xffffffffu, Xl.z, mm), 0u);
+            const int pmm = __shfl_sync(0xffffffffu, G.p, mm);
+            const bool mlive = mm < G.n;
+            float ax = 0.f, ay = 0.f, az = 0.f, sc = 0.f;
+            int nn = 0, np = 0;
+            int sp = 0, nl = 0, nh = 0;
+            const int top = B.nlev - 1;
+            if (top == 0) {
+                nl = 1;
+                if (lane == 0) {
+                    sm.lf[0] = 0;
+                    sm.lfm[0] = (unsigned char)full;
+                }
+            } else {
+                if (lane == 0) {
+                    sm.stk[0] = (int)((unsigned)top << 28);
+                    sm.stm[0] = (unsigned char)full;
+                }
+                sp = 1;
+            }
+            __syncwarp();
+            // The one-particle kernel's loop: evaluate 32 buffered interactions (or
+            // the last few once the walk is done), test the particles of four
+            // opened leaves (or the last few), test the children of up to four
+            // opened nodes; with a member mask on every node, leaf and entry.
+            for (;;) {
+                const bool walk_done = sp == 0 && nl == 0;
+                if (nh >= 32 || (walk_done && nh > 0)) {
+                    const int k = min(nh, 32);
+#pragma unroll 2
+                    for (int jj = 0; jj < 8; ++jj) {
+                        const int c = sub + 4 * jj;
+                        if (c < k && mlive && ((sm.hm[c] >> mm) & 1) && sm.hq[c] != pmm) {
+                            const uint4 A = sm.hA[c];
+                            const float4 Bo = sm.hB[c];
+                            if (sm.hq[c] < 0) ++nn; else ++np;
+                            const float ex = fmaf((float)(int)(A.x - Xm.x), sf, Bo.x),
+                                        ey = fmaf((float)(int)(A.y - Xm.y), sf, Bo.y),
+                                        ez = fmaf((float)(int)(A.z - Xm.z), sf, Bo.z);
+                            const float r2 = ex * ex + ey * ey + ez * ez;
+                            if (r2 > 0.f) {
+                                float r;
+                                const float f = a.G * __uint_as_float(A.w) * grav_K(a, r2, r);
+                                ax = fmaf(f, ex, ax);
+                                ay = fmaf(f, ey, ay);
+                                az = fmaf(f, ez, az);
+                                sc = fmaf(fabsf(f), r, sc);
+                            }
+                        }
+                    }
+                    __syncwarp();
+                    nh -= k;   // <= 31 left: move entries [32, nh + 32) down
+                    uint4 vA = make_uint4(0u, 0u, 0u, 0u);
+                    float4 vB = make_float4(0.f, 0.f, 0.f, 0.f);
+                    int vq = 0, vm = 0;
+                    if ((int)lane < nh) {
+                        vA = sm.hA[lane + 32];
+                        vB = sm.hB[lane + 32];
+                        vq = sm.hq[lane + 32];
+                        vm = sm.hm[lane + 32];
+                    }
+                    __syncwarp();
+                    if ((int)lane < nh) {
+                        sm.hA[lane] = vA;
+                        sm.hB[lane] = vB;
+                        sm.hq[lane] = vq;
+                        sm.hm[lane] = vm;
+                    }
+                    __syncwarp();
+                    continue;
+                }
+                if (walk_done) break;
+                unsigned emask = 0u;   // members taking this lane's interaction
+                uint4 eA = make_uint4(0u, 0u, 0u, 0u);
+                float4 eB = make_float4(0.f, 0.f, 0.f, 0.f);
+                int eq = -1;
+                if (nl >= 4 || (sp == 0 && nl > 0)) {
+                    // the particles of leaves lf[0..k), lanes 8s..8s+7 on leaf s
+                    const int k = min(nl, 4);
+                    const int s = (int)(lane >> 3);
+                    if (s < k) {
+                        const unsigned M = sm.lfm[s];
+                        const long long q = B.off + (long long)sm.lf[s] * kLeaf + (lane & 7u);
+                        if (q < B.off + B.n) {
+                            const uint4 Xq = a.posm[q];
+                            bool decided = false;
+                            if (gok) {
+                                unsigned hx, lx, hy, ly, hz, lz;
+                                grav_axis_pt(Xq.x, gex, spx, hx, lx);
+                                grav_axis_pt(Xq.y, gey, spy, hy, ly);
+                                grav_axis_pt(Xq.z, gez, spz, hz, lz);
+                                const unsigned long long U = (unsigned long long)hx * hx +
+                                                             (unsigned long long)hy * hy +
+                                                             (unsigned long long)hz * hz;
+                                const unsigned long long Lw = (unsigned long long)lx * lx +
+                                                              (unsigned long long)ly * ly +
+                                                              (unsigned long long)lz * lz;
+                                if (Lw >= RCi) {
+                                    decided = true;
+                                } else if (U < RCi) {
+                                    decided = true;
+                                    emask = M;
+                                }
+                            }
+                            if (!decided) {
+                                for (unsigned r = M; r; r &= r - 1u) {
+                                    const int m = __ffs(r) - 1;
+                                    const uint4 Y = sm.mX[m];
+                                    const unsigned gx = (unsigned)abs((int)(Xq.x - Y.x)) >> 8,
+                                                   gy = (unsigned)abs((int)(Xq.y - Y.y)) >> 8,
+                                                   gz = (unsigned)abs((int)(Xq.z - Y.z)) >> 8;
+                                    const unsigned long long D2 = (unsigned long long)gx * gx +
+                                                                  (unsigned long long)gy * gy +
+                                                                  (unsigned long long)gz * gz;
+                                    if (D2 < RCi) emask |= 1u << m;
+                                }
+                            }
+                            eA = Xq;
+                            eq = (int)q;
+                        }
+                    }
+                    nl -= k;   // <= 31 left: move lf[k..nl+k) down
+                    const int v = (int)lane < nl ? sm.lf[lane + k] : 0;
+                    const unsigned char vm = (int)lane < nl ? sm.lfm[lane + k] : (unsigned char)0;
+                    __syncwarp();
+                    if ((int)lane < nl) {
+                        sm.lf[lane] = v;
+                        sm.lfm[lane] = vm;
+                    }
+                } else {
+                    // the children of up to four opened nodes, one per lane
+                    const int npop = sp <= 96 ? min(4, sp) : 1;
+                    const int slot = (int)(lane >> 3);
+                    int lev = -1, child = -1;
+                    unsigned M = 0u;
+                    if (slot < npop) {
+                        const unsigned en = (unsigned)sm.stk[sp - 1 - slot];
+                        M = sm.stm[sp - 1 - slot];
+                        const int k = (int)(en >> 28), tt = (int)(en & 0x0fffffffu);
+                        const int c = tt * kFan + (int)(lane & 7u);
+                        if (c < B.lvl_n[k - 1]) {
+                            lev = k - 1;
+                            child = c;
+                        }
+                    }
+                    __syncwarp();
+                    sp -= npop;
+                    unsigned om = 0u;   // members that open the child
+                    if (child >= 0) {
+                        const int nd = B.lvl_off[lev] + child;
+                        const uint4 lo = a.node_lo[nd], hi = a.node_hi[nd];
+                        bool decided = false;
+                        if (gok) {
+                            unsigned long long D2 = 0ull, F2 = 0ull;
+                            unsigned l = 0u;
+                            bool ok = true;
+                            grav_axis_group(gex, spx, lo.x, hi.x, D2, F2, l, ok);
+                            grav_axis_group(gey, spy, lo.y, hi.y, D2, F2, l, ok);
+                            grav_axis_group(gez, spz, lo.z, hi.z, D2, F2, l, ok);
+                            if (D2 >= RCi) {
+                                decided = true;
+                            } else if (ok && grav_accept(a.P, D2, F2, (unsigned long long)l * l, RCi)) {
+                                decided = true;
+                                emask = M;
+                            }
+                        }
+                        if (!decided) {
+                            for (unsigned r = M; r; r &= r - 1u) {
+                                const int m = __ffs(r) - 1;
+                                unsigned long long D2, F2, L2;
+                                grav_box(sm.mX[m], lo, hi, D2, F2, L2);
+                                if (D2 < RCi) {
+                                    if (grav_accept(a.P, D2, F2, L2, RCi)) emask |= 1u << m;
+                                    else om |= 1u << m;
+                                }
+                            }
+                        }
+                        if (emask) {
+                            const float4 nm = a.node_m[nd];
+                            eA = a.node_c[nd];
+                            eA.w = __float_as_uint(nm.w);
+                            eB = make_float4(nm.x, nm.y, nm.z, 0.f);
+                        }
+                    }
+                    const bool push = om != 0u && lev > 0, leaf = om != 0u && lev == 0;
+                    const unsigned bp = __ballot_sync(0xffffffffu, push), bl = __ballot_sync(0xffffffffu, leaf);
+                    if (push) {
+                        const int o = sp + __popc(bp & lt);
+                        sm.stk[o] = (int)(((unsigned)lev << 28) | (unsigned)child);
+                        sm.stm[o] = (unsigned char)om;
+                    }
+                    if (leaf) {
+                        const int o = nl + __popc(bl & lt);
+                        sm.lf[o] = child;
+                        sm.lfm[o] = (unsigned char)om;
+                    }
+                    sp += __popc(bp);
+                    nl += __popc(bl);
+                }
+                // append this step's interactions to the buffer
+                const bool take = emask != 0u;
+                const unsigned bt = __ballot_sync(0xffffffffu, take);
+                if (take) {
+                    const int o = nh + __popc(bt & lt);
+                    sm.hA[o] = eA;
+                    sm.hB[o] = eB;
+                    sm.hq[o] = eq;
+                    sm.hm[o] = (int)emask;
+                }
+                nh += __popc(bt);
+                __syncwarp();
+            }
+            // per member: fold its quad's sums, write its outputs
+            grav_fold_quad2(ax, ay);
+            grav_fold_quad2(az, sc);
+            nn += __shfl_xor_sync(0xffffffffu, nn, 1);
+            nn += __shfl_xor_sync(0xffffffffu, nn, 2);
+            np += __shfl_xor_sync(0xffffffffu, np, 1);
+            np += __shfl_xor_sync(0xffffffffu, np, 2);
+            if (mlive) {
+                const int oi = a.perm[pmm];
+                if (sub < 3) a.acc[3 * (size_t)oi + sub] = sub == 0 ? ax : (sub == 1 ? ay : az);
+                if (sub == 3) {
+                    if (a.n_nodes) a.n_nodes[oi] = nn;
+                    if (a.n_pairs) a.n_pairs[oi] = np;
+                }
+                if (sub == 0) {
+                    c_nodes += (unsigned long long)nn;
+                    c_pairs += (unsigned long long)np;
+                }
+            }
+            __syncwarp();
+        }
+    }
+    c_nodes = warp_sum(c_nodes);
+    c_pairs = warp_sum(c_pairs);
+    if (lane == 0 && (c_nodes | c_pairs)) {
+        atomicAdd(&a.ctr->grav_nodes, c_nodes);
+        atomicAdd(&a.ctr->grav_pairs, c_pairs);
+    }
+}
+
 cudaError_t launch_gravity(sph_ctx* ctx, const GravityLaunch& L, int64_t n_active, cudaStream_t s) {
     sph_grid* g = const_cast<sph_grid*>(L.g);
     const int nb = g->n_boxes;
@@ -375,9 +766,16 @@ cudaError_t launch_gravity(sph_ctx* ctx, const GravityLaunch& L, int64_t n_activ
     a.hs = (float)L.h_soft;
     a.inv_hs = L.h_soft > 0.0 ? (float)(1.0 / L.h_soft) : 0.f;
     a.inv2rs = L.r_split > 0.0 ? (float)(0.5 / L.r_split) : 0.f;
-    const long long want = (n_active + kWppWarps - 1) / kWppWarps;
-    const int blocks = (int)std::max<long long>(1, std::min<long long>((long long)ctx->sm_count * 8, want));
-    k_gravity<<<blocks, kWppThreads, 0, s>>>(a);
+    if (wpp_groups_pay(ctx, n_active, g->n)) {
+        // groups of up to 8 particles of a leaf-parent node share one walk
+        const long long want = (n_active + kGgMembers * kWppWarps - 1) / (kGgMembers * kWppWarps);
+        const int blocks = (int)std::max<long long>(1, std::min<long long>((long long)ctx->sm_count * 8, want));
+        k_gravity_group<<<blocks, kWppThreads, 0, s>>>(a);
+    } else {
+        const long long want = (n_active + kWppWarps - 1) / kWppWarps;
+        const int blocks = (int)std::max<long long>(1, std::min<long long>((long long)ctx->sm_count * 8, want));
+        k_gravity<<<blocks, kWppThreads, 0, s>>>(a);
+    }
     ++ctx->launches;
     return cudaGetLastError();
 }

@@ -76,12 +76,18 @@ def test_gravity_parity_clustered(S, ctx, theta):
 
 def test_gravity_subset_matches_full_pass(S, ctx):
     p = as_f32(W.clustered(20_000, 12, seed=402))
-    gp = S.gravity_params(G=2.0, theta=0.6, **_split(p.n))
+    sp = _split(p.n)
+    gp = S.gravity_params(G=2.0, theta=0.6, **sp)
     full = _gpu(S, ctx, p, gp)
     act = np.arange(0, p.n, 3, dtype=np.int32)
     sub = _gpu(S, ctx, p, gp, active=act)
-    for a, b in zip(full[:3], sub[:3]):
-        assert np.array_equal(a[act], b[act])
+    # every decision is the same exact rule: identical counts; the full pass
+    # shares walks among groups of particles and the sparse subset walks one
+    # particle at a time, so the sums differ in rounding order only
+    assert np.array_equal(full[1][act], sub[1][act]) and np.array_equal(full[2][act], sub[2][act])
+    o = oracle.gravity(oracle.quantize(p.pos), p.mass, G=2.0, theta=0.6, **sp)
+    err = np.linalg.norm(full[0][act] - sub[0][act], axis=1)
+    assert np.all(err <= TOL * o["scale"][act]), (err / o["scale"][act]).max()
     rest = np.setdiff1d(np.arange(p.n), act)
     assert np.all(sub[1][rest] == -1)
 
