@@ -41,10 +41,17 @@ FLOPS_DENSITY_PAIR = 30.0   # FP32 flops per density pair (FMA = 2), one pass at
 FLOPS_FORCE_PAIR = 90.0     # FP32 flops per force pair
 FLOPS_GRAV_INTERACTION = 40.0   # FP32 flops per gravity interaction (softened, split pair or node term)
 FP32_LANES_PER_SM = 128
-# DRAM bytes (read + write) of one k_density_wpp launch per active particle: 592.06 MB measured by
-# ncu (dram__bytes_read.sum + dram__bytes_write.sum) on the 2,000,000-particle 100 % sub-step of
-# this benchmark's workload; scaled by the active particles of a launch
-DENSITY_DRAM_BYTES_PER_ACTIVE = 592.064768e6 / 2_000_000
+# ncu figures of the density pass (k_density_mp, then k_density_wpp for the particles it
+# leaves) on the 2,000,000-particle 100 % sub-step of this benchmark's workload (one launch of
+# each, --set full, --clock-control none): DRAM bytes (dram__bytes_read.sum +
+# dram__bytes_write.sum), warp instructions (smsp__inst_executed.sum), serialised durations,
+# and the member-parallel kernel's pipe utilisation; the call counted 118,572,011 density pairs
+DENSITY_NCU_2M = {"kernels": "k_density_mp + k_density_wpp", "launch": "2M clustered, 100 % sub-step",
+                  "dram_bytes": 588.983808e6 + 115.42784e6, "warp_inst": 3.405121628e9 + 9.69458404e8,
+                  "ms": 4.400352 + 1.624064, "density_pairs": 118_572_011,
+                  "fma_pipe_pct": 25.84, "alu_pipe_pct": 40.51, "issue_active_pct": 62.60}
+# DRAM bytes of one density launch per active particle, scaled by the active particles of a launch
+DENSITY_DRAM_BYTES_PER_ACTIVE = DENSITY_NCU_2M["dram_bytes"] / 2_000_000
 H_PERTURB = 0.02            # per-step log-normal scatter of the h guesses: the density change between steps
 
 
@@ -703,10 +710,16 @@ def main():
     setup_s = wl["setup_s"]
     dpar, fpar, tuned = autotune.tune(ctx, wl["grid"], wl["st"], wl["vel"], wl["u"], wl["h"], wl["h_ins"][0],
                                       tag="clustered-100pct")
+    # the group span of the member-parallel kernels, tuned on the 10 % sub-step
+    span, span_rep = autotune.tune_group_span(ctx, wl["grid"], wl["st"], wl["vel"], wl["u"], wl["h"], wl["h_ins"][1],
+                                              wl["acts"][1], dpar, fpar, tag="clustered-10pct")
+    dpar.group_size = span
+    fpar.group_size = span
+    tuned["group_span"] = span_rep
     dtime = S.default_params(flags=dpar.flags | S.SPH_TIME_KERNELS, blocks_per_sm=dpar.blocks_per_sm,
-                             walk_radius=dpar.walk_radius)
+                             walk_radius=dpar.walk_radius, group_size=span)
     ftime = S.default_params(flags=fpar.flags | S.SPH_TIME_KERNELS, blocks_per_sm=fpar.blocks_per_sm,
-                             walk_radius=fpar.walk_radius)
+                             walk_radius=fpar.walk_radius, group_size=span)
 
     clocks = Clocks(local)
     res_g = graph_steps(S, ctx, wl, dpar, fpar, args.steps, args.warmup, dist)
@@ -755,11 +768,22 @@ def main():
     traffic = DENSITY_DRAM_BYTES_PER_ACTIVE * active_per_launch if kern == dname else None
     roofline = {"bound": "alu", "kernel": kern, "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
                 "frac": achieved / peak_tf if achieved else None, "traffic": traffic,
-                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the 2M 100 % density launch, "
-                                  "per active particle, times the mean active particles of a timed launch"
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the 2M 100 % density "
+                                  "launches (both kernels), per active particle, times the mean active particles "
+                                  "of a timed launch"
                                   if traffic else None,
                 "peak_source": f"{sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
                                f"{pk.get('sm_max_mhz', 2070.0)} MHz ({src} max SM clock)",
+                "dram_gbs": (traffic / (kms / max(kl, 1) / 1e3) / 1e9) if traffic and kms > 0 else None,
+                "dram_gbs_source": "traffic / the launch's CUDA-event time" if traffic else None,
+                "fma_pipe_pct": DENSITY_NCU_2M["fma_pipe_pct"] if kern == dname else None,
+                "alu_pipe_pct": DENSITY_NCU_2M["alu_pipe_pct"] if kern == dname else None,
+                "warp_inst_per_pair": (DENSITY_NCU_2M["warp_inst"] / DENSITY_NCU_2M["density_pairs"]
+                                       if kern == dname else None),
+                "ncu_2M": {**DENSITY_NCU_2M, "dram_gbs": DENSITY_NCU_2M["dram_bytes"] / (DENSITY_NCU_2M["ms"] / 1e3) / 1e9,
+                           "note": "pipe percentages of k_density_mp (sm__pipe_fma/alu_cycles_active, pct of "
+                                   "peak sustained active); durations serialised under ncu"}
+                if kern == dname else None,
                 "density_kernel_ms_per_step": res["dens_ms"] / args.steps,
                 "force_kernel_ms_per_step": res["force_ms"] / args.steps,
                 "density_tflops": dens_f / (res["dens_ms"] / 1e3) / 1e12 if res["dens_ms"] else None,
@@ -793,7 +817,8 @@ def main():
                            "n": args.n, "pairs_per_step": pairs_step, "l2": "inputs exceed L2 (>1 GB)",
                            "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                            "h_guess_scatter": H_PERTURB,
-                           "tuned": {"density": tuned["density"], "force": tuned["force"]},
+                           "tuned": {"density": tuned["density"], "force": tuned["force"],
+                                     "group_span": tuned["group_span"]["group_size"]},
                            "eager_ms_per_step": res["ms"] / args.steps,
                            "eager_value": res["pairs"] / (res["ms"] / 1e3)},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,

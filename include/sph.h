@@ -92,7 +92,11 @@ typedef struct {
     double alpha_visc;  /* artificial-viscosity alpha */
     double gamma;       /* adiabatic index */
     int    flags;       /* SPH_* flags above */
-    int    group_size;  /* unused (the warp-group path is no longer built): 0, 16 or 32 */
+    int    group_size;  /* default path: a group of the member-parallel kernels (up to 8 active
+                           particles sharing one walk) never leaves an aligned run of this many
+                           sorted particles: 0 = library default (64, a leaf-parent node), else a
+                           power of two in [8, 4096]. Larger spans make fuller groups of sparse
+                           active sets with larger boxes. */
     int    blocks_per_sm; /* persistent CTAs per SM: 0 = library default */
     double walk_radius; /* density, default path: radius of a particle's candidate (near) list
                            as a multiple of its starting h, in [1, 2]; 0 = library default
@@ -173,6 +177,8 @@ sph_status sph_build_grid_batched(sph_ctx *ctx, const void *pos, int pos_is_f64,
 sph_status sph_grid_update(sph_ctx *ctx, sph_grid *grid, const void *pos, int pos_is_f64,
                            const float *mass, void *stream);
 
+/* Frees a grid (NULL: nothing). Needs no live context: a grid may be freed
+ * after the context that built it was destroyed. */
 void sph_grid_free(sph_grid *grid);
 int64_t sph_grid_size(const sph_grid *grid);
 

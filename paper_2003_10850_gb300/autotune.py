@@ -7,7 +7,10 @@ in paper_2003_10850_gb300/_build/autotune.json. The knobs are those of
 sph_params: persistent blocks per SM (a register budget) and the walk radius
 of the density pass (the radius of its near lists, as a multiple of h: larger
 radii mean longer lists but fewer walks again when h grows), against the
-per-thread walks as the other kernel family.
+per-thread walks as the other kernel family; and, on a partial active set
+(`tune_group_span`), the group span of the member-parallel kernels (how far
+apart in sorted order the up to 8 particles sharing a walk may lie: wider
+spans make fuller groups of sparse sets, with larger boxes).
 """
 from __future__ import annotations
 
@@ -97,3 +100,40 @@ def tune(ctx, grid, st, vel, u, h, h_guess, active=None, tag="default", reps=2, 
     cache[key] = entry
     _save(cache)
     return default_params(**best_d), default_params(**best_f), entry
+
+
+GROUP_SPANS = (64, 512, 4096)
+
+
+def tune_group_span(ctx, grid, st, vel, u, h, h_guess, active, dparams, fparams, tag="default", reps=2,
+                    use_cache=True):
+    """Times density + force on `active` (a partial active set, where groups
+    form from sparse particles) for each group span of GROUP_SPANS with the
+    other knobs of dparams/fparams, and returns the fastest span (cached like
+    tune())."""
+    key = f"{torch.cuda.get_device_name()}|n={grid.n}|{tag}|group_span"
+    cache = _load() if use_cache else {}
+    if key in cache:
+        return cache[key]["group_size"], cache[key]
+    rep = {}
+    best, best_t = GROUP_SPANS[0], float("inf")
+    for gs in GROUP_SPANS:
+        dp = default_params(flags=dparams.flags, blocks_per_sm=dparams.blocks_per_sm,
+                            walk_radius=dparams.walk_radius, group_size=gs)
+        fp = default_params(flags=fparams.flags, blocks_per_sm=fparams.blocks_per_sm, group_size=gs)
+
+        def run():
+            h.copy_(h_guess)
+            sph_density(ctx, grid, h, active, st["rho"], st["omega"], st["n_ngb"], st["flags"], None, dp)
+            sph_hydro_force(ctx, grid, vel, u, h, st["rho"], st["omega"], active, st["acc"], st["dudt"], st["vsig"],
+                            None, fp)
+
+        t = _time(run, reps)
+        sph_sync_status(ctx, raise_on_error=False)
+        rep[str(gs)] = t
+        if t < best_t:
+            best, best_t = gs, t
+    entry = {"group_size": best, "ms": best_t, "trials": rep}
+    cache[key] = entry
+    _save(cache)
+    return best, entry

@@ -32,8 +32,8 @@ sph_status check_params(sph_ctx* ctx, const sph_params* p) {
     if (p->max_iter < 0 || p->max_iter > 10000) return fail(ctx, SPH_ERR_INVALID, "params.max_iter out of range");
     if (!std::isfinite(p->alpha_visc) || p->alpha_visc < 0) return fail(ctx, SPH_ERR_INVALID, "params.alpha_visc must be >= 0");
     if (!std::isfinite(p->gamma) || p->gamma <= 1.0) return fail(ctx, SPH_ERR_INVALID, "params.gamma must be > 1");
-    if (p->group_size != 0 && p->group_size != 16 && p->group_size != 32)
-        return fail(ctx, SPH_ERR_INVALID, "params.group_size must be 0, 16 or 32");
+    if (p->group_size != 0 && (p->group_size < 8 || p->group_size > 4096 || (p->group_size & (p->group_size - 1))))
+        return fail(ctx, SPH_ERR_INVALID, "params.group_size must be 0 (default) or a power of two in [8, 4096]");
     if (p->blocks_per_sm < 0 || p->blocks_per_sm > 32) return fail(ctx, SPH_ERR_INVALID, "params.blocks_per_sm out of range");
     if (!(p->walk_radius == 0.0 || (p->walk_radius >= 1.0 && p->walk_radius <= 2.0)))
         return fail(ctx, SPH_ERR_INVALID, "params.walk_radius must be 0 (default) or in [1, 2]");
@@ -176,7 +176,9 @@ sph_status sph_grid_update(sph_ctx* ctx, sph_grid* grid, const void* pos, int po
 
 void sph_grid_free(sph_grid* g) {
     if (!g) return;
-    cudaSetDevice(g->ctx->device);
+    // the grid's own device: a grid may outlive its context (a garbage
+    // collector finalises them in any order)
+    cudaSetDevice(g->device);
     grid_free(g);
 }
 
@@ -227,6 +229,7 @@ static sph_status density_call(sph_ctx* ctx, const sph_grid* grid, float* h, con
     a.fp64 = (params->flags & SPH_FP64) ? 1 : 0;
     a.blocks_per_sm = params->blocks_per_sm;
     a.walk_radius = params->walk_radius;
+    a.group_span = params->group_size;
     a.time_kernels = (params->flags & SPH_TIME_KERNELS) ? 1 : 0;
     a.buffered = (params->flags & SPH_DENSITY_BUFFERED) ? 1 : 0;
     a.active_list = active ? 1 : 0;
@@ -297,6 +300,7 @@ static sph_status force_call(sph_ctx* ctx, const sph_grid* grid, const float* ve
     a.gamma = params->gamma;
     a.fp64 = (params->flags & SPH_FP64) ? 1 : 0;
     a.blocks_per_sm = params->blocks_per_sm;
+    a.group_span = params->group_size;
     a.time_kernels = (params->flags & SPH_TIME_KERNELS) ? 1 : 0;
     a.divv = divv;
     a.curlv = curlv;

@@ -463,7 +463,7 @@ __global__ void __launch_bounds__(kWppThreads) k_gravity_group(GravArgs a) {
         if (t0 >= cnt) break;
         const int t1 = min(t0 + kGgMembers, cnt);
         for (int t = t0; t < t1;) {
-            const WppGroup G = wpp_group(a.boxes, a.n_boxes, a.act, t, t1);
+            const WppGroup G = wpp_group(a.boxes, a.n_boxes, a.act, t, t1, 6);
             t += G.n;
             const BoxDesc& B = a.boxes[G.box];
             const float sf = B.sf;

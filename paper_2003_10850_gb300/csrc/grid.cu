@@ -459,6 +459,7 @@ sph_status grid_build(sph_ctx* ctx, const void* pos, int f64, const float* mass,
                       const double* Ls, int nb, cudaStream_t s, sph_grid** out) {
     sph_grid* g = new sph_grid();
     g->ctx = ctx;
+    g->device = ctx->device;
     const int n = (int)offs[nb];
     g->n = n;
     g->n_boxes = nb;

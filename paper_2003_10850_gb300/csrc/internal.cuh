@@ -26,6 +26,7 @@ struct sph_ctx {
 
 struct sph_grid {
     sph_ctx* ctx = nullptr;
+    int device = 0;                        // the context's device: freeing needs no live context
     int64_t n = 0;
     int n_boxes = 0;
     int box_bits = 0;
@@ -154,6 +155,7 @@ struct DensityLaunch {
     int fp64;
     int blocks_per_sm;
     double walk_radius;   // 0: default
+    int group_span = 0;   // sorted particles a group stays within (power of two; 0: default)
     int time_kernels;
     int buffered;
     int active_list = 0;  // the caller gave an active list (the device count may be below n_active)
@@ -182,6 +184,7 @@ struct ForceLaunch {
     double alpha, gamma;
     int fp64;
     int blocks_per_sm;
+    int group_span = 0;   // as DensityLaunch
     int time_kernels;
     // Balsara's switch (default path only; NULL: no switch)
     const float* divv = nullptr;

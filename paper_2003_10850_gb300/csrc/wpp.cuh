@@ -51,7 +51,7 @@ constexpr int kWppLeaves = 128;      // leaf list per warp; a step adds <= 32
 constexpr int kWppHits = 64;         // hit buffer per warp; drained at >= 32
 constexpr int kWppNear = 128;        // density: pairs within the walk radius, kept across h iterations
 constexpr int kWppGrpLeaves = 448;   // leaf list of a group walk, shared by the group's particles
-constexpr int kWppGrpSpan = 64;      // a group never leaves one leaf-parent node (kLeaf * kFan particles)
+constexpr int kWppGrpSpan = 64;      // default group span: one leaf-parent node (kLeaf * kFan particles)
 constexpr float kWppWalkR = 1.04f;   // default walk radius of the density pass (times the starting h)
 
 // Stack bound: a pop-4 step starts from sp <= 96 and ends at sp <= 92 + 32 =
@@ -99,6 +99,8 @@ struct WppArgs {
     int max_iter;
     int guess_h, fixed_h;
     float walk_r;                // density: near-list radius / h (see kWppWalkR)
+    int grp_shift;               // log2 of the group span (a group stays within an aligned run of
+                                 // 2^grp_shift sorted particles)
     // force
     const float4* fvel;
     const float4* fthermo;
@@ -381,15 +383,17 @@ __device__ __forceinline__ void wpp_walk(WppSmem& sm, const BoxDesc& B, const ui
 }
 
 // A group: the leading run of the remaining active particles act[t..t1) that
-// lie in the box and the leaf-parent node (kWppGrpSpan sorted particles) of
-// act[t]. Lane l < n holds member l's sorted index in p (other lanes: -1).
+// lie in the box and the aligned run of 2^shift sorted particles (by default
+// kWppGrpSpan: the leaf-parent node) of act[t]. Lane l < n holds member l's
+// sorted index in p (other lanes: -1).
 struct WppGroup {
     int n;
     int p;
     int box;
 };
 
-__device__ __forceinline__ WppGroup wpp_group(const BoxDesc* boxes, int nb, const int32_t* act, int t, int t1) {
+__device__ __forceinline__ WppGroup wpp_group(const BoxDesc* boxes, int nb, const int32_t* act, int t, int t1,
+                                              int shift) {
     const unsigned lane = lane_id();
     const int rem = t1 - t;
     int pl = -1, bl = 0;
@@ -399,7 +403,7 @@ __device__ __forceinline__ WppGroup wpp_group(const BoxDesc* boxes, int nb, cons
     }
     const int p0 = __shfl_sync(0xffffffffu, pl, 0), b0 = __shfl_sync(0xffffffffu, bl, 0);
     const long long off = boxes[b0].off;
-    const bool same = (int)lane < rem && bl == b0 && (pl - off) / kWppGrpSpan == (p0 - off) / kWppGrpSpan;
+    const bool same = (int)lane < rem && bl == b0 && ((pl - off) >> shift) == ((p0 - off) >> shift);
     const unsigned m = __ballot_sync(0xffffffffu, same);
     WppGroup g;
     g.n = __ffs(~m) - 1;   // rem <= 8, so ~m has a set bit
@@ -731,6 +735,13 @@ static inline void wpp_shape(sph_ctx* ctx, int bps, int64_t n_active, int& block
     chunk = (int)std::max<long long>(1, std::min<long long>(kMpMembers, n_active / (warps * 4)));
 }
 
+// log2 of a group span (0: the default kWppGrpSpan)
+static inline int wpp_grp_shift(int span) {
+    int s = 0;
+    while ((1 << s) < (span > 0 ? span : kWppGrpSpan)) ++s;
+    return s;
+}
+
 static inline WppArgs wpp_common(sph_ctx* ctx, const sph_grid* g, unsigned* queue) {
     WppArgs c = {};
     c.boxes = g->boxes;
@@ -747,6 +758,7 @@ static inline WppArgs wpp_common(sph_ctx* ctx, const sph_grid* g, unsigned* queu
     c.node_hi = g->node_hi;
     c.ctr = ctx->counters;
     c.n_total = (int)g->n;
+    c.grp_shift = 6;   // kWppGrpSpan
     return c;
 }
 

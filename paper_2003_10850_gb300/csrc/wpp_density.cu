@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_density_mp(WppArgs a) {
         if (t0 >= cnt) break;
         const int t1 = min(t0 + a.chunk, cnt);
         for (int t = t0; t < t1;) {
-            const WppGroup G = wpp_group(a.boxes, a.n_boxes, a.act, t, t1);
+            const WppGroup G = wpp_group(a.boxes, a.n_boxes, a.act, t, t1, a.grp_shift);
             t += G.n;
             const BoxDesc& B = a.boxes[G.box];
             const float sf = B.sf;
@@ -601,7 +601,7 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_density_wpp(WppArgs a) {
         if (t0 >= cnt) break;
         const int t1 = min(t0 + a.chunk, cnt);
         for (int t = t0; t < t1;) {
-            const WppGroup G = wpp_group(a.boxes, a.n_boxes, a.act, t, t1);
+            const WppGroup G = wpp_group(a.boxes, a.n_boxes, a.act, t, t1, a.grp_shift);
             t += G.n;
             const BoxDesc& B = a.boxes[G.box];
             const float sf = B.sf;
@@ -1227,6 +1227,7 @@ cudaError_t launch_density_wpp(sph_ctx* ctx, const DensityLaunch& a, int64_t n_a
     c.guess_h = a.guess_h;
     c.fixed_h = a.fixed_h;
     c.walk_r = a.walk_radius > 0.0 ? (float)a.walk_radius : kWppWalkR;
+    c.grp_shift = wpp_grp_shift(a.group_span);
     // the scratch holds kMpWarpsPerSm warps per SM of the device the grid was built on
     c.mp_j = g->ctx->sm_count >= ctx->sm_count ? g->mp_j : nullptr;
     if (a.divv) {

@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_force_wpp(WppArgs a) {
         if (t0 >= cnt) break;
         const int t1 = min(t0 + chunk, cnt);
         for (int t = t0; t < t1;) {
-            const WppGroup G = wpp_group(a.boxes, a.n_boxes, act, t, t1);
+            const WppGroup G = wpp_group(a.boxes, a.n_boxes, act, t, t1, a.grp_shift);
             t += G.n;
             const BoxDesc& B = a.boxes[G.box];
             const float sf = B.sf;
@@ -358,7 +358,7 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_force_mp(WppArgs a) {
         if (t0 >= cnt) break;
         const int t1 = min(t0 + a.chunk, cnt);
         for (int t = t0; t < t1;) {
-            const WppGroup G = wpp_group(a.boxes, a.n_boxes, a.act, t, t1);
+            const WppGroup G = wpp_group(a.boxes, a.n_boxes, a.act, t, t1, a.grp_shift);
             t += G.n;
             const BoxDesc& B = a.boxes[G.box];
             const float sf = B.sf;
@@ -666,6 +666,7 @@ cudaError_t launch_force_wpp(sph_ctx* ctx, const ForceLaunch& a, int64_t n_activ
     ++ctx->launches;
     if ((e = cudaMemsetAsync(ctx->queue + 3, 0, sizeof(unsigned), s))) return e;
     WppArgs c = wpp_common(ctx, g, ctx->queue + 3);
+    c.grp_shift = wpp_grp_shift(a.group_span);
     int blocks = 0;
     const int bps = a.blocks_per_sm > 0 ? a.blocks_per_sm : kWppForceBps;
     wpp_shape(ctx, bps, n_active, blocks, c.chunk);

@@ -3,10 +3,14 @@ device bookkeeping bit for bit against the oracle's rules, and a dt_max cycle
 of the integrator against the FP64 oracle integrator on the same bins.
 
 Tolerances: bins and active sets exact (integer decisions, both sides in
-FP32 from the same inputs); velocities and energies within 2e-3 of the
-accumulated scale sum_steps scale * |dt| of their kicks (the force tolerance
-of 1e-4 of the pair-term scale, with room for the positions the two sides
-drift apart by), positions within dt_max times that.
+FP32 from the same inputs). Velocities within 1e-4 of the accumulated scale
+sum_steps scale * |dt| of their kicks (the force tolerance of 1e-4 of the
+pair-term scale; measured up to 4e-6 over three seeds), positions within
+dt_max times that. Energies within 5e-4 of their accumulated scale (measured
+up to 2e-4): du/dt sums v_ij . grad W with v_ij = v_i - v_j formed in FP32 from
+velocities that carry the blobs' bulk flow, so each difference keeps the
+rounding of |v_i| (6e-8 of it), which is up to 1e-4 of a small |v_ij|; the
+accelerations are dominated by the pressure terms, which take no velocity.
 """
 import numpy as np
 import pytest
@@ -86,13 +90,13 @@ def test_kdk_cycle_against_oracle(S, ctx):
     v_g, u_g = (host(t).astype(np.float64) for t in g.synchronized_velocity())
     v_o, u_o = ref.synchronized_velocity()
     dv = np.linalg.norm(v_g - v_o, axis=1)
-    assert np.all(dv <= 2e-3 * ref.scale_a + 1e-6 * (np.linalg.norm(v_o, axis=1) + 0.1)), \
+    assert np.all(dv <= 1e-4 * ref.scale_a + 1e-6 * (np.linalg.norm(v_o, axis=1) + 0.1)), \
         (dv / (ref.scale_a + 1e-30)).max()
     du = np.abs(u_g - u_o)
-    assert np.all(du <= 2e-3 * ref.scale_u + 1e-6 * np.abs(u_o))
+    assert np.all(du <= 5e-4 * ref.scale_u + 1e-6 * np.abs(u_o)), (du / (ref.scale_u + 1e-30)).max()
     dx = host(g.pos) - ref.pos
     dx -= np.round(dx)
-    assert np.all(np.linalg.norm(dx, axis=1) <= dt_max * (2e-3 * ref.scale_a + 1e-6) + 1e-9)
+    assert np.all(np.linalg.norm(dx, axis=1) <= dt_max * (1e-4 * ref.scale_a + 1e-6) + 1e-9)
     # the cycle moved the gas and changed its energy
     assert np.abs(v_o - p.vel).max() > 100 * dv.max()
     assert np.all(u_o > 0)

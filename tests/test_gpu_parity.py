@@ -436,6 +436,28 @@ def test_active_subset(S, ctx, path, clustered50k):
     assert np.all(gf3["acc"][inact] == 0)
 
 
+@pytest.mark.parametrize("span", [8, 512, 4096])
+def test_group_span(S, ctx, span, clustered50k):
+    """The member-parallel kernels with groups confined to aligned runs of 8,
+    512 or 4096 sorted particles (params.group_size) on half the particles
+    active: the same results as the oracle (a group only changes which walk
+    a particle shares)."""
+    p, (X, d, _) = clustered50k
+    act = W.sample_indices(p.n, p.n // 2, seed=29).astype(np.int32)
+    params = S.default_params(box=p.box, group_size=span)
+    grid = gpu_grid(S, ctx, p, params)
+    h0 = np.full(p.n, -7.0, np.float32)
+    h0[act] = (d["h"][act] * 1.02).astype(np.float32)
+    g = gpu_density(S, ctx, grid, h0, params, active=act)
+    assert g["rc"] == 0
+    assert rel(g["h"][act], d["h"][act]).max() <= 1e-5
+    assert rel(g["rho"][act], d["rho"][act]).max() <= 1e-5
+    h, rho, om = _oracle_inputs32(d)
+    f = oracle.force(X, p.vel, p.mass, p.u, h, rho, om, box=p.box, active=act.astype(np.int64))
+    gf = gpu_force(S, ctx, grid, p, h, rho, om, params, active=act)
+    check_force(gf, f, act, 1e-4)
+
+
 @pytest.mark.parametrize("path", PATHS)
 def test_batched_boxes(S, ctx, path):
     sizes = (4096, 9000, 30000, 2000)
@@ -512,6 +534,11 @@ def test_error_statuses(S, ctx):
         S.sph_build_grid(ctx, dev(q.pos), dev(q.mass), S.default_params(box=-1.0))
     with pytest.raises(TypeError):
         S.sph_build_grid(ctx, dev(q.pos).double().cpu(), dev(q.mass), params)
+    # a group span must be a power of two in [8, 4096]
+    for gs in (12, 4, 8192):
+        with pytest.raises(S.SPHError) as e:
+            gpu_density(S, ctx, grid, np.full(q.n, 0.01, np.float32), S.default_params(group_size=gs))
+        assert e.value.status == abi.SPH_ERR_INVALID
     # the warp-group and cooperative paths are no longer built: their flags are rejected
     for fl in (S.SPH_WARP_GROUP, S.SPH_COOP_WALK):
         with pytest.raises(S.SPHError) as e:
