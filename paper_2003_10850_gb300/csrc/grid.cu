@@ -204,51 +204,79 @@ __global__ void k_rs_hist(const unsigned long long* __restrict__ keys, int n, in
     counts[threadIdx.x * nblk + blockIdx.x] = hist[threadIdx.x];
 }
 
-// Each block re-reads its tile in rounds of 256 consecutive items; within a
+// Each block ranks its tile in rounds of 256 consecutive items; within a
 // round the rank of an item among equal digits is (items of earlier warps) +
 // (earlier lanes of its warp with the same digit), so the order of equal
-// digits is preserved (stable).
-__global__ void k_rs_scatter(const unsigned long long* __restrict__ kin, const unsigned* __restrict__ vin,
-                             unsigned long long* __restrict__ kout, unsigned* __restrict__ vout, int n,
-                             int shift, const unsigned* __restrict__ offs, int nblk) {
-    __shared__ unsigned base[256];
+// digits is preserved (stable). The ranks place the tile's items in digit
+// order in shared memory (their tile indices); the items are then written
+// out in that order, so that consecutive threads write consecutive places of
+// a digit's run (coalesced) instead of one scattered place each.
+__global__ void __launch_bounds__(kRsT) k_rs_scatter(const unsigned long long* __restrict__ kin,
+                                                     const unsigned* __restrict__ vin,
+                                                     unsigned long long* __restrict__ kout,
+                                                     unsigned* __restrict__ vout, int n, int shift,
+                                                     const unsigned* __restrict__ offs,
+                                                     const unsigned* __restrict__ counts, int nblk) {
+    __shared__ unsigned short at[kRsTile];     // tile index of the item at each place of the tile
+    __shared__ unsigned start[256];             // first place of each digit's run in the tile
+    __shared__ unsigned run[256];               // places taken so far by each digit
     __shared__ unsigned wcnt[kRsT / 32][256];
+    __shared__ unsigned wsum[kRsT / 32];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    base[tid] = offs[tid * nblk + blockIdx.x];
+    // exclusive scan of the tile's digit counts (one digit per thread)
+    {
+        const unsigned c = counts[tid * nblk + blockIdx.x];
+        unsigned x = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[warp] = x;
+        __syncthreads();
+        unsigned w0 = 0;
+        for (int w = 0; w < warp; ++w) w0 += wsum[w];
+        start[tid] = w0 + x - c;
+        run[tid] = w0 + x - c;
+    }
 #pragma unroll
     for (int w = 0; w < kRsT / 32; ++w) wcnt[w][tid] = 0;
     __syncthreads();
     const int tile = blockIdx.x * kRsTile;
     for (int r = 0; r < kRsIPT; ++r) {
-        int k = tile + r * kRsT + tid;
-        bool valid = k < n;
-        unsigned long long key = valid ? kin[k] : 0ull;
-        unsigned val = valid ? vin[k] : 0u;
-        unsigned d = valid ? ((unsigned)(key >> shift) & 255u) : 256u;
-        unsigned peers = __match_any_sync(0xffffffffu, d);
-        unsigned lt = peers & ((1u << lane) - 1u);
+        const int k = tile + r * kRsT + tid;
+        const bool valid = k < n;
+        const unsigned d = valid ? ((unsigned)(kin[k] >> shift) & 255u) : 256u;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const unsigned lt = peers & ((1u << lane) - 1u);
         if (valid && lt == 0u) wcnt[warp][d] = __popc(peers);
         __syncthreads();
         {
-            unsigned s = base[tid];
+            unsigned s = run[tid];
 #pragma unroll
             for (int w = 0; w < kRsT / 32; ++w) {
-                unsigned t = wcnt[w][tid];
+                const unsigned t = wcnt[w][tid];
                 wcnt[w][tid] = s;
                 s += t;
             }
-            base[tid] = s;
+            run[tid] = s;
         }
         __syncthreads();
-        if (valid) {
-            unsigned p = wcnt[warp][d] + __popc(lt);
-            kout[p] = key;
-            vout[p] = val;
-        }
+        if (valid) at[wcnt[warp][d] + __popc(lt)] = (unsigned short)(r * kRsT + tid);
         __syncthreads();
 #pragma unroll
         for (int w = 0; w < kRsT / 32; ++w) wcnt[w][tid] = 0;
         __syncthreads();
+    }
+    // write out in place order: place p of digit d goes to its run's global start
+    const int tn = min(kRsTile, n - tile);
+    for (int p = tid; p < tn; p += kRsT) {
+        const int i = tile + (int)at[p];
+        const unsigned long long key = kin[i];
+        const unsigned d = (unsigned)(key >> shift) & 255u;
+        const unsigned g = offs[d * nblk + blockIdx.x] + ((unsigned)p - start[d]);
+        kout[g] = key;
+        vout[g] = vin[i];
     }
 }
 
@@ -261,7 +289,7 @@ static void radix_sort(unsigned long long* keys, unsigned* vals, unsigned long l
     for (int shift = 0; shift < end_bit; shift += 8) {
         k_rs_hist<<<nblk, kRsT, 0, s>>>(ka, n, shift, counts, nblk);
         scan_exclusive<uint32_t>(counts, 256 * nblk, cscan, tmp, s, nl);
-        k_rs_scatter<<<nblk, kRsT, 0, s>>>(ka, va, kb, vb, n, shift, cscan, nblk);
+        k_rs_scatter<<<nblk, kRsT, 0, s>>>(ka, va, kb, vb, n, shift, cscan, counts, nblk);
         *nl += 2;
         std::swap(ka, kb);
         std::swap(va, vb);

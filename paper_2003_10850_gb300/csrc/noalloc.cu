@@ -15,7 +15,8 @@ namespace sph {
 // kernels of the grid build (grid.cu), reused unchanged
 __global__ void k_rs_hist(const unsigned long long* keys, int n, int shift, unsigned* counts, int nblk);
 __global__ void k_rs_scatter(const unsigned long long* kin, const unsigned* vin, unsigned long long* kout,
-                             unsigned* vout, int n, int shift, const unsigned* offs, int nblk);
+                             unsigned* vout, int n, int shift, const unsigned* offs, const unsigned* counts,
+                             int nblk);
 __global__ void k_iota(int32_t* a, int n);
 }  // namespace sph
 
@@ -93,7 +94,7 @@ extern "C" sph_status sph_sort_keys_static(const uint64_t* keys, int64_t n, uint
         if (cudaGetLastError() != cudaSuccess) return SPH_ERR_CUDA;
         sph::scan_exclusive<uint32_t>(counts, 256 * nblk, cscan, tmp, s, &launches);
         if (cudaGetLastError() != cudaSuccess) return SPH_ERR_CUDA;
-        sph::k_rs_scatter<<<nblk, 256, 0, s>>>(ka, va, kb, vb, nn, shift, cscan, nblk);
+        sph::k_rs_scatter<<<nblk, 256, 0, s>>>(ka, va, kb, vb, nn, shift, cscan, counts, nblk);
         if (cudaGetLastError() != cudaSuccess) return SPH_ERR_CUDA;
         std::swap(ka, kb);
         std::swap(va, vb);
