@@ -47,9 +47,10 @@ FP32_LANES_PER_SM = 128
 # dram__bytes_write.sum), warp instructions (smsp__inst_executed.sum), serialised durations,
 # and the member-parallel kernel's pipe utilisation; the call counted 118,572,011 density pairs
 DENSITY_NCU_2M = {"kernels": "k_density_mp + k_density_wpp", "launch": "2M clustered, 100 % sub-step",
-                  "dram_bytes": 588.983808e6 + 115.42784e6, "warp_inst": 3.405121628e9 + 9.69458404e8,
-                  "ms": 4.400352 + 1.624064, "density_pairs": 118_572_011,
-                  "fma_pipe_pct": 25.84, "alu_pipe_pct": 40.51, "issue_active_pct": 62.60}
+                  "dram_bytes": (129.718016e6 + 458.693888e6) + (72.817152e6 + 42.396928e6),
+                  "warp_inst": 3.403872364e9 + 9.68670724e8,
+                  "ms": 4.384064 + 1.612096, "density_pairs": 118_572_011,
+                  "fma_pipe_pct": 26.62, "alu_pipe_pct": 39.68, "issue_active_pct": 62.85}
 # DRAM bytes of one density launch per active particle, scaled by the active particles of a launch
 DENSITY_DRAM_BYTES_PER_ACTIVE = DENSITY_NCU_2M["dram_bytes"] / 2_000_000
 H_PERTURB = 0.02            # per-step log-normal scatter of the h guesses: the density change between steps

@@ -546,6 +546,20 @@ def test_error_statuses(S, ctx):
         assert e.value.status == abi.SPH_ERR_INVALID
 
 
+def test_grid_freed_after_its_context(S):
+    """A garbage collector may finalise a grid after the context that built
+    it: freeing it then must not touch the destroyed context, nor leave a CUDA
+    error pending for the caller's next call."""
+    p = as_f32(W.lattice(8, 0.2, seed=3))
+    c2 = S.Context(0)
+    grid = gpu_grid(S, c2, p, S.default_params())
+    c2.close()
+    grid.free()
+    x = torch.zeros(16, device="cuda")   # raises if an error were left pending
+    torch.cuda.synchronize()
+    assert float(x.sum()) == 0.0
+
+
 def test_single_particle_and_tiny(S, ctx):
     from paper_2003_10850_gb300 import abi
     p = as_f32(W.lattice(1, 0.0, seed=0))
