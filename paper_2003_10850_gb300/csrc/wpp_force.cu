@@ -248,14 +248,20 @@ __global__ void __launch_bounds__(128, 8) k_force_list(WppArgs a) {
         const int tot = live ? cn + (int)ec : 0;
         const int32_t* ln = a.nbr + (live ? a.nbr_off[pp] : 0);
         const int32_t* le = a.ext + (size_t)pp * kExtCap;
-        // two pairs per lane per step (k and k + 8), their loads issued together;
+        // two pairs per lane per step (k and k + 8), their loads issued together,
+        // and the next step's partner indices loaded ahead of this step's gathers;
         // each lane sums its pairs in the order k, k + 8, k + 16, ...
+        auto partner = [&](int k) { return k < cn ? ln[k] : le[k - cn]; };
+        int q0n = sub < tot ? partner(sub) : 0;
+        int q1n = sub + 8 < tot ? partner(sub + 8) : q0n;
         for (int k = sub; __any_sync(0xffffffffu, k < tot); k += 16) {
+            const int q0 = q0n, q1 = q1n;
+            if (k + 16 < tot) q0n = partner(k + 16);
+            if (k + 24 < tot) q1n = partner(k + 24);
+            else q1n = q0n;
             if (k < tot) {
                 const int k1 = k + 8;
                 const bool two = k1 < tot;
-                const int q0 = k < cn ? ln[k] : le[k - cn];
-                const int q1 = two ? (k1 < cn ? ln[k1] : le[k1 - cn]) : q0;
                 const uint4 X0 = a.posm[q0], X1 = a.posm[q1];
                 const float4 v0 = __ldg(a.fvm + q0), v1 = __ldg(a.fvm + q1);
                 const float4 t0v = __ldg(a.fthermo + q0), t1v = __ldg(a.fthermo + q1);
