@@ -543,12 +543,17 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_force_mp(WppArgs a) {
                 }
                 if ((int)lane < kMpMembers) sm.cnt[lane] = cmine;
                 __syncwarp();
-                // pair terms from each member's list (as k_force_list)
-                for (int m = 0; m < G.n; ++m) {
-                    const int tot = sm.cnt[m];
-                    if (tot > kFmCap) continue;
-                    const int p = __shfl_sync(0xffffffffu, G.p, m);
-                    const uint4 Xi = sm.X[m];
+                // pair terms from the members' lists as k_force_list sums them: four
+                // members at a time, eight lanes each, two pairs per lane per step with
+                // the next step's partner indices loaded ahead
+                for (int m0 = 0; m0 < G.n; m0 += 4) {
+                    const int m = m0 + (int)(lane >> 3), sub = (int)(lane & 7u);
+                    const int tot0 = m < G.n ? sm.cnt[m] : 0;
+                    const bool live = m < G.n && tot0 <= kFmCap;
+                    const int tot = live ? tot0 : 0;
+                    const int mq = m < G.n ? m : 0;
+                    const int p = __shfl_sync(0xffffffffu, G.p, mq);
+                    const uint4 Xi = sm.X[mq];
                     const int oi = a.perm[p];
                     const float4 vi = a.fvm[p];
                     const float4 thi = a.fthermo[p];
@@ -558,46 +563,57 @@ __global__ void __launch_bounds__(kWppThreads, MINB) k_force_mp(WppArgs a) {
                                          kNorm * thi.w * thi.w * thi.w * thi.w, bi.x, ci.x, ci.y, bi.y};
                     float Sx = 0.f, Sy = 0.f, Sz = 0.f, Su = 0.f, Sc = 0.f, vsmax = 0.f;
                     unsigned long long hs = 0;
-                    const int32_t* lst = pj + m * kFmCap;
-                    for (int k = (int)lane; k < tot; k += 64) {
-                        const int k1 = k + 32;
-                        const bool two = k1 < tot;
-                        const int q0 = lst[k], q1 = two ? lst[k1] : q0;
-                        const uint4 X0 = a.posm[q0], X1 = a.posm[q1];
-                        const float4 v0 = __ldg(a.fvm + q0), v1 = __ldg(a.fvm + q1);
-                        const float4 th0 = __ldg(a.fthermo + q0), th1 = __ldg(a.fthermo + q1);
-                        const float2 b0 = wpp_visc_j<VISC>(a, q0), b1 = wpp_visc_j<VISC>(a, q1);
-                        const float2 c0 = COND ? __ldg(a.fcond + q0) : make_float2(0.f, 0.f);
-                        const float2 c1 = COND ? __ldg(a.fcond + q1) : make_float2(0.f, 0.f);
-                        wpp_force_pair<VISC, COND>(I, (float)(int)(X0.x - Xi.x) * sf, (float)(int)(X0.y - Xi.y) * sf,
-                                                   (float)(int)(X0.z - Xi.z) * sf, v0, th0, b0, c0, a.alpha, Sx, Sy, Sz,
-                                                   Su, Sc, vsmax);
-                        if (HASH) hs += splitmix64((unsigned long long)a.perm[q0]);
-                        if (two) {
-                            wpp_force_pair<VISC, COND>(I, (float)(int)(X1.x - Xi.x) * sf, (float)(int)(X1.y - Xi.y) * sf,
-                                                       (float)(int)(X1.z - Xi.z) * sf, v1, th1, b1, c1, a.alpha, Sx, Sy,
-                                                       Sz, Su, Sc, vsmax);
-                            if (HASH) hs += splitmix64((unsigned long long)a.perm[q1]);
+                    const int32_t* lst = pj + mq * kFmCap;
+                    int q0n = sub < tot ? lst[sub] : 0;
+                    int q1n = sub + 8 < tot ? lst[sub + 8] : q0n;
+                    for (int k = sub; __any_sync(0xffffffffu, k < tot); k += 16) {
+                        const int q0 = q0n, q1 = q1n;
+                        if (k + 16 < tot) q0n = lst[k + 16];
+                        q1n = k + 24 < tot ? lst[k + 24] : q0n;
+                        if (k < tot) {
+                            const bool two = k + 8 < tot;
+                            const uint4 X0 = a.posm[q0], X1 = a.posm[q1];
+                            const float4 v0 = __ldg(a.fvm + q0), v1 = __ldg(a.fvm + q1);
+                            const float4 th0 = __ldg(a.fthermo + q0), th1 = __ldg(a.fthermo + q1);
+                            const float2 b0 = wpp_visc_j<VISC>(a, q0), b1 = wpp_visc_j<VISC>(a, q1);
+                            const float2 c0 = COND ? __ldg(a.fcond + q0) : make_float2(0.f, 0.f);
+                            const float2 c1 = COND ? __ldg(a.fcond + q1) : make_float2(0.f, 0.f);
+                            wpp_force_pair<VISC, COND>(I, (float)(int)(X0.x - Xi.x) * sf,
+                                                       (float)(int)(X0.y - Xi.y) * sf, (float)(int)(X0.z - Xi.z) * sf,
+                                                       v0, th0, b0, c0, a.alpha, Sx, Sy, Sz, Su, Sc, vsmax);
+                            if (HASH) hs += splitmix64((unsigned long long)a.perm[q0]);
+                            if (two) {
+                                wpp_force_pair<VISC, COND>(I, (float)(int)(X1.x - Xi.x) * sf,
+                                                           (float)(int)(X1.y - Xi.y) * sf,
+                                                           (float)(int)(X1.z - Xi.z) * sf, v1, th1, b1, c1, a.alpha,
+                                                           Sx, Sy, Sz, Su, Sc, vsmax);
+                                if (HASH) hs += splitmix64((unsigned long long)a.perm[q1]);
+                            }
                         }
                     }
-                    const float fs = wpp_fold4(Sx, Sy, Sz, Su);
-                    vsmax = warp_max(vsmax);
-                    if (HASH) hs = warp_sum(hs);
-                    if ((lane & 7u) == 0u) {
-                        const int comp = (int)(lane >> 3);
-                        if (comp < 3) a.acc[3 * (size_t)oi + comp] = fs;
-                        else a.dudt[oi] = fs;
+                    const float fs = wpp_fold4_oct(Sx, Sy, Sz, Su);
+#pragma unroll
+                    for (int o = 4; o > 0; o >>= 1) {
+                        vsmax = fmaxf(vsmax, __shfl_xor_sync(0xffffffffu, vsmax, o));
+                        if (HASH) hs += __shfl_xor_sync(0xffffffffu, hs, o);
                     }
-                    if (COND) {
-                        float cs, cc, z0, z1;
-                        wpp_fold2(Sc, 0.f, cs, cc, z0, z1);
-                        if (lane == 0) a.dudt_cond[oi] = __fsub_rn(cs, cc);
+                    const float cs = COND ? wpp_fold1_oct(Sc) : 0.f;
+                    if (live) {
+                        if ((sub & 1) == 0) {
+                            const int comp = sub >> 1;
+                            if (comp < 3) a.acc[3 * (size_t)oi + comp] = fs;
+                            else a.dudt[oi] = fs;
+                        }
+                        if (sub == 0) {
+                            if (COND) a.dudt_cond[oi] = cs;
+                            a.vsig[oi] = vsmax;
+                            if (HASH) a.hash[oi] = hs;
+                        }
                     }
-                    if (lane == 0) {
-                        a.vsig[oi] = vsmax;
-                        if (HASH) a.hash[oi] = hs;
-                        c_pairs += (unsigned long long)tot;
-                    }
+                    // lane 0 keeps the warp's pair count
+                    const int tsum = __shfl_sync(0xffffffffu, tot, 0) + __shfl_sync(0xffffffffu, tot, 8) +
+                                     __shfl_sync(0xffffffffu, tot, 16) + __shfl_sync(0xffffffffu, tot, 24);
+                    if (lane == 0) c_pairs += (unsigned long long)tsum;
                 }
                 __syncwarp();
             }
