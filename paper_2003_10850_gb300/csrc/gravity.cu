@@ -371,7 +371,8 @@ struct GravGroupSmem {
     int stk[kGravStack];
     unsigned char stm[kGravStack];   // member mask of each stacked node
     int lf[kGravLeaves];
-    unsigned char lfm[kGravLeaves];  // member mask of each opened leaf
+    unsigned short lfm[kGravLeaves]; // member mask of each opened leaf; bit 8: every particle of it
+                                     // lies inside the cutoff of every member (no tests needed)
     uint4 hA[kGravHits];    // integer anchor (particle position or node centre), mass bits
     float4 hB[kGravHits];   // offset from the anchor (box units: a node's centre of mass)
     int hq[kGravHits];      // particle index (-1: a node)
@@ -498,7 +499,7 @@ __global__ void __launch_bounds__(kWppThreads) k_gravity_group(GravArgs a) {
                 nl = 1;
                 if (lane == 0) {
                     sm.lf[0] = 0;
-                    sm.lfm[0] = (unsigned char)full;
+                    sm.lfm[0] = (unsigned short)full;
                 }
             } else {
                 if (lane == 0) {
@@ -568,12 +569,16 @@ __global__ void __launch_bounds__(kWppThreads) k_gravity_group(GravArgs a) {
                     const int k = min(nl, 4);
                     const int s = (int)(lane >> 3);
                     if (s < k) {
-                        const unsigned M = sm.lfm[s];
+                        const unsigned M = sm.lfm[s] & 0xffu;
+                        const bool allin = (sm.lfm[s] >> 8) != 0u;
                         const long long q = B.off + (long long)sm.lf[s] * kLeaf + (lane & 7u);
                         if (q < B.off + B.n) {
                             const uint4 Xq = a.posm[q];
                             bool decided = false;
-                            if (gok) {
+                            if (allin) {
+                                decided = true;
+                                emask = M;
+                            } else if (gok) {
                                 unsigned hx, lx, hy, ly, hz, lz;
                                 grav_axis_pt(Xq.x, gex, spx, hx, lx);
                                 grav_axis_pt(Xq.y, gey, spy, hy, ly);
@@ -610,7 +615,7 @@ __global__ void __launch_bounds__(kWppThreads) k_gravity_group(GravArgs a) {
                     }
                     nl -= k;   // <= 31 left: move lf[k..nl+k) down
                     const int v = (int)lane < nl ? sm.lf[lane + k] : 0;
-                    const unsigned char vm = (int)lane < nl ? sm.lfm[lane + k] : (unsigned char)0;
+                    const unsigned short vm = (int)lane < nl ? sm.lfm[lane + k] : (unsigned short)0;
                     __syncwarp();
                     if ((int)lane < nl) {
                         sm.lf[lane] = v;
@@ -635,6 +640,7 @@ __global__ void __launch_bounds__(kWppThreads) k_gravity_group(GravArgs a) {
                     __syncwarp();
                     sp -= npop;
                     unsigned om = 0u;   // members that open the child
+                    bool allin = false; // an opened leaf wholly inside every member's cutoff
                     if (child >= 0) {
                         const int nd = B.lvl_off[lev] + child;
                         const uint4 lo = a.node_lo[nd], hi = a.node_hi[nd];
@@ -652,6 +658,9 @@ __global__ void __launch_bounds__(kWppThreads) k_gravity_group(GravArgs a) {
                                 decided = true;
                                 emask = M;
                             }
+                            // a point of the box is no farther from a member than the box's
+                            // far side, so F2_G < RCi puts every particle inside the cutoff
+                            allin = ok && F2 < RCi;
                         }
                         if (!decided) {
                             for (unsigned r = M; r; r &= r - 1u) {
@@ -681,7 +690,7 @@ __global__ void __launch_bounds__(kWppThreads) k_gravity_group(GravArgs a) {
                     if (leaf) {
                         const int o = nl + __popc(bl & lt);
                         sm.lf[o] = child;
-                        sm.lfm[o] = (unsigned char)om;
+                        sm.lfm[o] = (unsigned short)(om | (allin ? 0x100u : 0u));
                     }
                     sp += __popc(bp);
                     nl += __popc(bl);
