@@ -1,10 +1,13 @@
-// tpp.cu -- thread-per-particle density and force kernels (the default path).
+// tpp.cu -- thread-per-particle density and force kernels (SPH_PER_THREAD_WALK,
+// and SPH_FP64 for the plain method in double; the default path is the
+// warp-per-group kernels of wpp_density.cu and wpp_force.cu), and the force
+// pass's per-particle packing (k_force_pack) that every force path reads.
 //
 // One thread per active particle, consecutive threads on Morton-consecutive
 // particles, each walking the hierarchy depth-first with its own radius, so a
 // particle only tests candidates whose leaf box its own sphere reaches (the
 // paper's per-particle tree walk, Sec. 1, done on the GPU). Versus the plain
-// FP32 baseline (density.cu, force.cu):
+// FP32 baseline (plain.cu):
 //   * the h iteration runs inside the kernel (FP64 Newton on N^(1/3) with a
 //     bracket, per thread), no host round trip per iteration;
 //   * candidate positions come as FP32 offsets from their leaf's centre,
