@@ -1,7 +1,15 @@
 #pragma once
-// wpp.cuh -- warp-per-particle density and force kernels (the default path):
+// wpp.cuh -- shared device code of the default path's density and force kernels.
 //
-// Work is handed out in chunks of up to 8 Morton-consecutive active particles.
+// Member-parallel kernels (k_density_mp, k_force_mp): a warp takes a group of up
+// to 8 active particles of one aligned run of sorted particles (a leaf-parent
+// node by default), walks the hierarchy once for the group, and tests each
+// candidate load against every member at once; the members' near or pair lists
+// are then evaluated with several lanes per member. What they cannot take (groups
+// of one, overflowing lists) goes to the one-particle kernels described next.
+//
+// One-particle kernels (k_density_wpp, k_force_wpp): work is handed out in
+// chunks of up to 8 Morton-consecutive active particles.
 // Those of one leaf-parent node form a group: the warp walks the hierarchy
 // once for the whole group (popping up to four nodes per step, one child per
 // lane) and keeps the group's leaf list in shared memory. Each particle then
@@ -22,10 +30,11 @@
 // the FP32 radius test.
 //
 // Neighbour lists: a density call records each active particle's neighbour
-// set at its final h. When every particle was active, the transpose adds each
-// particle's partners with h_i <= r_ij < h_j, and the force pass then reads
-// its pairs from the two lists (k_force_list) instead of walking; the walk
-// (k_force_wpp) serves the particles, or calls, the lists cannot.
+// set at its final h. When every particle was active (or with
+// SPH_PARTIAL_LISTS), the transpose adds each particle's partners with
+// h_i <= r_ij < h_j, and the force pass then reads its pairs from the two lists
+// (k_force_list) instead of walking; the walks serve the particles, or calls,
+// the lists cannot.
 #include <algorithm>
 
 #include "internal.cuh"

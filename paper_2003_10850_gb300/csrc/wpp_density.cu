@@ -1,5 +1,7 @@
-// wpp_density.cu -- the default density pass (k_density_wpp) and the neighbour-list
-// build that lets the force pass reuse its pair sets (k_list_ext, k_list_sort).
+// wpp_density.cu -- the default density pass (k_density_mp for groups of active
+// particles that share one walk, k_density_wpp one particle per warp for the
+// particles it leaves and for sparse active sets) and the neighbour-list build
+// that lets the force pass reuse its pair sets (k_list_ext, k_list_sort).
 #include "wpp.cuh"
 
 namespace sph {

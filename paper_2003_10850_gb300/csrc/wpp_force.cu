@@ -1,5 +1,7 @@
 // wpp_force.cu -- the default force pass: pairs from the density pass's neighbour
-// lists (k_force_list), and the walk for what they cannot serve (k_force_wpp).
+// lists (k_force_list), and the walk for what they cannot serve: member-parallel
+// for groups of active particles (k_force_mp), one particle per warp for the rest
+// (k_force_wpp).
 #include "wpp.cuh"
 
 namespace sph {
